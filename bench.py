@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""TT-ICE* increment-update throughput on one GB300 (and N independent replicas under torchrun).
+
+Workload (the video-shaped stream): frames of 480x640x3 moving Gaussian blobs (12 blobs, sigma
+8-40 px, per-channel amplitude U(0,1), linear trajectories reflected at the borders, N(0, 0.01^2)
+pixel noise) viewed as the 5-way tensor 20x24x20x32x3, FP32 input, eps = 0.1, increments of 8
+frames.  A step is one TT-ICE* update of one increment through the whole path (first pass with
+per-observation errors, skip test, subselection, per-core residual / Gram / truncated eigen-solve /
+CGS2 / append / padding, final projection and last-core append).  The stream is consumed in order:
+W warm-up increments, then K timed increments, each a fresh 29.5 MB slice of a pre-generated stream
+several GB long, so no timed step reads input that is resident in L2.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (20, 24, 20, 32, 3)
+EPS = 0.1
+WORKLOAD = "video 480x640x3 as 20x24x20x32x3, fp32 input, eps=0.1, 12 blobs, noise 0.01"
+METRIC = "increment elements/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_elements_per_s(budget_s: float, batch: int):
+    """The FP64 CPU oracle on the leading increments of the same stream (bounded sample)."""
+    import torch
+
+    from oracle.ttice_oracle import TTICEOracle
+    from tt_streams import blob_video
+
+    o = TTICEOracle(DIMS, EPS)
+    n_el = 0
+    t_busy = 0.0
+    k = 0
+    while t_busy < budget_s and k < 64:
+        Y = blob_video(k * batch, batch).double().numpy()
+        t = time.perf_counter()
+        o.update(Y)
+        t_busy += time.perf_counter() - t
+        n_el += Y.size
+        k += 1
+    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    return n_el / t_busy, k, t_busy, int(threads)
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    budget = max(2.0, 25.0 / max(args.steps + args.warmup, 1))
+    vals = []
+    for _ in range(args.warmup):
+        oracle_elements_per_s(budget / 4, args.batch)
+    t0 = time.perf_counter()
+    incs = 0
+    for _ in range(args.steps):
+        v, k, busy, threads = oracle_elements_per_s(budget, args.batch)
+        vals.append(v)
+        incs += k
+    wall = time.perf_counter() - t0
+    val = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "elements/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "batch": args.batch, "stream_prefix_increments": incs},
+        "cpu_baseline": {"value": val, "unit": "elements/s", "cores": threads, "kind": "oracle",
+                         "sample": f"leading increments of {args.batch} frames per step, ~{budget:.0f} s of CPU work each"},
+        "e2e": {"value": val, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--fp64-steps", type=int, default=12, help="steps of the FP64 path timed for comparison")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2211_12487_gb300 import ttice as T
+    from tt_streams import blob_video
+
+    b = args.batch
+    n_inc = args.warmup + args.steps
+    N = math.prod(DIMS)
+    seed = 1001 + 7919 * rank  # independent replicas per rank (weak scaling)
+    Y = torch.empty((n_inc * b,) + DIMS, dtype=torch.float32, device=dev)
+    for k in range(0, n_inc * b, 64):
+        c = min(64, n_inc * b - k)
+        Y[k:k + c] = blob_video(k, c, seed=seed, device=dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed_run(precision: str, steps: int, profile: bool):
+        h = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=b, max_rank=512)
+        for k in range(args.warmup):
+            h.update(Y[k * b:(k + 1) * b])
+        if profile:
+            h.profile(True)
+        st = torch.cuda.current_stream()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        l0 = T.ttice_kernel_launches()
+        barrier()
+        evs[0].record(st)
+        stats = []
+        for k in range(steps):
+            i = args.warmup + k
+            s = h.update(Y[i * b:(i + 1) * b])
+            evs[k + 1].record(st)
+            stats.append((s.skipped, s.n_selected, list(s.ranks[:len(DIMS) + 2])))
+        barrier()
+        launches = T.ttice_kernel_launches() - l0
+        lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+        total = evs[0].elapsed_time(evs[-1])
+        prof = h.profile_read() if profile else None
+        h.close()
+        return total, lat, stats, prof, launches
+
+    with ClockSampler(local) as clk:
+        total_ms, lat, stats, prof, launches = timed_run(args.precision, args.steps, True)
+    t = torch.tensor([total_ms], device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = ws * args.steps * b * N / (total_ms / 1e3)
+
+    # FP64 path on the same stream (the plain FP64 GPU TT-ICE), shorter
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        k64 = min(args.fp64_steps, args.steps)
+        tot64, lat64, _, _, _ = timed_run("fp64", k64, False)
+        fp64 = {"value": k64 * b * N / (tot64 / 1e3), "unit": "elements/s", "steps": k64,
+                "ms_per_step": tot64 / k64, "p50_ms": statistics.median(lat64)}
+
+    # end-to-end through the public API from pinned host memory, with the result read back
+    e2e = None
+    if not args.no_e2e:
+        Yh = Y.cpu().pin_memory()
+        h = T.TTICE(DIMS, EPS, precision=args.precision, input_dtype=torch.float32, max_batch=b)
+        buf = torch.empty((b,) + DIMS, dtype=torch.float32, device=dev)
+        d2h = 0
+        for k in range(args.warmup):
+            buf.copy_(Yh[k * b:(k + 1) * b], non_blocking=True)
+            h.update(buf)
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            i = args.warmup + k
+            buf.copy_(Yh[i * b:(i + 1) * b], non_blocking=True)
+            h.update(buf)
+            coeffs = h.last_core()[-b:]  # the step's result: its rows of the last core
+            d2h += coeffs.nbytes
+        barrier()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], device=dev)
+        if ws > 1:
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": ws * args.steps * b * N / float(tt.item()), "unit": "elements/s",
+               "h2d_bytes_per_step": b * N * 4, "d2h_bytes_per_step": int(d2h / args.steps)}
+        h.close()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peaks, peak_kind = _peaks()
+    # roofline of the dominant phase that has an algorithmic byte count
+    names = [k for k in prof if k != "updates"]
+    dom = max(names, key=lambda n: prof[n]["ms"])
+    hbm_phases = {"k1_stage1", "chain", "final", "d_project", "residual"}
+    pick = "k1_stage1"
+    roof = None
+    ph = prof[pick]
+    if ph["count"] > 0 and ph["ms"] > 0:
+        per_launch_s = ph["ms"] / ph["count"] / 1e3
+        achieved = ph["bytes"] / ph["count"] / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel": pick, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_kind": peak_kind, "bytes_per_launch": ph["bytes"] / ph["count"],
+                "avg_launch_ms": ph["ms"] / ph["count"]}
+    phase_share = {n: round(prof[n]["ms"] / max(total_ms, 1e-9), 4) for n in names}
+    cpu = None
+    if ws == 1 or rank == 0:
+        v, k, busy, threads = oracle_elements_per_s(args.cpu_budget, b)
+        cpu = {"value": v, "unit": "elements/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {k} increments of {b} frames of the same stream ({busy:.1f} s CPU)"}
+    skipped = sum(1 for s in stats if s[0])
+    line = {
+        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": b, "precision": args.precision,
+                   "l2": "each step reads a fresh 29.5 MB slice of a multi-GB pre-generated stream",
+                   "parallelism": f"replicas{ws}"},
+        "latency_ms": {"p50": statistics.median(lat), "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "max": max(lat)},
+        "increments": {"timed": args.steps, "skipped": skipped, "final_ranks": stats[-1][2]},
+        "roofline": roof,
+        "dominant_phase": dom,
+        "phase_share": phase_share,
+        "fp64_path": fp64,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

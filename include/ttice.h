@@ -1,0 +1,179 @@
+/*
+ * libttice -- incremental tensor-train decomposition (TT-ICE / TT-ICE*) on one GB300 GPU.
+ *
+ * The operation is the increment update of Algorithm 1 (TT-ICE) and Algorithm 2 (TT-ICE*) of
+ * "An Incremental Tensor Train Decomposition Algorithm" (arXiv 2211.12487): a batch of b new
+ * observations, each a d-way tensor of shape n_1 x ... x n_d, is projected onto the left-orthonormal
+ * cores U_1..U_d of the accumulation; every core whose residual exceeds its share of the error
+ * tolerance is expanded with just enough orthonormal residual directions (Eqs. 9-11), and the
+ * coefficients of the batch are appended to the growing last core (Eq. 13).
+ *
+ * Conventions shared by every entry point
+ *  - Memory: pointers documented "device" are CUDA device pointers; "host" pointers are ordinary
+ *    host memory.  The caller owns every buffer it passes; the library owns the cores.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls on
+ *    one handle must be issued from one host thread at a time; work is ordered on the given stream.
+ *  - Layout of an increment: b observations, observation-major, each observation in C order
+ *    (n_d fastest), i.e. a contiguous array of shape (b, n_1, ..., n_d).
+ *  - Core layout (Eq. 3): U_i is the (r_{i-1} n_i) x r_i unfolding of core G_i with row index
+ *    a*n_i + k for G_i[a, k, :] (rank index slower than the mode index).
+ *  - Errors: every function returns 0 (TTICE_OK) or a negative TTICE_E* code; ttice_strerror()
+ *    names it.  Nothing traps on the device: device-detected failures set a sticky status that the
+ *    next synchronising call returns.  A failing ttice_update leaves the decomposition exactly as it
+ *    was before the call (cores, ranks and last core are rolled back).
+ */
+#ifndef TTICE_H
+#define TTICE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TTICE_OK 0
+#define TTICE_EINVAL (-1)     /* bad argument (null pointer, size, mode) */
+#define TTICE_ENOMEM (-2)     /* device allocation failed */
+#define TTICE_ECAPACITY (-3)  /* a rank would exceed the capacity fixed at ttice_create */
+#define TTICE_ENONFINITE (-4) /* the increment holds NaN or Inf */
+#define TTICE_ETIMEOUT (-5)   /* an iterative device solve hit its iteration limit */
+#define TTICE_ECUDA (-6)      /* a CUDA runtime call failed */
+#define TTICE_EINTERNAL (-7)
+
+/* Skip test before any core update (Sec. 4.3, last heuristic). */
+#define TTICE_SKIP_NONE 0  /* never skip: plain TT-ICE behaviour */
+#define TTICE_SKIP_EXACT 1 /* skip iff the batch relative error (Eq. 20) <= eps (default) */
+#define TTICE_SKIP_MEAN 2  /* the paper's surrogate: skip iff mean_j eps_Y(j) <= eps */
+
+/* Relaxed tolerance for the selected observations (Sec. 4.3, subselection). */
+#define TTICE_EPSUPD_EXACT 0  /* Eq. 18 (default) */
+#define TTICE_EPSUPD_APPROX 1 /* Eq. 19, count-weighted */
+
+/* Arithmetic of the projections / contractions (the Gram, eigen-solve, CGS2 and all norms and
+ * thresholds are FP64 in every mode). */
+#define TTICE_FP64 0 /* FP64 everywhere: the plain FP64 GPU TT-ICE */
+#define TTICE_FP32 1 /* FP32 projections with FP32 accumulation (SIMT) */
+#define TTICE_TF32 2 /* TF32 tensor-core projections, FP32 accumulation */
+#define TTICE_BF16 3 /* BF16 tensor-core projections, FP32 accumulation */
+#define TTICE_SPLIT_BF16 4 /* three-term split-BF16 projections (~16 mantissa bits) */
+
+/* Element type of increments passed to ttice_update / ttice_project, and of reconstructions. */
+#define TTICE_F32 0
+#define TTICE_F64 1
+
+typedef struct ttice_s* ttice_t;
+
+typedef struct {
+  int skip_mode;        /* TTICE_SKIP_*, default TTICE_SKIP_EXACT */
+  int subselect;        /* 0/1: update only with observations whose eps_Y(j) > eps (Eq. 17), default 1 */
+  int eps_upd_mode;     /* TTICE_EPSUPD_*, default TTICE_EPSUPD_EXACT */
+  double occupancy_tau; /* core i is left alone iff r_i/(r_{i-1} n_i) >= tau (Eq. 16), default 1.0 */
+  int precision;        /* TTICE_FP64 .. TTICE_SPLIT_BF16, default TTICE_FP64 */
+  int input_dtype;      /* TTICE_F32 or TTICE_F64 */
+} ttice_heuristics;
+
+typedef struct {
+  int64_t max_batch;   /* largest b passed to update/project (default 32) */
+  int64_t max_rank;    /* capacity of every TT-rank r_1..r_d (default 512; also capped at the
+                          product of the leading mode sizes) */
+  int64_t obs_reserve; /* initial capacity of the last core in observations (grows by doubling) */
+} ttice_capacity;
+
+typedef struct {
+  int32_t skipped;        /* 1 if the core update was skipped (error already <= eps) */
+  int32_t n_selected;     /* |D|, observations used to update the cores (Eq. 17) */
+  double rel_err_before;  /* batch relative error against the cores before the update (Eq. 20) */
+  double eps_upd;         /* Eq. 18/19 (NaN when skipped) */
+  double eps_core;        /* per-core truncation threshold eps_upd ||D|| / sqrt(d) */
+  int64_t ranks[18];      /* r_0 .. r_d after the update (d <= 16), r_{d+1} = 1 */
+  int32_t new_dirs[16];   /* directions appended to each core U_1..U_d */
+  int64_t n_obs;          /* observations stored in the last core */
+  int64_t core_elems;     /* sum_i r_{i-1} n_i r_i over U_1..U_d plus r_d * n_obs (Eq. 22 denominator) */
+  int32_t eig_sweep_limit; /* eigen-solves of this update that stopped at their sweep limit */
+  int32_t reserved;
+} ttice_update_stats;
+
+/* Fill defaults. */
+void ttice_default_heuristics(ttice_heuristics* h);
+void ttice_default_capacity(ttice_capacity* c);
+
+/* Create an empty decomposition (all ranks 0, Sec. 5 init read as TT-ICE from empty cores, which
+ * equals TT-SVD of the first increment).  dims: host array of d mode sizes (1 <= d <= 16);
+ * eps: relative error bound eps_des in (0, 1) (Problem 1, Corollary 1).  h and cap may be NULL for
+ * defaults.  Allocates every core at capacity on the current CUDA device. */
+int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics* h,
+                 const ttice_capacity* cap, ttice_t* out);
+
+/* One TT-ICE* increment (Algorithm 2; with skip_mode NONE, subselect 0 and tau > 1 exactly
+ * Algorithm 1).  Y: device, `batch` observations of input_dtype, layout above; must stay valid
+ * until the call returns (the call synchronises `stream` at its decision points).  On success the
+ * batch is appended to the last core as observations n_obs .. n_obs+batch-1. */
+int ttice_update(ttice_t h, const void* Y, int64_t batch, void* stream);
+
+/* Sequential projection of `batch` observations onto U_1..U_d without changing the state
+ * (Algorithm 2 "project"; the relative prediction error of Sec. 5.1).  Y: device, input_dtype.
+ * coeffs: device, batch x r_d FP64, row j = coefficients of observation j (may be NULL).
+ * rel_err: device, batch FP64 relative errors eps_Y(j) of Eq. 17 (may be NULL).  Asynchronous. */
+int ttice_project(ttice_t h, const void* Y, int64_t batch, double* coeffs, double* rel_err,
+                  void* stream);
+
+/* Current TT-ranks r_0 .. r_d, r_{d+1}=1 into ranks (host, d+2 entries). */
+int ttice_ranks(ttice_t h, int64_t* ranks);
+
+/* Reconstruct stored observations first .. first+count-1 (Eq. 14): out is a device array of
+ * count observations in the increment layout, element type out_dtype (TTICE_F32/F64). Asynchronous. */
+int ttice_reconstruct(ttice_t h, int64_t first, int64_t count, void* out, int out_dtype,
+                      void* stream);
+
+/* Statistics of the last update. */
+int ttice_stats(ttice_t h, ttice_update_stats* st);
+
+/* Copy core U_i (1 <= i <= d) to host as a row-major (r_{i-1} n_i) x r_i FP64 matrix; rows/cols
+ * receive its shape.  host may be NULL to query the shape.  Synchronous. */
+int ttice_get_core(ttice_t h, int i, double* host, int64_t* rows, int64_t* cols);
+
+/* Copy the last core (Eq. 13) to host as a row-major n_obs x r_d FP64 matrix (row j = coefficients
+ * of observation j, zero-extended).  host may be NULL to query the shape.  Synchronous. */
+int ttice_get_last_core(ttice_t h, double* host, int64_t* n_obs, int64_t* rd);
+
+/* Replace the whole state with host data: ranks r_0..r_d (d+1 entries, r_0 = 1), cores[i] a
+ * row-major (r_i n_{i+1}) x r_{i+1} FP64 matrix for i = 0..d-1, last: n_obs x r_d row-major.
+ * Used to resume from stored cores (the cores are the compressed format) and by lockstep tests. */
+int ttice_load(ttice_t h, const int64_t* ranks, const double* const* cores, const double* last,
+               int64_t n_obs);
+
+/* Device-time profile of ttice_update, by phase of Algorithm 2.  Times come from CUDA events
+ * recorded on the update's stream around each phase; bytes and flops are the algorithmic amounts
+ * (what the method must read, write and compute for the sizes involved, not what the kernels
+ * happen to move).  Phases:
+ *   0 first pass over the increment, stage 1 (U_1^T Y_1, residual norms, ||y||^2; Eq. 6, Eq. 17)
+ *   1 first pass, stages 2..d (Eq. 12 chain with residual norms)
+ *   2 residual of the selected observations against a core (Algorithm 2, R_i)
+ *   3 residual Gram matrix (Eq. 9 via R R^T or R^T R)
+ *   4 truncated eigen-solve, refinement and rank rule (Eq. 5 / Eq. 9)
+ *   5 CGS2, normalisation, sign and append (Eq. 10)
+ *   6 projection of the selected observations onto the updated core (D_{i+1}, Eq. 12)
+ *   7 final projection of the whole batch onto the updated cores and append (Eq. 13) */
+#define TTICE_NPHASES 8
+typedef struct {
+  double ms[TTICE_NPHASES];
+  double bytes[TTICE_NPHASES];
+  double flops[TTICE_NPHASES];
+  int64_t count[TTICE_NPHASES];
+  int64_t updates;
+} ttice_profile;
+
+/* Enable (1) or disable (0) phase profiling of h; enabling also clears the accumulated profile. */
+int ttice_profile_enable(ttice_t h, int on);
+/* Accumulated profile since the last enable.  Host struct. */
+int ttice_profile_read(ttice_t h, ttice_profile* out);
+/* Kernel launches issued by this library in this process so far. */
+int64_t ttice_kernel_launches(void);
+
+void ttice_destroy(ttice_t h);
+const char* ttice_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTICE_H */

@@ -1,0 +1,286 @@
+// Multi-CTA block Jacobi eigen-solver for the residual Gram matrices of Eq. 9 (s up to 1024).
+//
+// Two-sided cyclic block Jacobi (Golub & Van Loan, Sec. 8.5, block variant): the matrix is split
+// into nb blocks of BS rows/columns; the block pairs (I, J) of one round come from the round-robin
+// ordering on block indices, so the nb/2 pairs of a round are disjoint.  One round is three kernels:
+//   solve: one CTA per pair loads the 2BS x 2BS submatrix A[I u J, I u J] into shared memory and
+//          applies one cyclic sweep of scalar Jacobi rotations to it, accumulating the orthogonal
+//          Q (2BS x 2BS) of the sweep;
+//   rows:  A[I u J, :] <- Q^T A[I u J, :] for every pair (disjoint row sets), tiled over columns;
+//   cols:  A[:, I u J] <- A[:, I u J] Q and V[:, I u J] <- V[:, I u J] Q, tiled over rows.
+// A sweep is nb-1 rounds; a flag raised by any significant rotation keeps the next sweep alive, and
+// every kernel returns at once after a sweep without one, so a fixed launch sequence costs almost
+// nothing once converged.  Padding to nb*BS adds zero rows/columns, which no rotation touches (their
+// off-diagonal entries are exactly zero), so the first s coordinates carry the eigenpairs.
+#include <algorithm>
+#include <cfloat>
+
+#include "ttice_internal.cuh"
+
+namespace ttice {
+namespace {
+
+template <typename T> struct BJ;
+template <> struct BJ<float> {
+  static constexpr int BS = 32;
+  static __device__ float eps() { return FLT_EPSILON; }
+};
+template <> struct BJ<double> {
+  static constexpr int BS = 16;
+  static __device__ double eps() { return DBL_EPSILON; }
+};
+
+constexpr int kTile = 64;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void circle_pair(int players, int round, int k, int* p, int* q) {
+  int a, b;
+  if (k == 0) { a = round; b = players - 1; }
+  else { a = (round + k) % (players - 1); b = (round - k + (players - 1)) % (players - 1); }
+  *p = a < b ? a : b;
+  *q = a < b ? b : a;
+}
+
+template <typename T>
+__global__ void bj_init(const double* G, int64_t ldg, int s, int sp, T* A, T* V, double* fro,
+                        int* flags) {
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)sp * sp;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / sp), j = (int)(e % sp);
+    double g = (i < s && j < s) ? G[i * ldg + j] : 0.0;
+    acc += g * g;
+    A[e] = (T)g;
+    V[(int64_t)j * sp + i] = (i == j) ? T(1) : T(0);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(fro, acc);
+  if (blockIdx.x == 0 && threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bj_solve(const T* A, int sp, int nb, int round, T* Qb,
+                                                     const double* fro, int* flags) {
+  constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
+  if (flags[1]) return;
+  __shared__ T S[N2][N2 + 1];
+  __shared__ T Q[N2][N2 + 1];
+  __shared__ T rc[BS], rs[BS];
+  __shared__ int rp[BS], rq[BS];
+  __shared__ int any;
+  int bi, bj;
+  circle_pair(nb, round, blockIdx.x, &bi, &bj);
+  const int tid = threadIdx.x;
+  auto gidx = [&](int a) { return a < BS ? bi * BS + a : bj * BS + (a - BS); };
+  for (int e = tid; e < N2 * N2; e += kThreads) {
+    const int a = e / N2, b = e % N2;
+    S[a][b] = A[(int64_t)gidx(a) * sp + gidx(b)];
+    Q[a][b] = (a == b) ? T(1) : T(0);
+  }
+  if (tid == 0) any = 0;
+  __syncthreads();
+  const T teps = BJ<T>::eps();
+  const T floor_abs = (T)((double)teps * sqrt(*fro));
+  for (int round2 = 0; round2 < N2 - 1; ++round2) {
+    if (tid < BS) {
+      int p, q;
+      circle_pair(N2, round2, tid, &p, &q);
+      const T apq = S[p][q], app = S[p][p], aqq = S[q][q];
+      T c = T(1), sn = T(0);
+      if (fabs(apq) > floor_abs && fabs(apq) > teps * sqrt(fabs(app * aqq))) {
+        const T tau = (aqq - app) / (T(2) * apq);
+        const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+        c = T(1) / sqrt(T(1) + t * t);
+        sn = t * c;
+        any = 1;
+      }
+      rc[tid] = c; rs[tid] = sn; rp[tid] = p; rq[tid] = q;
+    }
+    __syncthreads();
+    for (int e = tid; e < BS * N2; e += kThreads) {  // rows of S
+      const int k = e / N2, j = e % N2;
+      if (rs[k] == T(0)) continue;
+      const int p = rp[k], q = rq[k];
+      const T c = rc[k], sn = rs[k];
+      const T xp = S[p][j], xq = S[q][j];
+      S[p][j] = c * xp - sn * xq;
+      S[q][j] = sn * xp + c * xq;
+    }
+    __syncthreads();
+    for (int e = tid; e < BS * N2; e += kThreads) {  // columns of S and of Q
+      const int k = e / N2, i = e % N2;
+      if (rs[k] == T(0)) continue;
+      const int p = rp[k], q = rq[k];
+      const T c = rc[k], sn = rs[k];
+      const T xp = S[i][p], xq = S[i][q];
+      S[i][p] = c * xp - sn * xq;
+      S[i][q] = sn * xp + c * xq;
+      const T vp = Q[i][p], vq = Q[i][q];
+      Q[i][p] = c * vp - sn * vq;
+      Q[i][q] = sn * vp + c * vq;
+    }
+    __syncthreads();
+  }
+  T* Qo = Qb + (int64_t)blockIdx.x * N2 * N2;
+  for (int e = tid; e < N2 * N2; e += kThreads) Qo[e] = Q[e / N2][e % N2];
+  if (tid == 0 && any) atomicOr(flags, 1);
+}
+
+// A[I u J, tile] <- Q^T A[I u J, tile]
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bj_rows(T* A, int sp, int nb, int round, const T* Qb,
+                                                    const int* flags) {
+  constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
+  if (flags[1]) return;
+  __shared__ T Q[N2][N2 + 1];
+  __shared__ T X[N2][kTile + 1];
+  int bi, bj;
+  circle_pair(nb, round, blockIdx.x, &bi, &bj);
+  const int c0 = blockIdx.y * kTile;
+  const int tid = threadIdx.x;
+  const T* Qi = Qb + (int64_t)blockIdx.x * N2 * N2;
+  auto gidx = [&](int a) { return a < BS ? bi * BS + a : bj * BS + (a - BS); };
+  for (int e = tid; e < N2 * N2; e += kThreads) Q[e / N2][e % N2] = Qi[e];
+  for (int e = tid; e < N2 * kTile; e += kThreads) {
+    const int a = e / kTile, c = e % kTile;
+    X[a][c] = (c0 + c < sp) ? A[(int64_t)gidx(a) * sp + c0 + c] : T(0);
+  }
+  __syncthreads();
+  for (int e = tid; e < N2 * kTile; e += kThreads) {
+    const int a = e / kTile, c = e % kTile;
+    if (c0 + c >= sp) continue;
+    T acc = T(0);
+#pragma unroll 8
+    for (int b = 0; b < N2; ++b) acc = fma(Q[b][a], X[b][c], acc);
+    A[(int64_t)gidx(a) * sp + c0 + c] = acc;
+  }
+}
+
+// A[tile, I u J] <- A[tile, I u J] Q ; V[tile, I u J] <- V[tile, I u J] Q (V column-major)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bj_cols(T* A, T* V, int sp, int nb, int round,
+                                                    const T* Qb, const int* flags) {
+  constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
+  if (flags[1]) return;
+  __shared__ T Q[N2][N2 + 1];
+  __shared__ T X[kTile][N2 + 1];  // the A tile, then the V tile (both as [row][pair column])
+  int bi, bj;
+  circle_pair(nb, round, blockIdx.x, &bi, &bj);
+  const int r0 = blockIdx.y * kTile;
+  const int tid = threadIdx.x;
+  const T* Qi = Qb + (int64_t)blockIdx.x * N2 * N2;
+  auto gidx = [&](int a) { return a < BS ? bi * BS + a : bj * BS + (a - BS); };
+  for (int e = tid; e < N2 * N2; e += kThreads) Q[e / N2][e % N2] = Qi[e];
+  for (int e = tid; e < kTile * N2; e += kThreads) {
+    const int i = e / N2, a = e % N2;
+    X[i][a] = (r0 + i < sp) ? A[(int64_t)(r0 + i) * sp + gidx(a)] : T(0);
+  }
+  __syncthreads();
+  for (int e = tid; e < kTile * N2; e += kThreads) {
+    const int i = e / N2, a = e % N2;
+    if (r0 + i >= sp) continue;
+    T acc = T(0);
+#pragma unroll 8
+    for (int b = 0; b < N2; ++b) acc = fma(X[i][b], Q[b][a], acc);
+    A[(int64_t)(r0 + i) * sp + gidx(a)] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < N2 * kTile; e += kThreads) {
+    const int a = e / kTile, i = e % kTile;
+    X[i][a] = (r0 + i < sp) ? V[(int64_t)gidx(a) * sp + r0 + i] : T(0);
+  }
+  __syncthreads();
+  for (int e = tid; e < N2 * kTile; e += kThreads) {
+    const int a = e / kTile, i = e % kTile;
+    if (r0 + i >= sp) continue;
+    T acc = T(0);
+#pragma unroll 8
+    for (int b = 0; b < N2; ++b) acc = fma(X[i][b], Q[b][a], acc);
+    V[(int64_t)gidx(a) * sp + r0 + i] = acc;
+  }
+}
+
+__global__ void bj_sweep_end(int* flags, int max_sweeps) {
+  if (flags[1]) return;
+  flags[2] += 1;
+  if (flags[0] == 0) flags[1] = 1;
+  else if (flags[2] >= max_sweeps) flags[3] = 1;  // sweep limit reached while still rotating
+  flags[0] = 0;
+}
+
+// eigenvalues = diag(A)[0..s), sorted descending (ties by index); eigenvectors follow.
+template <typename T>
+__global__ void bj_finish(const T* A, const T* V, int sp, int s, T* w, T* Vout) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
+    const T di = A[(int64_t)i * sp + i];
+    int rank = 0;
+    for (int j = 0; j < s; ++j) {
+      const T dj = A[(int64_t)j * sp + j];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    w[rank] = di;
+    const T* src = V + (int64_t)i * sp;
+    T* dst = Vout + (int64_t)rank * s;
+    for (int r = 0; r < s; ++r) dst[r] = src[r];
+  }
+}
+
+}  // namespace
+
+template <typename T>
+int64_t block_jacobi_work(int s) {
+  constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
+  int nb = (s + BS - 1) / BS;
+  nb += nb & 1;
+  const int64_t sp = (int64_t)nb * BS;
+  return 2 * sp * sp + (int64_t)(nb / 2) * N2 * N2 + 16;
+}
+
+template <typename T>
+cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout, T* work,
+                             double* fro, int* flags, int max_sweeps, cudaStream_t st) {
+  constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
+  if (s <= 0) return cudaSuccess;
+  int nb = (s + BS - 1) / BS;
+  nb += nb & 1;
+  if (nb < 2) nb = 2;
+  const int sp = nb * BS;
+  T* A = work;
+  T* V = work + (int64_t)sp * sp;
+  T* Qb = V + (int64_t)sp * sp;
+  const int npairs = nb / 2;
+  TT_CUDA(cudaMemsetAsync(fro, 0, sizeof(double), st));
+  TT_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+  {
+    int64_t n = (int64_t)sp * sp;
+    int grid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8);
+    note_launch();
+    bj_init<T><<<grid, kThreads, 0, st>>>(G, ldg, s, sp, A, V, fro, flags);
+  }
+  const int tiles = (sp + kTile - 1) / kTile;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int round = 0; round < nb - 1; ++round) {
+      note_launch();
+      bj_solve<T><<<npairs, kThreads, 0, st>>>(A, sp, nb, round, Qb, fro, flags);
+      note_launch();
+      bj_rows<T><<<dim3(npairs, tiles), kThreads, 0, st>>>(A, sp, nb, round, Qb, flags);
+      note_launch();
+      bj_cols<T><<<dim3(npairs, tiles), kThreads, 0, st>>>(A, V, sp, nb, round, Qb, flags);
+    }
+    note_launch();
+    bj_sweep_end<<<1, 1, 0, st>>>(flags, max_sweeps);
+  }
+  note_launch();
+  bj_finish<T><<<(s + 127) / 128, 128, 0, st>>>(A, V, sp, s, w, Vout);
+  (void)N2;
+  return cudaGetLastError();
+}
+
+template int64_t block_jacobi_work<float>(int);
+template int64_t block_jacobi_work<double>(int);
+template cudaError_t block_jacobi_eig<float>(const double*, int64_t, int, float*, float*, float*,
+                                             double*, int*, int, cudaStream_t);
+template cudaError_t block_jacobi_eig<double>(const double*, int64_t, int, double*, double*,
+                                              double*, double*, int*, int, cudaStream_t);
+
+}  // namespace ttice

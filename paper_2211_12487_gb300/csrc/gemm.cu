@@ -1,0 +1,178 @@
+// Generic strided, batched SIMT GEMM used by the FP64 path and by the small contractions of every
+// path: projections U_i^T Y_i (Eq. 12), back-projections and residuals (Eq. 6), residual Gram
+// matrices (Eq. 9 via R R^T), CGS2 projections (Eq. 10) and reconstructions (Eq. 14).
+//
+// Tiles of BM x BN outputs, BK-deep K slices staged in shared memory (converted to the accumulator
+// type on load), TM x TN outputs per thread.  Loads follow whichever operand stride is 1, so both
+// K-contiguous and M/N-contiguous operands are read coalesced.  The epilogue forms
+// alpha*acc + beta*X, optionally accumulates the squared entries per batch (FP64 atomics), and either
+// stores or atomically adds into C (the latter enables split-K and reductions over a batch index).
+#include <algorithm>
+
+#include "ttice_internal.cuh"
+
+namespace ttice {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ld_elem(const void* p, int64_t off) {
+  return static_cast<const T*>(p)[off];
+}
+
+template <typename TA, typename TB, typename TX, typename TC, typename ACC, int BM, int BN, int BK,
+          int TM, int TN>
+__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64_t kchunk) {
+  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+  __shared__ ACC As[BK][BM + 1];
+  __shared__ ACC Bs[BK][BN + 1];
+  const int z = blockIdx.z;
+  const int zb = z / ksplit, zk = z % ksplit;
+  const int z1 = zb / g.bdiv, z2 = zb % g.bdiv;
+  const int64_t aoff = z1 * g.A.bs1 + z2 * g.A.bs2;
+  const int64_t boff = z1 * g.B.bs1 + z2 * g.B.bs2;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  const int64_t kbeg = zk * kchunk;
+  const int64_t kend = min(g.K, kbeg + kchunk);
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  const bool a_kfast = (g.A.cs == 1);
+  const bool b_nfast = (g.B.cs == 1);
+
+  ACC acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = ACC(0);
+
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      int mm, kk;
+      if (a_kfast) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      ACC v = ACC(0);
+      if (gm < g.M && gk < kend) v = (ACC)ld_elem<TA>(g.A.p, aoff + gm * g.A.rs + gk * g.A.cs);
+      As[kk][mm] = v;
+    }
+    for (int e = tid; e < BN * BK; e += 256) {
+      int nn, kk;
+      if (b_nfast) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      ACC v = ACC(0);
+      if (gn < g.N && gk < kend) v = (ACC)ld_elem<TB>(g.B.p, boff + gk * g.B.rs + gn * g.B.cs);
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      ACC a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * (BM / TM)];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * (BN / TN)];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+  double ss = 0.0;
+  double rowss[TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) rowss[i] = 0.0;
+  TC* C = static_cast<TC*>(g.C);
+  const int64_t coff = z1 * g.c_bs1 + z2 * g.c_bs2;
+  const int64_t xoff = z1 * g.X.bs1 + z2 * g.X.bs2;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t gm = m0 + ty + i * (BM / TM);
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gn = n0 + tx + j * (BN / TN);
+      if (gm < g.M && gn < g.N) {
+        double v = g.alpha * (double)acc[i][j];
+        if (g.X.p) v += g.beta * (double)ld_elem<TX>(g.X.p, xoff + gm * g.X.rs + gn * g.X.cs);
+        const TC cv = (TC)v;
+        if (g.norm) {
+          ss += (double)cv * (double)cv;
+          rowss[i] += (double)cv * (double)cv;
+        }
+        if (g.store) {
+          TC* dst = C + coff + gm * g.c_rs + gn * g.c_cs;
+          if (g.atomic) atomicAdd(dst, cv);
+          else *dst = cv;
+        }
+      }
+    }
+  }
+  if (g.norm && g.norm_rows) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int64_t gm = m0 + ty + i * (BM / TM);
+      if (gm < g.M && rowss[i] != 0.0) atomicAdd(g.norm + gm, rowss[i]);
+    }
+  } else if (g.norm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((tid & 31) == 0 && ss != 0.0) atomicAdd(g.norm + z1, ss);
+  }
+}
+
+template <typename TA, typename TB, typename TX, typename TC, typename ACC, int BM, int BN, int BK,
+          int TM, int TN>
+cudaError_t run(const GemmArgs& g, cudaStream_t st) {
+  const int64_t gx = (g.N + BN - 1) / BN, gy = (g.M + BM - 1) / BM;
+  int ksplit = 1;
+  int64_t kchunk = g.K > 0 ? g.K : 1;
+  if (g.atomic && g.allow_splitk && !g.X.p && !g.norm) {
+    const int64_t tiles = gx * gy * g.nbatch;
+    const int64_t target = 2 * 152;
+    if (tiles < target && g.K > 4 * BK) {
+      int64_t want = (target + tiles - 1) / tiles;
+      int64_t maxs = (g.K + 4 * BK - 1) / (4 * BK);
+      ksplit = (int)std::min<int64_t>(std::min<int64_t>(want, maxs), 4096);
+      kchunk = (g.K + ksplit - 1) / ksplit;
+      kchunk = (kchunk + BK - 1) / BK * BK;
+      ksplit = (int)((g.K + kchunk - 1) / kchunk);
+    }
+  }
+  if (gx == 0 || gy == 0 || g.nbatch == 0) return cudaSuccess;
+  if (gy > 65535 || (int64_t)g.nbatch * ksplit > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(g.nbatch * ksplit));
+  note_launch();
+  gemm_kernel<TA, TB, TX, TC, ACC, BM, BN, BK, TM, TN><<<grid, 256, 0, st>>>(g, ksplit, kchunk);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename TA, typename TB, typename TX, typename TC, typename ACC>
+cudaError_t gemm(const GemmArgs& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.nbatch <= 0) return cudaSuccess;
+  if (g.M <= 16) return run<TA, TB, TX, TC, ACC, 16, 256, 16, 2, 8>(g, st);
+  if (g.M <= 32) return run<TA, TB, TX, TC, ACC, 32, 128, 16, 4, 4>(g, st);
+  if (g.N <= 16) return run<TA, TB, TX, TC, ACC, 256, 16, 16, 8, 2>(g, st);
+  return run<TA, TB, TX, TC, ACC, 64, 64, 16, 4, 4>(g, st);
+}
+
+#define TT_GEMM_INST(TA, TB, TX, TC, ACC) \
+  template cudaError_t gemm<TA, TB, TX, TC, ACC>(const GemmArgs&, cudaStream_t);
+
+// FP64 path
+TT_GEMM_INST(double, double, double, double, double)
+TT_GEMM_INST(double, float, float, double, double)
+TT_GEMM_INST(double, double, float, double, double)
+TT_GEMM_INST(double, float, double, double, double)
+// FP32 projections
+TT_GEMM_INST(float, float, float, float, float)
+TT_GEMM_INST(float, double, double, float, float)
+TT_GEMM_INST(float, float, double, float, float)
+TT_GEMM_INST(float, double, float, float, float)
+// Gram of FP32 residuals in FP64
+TT_GEMM_INST(float, float, float, double, double)
+TT_GEMM_INST(float, double, double, double, double)
+// reconstruction into FP32 outputs
+TT_GEMM_INST(double, double, double, float, double)
+
+}  // namespace ttice

@@ -1,0 +1,964 @@
+// libttice host side: the handle, the C-ABI entry points and the orchestration of one TT-ICE*
+// increment (Algorithm 2) over the device kernels.
+//
+// Device state of a handle (all zero-initialised, so the padding of Eq. 11 is implicit):
+//   U[i]   core i (0-based; the paper's U_{i+1}) as a column-major (cap_i n_i) x cap_{i+1} FP64 array.
+//          Only the leading (r_i n_i) x r_{i+1} block is non-zero; appending a column (Eq. 10) writes
+//          the next column, growing r_i appends zero rows at the bottom of U[i+1] for free.
+//   Uf[i]  FP32 mirror of U[i] (used by the FP32 projections).
+//   last   the last core (Eq. 13): row j = the r_d coefficients of observation j (ld cap_d), with the
+//          implicit zero extension of Theorem 2.
+// Stage buffers hold the chain of projections Y_{i+1} = reshape(U_i^T Y_i) (Eq. 12) observation-
+// major: observation z, row a, column l at z*(r_{i+1} L_i) + a*L_i + l, which is also the (r_{i+1}
+// n_{i+1}) x L_{i+1} unfolding consumed by the next stage.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ttice_internal.cuh"
+
+using namespace ttice;
+
+struct ttice_s {
+  int d = 0;
+  int64_t n[kMaxD] = {};
+  int64_t L[kMaxD] = {};  // L[i] = n[i+1] * ... * n[d-1]
+  int64_t N = 0;
+  double eps = 0.0;
+  ttice_heuristics h{};
+  ttice_capacity capc{};
+  int64_t cap[kMaxD + 1] = {};  // rank capacities, cap[0] = 1
+  int64_t ldu[kMaxD] = {};      // rows of the U[i] allocation = cap[i] * n[i]
+  int64_t r[kMaxD + 1] = {};    // ranks r_0..r_d (host mirror), r[0] = 1
+  double* U[kMaxD] = {};
+  float* Uf[kMaxD] = {};
+  double* last = nullptr;
+  int64_t last_cap = 0;  // observations
+  int64_t n_obs = 0;
+  int wt_bytes = 8;  // working type of stage buffers: 8 (FP64 path) or 4
+  // workspace
+  void* stage[kMaxD] = {};
+  void* dstage[kMaxD] = {};
+  void* dgather = nullptr;
+  void* Rbuf = nullptr;
+  int64_t s_max = 0;
+  double* G = nullptr;
+  float* w32 = nullptr;
+  float* V32 = nullptr;
+  double* w64 = nullptr;
+  double* V64 = nullptr;
+  double* work64 = nullptr;
+  double* bjw64 = nullptr;  // block Jacobi scratch (FP64 path)
+  float* bjw32 = nullptr;   // block Jacobi scratch (FP32 eigenvectors of the mixed paths)
+  double* fro = nullptr;
+  int* bjflags = nullptr;
+  double* Q = nullptr;   // s_max x kRR
+  double* Q2 = nullptr;  // s_max x kRR
+  double* GQ = nullptr;  // s_max x kRR
+  double* Ssm = nullptr; // kRR x kRR
+  double* Rinv = nullptr;
+  double* H = nullptr;
+  double* Z = nullptr;   // kRR x kRR eigenvectors
+  double* theta = nullptr;
+  double* Vn = nullptr;  // new directions, max_m x kRR
+  double* Vn2 = nullptr;
+  double* P = nullptr;   // cap x kRR projections for CGS2
+  int64_t max_m = 0;
+  double* rho2 = nullptr;
+  double* y2 = nullptr;
+  double* trace = nullptr;
+  Decision* dec = nullptr;
+  int* sel = nullptr;
+  int* ibuf = nullptr;  // [0] rank, [1] eig status, [2] chol status, [3] nonfinite
+  Decision* h_dec = nullptr;  // pinned
+  int* h_sel = nullptr;       // pinned
+  int* h_int = nullptr;       // pinned
+  float* h_w32 = nullptr;     // pinned, s_max
+  ttice_update_stats stats{};
+  // phase profiling
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> marks;  // (phase, index of the start event; end = +1)
+  ttice_profile prof{};
+};
+
+namespace {
+
+enum Phase {
+  PH_K1 = 0, PH_CHAIN = 1, PH_RESID = 2, PH_GRAM = 3, PH_EIG = 4, PH_ORTH = 5, PH_DPROJ = 6,
+  PH_FINAL = 7
+};
+
+cudaEvent_t next_event(ttice_s* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Record the start of a phase and add its algorithmic bytes / flops.
+void ph_begin(ttice_s* h, int ph, cudaStream_t st, double bytes, double flops) {
+  if (!h->prof_on) return;
+  h->marks.push_back({ph, h->ev_used});
+  cudaEventRecord(next_event(h), st);
+  h->prof.bytes[ph] += bytes;
+  h->prof.flops[ph] += flops;
+  h->prof.count[ph] += 1;
+}
+void ph_end(ttice_s* h, cudaStream_t st) {
+  if (!h->prof_on) return;
+  cudaEventRecord(next_event(h), st);
+}
+// After the stream has been synchronised: fold the recorded event pairs into the profile.
+void ph_collect(ttice_s* h) {
+  if (!h->prof_on) return;
+  for (auto& m : h->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[m.second], h->ev_pool[m.second + 1]) == cudaSuccess)
+      h->prof.ms[m.first] += ms;
+  }
+  h->marks.clear();
+  h->ev_used = 0;
+}
+
+constexpr int kRR = 96;         // largest Rayleigh-Ritz subspace
+constexpr int kDirectEig = 32;  // Gram matrices up to this size are diagonalised in FP64 directly
+constexpr int kMaxEig = 1024;
+constexpr int kMaxSweeps64 = 15;  // block Jacobi sweep limits (quadratic convergence needs ~6-10)
+constexpr int kMaxSweeps32 = 12;
+
+int cu(cudaError_t e) { return e == cudaSuccess ? TTICE_OK : TTICE_ECUDA; }
+#define TT_TRY(...)                      \
+  do {                                   \
+    int rc__ = (__VA_ARGS__);            \
+    if (rc__ != TTICE_OK) return rc__;   \
+  } while (0)
+#define TT_CU(...) TT_TRY(cu(__VA_ARGS__))
+
+template <typename T>
+int dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) return TTICE_OK;
+  if (cudaMalloc((void**)p, (size_t)count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return TTICE_ENOMEM;
+  }
+  if (cudaMemset(*p, 0, (size_t)count * sizeof(T)) != cudaSuccess) return TTICE_ECUDA;
+  return TTICE_OK;
+}
+int dalloc_bytes(void** p, int64_t bytes) {
+  return dalloc<unsigned char>(reinterpret_cast<unsigned char**>(p), bytes);
+}
+
+void free_all(ttice_s* h) {
+  for (int i = 0; i < kMaxD; ++i) {
+    cudaFree(h->U[i]); cudaFree(h->Uf[i]); cudaFree(h->stage[i]); cudaFree(h->dstage[i]);
+  }
+  void* ptrs[] = {h->bjw64, h->bjw32, h->fro, h->bjflags,
+                  h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
+                  h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
+                  h->Vn2, h->P, h->rho2, h->y2, h->trace, h->dec, h->sel, h->ibuf};
+  for (void* p : ptrs) cudaFree(p);
+  cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32);
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------- GEMM helpers
+// W(z) = U_i^T X(z) for every observation z: M = r_{i+1}, K = m_i, N = L_i.
+template <typename TU, typename TX, typename TW>
+int proj(const TU* Ui, int64_t ldu, const TX* X, int64_t m, int64_t L, int64_t rnext, int b, TW* W,
+         cudaStream_t st) {
+  GemmArgs g;
+  g.M = rnext; g.N = L; g.K = m;
+  g.A.p = Ui; g.A.rs = ldu; g.A.cs = 1;
+  g.B.p = X; g.B.rs = L; g.B.cs = 1; g.B.bs1 = m * L;
+  g.C = W; g.c_rs = L; g.c_cs = 1; g.c_bs1 = rnext * L;
+  g.nbatch = b;
+  using ACC = typename std::conditional<sizeof(TW) == 8, double, float>::type;
+  return cu(gemm<TU, TX, TX, TW, ACC>(g, st));
+}
+
+// R(z) = X(z) - U_i W(z); norm[z] += ||R(z)||^2; R stored iff R != nullptr.
+template <typename TU, typename TW, typename TX, typename TR>
+int resid(const TU* Ui, int64_t ldu, const TW* W, const TX* X, int64_t m, int64_t L, int64_t rnext,
+          int b, TR* R, double* norm, cudaStream_t st) {
+  GemmArgs g;
+  g.M = m; g.N = L; g.K = rnext;
+  g.A.p = Ui; g.A.rs = 1; g.A.cs = ldu;
+  g.B.p = W; g.B.rs = L; g.B.cs = 1; g.B.bs1 = rnext * L;
+  g.X.p = X; g.X.rs = L; g.X.cs = 1; g.X.bs1 = m * L;
+  g.alpha = -1.0; g.beta = 1.0;
+  g.C = R; g.c_rs = L; g.c_cs = 1; g.c_bs1 = m * L;
+  g.store = R != nullptr;
+  g.norm = norm;
+  g.nbatch = b;
+  using ACC = typename std::conditional<sizeof(TW) == 8, double, float>::type;
+  return cu(gemm<TU, TW, TX, TR, ACC>(g, st));
+}
+
+template <typename T>
+int sumsq(const T* X, int b, int64_t n, double* out, cudaStream_t st) {
+  return cu(launch_sum_squares<T>(X, b, n, out, st));
+}
+
+// ---------------------------------------------------------------- chain projection
+// Project b observations of X0 (stage-0 layout) through U_1..U_d into `bufs`; with `errors`,
+// rho2[z] = sum_i ||R_i(z)||^2 (the orthogonal decomposition of ||y - ~y||^2) and y2[z] = ||y_z||^2.
+template <typename WT, typename TY>
+int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_t st) {
+  const WT* Xw = nullptr;
+  const double sw = sizeof(WT), sy = sizeof(TY);
+  if (errors) {
+    TT_CU(cudaMemsetAsync(h->rho2, 0, b * sizeof(double), st));
+    TT_CU(cudaMemsetAsync(h->y2, 0, b * sizeof(double), st));
+    const double N = (double)h->N, r1 = (double)h->r[1];
+    ph_begin(h, PH_K1, st, b * (sy * N + sw * r1 * h->L[0]), b * (4.0 * N * r1 + 4.0 * N));
+    TT_TRY(sumsq<TY>(X0, b, h->N, h->y2, st));
+  } else {
+    double by = sy * b * h->N, fl = 0.0;
+    for (int i = 0; i < h->d; ++i) {
+      const double out = (double)b * h->r[i + 1] * h->L[i];
+      by += sw * out * (i + 1 < h->d ? 2.0 : 1.0);
+      fl += 2.0 * b * (double)h->r[i] * h->n[i] * h->L[i] * h->r[i + 1];
+    }
+    ph_begin(h, PH_FINAL, st, by, fl);
+  }
+  for (int i = 0; i < h->d; ++i) {
+    const int64_t m = h->r[i] * h->n[i], rn = h->r[i + 1], L = h->L[i];
+    WT* W = static_cast<WT*>(bufs[i]);
+    if (errors && i == 1) {
+      ph_end(h, st);
+      double by = 0.0, fl = 0.0;
+      for (int j = 1; j < h->d; ++j) {
+        const double mj = (double)h->r[j] * h->n[j];
+        by += sw * b * (mj * h->L[j] + (double)h->r[j + 1] * h->L[j]);
+        fl += (double)b * h->L[j] * (4.0 * mj * h->r[j + 1] + 2.0 * mj);
+      }
+      ph_begin(h, PH_CHAIN, st, by, fl);
+    }
+    if (rn == 0 || m == 0) {
+      // nothing is represented from here on: the whole remaining stage is residual
+      if (errors && m > 0) {
+        if (i == 0) TT_TRY(sumsq<TY>(X0, b, m * L, h->rho2, st));
+        else TT_TRY(sumsq<WT>(Xw, b, m * L, h->rho2, st));
+      }
+      // zero the coefficients of the remaining stages
+      for (int j = i; j < h->d; ++j) {
+        const int64_t sz = (int64_t)b * h->r[j + 1] * h->L[j];
+        if (sz > 0) TT_CU(cudaMemsetAsync(bufs[j], 0, sz * sizeof(WT), st));
+      }
+      ph_end(h, st);
+      return TTICE_OK;
+    }
+    const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
+                                     : reinterpret_cast<const WT*>(h->Uf[i]);
+    if (i == 0) {
+      TT_TRY(proj<WT, TY, WT>(Ui, h->ldu[i], X0, m, L, rn, b, W, st));
+      if (errors) TT_TRY((resid<WT, WT, TY, WT>(Ui, h->ldu[i], W, X0, m, L, rn, b, nullptr, h->rho2, st)));
+    } else {
+      TT_TRY(proj<WT, WT, WT>(Ui, h->ldu[i], Xw, m, L, rn, b, W, st));
+      if (errors) TT_TRY((resid<WT, WT, WT, WT>(Ui, h->ldu[i], W, Xw, m, L, rn, b, nullptr, h->rho2, st)));
+    }
+    Xw = W;
+  }
+  ph_end(h, st);
+  return TTICE_OK;
+}
+
+int sync_read(ttice_s* h, cudaStream_t st) {
+  TT_CU(cudaStreamSynchronize(st));
+  return TTICE_OK;
+}
+
+// ---------------------------------------------------------------- truncated SVD of one residual
+// Residual R (observation-major blocks, m x L each, nsel blocks) -> new directions Vn (m x rR,
+// column-major, ld m), rR returned through *rR_out.
+template <typename WT>
+int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int nsel, double eps_c,
+                   int max_new, int* rR_out, cudaStream_t st) {
+  const int64_t c = L * nsel;
+  const bool left = m <= c;  // Gram on the row side (R R^T) or the column side (R^T R)
+  const int64_t s = left ? m : c;
+  if (s > kMaxEig) return TTICE_ECAPACITY;
+  using ACC = double;
+  // Gram (FP64 accumulation)
+  ph_begin(h, PH_GRAM, st, (double)sizeof(WT) * m * c + 8.0 * s * s, 2.0 * (double)s * s * (left ? c : m));
+  TT_CU(cudaMemsetAsync(h->G, 0, (size_t)s * s * sizeof(double), st));
+  {
+    GemmArgs g;
+    g.atomic = 1; g.allow_splitk = 1;
+    g.C = h->G;
+    if (left) {
+      g.M = m; g.N = m; g.K = L;
+      g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
+      g.B.p = R; g.B.rs = 1; g.B.cs = L; g.B.bs1 = m * L;
+      g.c_rs = s; g.c_cs = 1;
+      g.nbatch = nsel;
+    } else {
+      g.M = L; g.N = L; g.K = m;
+      g.A.p = R; g.A.rs = 1; g.A.cs = L; g.A.bs1 = m * L;
+      g.B.p = R; g.B.rs = L; g.B.cs = 1; g.B.bs2 = m * L;
+      g.c_rs = s; g.c_cs = 1; g.c_bs1 = L * s; g.c_bs2 = L;
+      g.nbatch = nsel * nsel; g.bdiv = nsel;
+    }
+    TT_CU((gemm<WT, WT, WT, double, ACC>(g, st)));
+  }
+  TT_CU(launch_trace(h->G, s, (int)s, h->trace, st));
+  ph_end(h, st);
+  ph_begin(h, PH_EIG, st, 0.0, 0.0);
+  const double* d_eps = &h->dec->eps_c;  // the per-core threshold decided on the device
+
+  const double* Vdir = nullptr;  // s x K Ritz / eigen vectors (column-major, ld s)
+  const double* thet = nullptr;
+  int K = 0;
+  if (sizeof(WT) == 8 || s <= kDirectEig) {
+    // FP64 eigen-solve: one CTA for small Gram matrices, the multi-CTA block Jacobi otherwise.
+    if (s <= kDirectEig) {
+      TT_CU(jacobi_eig<double>(h->G, s, (int)s, h->w64, h->V64, h->work64, h->ibuf + 1, st));
+    } else {
+      TT_CU(block_jacobi_eig<double>(h->G, s, (int)s, h->w64, h->V64, h->bjw64, h->fro, h->bjflags,
+                                     kMaxSweeps64, st));
+      TT_CU(cudaMemcpyAsync(h->ibuf + 1, h->bjflags + 3, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    }
+    // Energy of R along each eigenvector, measured on R itself (||q_j^T R||^2 or ||R v_j||^2) so
+    // that the truncation tail does not inherit the squared rounding of the Gram matrix.  The
+    // eigenbasis is complete, so these energies sum to ||R||^2 and the tail is summed directly.
+    double* e = h->theta;
+    TT_CU(cudaMemsetAsync(e, 0, s * sizeof(double), st));
+    if (left) {
+      GemmArgs g;  // E = V^T R, row norms
+      g.M = s; g.N = L; g.K = m;
+      g.A.p = h->V64; g.A.rs = s; g.A.cs = 1;
+      g.B.p = R; g.B.rs = L; g.B.cs = 1; g.B.bs1 = m * L;
+      g.store = 0; g.norm = e; g.norm_rows = 1;
+      g.nbatch = nsel;
+      TT_CU((gemm<double, WT, double, double, double>(g, st)));
+    } else {
+      TT_CU(cudaMemsetAsync(h->Vn, 0, (size_t)m * s * sizeof(double), st));
+      GemmArgs g;  // E = R V (m x s), column norms
+      g.M = m; g.N = s; g.K = L; g.atomic = 1; g.allow_splitk = 1;
+      g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
+      g.B.p = h->V64; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
+      g.C = h->Vn; g.c_rs = 1; g.c_cs = m;
+      g.nbatch = nsel;
+      TT_CU((gemm<WT, double, double, double, double>(g, st)));
+      TT_CU(launch_col_norms(h->Vn, m, (int)s, m, e, st));
+    }
+    TT_CU(launch_rank_rule(e, (int)s, 1, h->trace, d_eps, max_new, h->ibuf, st));
+    Vdir = h->V64; thet = h->w64; K = (int)s;
+  } else {
+    // FP32 block Jacobi for approximate eigenvectors, then FP64 Rayleigh-Ritz on the leading K.
+    TT_CU(block_jacobi_eig<float>(h->G, s, (int)s, h->w32, h->V32, h->bjw32, h->fro, h->bjflags,
+                                  kMaxSweeps32, st));
+    TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, s * sizeof(float), cudaMemcpyDeviceToHost, st));
+    ph_end(h, st);
+    TT_TRY(sync_read(h, st));
+    ph_begin(h, PH_EIG, st, 0.0, 0.0);
+    // size of the Rayleigh-Ritz subspace from the FP32 spectrum (only sizes a buffer; the rank
+    // itself is decided below from FP64 Ritz values)
+    double tail = 0.0;
+    int r32 = (int)s;
+    for (int j = (int)s - 1; j >= 0; --j) {
+      tail += std::max((double)h->h_w32[j], 0.0);
+      if (std::sqrt(tail) <= eps_c) r32 = j; else break;
+    }
+    K = std::min<int>((int)s, std::min(r32 + 8, kRR));
+    if (r32 + 1 > kRR) return TTICE_ECAPACITY;
+    TT_CU(launch_to_f64<float>(h->V32, s * K, h->Q, st));
+    // CholQR2: orthonormalise Q in FP64
+    for (int pass = 0; pass < 2; ++pass) {
+      TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)K * K * sizeof(double), st));
+      GemmArgs g;  // S = Q^T Q
+      g.M = K; g.N = K; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+      g.A.p = h->Q; g.A.rs = s; g.A.cs = 1;
+      g.B.p = h->Q; g.B.rs = 1; g.B.cs = s;
+      g.C = h->Ssm; g.c_rs = 1; g.c_cs = K;
+      TT_CU((gemm<double, double, double, double, double>(g, st)));
+      TT_CU(launch_chol_inv(h->Ssm, K, h->Rinv, h->ibuf + 2, st));
+      GemmArgs q;  // Q2 = Q Rinv
+      q.M = s; q.N = K; q.K = K;
+      q.A.p = h->Q; q.A.rs = 1; q.A.cs = s;
+      q.B.p = h->Rinv; q.B.rs = 1; q.B.cs = K;
+      q.C = h->Q2; q.c_rs = 1; q.c_cs = s;
+      TT_CU((gemm<double, double, double, double, double>(q, st)));
+      std::swap(h->Q, h->Q2);
+    }
+    {  // GQ = G Q ; H = Q^T GQ
+      GemmArgs g;
+      g.M = s; g.N = K; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+      g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
+      g.B.p = h->Q; g.B.rs = 1; g.B.cs = s;
+      g.C = h->GQ; g.c_rs = 1; g.c_cs = s;
+      TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * K * sizeof(double), st));
+      TT_CU((gemm<double, double, double, double, double>(g, st)));
+      TT_CU(cudaMemsetAsync(h->H, 0, (size_t)K * K * sizeof(double), st));
+      GemmArgs hh;
+      hh.M = K; hh.N = K; hh.K = s; hh.atomic = 1; hh.allow_splitk = 1;
+      hh.A.p = h->Q; hh.A.rs = s; hh.A.cs = 1;
+      hh.B.p = h->GQ; hh.B.rs = 1; hh.B.cs = s;
+      hh.C = h->H; hh.c_rs = K; hh.c_cs = 1;
+      TT_CU((gemm<double, double, double, double, double>(hh, st)));
+    }
+    TT_CU(jacobi_eig<double>(h->H, K, K, h->theta, h->Z, h->work64, h->ibuf + 1, st));
+    TT_CU(launch_rank_rule(h->theta, K, K == s, h->trace, d_eps, max_new, h->ibuf, st));
+    {  // Ritz vectors Q2 = Q Z
+      GemmArgs g;
+      g.M = s; g.N = K; g.K = K;
+      g.A.p = h->Q; g.A.rs = 1; g.A.cs = s;
+      g.B.p = h->Z; g.B.rs = 1; g.B.cs = K;
+      g.C = h->Q2; g.c_rs = 1; g.c_cs = s;
+      TT_CU((gemm<double, double, double, double, double>(g, st)));
+    }
+    Vdir = h->Q2; thet = h->theta;
+  }
+  TT_CU(cudaMemcpyAsync(h->h_int, h->ibuf, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  ph_end(h, st);
+  TT_TRY(sync_read(h, st));
+  int rR = h->h_int[0];
+  if (h->h_int[1] != 0) h->stats.eig_sweep_limit += 1;  // unconverged sweeps: energies are still measured
+  if (rR < 0) return TTICE_ECAPACITY;  // Rayleigh-Ritz subspace too small for the tolerance
+  *rR_out = rR;
+  if (rR == 0) return TTICE_OK;
+  if (rR > kRR) return TTICE_ECAPACITY;
+  // directions in R^m (part of the eigen-solve phase)
+  ph_begin(h, PH_EIG, st, 0.0, 0.0);
+  if (left) {
+    TT_CU(cudaMemcpy2DAsync(h->Vn, m * sizeof(double), Vdir, s * sizeof(double), m * sizeof(double),
+                            rR, cudaMemcpyDeviceToDevice, st));
+  } else {
+    // u_j = R v_j / sqrt(theta_j), v_j indexed by (observation, l)
+    TT_CU(cudaMemsetAsync(h->Vn, 0, (size_t)m * rR * sizeof(double), st));
+    GemmArgs g;
+    g.M = m; g.N = rR; g.K = L; g.atomic = 1; g.allow_splitk = 1;
+    g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
+    g.B.p = Vdir; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
+    g.C = h->Vn; g.c_rs = 1; g.c_cs = m;
+    g.nbatch = nsel;
+    TT_CU((gemm<WT, double, double, double, double>(g, st)));
+    TT_CU(launch_scale_cols_rsqrt(h->Vn, m, rR, m, thet, st));
+  }
+  ph_end(h, st);
+  return TTICE_OK;
+}
+
+// CGS2 of the new directions Vn (m x k) against U[core] (m x r), CholQR2 among themselves,
+// canonical sign, and append as columns r..r+k-1 of U[core] (Eq. 10).
+int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
+  const int64_t r = h->r[core + 1];
+  double* U = h->U[core];
+  const int64_t ld = h->ldu[core];
+  for (int pass = 0; pass < 2 && r > 0; ++pass) {
+    GemmArgs a;  // P = U^T Vn  (r x k, column-major ld r)
+    a.M = r; a.N = k; a.K = m; a.atomic = 1; a.allow_splitk = 1;
+    a.A.p = U; a.A.rs = ld; a.A.cs = 1;
+    a.B.p = h->Vn; a.B.rs = 1; a.B.cs = m;
+    a.C = h->P; a.c_rs = 1; a.c_cs = r;
+    TT_CU(cudaMemsetAsync(h->P, 0, (size_t)r * k * sizeof(double), st));
+    TT_CU((gemm<double, double, double, double, double>(a, st)));
+    GemmArgs b;  // Vn = Vn - U P
+    b.M = m; b.N = k; b.K = r;
+    b.A.p = U; b.A.rs = 1; b.A.cs = ld;
+    b.B.p = h->P; b.B.rs = 1; b.B.cs = r;
+    b.X.p = h->Vn; b.X.rs = 1; b.X.cs = m;
+    b.alpha = -1.0; b.beta = 1.0;
+    b.C = h->Vn; b.c_rs = 1; b.c_cs = m;
+    TT_CU((gemm<double, double, double, double, double>(b, st)));
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)k * k * sizeof(double), st));
+    GemmArgs g;  // S = Vn^T Vn
+    g.M = k; g.N = k; g.K = m; g.atomic = 1; g.allow_splitk = 1;
+    g.A.p = h->Vn; g.A.rs = m; g.A.cs = 1;
+    g.B.p = h->Vn; g.B.rs = 1; g.B.cs = m;
+    g.C = h->Ssm; g.c_rs = 1; g.c_cs = k;
+    TT_CU((gemm<double, double, double, double, double>(g, st)));
+    TT_CU(launch_chol_inv(h->Ssm, k, h->Rinv, h->ibuf + 2, st));
+    GemmArgs q;  // Vn2 = Vn Rinv
+    q.M = m; q.N = k; q.K = k;
+    q.A.p = h->Vn; q.A.rs = 1; q.A.cs = m;
+    q.B.p = h->Rinv; q.B.rs = 1; q.B.cs = k;
+    q.C = h->Vn2; q.c_rs = 1; q.c_cs = m;
+    TT_CU((gemm<double, double, double, double, double>(q, st)));
+    std::swap(h->Vn, h->Vn2);
+  }
+  TT_CU(launch_canonical_sign(h->Vn, m, k, m, st));
+  TT_CU(launch_copy_cols(h->Vn, m, m, k, U + r * ld, ld, h->Uf[core] ? h->Uf[core] + r * ld : nullptr,
+                         st));
+  return TTICE_OK;
+}
+
+int grow_last(ttice_s* h, int64_t need) {
+  if (need <= h->last_cap) return TTICE_OK;
+  int64_t nc = std::max<int64_t>(h->last_cap * 2, need);
+  double* p = nullptr;
+  TT_TRY(dalloc<double>(&p, nc * h->cap[h->d]));
+  if (h->last) {
+    if (cudaMemcpy(p, h->last, (size_t)h->last_cap * h->cap[h->d] * sizeof(double),
+                   cudaMemcpyDeviceToDevice) != cudaSuccess) {
+      cudaFree(p);
+      return TTICE_ECUDA;
+    }
+    cudaFree(h->last);
+  }
+  h->last = p;
+  h->last_cap = nc;
+  return TTICE_OK;
+}
+
+void fill_stats(ttice_s* h) {
+  for (int i = 0; i <= h->d; ++i) h->stats.ranks[i] = h->r[i];
+  h->stats.ranks[h->d + 1] = 1;
+  h->stats.n_obs = h->n_obs;
+  int64_t e = 0;
+  for (int i = 0; i < h->d; ++i) e += h->r[i] * h->n[i] * h->r[i + 1];
+  e += h->r[h->d] * h->n_obs;
+  h->stats.core_elems = e;
+}
+
+// Undo the rank growth of a failed update: zero the appended columns (which also removes every
+// entry they had in padded rows) and restore the ranks.
+void rollback(ttice_s* h, const int64_t* r_old, cudaStream_t st) {
+  for (int i = 0; i < h->d; ++i) {
+    if (h->r[i + 1] > r_old[i + 1]) {
+      const int64_t ld = h->ldu[i];
+      const size_t bytes = (size_t)(h->r[i + 1] - r_old[i + 1]) * ld;
+      cudaMemsetAsync(h->U[i] + r_old[i + 1] * ld, 0, bytes * sizeof(double), st);
+      if (h->Uf[i]) cudaMemsetAsync(h->Uf[i] + r_old[i + 1] * ld, 0, bytes * sizeof(float), st);
+    }
+  }
+  for (int i = 0; i <= h->d; ++i) h->r[i] = r_old[i];
+  cudaStreamSynchronize(st);
+}
+
+template <typename WT, typename TY>
+int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
+  TT_TRY(grow_last(h, h->n_obs + b));
+  void** S1 = h->stage;
+  TT_TRY((chain<WT, TY>(h, Y, b, S1, true, st)));
+  TT_CU(launch_decision(h->rho2, h->y2, b, h->eps, h->d, h->h.skip_mode, h->h.subselect,
+                        h->h.eps_upd_mode, h->dec, h->sel, st));
+  TT_CU(cudaMemcpyAsync(h->h_dec, h->dec, sizeof(Decision), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_sel, h->sel, b * sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_TRY(sync_read(h, st));
+  const Decision dec = *h->h_dec;
+  if (dec.nonfinite) return TTICE_ENONFINITE;
+  std::memset(&h->stats, 0, sizeof(h->stats));
+  h->stats.skipped = dec.skip;
+  h->stats.n_selected = dec.nsel;
+  h->stats.rel_err_before = dec.batch_err;
+  h->stats.eps_upd = dec.eps_upd;
+  h->stats.eps_core = dec.eps_c;
+
+  if (!dec.skip && dec.nsel > 0) {
+    int64_t r_old[kMaxD + 1];
+    std::memcpy(r_old, h->r, sizeof(r_old));
+    const int nsel = dec.nsel;
+    const TY* D0 = Y;
+    if (nsel < b) {
+      TT_CU(launch_gather_obs<TY>(Y, static_cast<TY*>(h->dgather), h->sel, nsel, h->N, st));
+      D0 = static_cast<const TY*>(h->dgather);
+    }
+    const WT* X = nullptr;  // stage input for i >= 1
+    int rc = TTICE_OK;
+    for (int i = 0; i < h->d && rc == TTICE_OK; ++i) {
+      const int64_t m = h->r[i] * h->n[i], L = h->L[i];
+      const int64_t ri = h->r[i + 1];
+      int grew = 0;
+      if (m > 0 && !((double)ri >= h->h.occupancy_tau * (double)m)) {
+        WT* R = static_cast<WT*>(h->Rbuf);
+        const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
+                                         : reinterpret_cast<const WT*>(h->Uf[i]);
+        WT* Wt = static_cast<WT*>(h->dstage[i]);
+        {
+          const double sx = (i == 0) ? sizeof(TY) : sizeof(WT), sw = sizeof(WT);
+          ph_begin(h, PH_RESID, st, nsel * (sx * m * L + sw * m * L + 2.0 * sw * ri * L),
+                   4.0 * nsel * (double)m * L * ri);
+        }
+        if (ri > 0) {
+          if (i == 0) {
+            rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0, m, L, ri, nsel, Wt, st);
+            if (rc == TTICE_OK) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wt, D0, m, L, ri, nsel, R, nullptr, st);
+          } else {
+            rc = proj<WT, WT, WT>(Ui, h->ldu[i], X, m, L, ri, nsel, Wt, st);
+            if (rc == TTICE_OK) rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wt, X, m, L, ri, nsel, R, nullptr, st);
+          }
+        } else {
+          if (i == 0) rc = cu(launch_cast<TY, WT>(D0, R, (int64_t)nsel * m * L, st));
+          else rc = cu(cudaMemcpyAsync(R, X, (size_t)nsel * m * L * sizeof(WT), cudaMemcpyDeviceToDevice, st));
+        }
+        ph_end(h, st);
+        if (rc != TTICE_OK) break;
+        const int max_new = (int)(m - ri);
+        int rR = 0;
+        rc = truncated_dirs<WT>(h, i, R, m, L, nsel, dec.eps_c, max_new, &rR, st);
+        if (rc != TTICE_OK) break;
+        if (rR > 0) {
+          if (ri + rR > h->cap[i + 1]) { rc = TTICE_ECAPACITY; break; }
+          ph_begin(h, PH_ORTH, st, 8.0 * m * (2.0 * ri + 3.0 * rR),
+                   8.0 * m * ri * rR + 8.0 * m * (double)rR * rR);
+          rc = orthonormalize_append(h, i, m, rR, st);
+          ph_end(h, st);
+          if (rc != TTICE_OK) break;
+          h->r[i + 1] = ri + rR;
+          grew = rR;
+        }
+      }
+      h->stats.new_dirs[i] = grew;
+      // D_{i+1} = reshape(U_i^T D_i) with the updated core
+      if (i + 1 < h->d) {
+        const int64_t rn = h->r[i + 1];
+        const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
+                                         : reinterpret_cast<const WT*>(h->Uf[i]);
+        WT* Wn = static_cast<WT*>(h->dstage[i]);
+        if (m == 0 || rn == 0) break;  // nothing flows to the next cores
+        {
+          const double sx = (i == 0) ? sizeof(TY) : sizeof(WT);
+          ph_begin(h, PH_DPROJ, st, nsel * (sx * m * L + sizeof(WT) * (double)rn * L),
+                   2.0 * nsel * (double)m * L * rn);
+        }
+        if (i == 0) rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0, m, L, rn, nsel, Wn, st);
+        else rc = proj<WT, WT, WT>(Ui, h->ldu[i], X, m, L, rn, nsel, Wn, st);
+        ph_end(h, st);
+        X = Wn;
+      }
+    }
+    if (rc != TTICE_OK) {
+      rollback(h, r_old, st);
+      h->marks.clear();
+      h->ev_used = 0;
+      return rc;
+    }
+    // project every observation onto the updated cores (Algorithm 2, last two steps)
+    TT_TRY((chain<WT, TY>(h, Y, b, S1, false, st)));
+  }
+  const int rd = (int)h->r[h->d];
+  TT_CU(launch_append_last_t<WT>(static_cast<const WT*>(S1[h->d - 1]), b, rd, h->last, h->n_obs,
+                                 h->cap[h->d], st));
+  TT_TRY(sync_read(h, st));
+  h->n_obs += b;
+  fill_stats(h);
+  ph_collect(h);
+  if (h->prof_on) h->prof.updates += 1;
+  return TTICE_OK;
+}
+
+template <typename WT, typename TY>
+int project_impl(ttice_s* h, const TY* Y, int b, double* coeffs, double* rel, cudaStream_t st) {
+  TT_TRY((chain<WT, TY>(h, Y, b, h->stage, rel != nullptr, st)));
+  const int rd = (int)h->r[h->d];
+  if (coeffs && rd > 0) TT_CU((launch_cast<WT, double>(static_cast<const WT*>(h->stage[h->d - 1]), coeffs, (int64_t)b * rd, st)));
+  if (rel) TT_CU(launch_rel_err(h->rho2, h->y2, b, rel, st));
+  return TTICE_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+void ttice_default_heuristics(ttice_heuristics* h) {
+  if (!h) return;
+  h->skip_mode = TTICE_SKIP_EXACT;
+  h->subselect = 1;
+  h->eps_upd_mode = TTICE_EPSUPD_EXACT;
+  h->occupancy_tau = 1.0;
+  h->precision = TTICE_FP64;
+  h->input_dtype = TTICE_F32;
+}
+
+void ttice_default_capacity(ttice_capacity* c) {
+  if (!c) return;
+  c->max_batch = 32;
+  c->max_rank = 512;
+  c->obs_reserve = 1024;
+}
+
+const char* ttice_strerror(int code) {
+  switch (code) {
+    case TTICE_OK: return "ok";
+    case TTICE_EINVAL: return "invalid argument";
+    case TTICE_ENOMEM: return "device allocation failed";
+    case TTICE_ECAPACITY: return "rank capacity or solver limit exceeded";
+    case TTICE_ENONFINITE: return "increment contains NaN or Inf";
+    case TTICE_ETIMEOUT: return "iterative device solve hit its iteration limit";
+    case TTICE_ECUDA: return "CUDA runtime error";
+    default: return "internal error";
+  }
+}
+
+int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics* hp,
+                 const ttice_capacity* cp, ttice_t* out) {
+  if (!dims || !out || d < 1 || d > kMaxD || !(eps > 0.0) || !(eps < 1.0)) return TTICE_EINVAL;
+  *out = nullptr;
+  ttice_s* h = new (std::nothrow) ttice_s();
+  if (!h) return TTICE_ENOMEM;
+  ttice_default_heuristics(&h->h);
+  ttice_default_capacity(&h->capc);
+  if (hp) h->h = *hp;
+  if (cp) h->capc = *cp;
+  if (h->h.precision != TTICE_FP64 && h->h.precision != TTICE_FP32) { delete h; return TTICE_EINVAL; }
+  if (h->h.input_dtype != TTICE_F32 && h->h.input_dtype != TTICE_F64) { delete h; return TTICE_EINVAL; }
+  if (h->capc.max_batch < 1 || h->capc.max_rank < 1) { delete h; return TTICE_EINVAL; }
+  h->d = d;
+  h->eps = eps;
+  h->N = 1;
+  for (int i = 0; i < d; ++i) {
+    if (dims[i] < 1) { delete h; return TTICE_EINVAL; }
+    h->n[i] = dims[i];
+    h->N *= dims[i];
+  }
+  for (int i = 0; i < d; ++i) {
+    int64_t l = 1;
+    for (int j = i + 1; j < d; ++j) l *= h->n[j];
+    h->L[i] = l;
+  }
+  h->cap[0] = 1;
+  h->r[0] = 1;
+  for (int i = 1; i <= d; ++i) h->cap[i] = std::min<int64_t>(h->capc.max_rank, h->cap[i - 1] * h->n[i - 1]);
+  h->wt_bytes = (h->h.precision == TTICE_FP64) ? 8 : 4;
+  const int64_t B = h->capc.max_batch;
+  int rc = TTICE_OK;
+  int64_t max_mL = 0;
+  for (int i = 0; i < d && rc == TTICE_OK; ++i) {
+    h->ldu[i] = h->cap[i] * h->n[i];
+    h->max_m = std::max(h->max_m, h->ldu[i]);
+    rc = dalloc<double>(&h->U[i], h->ldu[i] * h->cap[i + 1]);
+    if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->Uf[i], h->ldu[i] * h->cap[i + 1]);
+    const int64_t st_elems = B * h->cap[i + 1] * h->L[i];
+    if (rc == TTICE_OK) rc = dalloc_bytes(&h->stage[i], st_elems * h->wt_bytes);
+    if (rc == TTICE_OK) rc = dalloc_bytes(&h->dstage[i], st_elems * h->wt_bytes);
+    max_mL = std::max(max_mL, h->ldu[i] * h->L[i]);
+    h->s_max = std::max(h->s_max, std::min<int64_t>(h->ldu[i], h->L[i] * B));
+  }
+  h->s_max = std::min<int64_t>(h->s_max, kMaxEig);
+  const int64_t s = std::max<int64_t>(h->s_max, 1);
+  const int in_bytes = h->h.input_dtype == TTICE_F32 ? 4 : 8;
+  if (rc == TTICE_OK) rc = dalloc_bytes(&h->dgather, B * h->N * in_bytes);
+  if (rc == TTICE_OK) rc = dalloc_bytes(&h->Rbuf, B * max_mL * h->wt_bytes);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->G, s * s);
+  if (rc == TTICE_OK) rc = dalloc<float>(&h->w32, s);
+  if (rc == TTICE_OK) rc = dalloc<float>(&h->V32, s * s);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->w64, std::max<int64_t>(s, kRR));
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->V64, std::max<int64_t>(s * s, (int64_t)kRR * kRR));
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->work64, 2 * std::max<int64_t>(s, kRR) * (std::max<int64_t>(s, kRR) + 1));
+  if (rc == TTICE_OK && h->wt_bytes == 8) rc = dalloc<double>(&h->bjw64, block_jacobi_work<double>((int)s));
+  if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->bjw32, block_jacobi_work<float>((int)s));
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->fro, 1);
+  if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 4);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->Q, s * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->Q2, s * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->GQ, s * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->Ssm, kRR * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->Rinv, kRR * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->H, kRR * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->Z, kRR * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->theta, kRR + 8);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->Vn, h->max_m * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->Vn2, h->max_m * kRR);
+  int64_t maxcap = 1;
+  for (int i = 1; i <= d; ++i) maxcap = std::max(maxcap, h->cap[i]);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->P, maxcap * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->rho2, B);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->y2, B);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->trace, 1);
+  if (rc == TTICE_OK) rc = dalloc<Decision>(&h->dec, 1);
+  if (rc == TTICE_OK) rc = dalloc<int>(&h->sel, B);
+  if (rc == TTICE_OK) rc = dalloc<int>(&h->ibuf, 16);
+  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_dec, sizeof(Decision)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_sel, B * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_int, 16 * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_w32, s * sizeof(float)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK) rc = grow_last(h, std::max<int64_t>(h->capc.obs_reserve, 1));
+  if (rc == TTICE_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TTICE_ECUDA;
+  if (rc != TTICE_OK) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  fill_stats(h);
+  *out = h;
+  return TTICE_OK;
+}
+
+void ttice_destroy(ttice_t h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  free_all(h);
+  delete h;
+}
+
+int ttice_update(ttice_t h, const void* Y, int64_t batch, void* stream) {
+  if (!h || !Y || batch < 1 || batch > h->capc.max_batch) return TTICE_EINVAL;
+  cudaStream_t st = S(stream);
+  const int b = (int)batch;
+  if (h->wt_bytes == 8) {
+    if (h->h.input_dtype == TTICE_F32) return update_impl<double, float>(h, (const float*)Y, b, st);
+    return update_impl<double, double>(h, (const double*)Y, b, st);
+  }
+  if (h->h.input_dtype == TTICE_F32) return update_impl<float, float>(h, (const float*)Y, b, st);
+  return update_impl<float, double>(h, (const double*)Y, b, st);
+}
+
+int ttice_project(ttice_t h, const void* Y, int64_t batch, double* coeffs, double* rel_err,
+                  void* stream) {
+  if (!h || !Y || batch < 1 || batch > h->capc.max_batch) return TTICE_EINVAL;
+  cudaStream_t st = S(stream);
+  const int b = (int)batch;
+  if (h->wt_bytes == 8) {
+    if (h->h.input_dtype == TTICE_F32) return project_impl<double, float>(h, (const float*)Y, b, coeffs, rel_err, st);
+    return project_impl<double, double>(h, (const double*)Y, b, coeffs, rel_err, st);
+  }
+  if (h->h.input_dtype == TTICE_F32) return project_impl<float, float>(h, (const float*)Y, b, coeffs, rel_err, st);
+  return project_impl<float, double>(h, (const double*)Y, b, coeffs, rel_err, st);
+}
+
+int ttice_ranks(ttice_t h, int64_t* ranks) {
+  if (!h || !ranks) return TTICE_EINVAL;
+  for (int i = 0; i <= h->d; ++i) ranks[i] = h->r[i];
+  ranks[h->d + 1] = 1;
+  return TTICE_OK;
+}
+
+int ttice_stats(ttice_t h, ttice_update_stats* st) {
+  if (!h || !st) return TTICE_EINVAL;
+  *st = h->stats;
+  return TTICE_OK;
+}
+
+int ttice_reconstruct(ttice_t h, int64_t first, int64_t count, void* out, int out_dtype,
+                      void* stream) {
+  if (!h || !out || first < 0 || count < 1 || first + count > h->n_obs) return TTICE_EINVAL;
+  if (out_dtype != TTICE_F32 && out_dtype != TTICE_F64) return TTICE_EINVAL;
+  cudaStream_t st = S(stream);
+  const int d = h->d;
+  const int64_t rd = h->r[d];
+  if (rd == 0) {
+    return cu(cudaMemsetAsync(out, 0, (size_t)count * h->N * (out_dtype == TTICE_F32 ? 4 : 8), st));
+  }
+  double *bufA = nullptr, *bufB = nullptr;
+  if (d > 1) {
+    if (cudaMallocAsync((void**)&bufA, (size_t)count * h->N * sizeof(double), st) != cudaSuccess) return TTICE_ENOMEM;
+    if (cudaMallocAsync((void**)&bufB, (size_t)count * h->N * sizeof(double), st) != cudaSuccess) {
+      cudaFreeAsync(bufA, st);
+      return TTICE_ENOMEM;
+    }
+  }
+  // X (per observation r_{i+1} x rest) -> U_i X (per observation (r_i n_i) x rest)
+  const double* X = h->last + first * h->cap[d];
+  int64_t x_bs = h->cap[d];  // observation stride of X
+  int64_t rest = 1;
+  int rc = TTICE_OK;
+  double* bufs[2] = {bufA, bufB};
+  for (int i = d - 1; i >= 0 && rc == TTICE_OK; --i) {
+    const int64_t m = h->r[i] * h->n[i], rn = h->r[i + 1];
+    GemmArgs g;
+    g.M = m; g.N = rest; g.K = rn;
+    g.A.p = h->U[i]; g.A.rs = 1; g.A.cs = h->ldu[i];
+    g.B.p = X; g.B.rs = rest; g.B.cs = 1; g.B.bs1 = x_bs;
+    g.nbatch = (int)count;
+    g.c_rs = rest; g.c_cs = 1; g.c_bs1 = m * rest;
+    if (i == 0) {
+      g.C = out;
+      if (out_dtype == TTICE_F64) rc = cu(gemm<double, double, double, double, double>(g, st));
+      else rc = cu(gemm<double, double, double, float, double>(g, st));
+    } else {
+      double* dst = bufs[i & 1];
+      g.C = dst;
+      rc = cu(gemm<double, double, double, double, double>(g, st));
+      X = dst;
+      x_bs = m * rest;
+    }
+    rest *= h->n[i];
+  }
+  if (bufA) cudaFreeAsync(bufA, st);
+  if (bufB) cudaFreeAsync(bufB, st);
+  return rc;
+}
+
+int ttice_get_core(ttice_t h, int i, double* host, int64_t* rows, int64_t* cols) {
+  if (!h || i < 1 || i > h->d) return TTICE_EINVAL;
+  const int c = i - 1;
+  const int64_t m = h->r[c] * h->n[c], r = h->r[c + 1];
+  if (rows) *rows = m;
+  if (cols) *cols = r;
+  if (!host || m == 0 || r == 0) return TTICE_OK;
+  std::vector<double> tmp((size_t)m * r);
+  if (cudaMemcpy2D(tmp.data(), m * sizeof(double), h->U[c], h->ldu[c] * sizeof(double),
+                   m * sizeof(double), r, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return TTICE_ECUDA;
+  for (int64_t a = 0; a < m; ++a)
+    for (int64_t b = 0; b < r; ++b) host[a * r + b] = tmp[b * m + a];
+  return TTICE_OK;
+}
+
+int ttice_get_last_core(ttice_t h, double* host, int64_t* n_obs, int64_t* rd) {
+  if (!h) return TTICE_EINVAL;
+  const int64_t r = h->r[h->d];
+  if (n_obs) *n_obs = h->n_obs;
+  if (rd) *rd = r;
+  if (!host || h->n_obs == 0 || r == 0) return TTICE_OK;
+  if (cudaMemcpy2D(host, r * sizeof(double), h->last, h->cap[h->d] * sizeof(double),
+                   r * sizeof(double), h->n_obs, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return TTICE_ECUDA;
+  return TTICE_OK;
+}
+
+int ttice_profile_enable(ttice_t h, int on) {
+  if (!h) return TTICE_EINVAL;
+  h->prof_on = on != 0;
+  std::memset(&h->prof, 0, sizeof(h->prof));
+  h->marks.clear();
+  h->ev_used = 0;
+  return TTICE_OK;
+}
+
+int ttice_profile_read(ttice_t h, ttice_profile* out) {
+  if (!h || !out) return TTICE_EINVAL;
+  *out = h->prof;
+  return TTICE_OK;
+}
+
+int64_t ttice_kernel_launches(void) { return g_kernel_launches.load(); }
+
+int ttice_load(ttice_t h, const int64_t* ranks, const double* const* cores, const double* last,
+               int64_t n_obs) {
+  if (!h || !ranks || ranks[0] != 1 || n_obs < 0 || (n_obs > 0 && !last)) return TTICE_EINVAL;
+  for (int i = 1; i <= h->d; ++i) {
+    if (ranks[i] < 0 || ranks[i] > h->cap[i] || ranks[i] > ranks[i - 1] * h->n[i - 1]) return TTICE_ECAPACITY;
+    if (ranks[i] > 0 && !cores[i - 1]) return TTICE_EINVAL;
+  }
+  TT_TRY(grow_last(h, std::max<int64_t>(n_obs, 1)));
+  for (int i = 0; i < h->d; ++i) {
+    const int64_t ld = h->ldu[i], m = ranks[i] * h->n[i], r = ranks[i + 1];
+    std::vector<double> colmajor((size_t)ld * h->cap[i + 1], 0.0);
+    for (int64_t a = 0; a < m; ++a)
+      for (int64_t b = 0; b < r; ++b) colmajor[b * ld + a] = cores[i][a * r + b];
+    TT_CU(cudaMemcpy(h->U[i], colmajor.data(), colmajor.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (h->Uf[i]) {
+      std::vector<float> f(colmajor.begin(), colmajor.end());
+      TT_CU(cudaMemcpy(h->Uf[i], f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
+  const int64_t capd = h->cap[h->d];
+  std::vector<double> lc((size_t)h->last_cap * capd, 0.0);
+  for (int64_t j = 0; j < n_obs; ++j)
+    for (int64_t a = 0; a < ranks[h->d]; ++a) lc[j * capd + a] = last[j * ranks[h->d] + a];
+  TT_CU(cudaMemcpy(h->last, lc.data(), lc.size() * sizeof(double), cudaMemcpyHostToDevice));
+  for (int i = 0; i <= h->d; ++i) h->r[i] = ranks[i];
+  h->n_obs = n_obs;
+  fill_stats(h);
+  return TTICE_OK;
+}
+
+}  // extern "C"

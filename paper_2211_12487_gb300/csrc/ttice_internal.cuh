@@ -1,0 +1,133 @@
+// Internal declarations of libttice: device views, kernel launchers and the handle layout.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ttice.h"
+
+#include <atomic>
+
+namespace ttice {
+
+constexpr int kMaxD = 16;
+
+// Count of kernel launches issued by this library (process-wide), for launch accounting.
+extern std::atomic<long long> g_kernel_launches;
+inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// A strided matrix view with a two-level batch index: batch z -> (z1, z2) = (z / bdiv, z % bdiv),
+// element (row, col) of batch z at p + z1*bs1 + z2*bs2 + row*rs + col*cs (element units).
+struct View {
+  const void* p = nullptr;
+  int64_t rs = 0, cs = 0, bs1 = 0, bs2 = 0;
+};
+
+// C(z) = alpha * A(z) * B(z) + beta * X(z), M x N, inner dimension K.
+struct GemmArgs {
+  int64_t M = 0, N = 0, K = 0;
+  View A, B, X;
+  void* C = nullptr;
+  int64_t c_rs = 0, c_cs = 0, c_bs1 = 0, c_bs2 = 0;
+  double alpha = 1.0, beta = 0.0;
+  int nbatch = 1, bdiv = 1;
+  int atomic = 0;         // add into C with atomics (C zeroed by the caller); allows split-K
+  int store = 1;          // write C at all
+  double* norm = nullptr; // optional: += sum of squares of the C(z) entries into norm[z1]
+  int norm_rows = 0;      // with norm: accumulate per output row instead (norm[row])
+  int allow_splitk = 0;   // with atomic: split K across CTAs when the tile grid is small
+};
+
+template <typename TA, typename TB, typename TX, typename TC, typename ACC>
+cudaError_t gemm(const GemmArgs& g, cudaStream_t st);
+
+// Symmetric eigen-solve by cyclic two-sided Jacobi with round-robin parallel ordering.
+// G: FP64 s x s (leading dimension ldg, symmetric).  Works in T.  On return w[0..s) holds the
+// eigenvalues in descending order and V (s x s, column-major, ld s) the matching eigenvectors.
+// work: device scratch of 2*s*(s+1) T (eigenvector iterate, and the matrix when it does not fit in
+// shared memory).
+// status (device int): set to 1 if the sweep limit was hit.
+template <typename T>
+cudaError_t jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* V, T* work, int* status,
+                       cudaStream_t st);
+
+// Multi-CTA block Jacobi (see bjacobi.cu): same outputs as jacobi_eig.  work: block_jacobi_work<T>(s)
+// elements; fro: device double scratch; flags: device int[4] ([3] = 1 if the sweep limit was hit
+// while rotations were still significant).
+template <typename T>
+int64_t block_jacobi_work(int s);
+template <typename T>
+cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* V, T* work, double* fro,
+                             int* flags, int max_sweeps, cudaStream_t st);
+
+// Device-side decision of Algorithm 2 (skip test, subselection, eps_upd, per-core threshold).
+struct Decision {
+  int skip;
+  int nsel;
+  double batch_err;   // Eq. 20
+  double ynorm2;      // ||Y||^2
+  double dnorm2;      // ||D||^2
+  double eps_upd;     // Eq. 18 / 19
+  double eps_c;       // eps_upd ||D|| / sqrt(d)
+  int nonfinite;
+};
+
+cudaError_t launch_decision(const double* rho2, const double* y2, int b, double eps, int d,
+                            int skip_mode, int subselect, int eps_upd_mode, Decision* dec,
+                            int* sel, cudaStream_t st);
+
+// Rank rule of the delta-truncated SVD (Eq. 5 / Eq. 9) on Ritz values theta[0..K) (descending).
+// full: theta holds every eigenvalue of the Gram (tail summed directly from the smallest);
+// otherwise tail(r) = trace - sum_{j<r} theta_j.  Writes out[0] = r (or -1 if K too small),
+// out[1] = status.  max_new = m - r_i (directions available), cap_new = capacity left.
+cudaError_t launch_rank_rule(const double* theta, int K, int full, const double* trace,
+                             const double* eps_c, int max_new, int* out, cudaStream_t st);
+
+// Misc kernels.
+cudaError_t launch_fill(double* p, int64_t n, double v, cudaStream_t st);
+template <typename TI, typename TO>
+cudaError_t launch_cast(const TI* in, TO* out, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gather_obs(const T* Y, T* out, const int* sel, int nsel, int64_t N,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_sum_squares(const T* x, int b, int64_t N, double* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_check_finite(const T* x, int64_t n, int* flag, cudaStream_t st);
+// diag sum of an FP64 s x s matrix into *out
+cudaError_t launch_trace(const double* G, int64_t ldg, int s, double* out, cudaStream_t st);
+// columns of V (m x k, ld m): flip each so that its largest-|.| entry (lowest index on ties) is > 0
+cudaError_t launch_canonical_sign(double* V, int64_t m, int k, int64_t ld, cudaStream_t st);
+// Cholesky-QR step support: given S = V^T V (k x k, FP64, ld k), overwrite Rinv (k x k, ld k) with
+// the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  status=1 if not positive definite.
+cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st);
+// scale column j of V (m x k, ld) by 1/sqrt(theta[j])
+cudaError_t launch_scale_cols_rsqrt(double* V, int64_t m, int k, int64_t ld, const double* theta,
+                                    cudaStream_t st);
+// copy an m x k column-major block (ld_in) into U columns [c0, c0+k) (ld_out), with FP32 mirror
+cudaError_t launch_copy_cols(const double* in, int64_t ld_in, int64_t m, int k, double* out,
+                             int64_t ld_out, float* mirror, cudaStream_t st);
+// append b coefficient vectors (b x r, row-major) to the last core rows [n0, n0+b) (ld cap)
+cudaError_t launch_append_last(const double* coef, int b, int r, double* last, int64_t n0,
+                               int64_t ld, cudaStream_t st);
+template <typename TC>
+cudaError_t launch_append_last_t(const TC* coef, int b, int r, double* last, int64_t n0, int64_t ld,
+                                 cudaStream_t st);
+// out[j] = sum_i V[j*ld + i]^2 for the k columns of an m x k column-major matrix
+cudaError_t launch_col_norms(const double* V, int64_t m, int k, int64_t ld, double* out,
+                             cudaStream_t st);
+// rel[j] = sqrt(rho2[j]/y2[j]) (0 when y2 = 0)
+cudaError_t launch_rel_err(const double* rho2, const double* y2, int b, double* rel,
+                           cudaStream_t st);
+// gather top-K eigenvector columns of a float/double s x s column-major matrix into FP64 Q (s x K)
+template <typename T>
+cudaError_t launch_to_f64(const T* in, int64_t n, double* out, cudaStream_t st);
+
+}  // namespace ttice
+
+#define TT_CUDA(x)                               \
+  do {                                           \
+    cudaError_t e__ = (x);                       \
+    if (e__ != cudaSuccess) return e__;          \
+  } while (0)

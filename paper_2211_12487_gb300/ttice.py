@@ -1,0 +1,288 @@
+"""Python binding of libttice (include/ttice.h): argument marshalling only.
+
+Every entry point of the C ABI has a function of the same name here; each converts torch tensors to
+device pointers and the current torch CUDA stream to a cudaStream_t and calls the library.  All the
+arithmetic of the update runs in the library's CUDA kernels; there is no Python or CPU path.  If the
+shared library has not been built, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_void_p
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libttice.so")
+
+# constants mirrored from include/ttice.h
+TTICE_OK, TTICE_EINVAL, TTICE_ENOMEM, TTICE_ECAPACITY = 0, -1, -2, -3
+TTICE_ENONFINITE, TTICE_ETIMEOUT, TTICE_ECUDA, TTICE_EINTERNAL = -4, -5, -6, -7
+TTICE_SKIP_NONE, TTICE_SKIP_EXACT, TTICE_SKIP_MEAN = 0, 1, 2
+TTICE_EPSUPD_EXACT, TTICE_EPSUPD_APPROX = 0, 1
+TTICE_FP64, TTICE_FP32, TTICE_TF32, TTICE_BF16, TTICE_SPLIT_BF16 = 0, 1, 2, 3, 4
+TTICE_F32, TTICE_F64 = 0, 1
+
+PRECISIONS = {"fp64": TTICE_FP64, "fp32": TTICE_FP32, "tf32": TTICE_TF32, "bf16": TTICE_BF16,
+              "split_bf16": TTICE_SPLIT_BF16}
+SKIP_MODES = {"none": TTICE_SKIP_NONE, "exact": TTICE_SKIP_EXACT, "mean": TTICE_SKIP_MEAN}
+
+
+class ttice_heuristics(ctypes.Structure):
+    _fields_ = [("skip_mode", c_int), ("subselect", c_int), ("eps_upd_mode", c_int),
+                ("occupancy_tau", c_double), ("precision", c_int), ("input_dtype", c_int)]
+
+
+class ttice_capacity(ctypes.Structure):
+    _fields_ = [("max_batch", c_int64), ("max_rank", c_int64), ("obs_reserve", c_int64)]
+
+
+class ttice_update_stats(ctypes.Structure):
+    _fields_ = [("skipped", c_int32), ("n_selected", c_int32), ("rel_err_before", c_double),
+                ("eps_upd", c_double), ("eps_core", c_double), ("ranks", c_int64 * 18),
+                ("new_dirs", c_int32 * 16), ("n_obs", c_int64), ("core_elems", c_int64),
+                ("eig_sweep_limit", c_int32), ("reserved", c_int32)]
+
+
+TTICE_NPHASES = 8
+PHASE_NAMES = ["k1_stage1", "chain", "residual", "gram", "eig", "orth_append", "d_project", "final"]
+
+
+class ttice_profile(ctypes.Structure):
+    _fields_ = [("ms", c_double * TTICE_NPHASES), ("bytes", c_double * TTICE_NPHASES),
+                ("flops", c_double * TTICE_NPHASES), ("count", c_int64 * TTICE_NPHASES),
+                ("updates", c_int64)]
+
+
+class TTICEError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {ttice_strerror(code)} ({code})")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2211_12487_gb300.build.build() (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = POINTER
+    sig = {
+        "ttice_default_heuristics": (None, [P(ttice_heuristics)]),
+        "ttice_default_capacity": (None, [P(ttice_capacity)]),
+        "ttice_create": (c_int, [P(c_int64), c_int, c_double, P(ttice_heuristics), P(ttice_capacity),
+                                 P(c_void_p)]),
+        "ttice_update": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+        "ttice_project": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+        "ttice_ranks": (c_int, [c_void_p, P(c_int64)]),
+        "ttice_reconstruct": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int, c_void_p]),
+        "ttice_stats": (c_int, [c_void_p, P(ttice_update_stats)]),
+        "ttice_get_core": (c_int, [c_void_p, c_int, c_void_p, P(c_int64), P(c_int64)]),
+        "ttice_get_last_core": (c_int, [c_void_p, c_void_p, P(c_int64), P(c_int64)]),
+        "ttice_load": (c_int, [c_void_p, P(c_int64), P(c_void_p), c_void_p, c_int64]),
+        "ttice_profile_enable": (c_int, [c_void_p, c_int]),
+        "ttice_profile_read": (c_int, [c_void_p, P(ttice_profile)]),
+        "ttice_kernel_launches": (c_int64, []),
+        "ttice_destroy": (None, [c_void_p]),
+        "ttice_strerror": (ctypes.c_char_p, [c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def ttice_strerror(code: int) -> str:
+    return _lib.ttice_strerror(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != TTICE_OK:
+        raise TTICEError(code, what)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def ttice_default_heuristics() -> ttice_heuristics:
+    h = ttice_heuristics()
+    _lib.ttice_default_heuristics(ctypes.byref(h))
+    return h
+
+
+def ttice_default_capacity() -> ttice_capacity:
+    c = ttice_capacity()
+    _lib.ttice_default_capacity(ctypes.byref(c))
+    return c
+
+
+def ttice_create(dims, eps: float, heuristics: ttice_heuristics | None = None,
+                 capacity: ttice_capacity | None = None) -> int:
+    arr = (c_int64 * len(dims))(*[int(n) for n in dims])
+    out = c_void_p()
+    _check(_lib.ttice_create(arr, len(dims), float(eps),
+                             ctypes.byref(heuristics) if heuristics is not None else None,
+                             ctypes.byref(capacity) if capacity is not None else None,
+                             ctypes.byref(out)), "ttice_create")
+    return out.value
+
+
+def ttice_update(h: int, Y: torch.Tensor, batch: int | None = None, stream=None) -> None:
+    assert Y.is_cuda and Y.is_contiguous()
+    b = Y.shape[0] if batch is None else batch
+    _check(_lib.ttice_update(h, Y.data_ptr(), int(b), _stream_ptr(stream)), "ttice_update")
+
+
+def ttice_project(h: int, Y: torch.Tensor, coeffs: torch.Tensor | None, rel_err: torch.Tensor | None,
+                  stream=None) -> None:
+    assert Y.is_cuda and Y.is_contiguous()
+    _check(_lib.ttice_project(h, Y.data_ptr(), int(Y.shape[0]),
+                              coeffs.data_ptr() if coeffs is not None else None,
+                              rel_err.data_ptr() if rel_err is not None else None,
+                              _stream_ptr(stream)), "ttice_project")
+
+
+def ttice_ranks(h: int, d: int) -> list[int]:
+    arr = (c_int64 * (d + 2))()
+    _check(_lib.ttice_ranks(h, arr), "ttice_ranks")
+    return list(arr)
+
+
+def ttice_reconstruct(h: int, first: int, count: int, out: torch.Tensor, stream=None) -> None:
+    assert out.is_cuda and out.is_contiguous() and out.dtype in (torch.float32, torch.float64)
+    dt = TTICE_F32 if out.dtype == torch.float32 else TTICE_F64
+    _check(_lib.ttice_reconstruct(h, int(first), int(count), out.data_ptr(), dt, _stream_ptr(stream)),
+           "ttice_reconstruct")
+
+
+def ttice_stats(h: int) -> dict:
+    s = ttice_update_stats()
+    _check(_lib.ttice_stats(h, ctypes.byref(s)), "ttice_stats")
+    return s
+
+
+def ttice_get_core(h: int, i: int) -> np.ndarray:
+    rows, cols = c_int64(), c_int64()
+    _check(_lib.ttice_get_core(h, i, None, ctypes.byref(rows), ctypes.byref(cols)), "ttice_get_core")
+    out = np.zeros((rows.value, cols.value), dtype=np.float64)
+    if out.size:
+        _check(_lib.ttice_get_core(h, i, out.ctypes.data, ctypes.byref(rows), ctypes.byref(cols)),
+               "ttice_get_core")
+    return out
+
+
+def ttice_get_last_core(h: int) -> np.ndarray:
+    n, r = c_int64(), c_int64()
+    _check(_lib.ttice_get_last_core(h, None, ctypes.byref(n), ctypes.byref(r)), "ttice_get_last_core")
+    out = np.zeros((n.value, r.value), dtype=np.float64)
+    if out.size:
+        _check(_lib.ttice_get_last_core(h, out.ctypes.data, ctypes.byref(n), ctypes.byref(r)),
+               "ttice_get_last_core")
+    return out
+
+
+def ttice_load(h: int, ranks, cores, last: np.ndarray) -> None:
+    rk = (c_int64 * len(ranks))(*[int(r) for r in ranks])
+    keep = [np.ascontiguousarray(c, dtype=np.float64) for c in cores]
+    ptrs = (c_void_p * len(keep))(*[k.ctypes.data if k.size else None for k in keep])
+    lastc = np.ascontiguousarray(last, dtype=np.float64)
+    _check(_lib.ttice_load(h, rk, ptrs, lastc.ctypes.data if lastc.size else None, int(lastc.shape[0])),
+           "ttice_load")
+
+
+def ttice_profile_enable(h: int, on: bool = True) -> None:
+    _check(_lib.ttice_profile_enable(h, int(bool(on))), "ttice_profile_enable")
+
+
+def ttice_profile_read(h: int) -> dict:
+    p = ttice_profile()
+    _check(_lib.ttice_profile_read(h, ctypes.byref(p)), "ttice_profile_read")
+    return {name: {"ms": p.ms[i], "bytes": p.bytes[i], "flops": p.flops[i], "count": p.count[i]}
+            for i, name in enumerate(PHASE_NAMES)} | {"updates": p.updates}
+
+
+def ttice_kernel_launches() -> int:
+    return int(_lib.ttice_kernel_launches())
+
+
+def ttice_destroy(h: int) -> None:
+    _lib.ttice_destroy(h)
+
+
+class TTICE:
+    """One incremental TT decomposition living on the current CUDA device."""
+
+    def __init__(self, dims, eps: float, *, skip_mode: str = "exact", subselect: bool = True,
+                 eps_upd: str = "exact", tau: float = 1.0, precision: str = "fp64",
+                 input_dtype=torch.float32, max_batch: int = 32, max_rank: int = 512,
+                 obs_reserve: int = 1024):
+        self.dims = [int(n) for n in dims]
+        self.d = len(self.dims)
+        self.input_dtype = input_dtype
+        h = ttice_default_heuristics()
+        h.skip_mode = SKIP_MODES[skip_mode]
+        h.subselect = int(bool(subselect))
+        h.eps_upd_mode = TTICE_EPSUPD_EXACT if eps_upd == "exact" else TTICE_EPSUPD_APPROX
+        h.occupancy_tau = float(tau)
+        h.precision = PRECISIONS[precision]
+        h.input_dtype = TTICE_F32 if input_dtype == torch.float32 else TTICE_F64
+        c = ttice_default_capacity()
+        c.max_batch, c.max_rank, c.obs_reserve = int(max_batch), int(max_rank), int(obs_reserve)
+        self.h = ttice_create(self.dims, eps, h, c)
+
+    def update(self, Y: torch.Tensor, stream=None) -> ttice_update_stats:
+        assert Y.dtype == self.input_dtype and tuple(Y.shape[1:]) == tuple(self.dims)
+        ttice_update(self.h, Y, Y.shape[0], stream)
+        return ttice_stats(self.h)
+
+    def project(self, Y: torch.Tensor, stream=None):
+        assert Y.dtype == self.input_dtype and tuple(Y.shape[1:]) == tuple(self.dims)
+        rd = self.ranks()[self.d]
+        coeffs = torch.zeros((Y.shape[0], rd), dtype=torch.float64, device=Y.device)
+        rel = torch.zeros((Y.shape[0],), dtype=torch.float64, device=Y.device)
+        ttice_project(self.h, Y, coeffs, rel, stream)
+        return coeffs, rel
+
+    def ranks(self) -> list[int]:
+        return ttice_ranks(self.h, self.d)
+
+    def reconstruct(self, first: int, count: int, dtype=torch.float64, device="cuda") -> torch.Tensor:
+        out = torch.empty((count, *self.dims), dtype=dtype, device=device)
+        ttice_reconstruct(self.h, first, count, out)
+        return out
+
+    def stats(self):
+        return ttice_stats(self.h)
+
+    def core(self, i: int) -> np.ndarray:
+        return ttice_get_core(self.h, i)
+
+    def last_core(self) -> np.ndarray:
+        return ttice_get_last_core(self.h)
+
+    def load(self, ranks, cores, last) -> None:
+        ttice_load(self.h, ranks, cores, last)
+
+    def profile(self, on: bool = True) -> None:
+        ttice_profile_enable(self.h, on)
+
+    def profile_read(self) -> dict:
+        return ttice_profile_read(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            ttice_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

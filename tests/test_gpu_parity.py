@@ -1,0 +1,235 @@
+"""GPU path (libttice through its C ABI) against the FP64 CPU oracle on identical seeded inputs.
+
+Bars: identical ranks and skip / subselection decisions on every increment; reconstructions and
+projections within 1e-10 relative on the FP64 path; epsilon met on every increment on every path
+(Theorem 1 / Corollary 1); mixed-precision paths within a tolerance derived from FP32 rounding.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import ttice_oracle as O
+from tt_streams import blob_video, cp_cosine, random_tt
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2211_12487_gb300 import ttice
+
+    return ttice
+
+
+def _relmax(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _interface_projectors(cores):
+    A = np.ones((1, 1))
+    out = []
+    for U in cores:
+        if U.shape[1] == 0 or A.shape[1] == 0:
+            break
+        A = np.kron(A, np.eye(U.shape[0] // A.shape[1])) @ U
+        out.append(A @ A.T)
+    return out
+
+
+def run_pair(T, frames, batch, eps, *, precision="fp64", tol=1e-10, check_eps=True,
+             oracle_kw=None, gpu_kw=None):
+    """Stream `frames` through the GPU and the oracle; compare after every increment."""
+    dims = frames.shape[1:]
+    in_dtype = frames.dtype
+    g = T.TTICE(dims, eps, precision=precision, input_dtype=in_dtype, max_batch=batch,
+                **(gpu_kw or {}))
+    o = O.TTICEOracle(dims, eps, **(oracle_kw or {}))
+    dev = frames.to("cuda")
+    for k in range(0, frames.shape[0], batch):
+        Yk = frames[k:k + batch]
+        st = g.update(dev[k:k + batch])
+        so = o.update(Yk.double().numpy(), check_error=check_eps)
+        assert list(st.ranks[:len(dims) + 1]) == so.ranks[:len(dims) + 1], (k, list(st.ranks[:len(dims) + 2]), so.ranks)
+        assert bool(st.skipped) == so.skipped, k
+        assert st.n_selected == so.n_selected, k
+        assert st.rel_err_before == pytest.approx(so.rel_err_before, rel=max(tol, 1e-9), abs=1e-12)
+        if check_eps:
+            rec = g.reconstruct(k, Yk.shape[0]).cpu().numpy()
+            Y64 = Yk.double().numpy()
+            err = math.sqrt(((Y64 - rec) ** 2).sum() / max((Y64 ** 2).sum(), 1e-300))
+            assert err <= eps * (1 + 1e-9), (k, err)
+    n = frames.shape[0]
+    rec = g.reconstruct(0, n).cpu().numpy()
+    ref = o.reconstruct(0, n)
+    assert _relmax(rec, ref) < tol, _relmax(rec, ref)
+    Pg = _interface_projectors([g.core(i + 1) for i in range(len(dims))])
+    Po = _interface_projectors(o.U)
+    for a, b in zip(Pg, Po):
+        assert np.abs(a - b).max() < max(tol, 1e-12) * 100
+    for i in range(len(dims)):
+        Ug = g.core(i + 1)
+        assert np.abs(Ug.T @ Ug - np.eye(Ug.shape[1])).max() < 1e-12
+    g.close()
+    return o
+
+
+def test_cp_stream_fp64(T):
+    """16^4 cosine stream, FP64 input, eps=0.1, 200 single-tensor increments."""
+    Y = cp_cosine(0, 200)
+    run_pair(T, Y, 1, 0.1, check_eps=False)
+
+
+def test_cp_stream_fp64_eps_checked(T):
+    Y = cp_cosine(0, 30)
+    run_pair(T, Y, 1, 0.1)
+
+
+@pytest.mark.parametrize("batch", [1, 4])
+def test_video_small_fp64(T, batch):
+    Y = blob_video(0, 24, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=7)
+    run_pair(T, Y, batch, 0.1)
+
+
+def test_video_small_ragged_batches(T):
+    """Batches of different sizes in one stream, including a ragged tail."""
+    Y = blob_video(0, 23, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=8)
+    g = T.TTICE(Y.shape[1:], 0.05, input_dtype=torch.float32, max_batch=8)
+    o = O.TTICEOracle(Y.shape[1:], 0.05)
+    dev = Y.cuda()
+    k = 0
+    for b in (1, 8, 3, 5, 2, 4):
+        st = g.update(dev[k:k + b])
+        so = o.update(Y[k:k + b].double().numpy())
+        assert list(st.ranks[:6]) == so.ranks[:6]
+        k += b
+    assert _relmax(g.reconstruct(0, k).cpu().numpy(), o.reconstruct(0, k)) < 1e-10
+
+
+def test_video_c1_prefix_fp64(T):
+    """Full-size video frames 480x640x3 as 20x24x20x32x3, batches of 8 (first three increments)."""
+    Y = blob_video(0, 24)
+    run_pair(T, Y, 8, 0.1)
+
+
+def test_tt_ice_plain_and_paper_variants(T):
+    Y = blob_video(0, 16, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=9)
+    run_pair(T, Y, 4, 0.1, oracle_kw=dict(skip_mode=O.SKIP_NONE, subselect=False, tau=math.inf),
+             gpu_kw=dict(skip_mode="none", subselect=False, tau=math.inf))
+    run_pair(T, Y, 4, 0.1, check_eps=False, oracle_kw=dict(skip_mode=O.SKIP_MEAN, eps_upd_mode=O.EPS_UPD_APPROX, tau=0.8),
+             gpu_kw=dict(skip_mode="mean", eps_upd="approx", tau=0.8))
+
+
+def test_appendix_b_rank_recovery_gpu(T):
+    """Exactly low-rank 10x15x20 stream with TT-ranks [1,2,3,5,1] at eps = 1e-8 (Appendix B)."""
+    Y = random_tt(0, 120, ranks=(1, 2, 3, 5, 1), seed=11)
+    g = T.TTICE((10, 15, 20), 1e-8, input_dtype=torch.float64, max_batch=1)
+    dev = Y.cuda()
+    for k in range(120):
+        g.update(dev[k:k + 1])
+    assert g.ranks() == [1, 2, 3, 5, 1]
+    rec = g.reconstruct(0, 120).cpu().numpy()
+    Yn = Y.numpy()
+    assert math.sqrt(((rec - Yn) ** 2).sum() / (Yn ** 2).sum()) < 1e-8
+
+
+def test_project_matches_oracle(T):
+    Y = blob_video(0, 12, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=7)
+    Z = blob_video(100, 6, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=7)
+    g = T.TTICE(Y.shape[1:], 0.1, input_dtype=torch.float32, max_batch=6)
+    o = O.TTICEOracle(Y.shape[1:], 0.1)
+    for k in range(0, 12, 6):
+        g.update(Y[k:k + 6].cuda())
+        o.update(Y[k:k + 6].double().numpy())
+    coeffs, rel = g.project(Z.cuda())
+    c_o, rho2, y2 = o.errors(Z.double().numpy())
+    assert _relmax(coeffs.cpu().numpy(), c_o) < 1e-10
+    np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho2 / y2), rtol=1e-9)
+
+
+def test_subselect_golden_gpu(T):
+    g_ = json.load(open(os.path.join(GOLDEN, "subselect_example.json")))
+    e = g_["expect"]
+    g = T.TTICE(g_["dims"], g_["eps"], input_dtype=torch.float64, max_batch=2)
+    g.update(torch.tensor(g_["increment_1"], dtype=torch.float64).cuda())
+    st = g.update(torch.tensor(g_["increment_2"], dtype=torch.float64).cuda())
+    assert st.n_selected == 1
+    assert st.eps_upd == pytest.approx(e["eps_upd_exact"], abs=1e-15)
+    assert st.eps_core == pytest.approx(e["eps_core_exact"], abs=1e-15)
+    assert g.ranks() == e["ranks"]
+    np.testing.assert_allclose(g.core(1), np.array(e["U1"]), atol=1e-14)
+    np.testing.assert_allclose(g.core(2), np.array(e["U2"]), atol=1e-14)
+    np.testing.assert_allclose(g.last_core().T, np.array(e["last_core"]), atol=1e-14)
+
+
+def test_zero_observation_and_skip(T):
+    Y = cp_cosine(0, 3)
+    Y[1] = 0.0
+    g = T.TTICE((16, 16, 16, 16), 0.1, input_dtype=torch.float64, max_batch=2)
+    st = g.update(Y[:2].cuda())
+    assert st.n_selected == 1
+    assert np.abs(g.last_core()[1]).max() == 0.0
+    r = g.ranks()
+    st = g.update(Y[:1].cuda())  # same tensor again: represented exactly, skipped
+    assert st.skipped and g.ranks() == r
+
+
+def test_invalid_and_nonfinite_leave_state(T):
+    Y = cp_cosine(0, 4)
+    g = T.TTICE((16, 16, 16, 16), 0.1, input_dtype=torch.float64, max_batch=2)
+    g.update(Y[:1].cuda())
+    r = g.ranks()
+    last = g.last_core().copy()
+    with pytest.raises(T.TTICEError) as ei:
+        T.ttice_update(g.h, Y[:3].cuda(), 3)
+    assert ei.value.code == T.TTICE_EINVAL
+    bad = Y[1:2].clone()
+    bad[0, 0, 0, 0, 0] = float("nan")
+    with pytest.raises(T.TTICEError) as ei:
+        g.update(bad.cuda())
+    assert ei.value.code == T.TTICE_ENONFINITE
+    assert g.ranks() == r
+    np.testing.assert_array_equal(g.last_core(), last)
+
+
+def test_capacity_exceeded_rolls_back(T):
+    Y = blob_video(0, 8, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=7)
+    g = T.TTICE(Y.shape[1:], 0.01, input_dtype=torch.float32, max_batch=4, max_rank=3)
+    with pytest.raises(T.TTICEError) as ei:
+        g.update(Y[:4].cuda())
+    assert ei.value.code == T.TTICE_ECAPACITY
+    assert g.ranks() == [1, 0, 0, 0, 0, 0, 1]
+    for i in range(1, 6):
+        assert g.core(i).size == 0
+
+
+def test_lockstep_load(T):
+    """Load the oracle's state mid-stream, apply one increment on both sides, compare."""
+    Y = blob_video(0, 16, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=12)
+    o = O.TTICEOracle(Y.shape[1:], 0.1)
+    for k in range(0, 12, 4):
+        o.update(Y[k:k + 4].double().numpy())
+    g = T.TTICE(Y.shape[1:], 0.1, input_dtype=torch.float32, max_batch=4)
+    last = np.zeros((len(o.last), o.ranks[-1]))
+    for j, c in enumerate(o.last):
+        last[j, :c.shape[0]] = c
+    g.load(o.ranks, o.U, last)
+    assert _relmax(g.reconstruct(0, 12).cpu().numpy(), o.reconstruct(0, 12)) < 1e-12
+    st = g.update(Y[12:16].cuda())
+    so = o.update(Y[12:16].double().numpy())
+    assert list(st.ranks[:6]) == so.ranks[:6]
+    assert _relmax(g.reconstruct(0, 16).cpu().numpy(), o.reconstruct(0, 16)) < 1e-10
+
+
+def test_fp32_projection_mode(T):
+    """FP32 projections (FP64 Gram / eigen-solve / CGS2 / norms): epsilon met on every increment,
+    ranks equal to the oracle's, reconstructions within FP32-level error."""
+    Y = blob_video(0, 24, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=7)
+    run_pair(T, Y, 4, 0.1, precision="fp32", tol=1e-4)

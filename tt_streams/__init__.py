@@ -182,8 +182,8 @@ def random_tt(t0: int, count: int, *, dims=(10, 15, 20), ranks=(1, 2, 3, 5, 1), 
     for i in range(1, d):
         x = (x @ cores[i].reshape(ranks[i], -1)).reshape(-1, ranks[i + 1])
     last = cores[d].reshape(ranks[d], length)[:, t0:t0 + count]  # (r_d, count)
-    out = (x @ last).T.reshape((count,) + tuple(dims))
-    return out.to(device=device, dtype=dtype)
+    out = (x @ last).T.contiguous().reshape((count,) + tuple(dims))
+    return out.to(device=device, dtype=dtype).contiguous()
 
 
 STREAMS = {
