@@ -22,7 +22,7 @@ namespace {
 
 template <typename T> struct BJ;
 template <> struct BJ<float> {
-  static constexpr int BS = 32;
+  static constexpr int BS = 16;
   static __device__ float eps() { return FLT_EPSILON; }
 };
 template <> struct BJ<double> {
@@ -58,35 +58,37 @@ __global__ void bj_init(const double* G, int64_t ldg, int s, int sp, T* A, T* V,
   if (blockIdx.x == 0 && threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
 }
 
+// One CTA per block pair, one warp per rotation: the 2BS x 2BS subproblem lives in shared memory;
+// in each of the 2BS-1 rounds of a cyclic sweep, lane 0 of warp k computes the rotation of pair k
+// (broadcast by a shuffle), the warp combines the two rows of its pair, the CTA synchronises, the
+// warp combines the two columns (of S and of the accumulated Q), and the CTA synchronises again.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) bj_solve(const T* A, int sp, int nb, int round, T* Qb,
-                                                     const double* fro, int* flags) {
+__global__ void __launch_bounds__(32 * BJ<T>::BS) bj_solve(const T* A, int sp, int nb, int round,
+                                                           T* Qb, const double* fro, int* flags) {
   constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
+  static_assert(N2 == 32, "one lane per row/column element");
   if (flags[1]) return;
   __shared__ T S[N2][N2 + 1];
   __shared__ T Q[N2][N2 + 1];
-  __shared__ T rc[BS], rs[BS];
-  __shared__ int rp[BS], rq[BS];
-  __shared__ int any;
   int bi, bj;
   circle_pair(nb, round, blockIdx.x, &bi, &bj);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, k = tid >> 5, lane = tid & 31;
   auto gidx = [&](int a) { return a < BS ? bi * BS + a : bj * BS + (a - BS); };
-  for (int e = tid; e < N2 * N2; e += kThreads) {
+  for (int e = tid; e < N2 * N2; e += 32 * BS) {
     const int a = e / N2, b = e % N2;
     S[a][b] = A[(int64_t)gidx(a) * sp + gidx(b)];
     Q[a][b] = (a == b) ? T(1) : T(0);
   }
-  if (tid == 0) any = 0;
   __syncthreads();
   const T teps = BJ<T>::eps();
   const T floor_abs = (T)((double)teps * sqrt(*fro));
+  int any = 0;
   for (int round2 = 0; round2 < N2 - 1; ++round2) {
-    if (tid < BS) {
-      int p, q;
-      circle_pair(N2, round2, tid, &p, &q);
+    int p, q;
+    circle_pair(N2, round2, k, &p, &q);
+    T c = T(1), sn = T(0);
+    if (lane == 0) {
       const T apq = S[p][q], app = S[p][p], aqq = S[q][q];
-      T c = T(1), sn = T(0);
       if (fabs(apq) > floor_abs && fabs(apq) > teps * sqrt(fabs(app * aqq))) {
         const T tau = (aqq - app) / (T(2) * apq);
         const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
@@ -94,36 +96,28 @@ __global__ void __launch_bounds__(kThreads) bj_solve(const T* A, int sp, int nb,
         sn = t * c;
         any = 1;
       }
-      rc[tid] = c; rs[tid] = sn; rp[tid] = p; rq[tid] = q;
+    }
+    c = __shfl_sync(0xffffffffu, c, 0);
+    sn = __shfl_sync(0xffffffffu, sn, 0);
+    if (sn != T(0)) {  // rows p, q of S
+      const T xp = S[p][lane], xq = S[q][lane];
+      S[p][lane] = c * xp - sn * xq;
+      S[q][lane] = sn * xp + c * xq;
     }
     __syncthreads();
-    for (int e = tid; e < BS * N2; e += kThreads) {  // rows of S
-      const int k = e / N2, j = e % N2;
-      if (rs[k] == T(0)) continue;
-      const int p = rp[k], q = rq[k];
-      const T c = rc[k], sn = rs[k];
-      const T xp = S[p][j], xq = S[q][j];
-      S[p][j] = c * xp - sn * xq;
-      S[q][j] = sn * xp + c * xq;
-    }
-    __syncthreads();
-    for (int e = tid; e < BS * N2; e += kThreads) {  // columns of S and of Q
-      const int k = e / N2, i = e % N2;
-      if (rs[k] == T(0)) continue;
-      const int p = rp[k], q = rq[k];
-      const T c = rc[k], sn = rs[k];
-      const T xp = S[i][p], xq = S[i][q];
-      S[i][p] = c * xp - sn * xq;
-      S[i][q] = sn * xp + c * xq;
-      const T vp = Q[i][p], vq = Q[i][q];
-      Q[i][p] = c * vp - sn * vq;
-      Q[i][q] = sn * vp + c * vq;
+    if (sn != T(0)) {  // columns p, q of S and of Q
+      const T xp = S[lane][p], xq = S[lane][q];
+      S[lane][p] = c * xp - sn * xq;
+      S[lane][q] = sn * xp + c * xq;
+      const T vp = Q[lane][p], vq = Q[lane][q];
+      Q[lane][p] = c * vp - sn * vq;
+      Q[lane][q] = sn * vp + c * vq;
     }
     __syncthreads();
   }
   T* Qo = Qb + (int64_t)blockIdx.x * N2 * N2;
-  for (int e = tid; e < N2 * N2; e += kThreads) Qo[e] = Q[e / N2][e % N2];
-  if (tid == 0 && any) atomicOr(flags, 1);
+  for (int e = tid; e < N2 * N2; e += 32 * BS) Qo[e] = Q[e / N2][e % N2];
+  if (__syncthreads_or(any) && tid == 0) atomicOr(flags, 1);
 }
 
 // A[I u J, tile] <- Q^T A[I u J, tile]
@@ -261,7 +255,7 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int round = 0; round < nb - 1; ++round) {
       note_launch();
-      bj_solve<T><<<npairs, kThreads, 0, st>>>(A, sp, nb, round, Qb, fro, flags);
+      bj_solve<T><<<npairs, 32 * BS, 0, st>>>(A, sp, nb, round, Qb, fro, flags);
       note_launch();
       bj_rows<T><<<dim3(npairs, tiles), kThreads, 0, st>>>(A, sp, nb, round, Qb, flags);
       note_launch();

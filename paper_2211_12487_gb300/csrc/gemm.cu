@@ -38,11 +38,22 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
   const bool a_kfast = (g.A.cs == 1);
   const bool b_nfast = (g.B.cs == 1);
 
+  // FP32 products accumulated into FP64 every kMixSlabs K-slabs when the output is FP64
+  constexpr bool kMix = sizeof(ACC) == 4 && sizeof(TC) == 8;
+  constexpr int kMixSlabs = 4;
   ACC acc[TM][TN];
+  double acc64[kMix ? TM : 1][kMix ? TN : 1];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = ACC(0);
+  if constexpr (kMix) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc64[i][j] = 0.0;
+  }
+  int slab = 0;
 
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     for (int e = tid; e < BM * BK; e += 256) {
@@ -75,6 +86,21 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
+    if constexpr (kMix) {
+      if (++slab == kMixSlabs) {
+        slab = 0;
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) { acc64[i][j] += (double)acc[i][j]; acc[i][j] = ACC(0); }
+      }
+    }
+  }
+  if constexpr (kMix) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc64[i][j] += (double)acc[i][j];
   }
 
   double ss = 0.0;
@@ -91,7 +117,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
     for (int j = 0; j < TN; ++j) {
       const int64_t gn = n0 + tx + j * (BN / TN);
       if (gm < g.M && gn < g.N) {
-        double v = g.alpha * (double)acc[i][j];
+        double v;
+        if constexpr (kMix) v = g.alpha * acc64[i][j];
+        else v = g.alpha * (double)acc[i][j];
         if (g.X.p) v += g.beta * (double)ld_elem<TX>(g.X.p, xoff + gm * g.X.rs + gn * g.X.cs);
         const TC cv = (TC)v;
         if (g.norm) {
@@ -169,8 +197,10 @@ TT_GEMM_INST(float, float, float, float, float)
 TT_GEMM_INST(float, double, double, float, float)
 TT_GEMM_INST(float, float, double, float, float)
 TT_GEMM_INST(float, double, float, float, float)
-// Gram of FP32 residuals in FP64
+// Gram of FP32 residuals: FP64 accumulation of exact FP64 products, or FP32 products with FP64
+// accumulation across K-slabs
 TT_GEMM_INST(float, float, float, double, double)
+TT_GEMM_INST(float, float, float, double, float)
 TT_GEMM_INST(float, double, double, double, double)
 // reconstruction into FP32 outputs
 TT_GEMM_INST(double, double, double, float, double)

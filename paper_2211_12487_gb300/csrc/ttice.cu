@@ -65,6 +65,8 @@ struct ttice_s {
   double* H = nullptr;
   double* Z = nullptr;   // kRR x kRR eigenvectors
   double* theta = nullptr;
+  double* Ebuf = nullptr;  // R V for a column-side Gram (m x s)
+  int64_t max_ms = 0;
   double* Vn = nullptr;  // new directions, max_m x kRR
   double* Vn2 = nullptr;
   double* P = nullptr;   // cap x kRR projections for CGS2
@@ -166,7 +168,7 @@ void free_all(ttice_s* h) {
   void* ptrs[] = {h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->P, h->rho2, h->y2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->rho2, h->y2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32);
 }
@@ -218,12 +220,13 @@ template <typename WT, typename TY>
 int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_t st) {
   const WT* Xw = nullptr;
   const double sw = sizeof(WT), sy = sizeof(TY);
+  const bool fused_k1 = errors && h->r[1] > 0 && k1_supported<TY, WT>((int)h->n[0], (int)h->r[1]);
   if (errors) {
     TT_CU(cudaMemsetAsync(h->rho2, 0, b * sizeof(double), st));
     TT_CU(cudaMemsetAsync(h->y2, 0, b * sizeof(double), st));
     const double N = (double)h->N, r1 = (double)h->r[1];
     ph_begin(h, PH_K1, st, b * (sy * N + sw * r1 * h->L[0]), b * (4.0 * N * r1 + 4.0 * N));
-    TT_TRY(sumsq<TY>(X0, b, h->N, h->y2, st));
+    if (!fused_k1) TT_TRY(sumsq<TY>(X0, b, h->N, h->y2, st));
   } else {
     double by = sy * b * h->N, fl = 0.0;
     for (int i = 0; i < h->d; ++i) {
@@ -262,7 +265,9 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
     }
     const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
                                      : reinterpret_cast<const WT*>(h->Uf[i]);
-    if (i == 0) {
+    if (i == 0 && fused_k1) {
+      TT_CU((launch_k1<TY, WT>(X0, b, L, (int)m, (int)rn, Ui, h->ldu[i], W, h->y2, h->rho2, st)));
+    } else if (i == 0) {
       TT_TRY(proj<WT, TY, WT>(Ui, h->ldu[i], X0, m, L, rn, b, W, st));
       if (errors) TT_TRY((resid<WT, WT, TY, WT>(Ui, h->ldu[i], W, X0, m, L, rn, b, nullptr, h->rho2, st)));
     } else {
@@ -290,7 +295,6 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   const bool left = m <= c;  // Gram on the row side (R R^T) or the column side (R^T R)
   const int64_t s = left ? m : c;
   if (s > kMaxEig) return TTICE_ECAPACITY;
-  using ACC = double;
   // Gram (FP64 accumulation)
   ph_begin(h, PH_GRAM, st, (double)sizeof(WT) * m * c + 8.0 * s * s, 2.0 * (double)s * s * (left ? c : m));
   TT_CU(cudaMemsetAsync(h->G, 0, (size_t)s * s * sizeof(double), st));
@@ -311,7 +315,8 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
       g.c_rs = s; g.c_cs = 1; g.c_bs1 = L * s; g.c_bs2 = L;
       g.nbatch = nsel * nsel; g.bdiv = nsel;
     }
-    TT_CU((gemm<WT, WT, WT, double, ACC>(g, st)));
+    if constexpr (sizeof(WT) == 8) TT_CU((gemm<WT, WT, WT, double, double>(g, st)));
+    else TT_CU((gemm<WT, WT, WT, double, float>(g, st)));  // FP32 products, FP64 accumulation
   }
   TT_CU(launch_trace(h->G, s, (int)s, h->trace, st));
   ph_end(h, st);
@@ -344,15 +349,15 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
       g.nbatch = nsel;
       TT_CU((gemm<double, WT, double, double, double>(g, st)));
     } else {
-      TT_CU(cudaMemsetAsync(h->Vn, 0, (size_t)m * s * sizeof(double), st));
+      TT_CU(cudaMemsetAsync(h->Ebuf, 0, (size_t)m * s * sizeof(double), st));
       GemmArgs g;  // E = R V (m x s), column norms
       g.M = m; g.N = s; g.K = L; g.atomic = 1; g.allow_splitk = 1;
       g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
       g.B.p = h->V64; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
-      g.C = h->Vn; g.c_rs = 1; g.c_cs = m;
+      g.C = h->Ebuf; g.c_rs = 1; g.c_cs = m;
       g.nbatch = nsel;
       TT_CU((gemm<WT, double, double, double, double>(g, st)));
-      TT_CU(launch_col_norms(h->Vn, m, (int)s, m, e, st));
+      TT_CU(launch_col_norms(h->Ebuf, m, (int)s, m, e, st));
     }
     TT_CU(launch_rank_rule(e, (int)s, 1, h->trace, d_eps, max_new, h->ibuf, st));
     Vdir = h->V64; thet = h->w64; K = (int)s;
@@ -739,6 +744,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
     if (rc == TTICE_OK) rc = dalloc_bytes(&h->dstage[i], st_elems * h->wt_bytes);
     max_mL = std::max(max_mL, h->ldu[i] * h->L[i]);
     h->s_max = std::max(h->s_max, std::min<int64_t>(h->ldu[i], h->L[i] * B));
+    h->max_ms = std::max(h->max_ms, h->ldu[i] * std::min<int64_t>({h->ldu[i], h->L[i] * B, (int64_t)kMaxEig}));
   }
   h->s_max = std::min<int64_t>(h->s_max, kMaxEig);
   const int64_t s = std::max<int64_t>(h->s_max, 1);
@@ -762,7 +768,8 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Rinv, kRR * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->H, kRR * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Z, kRR * kRR);
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->theta, kRR + 8);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->theta, std::max<int64_t>(s, kRR) + 8);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->Ebuf, std::max<int64_t>(h->max_ms, 1));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Vn, h->max_m * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Vn2, h->max_m * kRR);
   int64_t maxcap = 1;

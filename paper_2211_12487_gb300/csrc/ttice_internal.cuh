@@ -84,6 +84,14 @@ cudaError_t launch_decision(const double* rho2, const double* y2, int b, double 
 cudaError_t launch_rank_rule(const double* theta, int K, int full, const double* trace,
                              const double* eps_c, int max_new, int* out, cudaStream_t st);
 
+// K1 (k1.cu): fused first pass of stage 1 -- W = U_1^T Y_1, ||y||^2 and ||Y_1 - U_1 W||^2 per
+// observation in one read of the increment.  Supported for n_1 <= 32 and 1 <= r_1 <= 32.
+template <typename TY, typename T>
+bool k1_supported(int n1, int r);
+template <typename TY, typename T>
+cudaError_t launch_k1(const TY* Y, int b, int64_t L, int n1, int r, const T* U, int64_t ldu, T* W,
+                      double* y2, double* rho2, cudaStream_t st);
+
 // Misc kernels.
 cudaError_t launch_fill(double* p, int64_t n, double v, cudaStream_t st);
 template <typename TI, typename TO>

@@ -33,11 +33,13 @@ def _relmax(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def _interface_projectors(cores):
+def _interface_projectors(cores, max_rows=2048):
+    """Projectors onto the spans of the left interface matrices (first i cores contracted);
+    gauge-free, so they can be compared across implementations.  Stops once they get large."""
     A = np.ones((1, 1))
     out = []
     for U in cores:
-        if U.shape[1] == 0 or A.shape[1] == 0:
+        if U.shape[1] == 0 or A.shape[1] == 0 or A.shape[0] * (U.shape[0] // A.shape[1]) > max_rows:
             break
         A = np.kron(A, np.eye(U.shape[0] // A.shape[1])) @ U
         out.append(A @ A.T)
