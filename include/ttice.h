@@ -90,7 +90,7 @@ typedef struct {
   int64_t n_obs;          /* observations stored in the last core */
   int64_t core_elems;     /* sum_i r_{i-1} n_i r_i over U_1..U_d plus r_d * n_obs (Eq. 22 denominator) */
   int32_t eig_sweep_limit; /* eigen-solves of this update that stopped at their sweep limit */
-  int32_t reserved;
+  int32_t eig_sweeps;      /* block-Jacobi sweeps spent by the eigen-solves of this update */
 } ttice_update_stats;
 
 /* Fill defaults. */

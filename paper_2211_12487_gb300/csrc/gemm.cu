@@ -135,10 +135,17 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
     }
   }
   if (g.norm && g.norm_rows) {
+    // reduce each tile row over the BN/TN threads that share it, then one atomic per row per CTA
+    __shared__ double rsum[BM];
+    for (int i = tid; i < BM; i += 256) rsum[i] = 0.0;
+    __syncthreads();
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int64_t gm = m0 + ty + i * (BM / TM);
-      if (gm < g.M && rowss[i] != 0.0) atomicAdd(g.norm + gm, rowss[i]);
+    for (int i = 0; i < TM; ++i)
+      if (rowss[i] != 0.0) atomicAdd(&rsum[ty + i * (BM / TM)], rowss[i]);
+    __syncthreads();
+    for (int i = tid; i < BM; i += 256) {
+      const int64_t gm = m0 + i;
+      if (gm < g.M && rsum[i] != 0.0) atomicAdd(g.norm + gm, rsum[i]);
     }
   } else if (g.norm) {
 #pragma unroll

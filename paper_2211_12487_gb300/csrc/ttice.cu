@@ -322,11 +322,12 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   ph_end(h, st);
   ph_begin(h, PH_EIG, st, 0.0, 0.0);
   const double* d_eps = &h->dec->eps_c;  // the per-core threshold decided on the device
+  TT_CU(cudaMemsetAsync(h->ibuf, 0, 4 * sizeof(int), st));
 
   const double* Vdir = nullptr;  // s x K Ritz / eigen vectors (column-major, ld s)
   const double* thet = nullptr;
   int K = 0;
-  if (sizeof(WT) == 8 || s <= kDirectEig) {
+  if (sizeof(WT) == 8) {
     // FP64 eigen-solve: one CTA for small Gram matrices, the multi-CTA block Jacobi otherwise.
     if (s <= kDirectEig) {
       TT_CU(jacobi_eig<double>(h->G, s, (int)s, h->w64, h->V64, h->work64, h->ibuf + 1, st));
@@ -334,6 +335,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
       TT_CU(block_jacobi_eig<double>(h->G, s, (int)s, h->w64, h->V64, h->bjw64, h->fro, h->bjflags,
                                      kMaxSweeps64, st));
       TT_CU(cudaMemcpyAsync(h->ibuf + 1, h->bjflags + 3, sizeof(int), cudaMemcpyDeviceToDevice, st));
+      TT_CU(cudaMemcpyAsync(h->ibuf + 3, h->bjflags + 2, sizeof(int), cudaMemcpyDeviceToDevice, st));
     }
     // Energy of R along each eigenvector, measured on R itself (||q_j^T R||^2 or ||R v_j||^2) so
     // that the truncation tail does not inherit the squared rounding of the Gram matrix.  The
@@ -362,12 +364,21 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     TT_CU(launch_rank_rule(e, (int)s, 1, h->trace, d_eps, max_new, h->ibuf, st));
     Vdir = h->V64; thet = h->w64; K = (int)s;
   } else {
-    // FP32 block Jacobi for approximate eigenvectors, then FP64 Rayleigh-Ritz on the leading K.
-    TT_CU(block_jacobi_eig<float>(h->G, s, (int)s, h->w32, h->V32, h->bjw32, h->fro, h->bjflags,
-                                  kMaxSweeps32, st));
+    // FP32 Jacobi (one CTA for small matrices, block Jacobi otherwise) for approximate
+    // eigenvectors, then FP64 Rayleigh-Ritz on the leading K of them.
+    if (s <= kDirectEig) {
+      TT_CU(cudaMemsetAsync(h->bjflags, 0, 4 * sizeof(int), st));
+      TT_CU(jacobi_eig<float>(h->G, s, (int)s, h->w32, h->V32, h->bjw32, h->bjflags + 3, st));
+    } else {
+      TT_CU(block_jacobi_eig<float>(h->G, s, (int)s, h->w32, h->V32, h->bjw32, h->fro, h->bjflags,
+                                    kMaxSweeps32, st));
+    }
     TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, s * sizeof(float), cudaMemcpyDeviceToHost, st));
+    TT_CU(cudaMemcpyAsync(h->h_int + 8, h->bjflags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     ph_end(h, st);
     TT_TRY(sync_read(h, st));
+    h->stats.eig_sweeps += h->h_int[10];
+    if (h->h_int[11]) h->stats.eig_sweep_limit += 1;
     ph_begin(h, PH_EIG, st, 0.0, 0.0);
     // size of the Rayleigh-Ritz subspace from the FP32 spectrum (only sizes a buffer; the rank
     // itself is decided below from FP64 Ritz values)
@@ -431,6 +442,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   TT_TRY(sync_read(h, st));
   int rR = h->h_int[0];
   if (h->h_int[1] != 0) h->stats.eig_sweep_limit += 1;  // unconverged sweeps: energies are still measured
+  if (sizeof(WT) == 8 && s > kDirectEig) h->stats.eig_sweeps += h->h_int[3];
   if (rR < 0) return TTICE_ECAPACITY;  // Rayleigh-Ritz subspace too small for the tolerance
   *rR_out = rR;
   if (rR == 0) return TTICE_OK;
