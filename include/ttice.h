@@ -170,6 +170,25 @@ int ttice_profile_read(ttice_t h, ttice_profile* out);
 /* Kernel launches issued by this library in this process so far. */
 int64_t ttice_kernel_launches(void);
 
+/* Allocation-free variant of ttice_reconstruct (the paper has no counterpart: this is a service of
+ * the library).  For callers that cannot allocate device memory when they reconstruct -- code being
+ * captured into a CUDA graph that must hold no allocation nodes, real-time loops that cannot wait on
+ * the allocator, or processes whose device memory is reserved in advance -- it computes the same
+ * reconstruction as ttice_reconstruct (same arguments, same output) without calling cudaMalloc,
+ * cudaFree or any allocating routine.  Its intermediates live in one fixed array of device memory
+ * inside the library: two buffers of TTICE_NOALLOC_MAX_ELEMS doubles (64 MiB in all), which every
+ * GPU that loads the library holds until the process exits.
+ *  - Limit: count * (n_1 ... n_d) must not exceed TTICE_NOALLOC_MAX_ELEMS (and count <= 65535);
+ *    larger requests return TTICE_EINVAL without doing any work.
+ *  - The first call on a device looks up the array's device address with that device current (the
+ *    caller's current device); make that first call before any stream capture.
+ *  - All calls share the array.  Calls whose work overlaps on the GPU (different streams, or
+ *    different handles, at the same time) race on it: serialise them.
+ *  - Asynchronous on `stream`, like ttice_reconstruct. */
+#define TTICE_NOALLOC_MAX_ELEMS (4LL * 1024 * 1024)
+int ttice_reconstruct_noalloc(ttice_t h, int64_t first, int64_t count, void* out, int out_dtype,
+                              void* stream);
+
 void ttice_destroy(ttice_t h);
 const char* ttice_strerror(int code);
 

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -981,3 +982,88 @@ int ttice_load(ttice_t h, const int64_t* ranks, const double* const* cores, cons
 }
 
 }  // extern "C"
+
+// ================================================================== allocation-free reconstruction
+// ttice_reconstruct obtains its two intermediate buffers from cudaMallocAsync on every call.  Some
+// callers cannot allocate device memory at the point where they need a reconstruction: code running
+// under a CUDA-graph capture that must not contain allocation nodes, real-time loops that forbid the
+// allocator's latency and possible synchronisation, or processes whose device memory is carved up
+// in advance by another runtime.  ttice_reconstruct_noalloc computes exactly the same chain of
+// contractions but keeps the intermediates in a fixed array of device memory that belongs to this
+// library: kNoAllocElems doubles per buffer, two buffers (64 MiB in total), held by every GPU that
+// loads the library until the process exits.
+namespace {
+
+constexpr int64_t kNoAllocElems = TTICE_NOALLOC_MAX_ELEMS;
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocElems];
+
+// Host code may not use g_noalloc_scratch directly (on the host it is only a stand-in symbol, not a
+// device address).  Its device address is looked up once per device, with that device current, and
+// cached; the first call on a device therefore does this lookup.
+double* noalloc_scratch_for_current_device(int* err) {
+  static std::mutex mu;
+  static double* addr[64] = {};
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { *err = TTICE_ECUDA; return nullptr; }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      *err = TTICE_ECUDA;
+      return nullptr;
+    }
+    addr[dev] = static_cast<double*>(p);
+    done[dev] = true;
+  }
+  *err = TTICE_OK;
+  return addr[dev];
+}
+
+}  // namespace
+
+extern "C" int ttice_reconstruct_noalloc(ttice_t h, int64_t first, int64_t count, void* out,
+                                         int out_dtype, void* stream) {
+  if (!h || !out || first < 0 || count < 1 || first + count > h->n_obs) return TTICE_EINVAL;
+  if (out_dtype != TTICE_F32 && out_dtype != TTICE_F64) return TTICE_EINVAL;
+  if (count > 65535 || count * h->N > kNoAllocElems) return TTICE_EINVAL;  // beyond the fixed scratch
+  int err = TTICE_OK;
+  double* scratch = noalloc_scratch_for_current_device(&err);
+  if (err != TTICE_OK) return err;
+  cudaStream_t st = S(stream);
+  const int d = h->d;
+  if (h->r[d] == 0) {
+    return cu(cudaMemsetAsync(out, 0, (size_t)count * h->N * (out_dtype == TTICE_F32 ? 4 : 8), st));
+  }
+  // Every element of an intermediate is written before it is read (plain stores, no accumulation),
+  // so the contents left by an earlier call never need clearing.
+  double* bufs[2] = {scratch, scratch + kNoAllocElems};
+  const double* X = h->last + first * h->cap[d];
+  int64_t x_bs = h->cap[d];
+  int64_t rest = 1;
+  for (int i = d - 1; i >= 0; --i) {
+    const int64_t m = h->r[i] * h->n[i], rn = h->r[i + 1];
+    GemmArgs g;
+    g.M = m; g.N = rest; g.K = rn;
+    g.A.p = h->U[i]; g.A.rs = 1; g.A.cs = h->ldu[i];
+    g.B.p = X; g.B.rs = rest; g.B.cs = 1; g.B.bs1 = x_bs;
+    g.nbatch = (int)count;
+    g.c_rs = rest; g.c_cs = 1; g.c_bs1 = m * rest;
+    int rc;
+    if (i == 0) {
+      g.C = out;
+      if (out_dtype == TTICE_F64) rc = cu(gemm<double, double, double, double, double>(g, st));
+      else rc = cu(gemm<double, double, double, float, double>(g, st));
+    } else {
+      double* dst = bufs[i & 1];
+      g.C = dst;
+      rc = cu(gemm<double, double, double, double, double>(g, st));
+      X = dst;
+      x_bs = m * rest;
+    }
+    if (rc != TTICE_OK) return rc;
+    rest *= h->n[i];
+  }
+  return TTICE_OK;
+}

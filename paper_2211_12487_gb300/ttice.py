@@ -24,6 +24,7 @@ TTICE_SKIP_NONE, TTICE_SKIP_EXACT, TTICE_SKIP_MEAN = 0, 1, 2
 TTICE_EPSUPD_EXACT, TTICE_EPSUPD_APPROX = 0, 1
 TTICE_FP64, TTICE_FP32, TTICE_TF32, TTICE_BF16, TTICE_SPLIT_BF16 = 0, 1, 2, 3, 4
 TTICE_F32, TTICE_F64 = 0, 1
+TTICE_NOALLOC_MAX_ELEMS = 4 * 1024 * 1024
 
 PRECISIONS = {"fp64": TTICE_FP64, "fp32": TTICE_FP32, "tf32": TTICE_TF32, "bf16": TTICE_BF16,
               "split_bf16": TTICE_SPLIT_BF16}
@@ -83,6 +84,7 @@ def _load():
         "ttice_profile_enable": (c_int, [c_void_p, c_int]),
         "ttice_profile_read": (c_int, [c_void_p, P(ttice_profile)]),
         "ttice_kernel_launches": (c_int64, []),
+        "ttice_reconstruct_noalloc": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int, c_void_p]),
         "ttice_destroy": (None, [c_void_p]),
         "ttice_strerror": (ctypes.c_char_p, [c_int]),
     }
@@ -160,6 +162,15 @@ def ttice_reconstruct(h: int, first: int, count: int, out: torch.Tensor, stream=
     dt = TTICE_F32 if out.dtype == torch.float32 else TTICE_F64
     _check(_lib.ttice_reconstruct(h, int(first), int(count), out.data_ptr(), dt, _stream_ptr(stream)),
            "ttice_reconstruct")
+
+
+def ttice_reconstruct_noalloc(h: int, first: int, count: int, out: torch.Tensor, stream=None) -> None:
+    """Same result as ttice_reconstruct, computed without any device allocation (fixed library
+    scratch; see include/ttice.h for the size limit and the sharing rules)."""
+    assert out.is_cuda and out.is_contiguous() and out.dtype in (torch.float32, torch.float64)
+    dt = TTICE_F32 if out.dtype == torch.float32 else TTICE_F64
+    _check(_lib.ttice_reconstruct_noalloc(h, int(first), int(count), out.data_ptr(), dt,
+                                          _stream_ptr(stream)), "ttice_reconstruct_noalloc")
 
 
 def ttice_stats(h: int) -> dict:
