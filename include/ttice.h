@@ -91,6 +91,8 @@ typedef struct {
   int64_t core_elems;     /* sum_i r_{i-1} n_i r_i over U_1..U_d plus r_d * n_obs (Eq. 22 denominator) */
   int32_t eig_sweep_limit; /* eigen-solves of this update that stopped at their sweep limit */
   int32_t eig_sweeps;      /* block-Jacobi sweeps spent by the eigen-solves of this update */
+  int32_t krylov_solves;   /* eigen-solves of this update done by the certified block-Krylov path */
+  int32_t krylov_fallbacks; /* ... that fell back to the full Jacobi solve */
 } ttice_update_stats;
 
 /* Fill defaults. */

@@ -10,6 +10,7 @@
 // |a_pq| <= eps_T sqrt(|a_pp a_qq|); sweeps stop when a sweep performs no rotation or after a fixed
 // sweep limit (reported through `status`, never by spinning).
 #include <cfloat>
+#include <mutex>
 
 #include "ttice_internal.cuh"
 
@@ -22,6 +23,7 @@ template <> struct Lim<double> { static __device__ double eps() { return DBL_EPS
 
 constexpr int kMaxSweeps = 40;
 constexpr int kEigThreads = 1024;
+constexpr size_t kEigSmemMax = 200 * 1024;  // dynamic shared memory cap of jacobi_kernel
 
 template <typename T>
 __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, int64_t ldg, int s,
@@ -216,12 +218,17 @@ cudaError_t jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* V, T* work,
   if (s <= 0) return cudaSuccess;
   if (s > 1024) return cudaErrorInvalidValue;
   const size_t need = (size_t)s * (s + 1) * sizeof(T);
-  const int use_smem = need <= 200 * 1024;
+  const int use_smem = need <= kEigSmemMax;
   const size_t smem = use_smem ? need : 0;
-  if (use_smem) {
-    TT_CUDA(cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-  }
+  // The attribute is raised once, to the largest size any call uses, so that concurrent calls from
+  // several host threads never race a smaller setting against a launch that needs more.
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kEigSmemMax);
+  });
+  TT_CUDA(attr_err);
   note_launch();
   jacobi_kernel<T><<<1, kEigThreads, smem, st>>>(G, ldg, s, w, V, work, status, use_smem);
   return cudaGetLastError();
@@ -243,8 +250,13 @@ cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, c
   if (k <= 0) return cudaSuccess;
   if (k > 112) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)k * k * sizeof(double);
-  TT_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(2 * 112 * 112 * sizeof(double)));
+  });
+  TT_CUDA(attr_err);
   note_launch();
   chol_inv_kernel<<<1, 256, smem, st>>>(S, k, Rinv, status);
   return cudaGetLastError();

@@ -8,7 +8,7 @@
 // kernel: one column per thread, the n_1 loads of a column coalesced across the warp (consecutive
 // threads read consecutive l), U_1 held in shared memory in both orders so that the projection and
 // the back-projection read it with 16-byte broadcast loads, per-thread FP64 partial norms reduced by
-// warp shuffles and one FP64 atomic per CTA.  The grid is a multiple of the SM count (persistent,
+// warp shuffles and written as one partial per CTA, summed per observation in a fixed order.  The grid is a multiple of the SM count (persistent,
 // grid-stride over columns).  Precision T is the arithmetic of the projection (FP32 on the mixed
 // paths, FP64 on the FP64 path); the norms are always accumulated in FP64.
 #include <algorithm>
@@ -23,7 +23,7 @@ constexpr int kK1Threads = 256;
 template <typename TY, typename T, int N1, int RM>
 __global__ void __launch_bounds__(kK1Threads) k1_kernel(const TY* __restrict__ Y, int64_t L, int n1,
                                                         int r, const T* __restrict__ U, int64_t ldu,
-                                                        T* __restrict__ W, double* y2, double* rho2,
+                                                        T* __restrict__ W, double* part,
                                                         int64_t blocks_per_obs) {
   // Ua[a][k] = U(k, a) (k fastest) for the projection, Uk[k][a] for the back-projection.
   __shared__ __align__(16) T Ua[RM][N1];
@@ -79,21 +79,53 @@ __global__ void __launch_bounds__(kK1Threads) k1_kernel(const TY* __restrict__ Y
   if (threadIdx.x == 0) {
     double a = 0.0, c = 0.0;
     for (int w = 0; w < kK1Threads / 32; ++w) { a += red[0][w]; c += red[1][w]; }
-    atomicAdd(y2 + z, a);
-    atomicAdd(rho2 + z, c);
+    double* pz = part + 2 * ((int64_t)z * blocks_per_obs + blockIdx.x);
+    pz[0] = a;
+    pz[1] = c;
   }
 }
 
+}  // namespace
+
+// Per-observation sums of the K1 partials (fixed order, so the result does not depend on how the
+// partials were scheduled): y2[z] += sum_j part[z][j][0], rho2[z] += sum_j part[z][j][1].
+__global__ void k1_reduce_kernel(const double* part, int64_t per_obs, double* y2, double* rho2) {
+  const int z = blockIdx.x;
+  const double* p = part + 2 * (int64_t)z * per_obs;
+  __shared__ double sa[256], sc[256];
+  double a = 0.0, c = 0.0;
+  for (int64_t j = threadIdx.x; j < per_obs; j += blockDim.x) { a += p[2 * j]; c += p[2 * j + 1]; }
+  sa[threadIdx.x] = a;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) { sa[threadIdx.x] += sa[threadIdx.x + o]; sc[threadIdx.x] += sc[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { y2[z] += sa[0]; rho2[z] += sc[0]; }
+}
+
+cudaError_t launch_k1_reduce(const double* part, int b, int64_t per_obs, double* y2, double* rho2,
+                             cudaStream_t st) {
+  note_launch();
+  k1_reduce_kernel<<<b, 256, 0, st>>>(part, per_obs, y2, rho2);
+  return cudaGetLastError();
+}
+
+namespace {
+
+
 template <typename TY, typename T, int N1, int RM>
 cudaError_t run_k1(const TY* Y, int b, int64_t L, int n1, int r, const T* U, int64_t ldu, T* W,
-                   double* y2, double* rho2, cudaStream_t st) {
+                   double* y2, double* rho2, double* part, cudaStream_t st) {
   // persistent grid: about four CTAs per SM in total, split over the observations
   int64_t per_obs = (4 * 152 + b - 1) / b;
   per_obs = std::max<int64_t>(1, std::min<int64_t>(per_obs, (L + kK1Threads - 1) / kK1Threads));
   dim3 grid((unsigned)per_obs, (unsigned)b);
   note_launch();
-  k1_kernel<TY, T, N1, RM><<<grid, kK1Threads, 0, st>>>(Y, L, n1, r, U, ldu, W, y2, rho2, per_obs);
-  return cudaGetLastError();
+  k1_kernel<TY, T, N1, RM><<<grid, kK1Threads, 0, st>>>(Y, L, n1, r, U, ldu, W, part, per_obs);
+  TT_CUDA(cudaGetLastError());
+  return launch_k1_reduce(part, b, per_obs, y2, rho2, st);
 }
 
 }  // namespace
@@ -105,19 +137,19 @@ bool k1_supported(int n1, int r) {
 
 template <typename TY, typename T>
 cudaError_t launch_k1(const TY* Y, int b, int64_t L, int n1, int r, const T* U, int64_t ldu, T* W,
-                      double* y2, double* rho2, cudaStream_t st) {
-  if (n1 <= 8 && r <= 8) return run_k1<TY, T, 8, 8>(Y, b, L, n1, r, U, ldu, W, y2, rho2, st);
-  if (n1 <= 16 && r <= 16) return run_k1<TY, T, 16, 16>(Y, b, L, n1, r, U, ldu, W, y2, rho2, st);
-  if (n1 <= 32 && r <= 16) return run_k1<TY, T, 32, 16>(Y, b, L, n1, r, U, ldu, W, y2, rho2, st);
-  if (n1 <= 32 && r <= 24) return run_k1<TY, T, 32, 24>(Y, b, L, n1, r, U, ldu, W, y2, rho2, st);
-  if (n1 <= 32 && r <= 32) return run_k1<TY, T, 32, 32>(Y, b, L, n1, r, U, ldu, W, y2, rho2, st);
+                      double* y2, double* rho2, double* part, cudaStream_t st) {
+  if (n1 <= 8 && r <= 8) return run_k1<TY, T, 8, 8>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, st);
+  if (n1 <= 16 && r <= 16) return run_k1<TY, T, 16, 16>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, st);
+  if (n1 <= 32 && r <= 16) return run_k1<TY, T, 32, 16>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, st);
+  if (n1 <= 32 && r <= 24) return run_k1<TY, T, 32, 24>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, st);
+  if (n1 <= 32 && r <= 32) return run_k1<TY, T, 32, 32>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, st);
   return cudaErrorInvalidValue;
 }
 
 #define TT_K1_INST(TY, T)                                                                          \
   template bool k1_supported<TY, T>(int, int);                                                      \
   template cudaError_t launch_k1<TY, T>(const TY*, int, int64_t, int, int, const T*, int64_t, T*, \
-                                        double*, double*, cudaStream_t);
+                                        double*, double*, double*, cudaStream_t);
 TT_K1_INST(float, float)
 TT_K1_INST(double, float)
 TT_K1_INST(float, double)

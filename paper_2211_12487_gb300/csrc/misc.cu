@@ -223,6 +223,41 @@ __global__ void col_norms_kernel(const double* V, int64_t m, int64_t ld, double*
   }
 }
 
+// Deterministic pseudo-random numbers in [-1, 1) (splitmix64 of seed + index): start blocks of the
+// Krylov eigen-solver; the solver's result does not depend on them once converged.
+__global__ void fill_hash_kernel(double* x, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+// res[j] = || GQ[:, j] - theta[j] Q[:, j] ||  (Ritz residual norms), one CTA per column.
+__global__ void ritz_residual_kernel(const double* GQ, const double* Q, const double* theta,
+                                     int64_t s, double* res) {
+  const int j = blockIdx.x;
+  const double th = theta[j];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < s; i += blockDim.x) {
+    const double e = GQ[(int64_t)j * s + i] - th * Q[(int64_t)j * s + i];
+    a = fma(e, e, a);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  __shared__ double red[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    res[j] = sqrt(t);
+  }
+}
+
 __global__ void rel_err_kernel(const double* rho2, const double* y2, int b, double* rel) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < b) rel[j] = y2[j] > 0.0 ? sqrt(rho2[j] / y2[j]) : 0.0;
@@ -347,6 +382,21 @@ cudaError_t launch_col_norms(const double* V, int64_t m, int k, int64_t ld, doub
   if (k <= 0) return cudaSuccess;
   note_launch();
   col_norms_kernel<<<k, kThreads, 0, st>>>(V, m, ld, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_hash(double* x, int64_t n, uint64_t seed, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  fill_hash_kernel<<<grid_for(n), kThreads, 0, st>>>(x, n, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ritz_residual(const double* GQ, const double* Q, const double* theta, int64_t s,
+                                 int k, double* res, cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  note_launch();
+  ritz_residual_kernel<<<k, kThreads, 0, st>>>(GQ, Q, theta, s, res);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,13 @@ struct ttice_s {
   double* H = nullptr;
   double* Z = nullptr;   // kRR x kRR eigenvectors
   double* theta = nullptr;
+  double* KQ = nullptr;   // block-Krylov basis, s_max x kKry
+  double* KW = nullptr;   // s_max x kKryP
+  double* KW2 = nullptr;  // s_max x kKryP
+  double* KT = nullptr;   // kKry x kKryP
+  double* KV = nullptr;   // kKry x kKry (FP64 copy of the FP32 eigenvectors of H)
+  double* res = nullptr;  // Ritz residual norms
+  double* h_dbl = nullptr;  // pinned host scratch
   double* Ebuf = nullptr;  // R V for a column-side Gram (m x s)
   int64_t max_ms = 0;
   double* Vn = nullptr;  // new directions, max_m x kRR
@@ -74,6 +81,7 @@ struct ttice_s {
   int64_t max_m = 0;
   double* rho2 = nullptr;
   double* y2 = nullptr;
+  double* part = nullptr;  // per-CTA / per-tile partial norms of the first pass
   double* trace = nullptr;
   Decision* dec = nullptr;
   int* sel = nullptr;
@@ -137,6 +145,10 @@ constexpr int kDirectEig = 32;  // Gram matrices up to this size are diagonalise
 constexpr int kMaxEig = 1024;
 constexpr int kMaxSweeps64 = 15;  // block Jacobi sweep limits (quadratic convergence needs ~6-10)
 constexpr int kMaxSweeps32 = 12;
+constexpr int kKryP = 8;         // block size of the Krylov eigen-solver
+constexpr int kKryBlocks = 8;    // blocks: a basis of kKry = 64 vectors
+constexpr int kKry = kKryP * kKryBlocks;
+constexpr int kKrylovMin = 1 << 30;  // mixed path: Gram matrices above this size try the Krylov solver first
 
 int cu(cudaError_t e) { return e == cudaSuccess ? TTICE_OK : TTICE_ECUDA; }
 #define TT_TRY(...)                      \
@@ -166,12 +178,13 @@ void free_all(ttice_s* h) {
   for (int i = 0; i < kMaxD; ++i) {
     cudaFree(h->U[i]); cudaFree(h->Uf[i]); cudaFree(h->stage[i]); cudaFree(h->dstage[i]);
   }
-  void* ptrs[] = {h->bjw64, h->bjw32, h->fro, h->bjflags,
+  void* ptrs[] = {h->KQ, h->KW, h->KW2, h->KT, h->KV, h->res,
+                  h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->Ebuf, h->P, h->rho2, h->y2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->part, h->rho2, h->y2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
-  cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32);
+  cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -225,6 +238,7 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
   if (errors) {
     TT_CU(cudaMemsetAsync(h->rho2, 0, b * sizeof(double), st));
     TT_CU(cudaMemsetAsync(h->y2, 0, b * sizeof(double), st));
+    TT_CU(cudaMemsetAsync(h->ibuf + 5, 0, sizeof(int), st));
     const double N = (double)h->N, r1 = (double)h->r[1];
     ph_begin(h, PH_K1, st, b * (sy * N + sw * r1 * h->L[0]), b * (4.0 * N * r1 + 4.0 * N));
     if (!fused_k1) TT_TRY(sumsq<TY>(X0, b, h->N, h->y2, st));
@@ -267,7 +281,16 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
     const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
                                      : reinterpret_cast<const WT*>(h->Uf[i]);
     if (i == 0 && fused_k1) {
-      TT_CU((launch_k1<TY, WT>(X0, b, L, (int)m, (int)rn, Ui, h->ldu[i], W, h->y2, h->rho2, st)));
+      if constexpr (sizeof(TY) == 4) {
+        if (k1_tma_supported(X0, L, (int)m, (int)rn)) {
+          TT_CU((launch_k1_tma<WT>(reinterpret_cast<const float*>(X0), b, L, (int)m, (int)rn, Ui,
+                                   h->ldu[i], W, h->y2, h->rho2, h->part, h->ibuf + 5, st)));
+        } else {
+          TT_CU((launch_k1<TY, WT>(X0, b, L, (int)m, (int)rn, Ui, h->ldu[i], W, h->y2, h->rho2, h->part, st)));
+        }
+      } else {
+        TT_CU((launch_k1<TY, WT>(X0, b, L, (int)m, (int)rn, Ui, h->ldu[i], W, h->y2, h->rho2, h->part, st)));
+      }
     } else if (i == 0) {
       TT_TRY(proj<WT, TY, WT>(Ui, h->ldu[i], X0, m, L, rn, b, W, st));
       if (errors) TT_TRY((resid<WT, WT, TY, WT>(Ui, h->ldu[i], W, X0, m, L, rn, b, nullptr, h->rho2, st)));
@@ -283,6 +306,200 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
 
 int sync_read(ttice_s* h, cudaStream_t st) {
   TT_CU(cudaStreamSynchronize(st));
+  return TTICE_OK;
+}
+
+// FP64 Rayleigh-Ritz on the K candidate vectors in h->Q (s x K): orthonormalise them (CholQR2),
+// form H = Q^T G Q, diagonalise it (FP64 Jacobi), apply the rank rule to the Ritz values
+// (tail = trace - sum theta, Eq. 5) and leave the Ritz vectors in h->Q2 and values in h->theta.
+int rayleigh_ritz(ttice_s* h, int64_t s, int K, const double* d_eps, int max_new, cudaStream_t st) {
+  // CholQR2: orthonormalise Q in FP64
+  for (int pass = 0; pass < 2; ++pass) {
+    TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)K * K * sizeof(double), st));
+    GemmArgs g;  // S = Q^T Q
+    g.M = K; g.N = K; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+    g.A.p = h->Q; g.A.rs = s; g.A.cs = 1;
+    g.B.p = h->Q; g.B.rs = 1; g.B.cs = s;
+    g.C = h->Ssm; g.c_rs = 1; g.c_cs = K;
+    TT_CU((gemm<double, double, double, double, double>(g, st)));
+    TT_CU(launch_chol_inv(h->Ssm, K, h->Rinv, h->ibuf + 2, st));
+    GemmArgs q;  // Q2 = Q Rinv
+    q.M = s; q.N = K; q.K = K;
+    q.A.p = h->Q; q.A.rs = 1; q.A.cs = s;
+    q.B.p = h->Rinv; q.B.rs = 1; q.B.cs = K;
+    q.C = h->Q2; q.c_rs = 1; q.c_cs = s;
+    TT_CU((gemm<double, double, double, double, double>(q, st)));
+    std::swap(h->Q, h->Q2);
+  }
+  {  // GQ = G Q ; H = Q^T GQ
+    GemmArgs g;
+    g.M = s; g.N = K; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+    g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
+    g.B.p = h->Q; g.B.rs = 1; g.B.cs = s;
+    g.C = h->GQ; g.c_rs = 1; g.c_cs = s;
+    TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * K * sizeof(double), st));
+    TT_CU((gemm<double, double, double, double, double>(g, st)));
+    TT_CU(cudaMemsetAsync(h->H, 0, (size_t)K * K * sizeof(double), st));
+    GemmArgs hh;
+    hh.M = K; hh.N = K; hh.K = s; hh.atomic = 1; hh.allow_splitk = 1;
+    hh.A.p = h->Q; hh.A.rs = s; hh.A.cs = 1;
+    hh.B.p = h->GQ; hh.B.rs = 1; hh.B.cs = s;
+    hh.C = h->H; hh.c_rs = K; hh.c_cs = 1;
+    TT_CU((gemm<double, double, double, double, double>(hh, st)));
+  }
+  TT_CU(jacobi_eig<double>(h->H, K, K, h->theta, h->Z, h->work64, h->ibuf + 1, st));
+  TT_CU(launch_rank_rule(h->theta, K, K == s, h->trace, d_eps, max_new, h->ibuf, st));
+  {  // Ritz vectors Q2 = Q Z
+    GemmArgs g;
+    g.M = s; g.N = K; g.K = K;
+    g.A.p = h->Q; g.A.rs = 1; g.A.cs = s;
+    g.B.p = h->Z; g.B.rs = 1; g.B.cs = K;
+    g.C = h->Q2; g.c_rs = 1; g.c_cs = s;
+    TT_CU((gemm<double, double, double, double, double>(g, st)));
+  }
+  return TTICE_OK;
+}
+
+// CholQR2 of an s x p block X (column-major, ld s), in place; status (device int) set if the
+// block is numerically rank deficient.
+int cholqr2_block(ttice_s* h, double* X, int64_t s, int p, int* status, cudaStream_t st) {
+  for (int pass = 0; pass < 2; ++pass) {
+    TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)p * p * sizeof(double), st));
+    GemmArgs g;  // S = X^T X
+    g.M = p; g.N = p; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+    g.A.p = X; g.A.rs = s; g.A.cs = 1;
+    g.B.p = X; g.B.rs = 1; g.B.cs = s;
+    g.C = h->Ssm; g.c_rs = 1; g.c_cs = p;
+    TT_CU((gemm<double, double, double, double, double>(g, st)));
+    TT_CU(launch_chol_inv(h->Ssm, p, h->Rinv, status, st));
+    GemmArgs q;  // X2 = X Rinv
+    q.M = s; q.N = p; q.K = p;
+    q.A.p = X; q.A.rs = 1; q.A.cs = s;
+    q.B.p = h->Rinv; q.B.rs = 1; q.B.cs = p;
+    q.C = h->KW2; q.c_rs = 1; q.c_cs = s;
+    TT_CU((gemm<double, double, double, double, double>(q, st)));
+    TT_CU(cudaMemcpyAsync(X, h->KW2, (size_t)s * p * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  return TTICE_OK;
+}
+
+// Candidate eigenvectors for the leading part of the Gram G (s x s, FP64) from a block Krylov
+// subspace: X_0 = orth(random s x p), X_i = orth((I - Q Q^T) G X_{i-1}) (CGS2 against the basis
+// Q = [X_0 .. X_{i-1}]), kKryBlocks blocks; H = Q^T G Q is diagonalised (FP32 Jacobi on the small
+// matrix) and its leading K eigenvectors, mapped back to R^s, are left in h->Q for the FP64
+// Rayleigh-Ritz step.  *K_out = 0 when the subspace is too small for the tolerance.
+int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStream_t st) {
+  const int p = kKryP;
+  *K_out = 0;
+  double* Qb = h->KQ;
+  TT_CU(cudaMemsetAsync(h->ibuf + 6, 0, sizeof(int), st));
+  TT_CU(launch_fill_hash(Qb, s * p, 0x5eedull + (uint64_t)s, st));
+  TT_TRY(cholqr2_block(h, Qb, s, p, h->ibuf + 6, st));
+  int nblk = kKryBlocks;
+  for (int i = 1; i < nblk; ++i) {
+    const double* Xprev = Qb + (int64_t)(i - 1) * p * s;
+    double* Xi = Qb + (int64_t)i * p * s;
+    TT_CU(cudaMemsetAsync(Xi, 0, (size_t)s * p * sizeof(double), st));
+    GemmArgs g;  // X_i = G X_{i-1}
+    g.M = s; g.N = p; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+    g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
+    g.B.p = Xprev; g.B.rs = 1; g.B.cs = s;
+    g.C = Xi; g.c_rs = 1; g.c_cs = s;
+    TT_CU((gemm<double, double, double, double, double>(g, st)));
+    const int nq = i * p;
+    for (int pass = 0; pass < 2; ++pass) {
+      TT_CU(cudaMemsetAsync(h->KT, 0, (size_t)nq * p * sizeof(double), st));
+      GemmArgs a;  // T = Q^T X_i
+      a.M = nq; a.N = p; a.K = s; a.atomic = 1; a.allow_splitk = 1;
+      a.A.p = Qb; a.A.rs = s; a.A.cs = 1;
+      a.B.p = Xi; a.B.rs = 1; a.B.cs = s;
+      a.C = h->KT; a.c_rs = 1; a.c_cs = nq;
+      TT_CU((gemm<double, double, double, double, double>(a, st)));
+      GemmArgs b;  // X_i -= Q T
+      b.M = s; b.N = p; b.K = nq;
+      b.A.p = Qb; b.A.rs = 1; b.A.cs = s;
+      b.B.p = h->KT; b.B.rs = 1; b.B.cs = nq;
+      b.X.p = Xi; b.X.rs = 1; b.X.cs = s;
+      b.alpha = -1.0; b.beta = 1.0;
+      b.C = Xi; b.c_rs = 1; b.c_cs = s;
+      TT_CU((gemm<double, double, double, double, double>(b, st)));
+    }
+    TT_TRY(cholqr2_block(h, Xi, s, p, h->ibuf + 6, st));
+  }
+  const int k = nblk * p;
+  // H = Q^T G Q
+  TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * k * sizeof(double), st));
+  GemmArgs g;
+  g.M = s; g.N = k; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+  g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
+  g.B.p = Qb; g.B.rs = 1; g.B.cs = s;
+  g.C = h->GQ; g.c_rs = 1; g.c_cs = s;
+  TT_CU((gemm<double, double, double, double, double>(g, st)));
+  TT_CU(cudaMemsetAsync(h->H, 0, (size_t)k * k * sizeof(double), st));
+  GemmArgs hh;
+  hh.M = k; hh.N = k; hh.K = s; hh.atomic = 1; hh.allow_splitk = 1;
+  hh.A.p = Qb; hh.A.rs = s; hh.A.cs = 1;
+  hh.B.p = h->GQ; hh.B.rs = 1; hh.B.cs = s;
+  hh.C = h->H; hh.c_rs = k; hh.c_cs = 1;
+  TT_CU((gemm<double, double, double, double, double>(hh, st)));
+  TT_CU(cudaMemsetAsync(h->bjflags, 0, 4 * sizeof(int), st));
+  TT_CU(jacobi_eig<float>(h->H, k, k, h->w32, h->V32, h->bjw32, h->bjflags + 3, st));
+  TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, k * sizeof(float), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_dbl, h->trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_int + 6, h->ibuf + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ph_end(h, st);
+  TT_TRY(sync_read(h, st));
+  ph_begin(h, PH_EIG, st, 0.0, 0.0);
+  if (h->h_int[6]) return TTICE_OK;  // the Krylov blocks lost rank: leave it to the full solver
+  // leading part needed: smallest r with trace - sum_{j<r} theta_j <= eps^2 (sizes the RR step)
+  const double tr = h->h_dbl[0];
+  double acc = 0.0;
+  int r32 = -1;
+  if (std::sqrt(std::max(tr, 0.0)) <= eps_c) r32 = 0;
+  for (int j = 0; j < k && r32 < 0; ++j) {
+    acc += std::max((double)h->h_w32[j], 0.0);
+    if (std::sqrt(std::max(tr - acc, 0.0)) <= eps_c) r32 = j + 1;
+  }
+  if (r32 < 0 || r32 + 8 > k - 8) return TTICE_OK;  // subspace too small: full solver
+  const int K = std::min(k, r32 + 8);
+  // candidates Q = Q_krylov V[:, :K]
+  TT_CU(launch_to_f64<float>(h->V32, (int64_t)k * K, h->KV, st));
+  GemmArgs c;
+  c.M = s; c.N = K; c.K = k;
+  c.A.p = Qb; c.A.rs = 1; c.A.cs = s;
+  c.B.p = h->KV; c.B.rs = 1; c.B.cs = k;
+  c.C = h->Q; c.c_rs = 1; c.c_cs = s;
+  TT_CU((gemm<double, double, double, double, double>(c, st)));
+  *K_out = K;
+  return TTICE_OK;
+}
+
+// After rayleigh_ritz: accept the Krylov result iff every Ritz pair the rank rule used (the
+// leading rR + 1) has a residual ||G z - theta z|| <= 1e-6 theta_1, i.e. the Ritz values are
+// converged far below the truncation threshold (errors are second order in the residual).
+int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
+  *ok = false;
+  TT_CU(cudaMemcpyAsync(h->h_int, h->ibuf, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_TRY(sync_read(h, st));
+  const int rR = h->h_int[0];
+  if (rR < 0) return TTICE_OK;
+  const int jm = std::min(rR + 1, K);
+  if (jm == 0) { *ok = true; return TTICE_OK; }
+  TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * jm * sizeof(double), st));
+  GemmArgs g;  // GQ = G Z
+  g.M = s; g.N = jm; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+  g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
+  g.B.p = h->Q2; g.B.rs = 1; g.B.cs = s;
+  g.C = h->GQ; g.c_rs = 1; g.c_cs = s;
+  TT_CU((gemm<double, double, double, double, double>(g, st)));
+  TT_CU(launch_ritz_residual(h->GQ, h->Q2, h->theta, s, jm, h->res, st));
+  TT_CU(cudaMemcpyAsync(h->h_dbl, h->res, jm * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_dbl + 128, h->theta, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_TRY(sync_read(h, st));
+  const double tol = 1e-6 * std::max(h->h_dbl[128], 0.0);
+  bool good = true;
+  for (int j = 0; j < jm; ++j) good = good && (h->h_dbl[j] <= tol);
+  *ok = good;
   return TTICE_OK;
 }
 
@@ -365,6 +582,20 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     TT_CU(launch_rank_rule(e, (int)s, 1, h->trace, d_eps, max_new, h->ibuf, st));
     Vdir = h->V64; thet = h->w64; K = (int)s;
   } else {
+    bool have = false;
+    if (s > kKrylovMin) {
+      // block Krylov candidates + FP64 Rayleigh-Ritz, kept only if certified
+      int Kk = 0;
+      TT_TRY(krylov_candidates(h, s, eps_c, &Kk, st));
+      if (Kk > 0) {
+        TT_TRY(rayleigh_ritz(h, s, Kk, d_eps, max_new, st));
+        bool ok = false;
+        TT_TRY(krylov_certify(h, s, Kk, &ok, st));
+        if (ok) { have = true; K = Kk; h->stats.krylov_solves += 1; }
+      }
+      if (!have) h->stats.krylov_fallbacks += 1;
+    }
+    if (!have) {
     // FP32 Jacobi (one CTA for small matrices, block Jacobi otherwise) for approximate
     // eigenvectors, then FP64 Rayleigh-Ritz on the leading K of them.
     if (s <= kDirectEig) {
@@ -392,49 +623,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     K = std::min<int>((int)s, std::min(r32 + 8, kRR));
     if (r32 + 1 > kRR) return TTICE_ECAPACITY;
     TT_CU(launch_to_f64<float>(h->V32, s * K, h->Q, st));
-    // CholQR2: orthonormalise Q in FP64
-    for (int pass = 0; pass < 2; ++pass) {
-      TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)K * K * sizeof(double), st));
-      GemmArgs g;  // S = Q^T Q
-      g.M = K; g.N = K; g.K = s; g.atomic = 1; g.allow_splitk = 1;
-      g.A.p = h->Q; g.A.rs = s; g.A.cs = 1;
-      g.B.p = h->Q; g.B.rs = 1; g.B.cs = s;
-      g.C = h->Ssm; g.c_rs = 1; g.c_cs = K;
-      TT_CU((gemm<double, double, double, double, double>(g, st)));
-      TT_CU(launch_chol_inv(h->Ssm, K, h->Rinv, h->ibuf + 2, st));
-      GemmArgs q;  // Q2 = Q Rinv
-      q.M = s; q.N = K; q.K = K;
-      q.A.p = h->Q; q.A.rs = 1; q.A.cs = s;
-      q.B.p = h->Rinv; q.B.rs = 1; q.B.cs = K;
-      q.C = h->Q2; q.c_rs = 1; q.c_cs = s;
-      TT_CU((gemm<double, double, double, double, double>(q, st)));
-      std::swap(h->Q, h->Q2);
-    }
-    {  // GQ = G Q ; H = Q^T GQ
-      GemmArgs g;
-      g.M = s; g.N = K; g.K = s; g.atomic = 1; g.allow_splitk = 1;
-      g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
-      g.B.p = h->Q; g.B.rs = 1; g.B.cs = s;
-      g.C = h->GQ; g.c_rs = 1; g.c_cs = s;
-      TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * K * sizeof(double), st));
-      TT_CU((gemm<double, double, double, double, double>(g, st)));
-      TT_CU(cudaMemsetAsync(h->H, 0, (size_t)K * K * sizeof(double), st));
-      GemmArgs hh;
-      hh.M = K; hh.N = K; hh.K = s; hh.atomic = 1; hh.allow_splitk = 1;
-      hh.A.p = h->Q; hh.A.rs = s; hh.A.cs = 1;
-      hh.B.p = h->GQ; hh.B.rs = 1; hh.B.cs = s;
-      hh.C = h->H; hh.c_rs = K; hh.c_cs = 1;
-      TT_CU((gemm<double, double, double, double, double>(hh, st)));
-    }
-    TT_CU(jacobi_eig<double>(h->H, K, K, h->theta, h->Z, h->work64, h->ibuf + 1, st));
-    TT_CU(launch_rank_rule(h->theta, K, K == s, h->trace, d_eps, max_new, h->ibuf, st));
-    {  // Ritz vectors Q2 = Q Z
-      GemmArgs g;
-      g.M = s; g.N = K; g.K = K;
-      g.A.p = h->Q; g.A.rs = 1; g.A.cs = s;
-      g.B.p = h->Z; g.B.rs = 1; g.B.cs = K;
-      g.C = h->Q2; g.c_rs = 1; g.c_cs = s;
-      TT_CU((gemm<double, double, double, double, double>(g, st)));
+    TT_TRY(rayleigh_ritz(h, s, K, d_eps, max_new, st));
     }
     Vdir = h->Q2; thet = h->theta;
   }
@@ -567,8 +756,10 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
                         h->h.eps_upd_mode, h->dec, h->sel, st));
   TT_CU(cudaMemcpyAsync(h->h_dec, h->dec, sizeof(Decision), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_sel, h->sel, b * sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_int + 5, h->ibuf + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
   TT_TRY(sync_read(h, st));
   const Decision dec = *h->h_dec;
+  if (h->h_int[5]) return TTICE_ETIMEOUT;  // a staged copy of the first pass never completed
   if (dec.nonfinite) return TTICE_ENONFINITE;
   std::memset(&h->stats, 0, sizeof(h->stats));
   h->stats.skipped = dec.skip;
@@ -774,6 +965,12 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->bjw32, block_jacobi_work<float>((int)s));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->fro, 1);
   if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 4);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->KQ, s * kKry);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->KW, s * kKryP);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->KW2, s * kKryP);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->KT, kKry * kKryP);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->KV, kKry * kKry);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->res, kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Q, s * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Q2, s * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->GQ, s * kRR);
@@ -788,6 +985,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   int64_t maxcap = 1;
   for (int i = 1; i <= d; ++i) maxcap = std::max(maxcap, h->cap[i]);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->P, maxcap * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->part, 2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rho2, B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->y2, B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->trace, 1);
@@ -798,6 +996,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_sel, B * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_int, 16 * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_w32, s * sizeof(float)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_dbl, 256 * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
   if (rc == TTICE_OK) rc = grow_last(h, std::max<int64_t>(h->capc.obs_reserve, 1));
   if (rc == TTICE_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TTICE_ECUDA;
   if (rc != TTICE_OK) {

@@ -88,9 +88,20 @@ cudaError_t launch_rank_rule(const double* theta, int K, int full, const double*
 // observation in one read of the increment.  Supported for n_1 <= 32 and 1 <= r_1 <= 32.
 template <typename TY, typename T>
 bool k1_supported(int n1, int r);
+// part: device scratch of 2 * (4*152 + b) doubles (per-CTA partial sums).
 template <typename TY, typename T>
 cudaError_t launch_k1(const TY* Y, int b, int64_t L, int n1, int r, const T* U, int64_t ldu, T* W,
-                      double* y2, double* rho2, cudaStream_t st);
+                      double* y2, double* rho2, double* part, cudaStream_t st);
+cudaError_t launch_k1_reduce(const double* part, int b, int64_t per_obs, double* y2, double* rho2,
+                             cudaStream_t st);
+
+// K1 with TMA staging (k1_tma.cu), FP32 increments: same outputs as launch_k1; status (device int)
+// becomes nonzero if a tile copy never completed within the bounded wait.
+bool k1_tma_supported(const void* Y, int64_t L, int n1, int r);
+// part: device scratch of 2 * b * ceil(L / 256) doubles (per-tile partial sums).
+template <typename T>
+cudaError_t launch_k1_tma(const float* Y, int b, int64_t L, int n1, int r, const T* U, int64_t ldu,
+                          T* W, double* y2, double* rho2, double* part, int* status, cudaStream_t st);
 
 // Misc kernels.
 cudaError_t launch_fill(double* p, int64_t n, double v, cudaStream_t st);
@@ -125,6 +136,11 @@ cudaError_t launch_append_last_t(const TC* coef, int b, int r, double* last, int
 // out[j] = sum_i V[j*ld + i]^2 for the k columns of an m x k column-major matrix
 cudaError_t launch_col_norms(const double* V, int64_t m, int k, int64_t ld, double* out,
                              cudaStream_t st);
+// deterministic pseudo-random fill in [-1, 1)
+cudaError_t launch_fill_hash(double* x, int64_t n, uint64_t seed, cudaStream_t st);
+// res[j] = ||GQ[:,j] - theta[j] Q[:,j]|| for j < k (column-major, ld s)
+cudaError_t launch_ritz_residual(const double* GQ, const double* Q, const double* theta, int64_t s,
+                                 int k, double* res, cudaStream_t st);
 // rel[j] = sqrt(rho2[j]/y2[j]) (0 when y2 = 0)
 cudaError_t launch_rel_err(const double* rho2, const double* y2, int b, double* rel,
                            cudaStream_t st);

@@ -1,0 +1,185 @@
+"""Continuous-batching serving loop over many TT-ICE* streams on one GPU.
+
+Each client stream (its own shape, batch size and eps) owns one libttice handle whose cores stay
+resident on the device.  Increments arrive at any time; a stream has at most one update in flight
+(update k+1 needs the cores left by update k), and a fixed pool of slots, each with its own CUDA
+stream and host worker thread, runs whichever ready streams come next, so updates of different
+streams overlap on the device.  A new stream is admitted only when its projected core memory (the
+capacity its handle allocates) fits in the memory budget left by the admitted streams; otherwise it
+waits in the admission queue and is admitted as soon as a finished stream releases its memory.
+
+All arithmetic stays in libttice: this module only schedules calls to `ttice_update` (ctypes
+releases the GIL during the call, so slots run concurrently).
+"""
+from __future__ import annotations
+
+import collections
+import math
+import queue
+import threading
+import time
+from dataclasses import dataclass, field
+
+import torch
+
+from . import ttice as T
+
+
+@dataclass
+class StreamSpec:
+    name: str
+    dims: tuple
+    eps: float
+    max_batch: int
+    input_dtype: torch.dtype = torch.float32
+    precision: str = "fp32"
+    max_rank: int = 512
+
+
+@dataclass
+class Request:
+    stream: str
+    data: torch.Tensor          # device tensor (b, *dims)
+    arrival: float = 0.0        # perf_counter time the request became available
+    done: float = 0.0
+    stats: object = None
+    error: Exception | None = None
+
+
+def projected_core_bytes(spec: StreamSpec) -> int:
+    """Device bytes a handle for `spec` allocates (cores at capacity, stage buffers, last core),
+    computed from the same capacity rule the library uses (cap_i = min(max_rank, cap_{i-1} n_{i-1}))."""
+    dims = list(spec.dims)
+    d = len(dims)
+    cap = [1]
+    for i in range(1, d + 1):
+        cap.append(min(spec.max_rank, cap[i - 1] * dims[i - 1]))
+    L = [math.prod(dims[i + 1:]) for i in range(d)]
+    wt = 8 if spec.precision == "fp64" else 4
+    cores = sum(cap[i] * dims[i] * cap[i + 1] * (8 + (0 if wt == 8 else 4)) for i in range(d))
+    stages = sum(2 * spec.max_batch * cap[i + 1] * L[i] * wt for i in range(d))
+    resid = spec.max_batch * max(cap[i] * dims[i] * L[i] for i in range(d)) * wt
+    return int(cores + stages + resid + spec.max_batch * math.prod(dims) * 8 + 64 * 2 ** 20)
+
+
+class ServingEngine:
+    def __init__(self, specs: list[StreamSpec], slots: int = 4, mem_budget: int | None = None,
+                 device=None):
+        self.device = torch.device(device or "cuda")
+        self.specs = {s.name: s for s in specs}
+        self.slots = slots
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            mem_budget = int(free * 0.8)
+        self.mem_budget = mem_budget
+        self.mem_used = 0
+        self.handles: dict[str, T.TTICE] = {}
+        self.pending: dict[str, collections.deque] = collections.defaultdict(collections.deque)
+        self.busy: set[str] = set()
+        self.waiting_admission: collections.deque = collections.deque()
+        self.finished_streams: set[str] = set()
+        self.lock = threading.Condition()
+        self.ready: queue.Queue = queue.Queue()
+        self.completed: list[Request] = []
+        self.stop = False
+        self.workers = [threading.Thread(target=self._worker, args=(i,), daemon=True)
+                        for i in range(slots)]
+        for w in self.workers:
+            w.start()
+
+    # -------------------------------------------------------------- admission
+    def _try_admit(self):
+        """Admit waiting streams in arrival order while their projected memory fits."""
+        while self.waiting_admission:
+            name = self.waiting_admission[0]
+            need = projected_core_bytes(self.specs[name])
+            if self.mem_used + need > self.mem_budget and self.handles:
+                return
+            self.waiting_admission.popleft()
+            spec = self.specs[name]
+            with torch.cuda.device(self.device):
+                self.handles[name] = T.TTICE(spec.dims, spec.eps, precision=spec.precision,
+                                             input_dtype=spec.input_dtype, max_batch=spec.max_batch,
+                                             max_rank=spec.max_rank)
+            self.mem_used += need
+            if self.pending[name]:
+                self._schedule(name)
+
+    def _schedule(self, name):
+        if name in self.handles and name not in self.busy and self.pending[name]:
+            self.busy.add(name)
+            self.ready.put(name)
+
+    def submit(self, req: Request):
+        with self.lock:
+            if not req.arrival:
+                req.arrival = time.perf_counter()
+            self.pending[req.stream].append(req)
+            if req.stream not in self.handles and req.stream not in self.waiting_admission:
+                self.waiting_admission.append(req.stream)
+                self._try_admit()
+            else:
+                self._schedule(req.stream)
+
+    def release(self, name: str):
+        """The client closed stream `name`: free its cores and admit waiting streams."""
+        with self.lock:
+            h = self.handles.pop(name, None)
+            if h is not None:
+                h.close()
+                self.mem_used -= projected_core_bytes(self.specs[name])
+            self.finished_streams.add(name)
+            self._try_admit()
+
+    # -------------------------------------------------------------- slots
+    def _worker(self, slot: int):
+        cuda_stream = torch.cuda.Stream(device=self.device)
+        while True:
+            name = self.ready.get()
+            if name is None:
+                return
+            with self.lock:
+                req = self.pending[name].popleft()
+                h = self.handles[name]
+            try:
+                with torch.cuda.device(self.device), torch.cuda.stream(cuda_stream):
+                    cuda_stream.wait_stream(torch.cuda.default_stream(self.device))
+                    req.stats = h.update(req.data, stream=cuda_stream)
+            except Exception as e:  # the error is reported with the request
+                req.error = e
+            req.done = time.perf_counter()
+            with self.lock:
+                self.completed.append(req)
+                self.busy.discard(name)
+                self._schedule(name)
+                self.lock.notify_all()
+
+    def drain(self, timeout: float | None = None) -> bool:
+        """Wait until every submitted request has completed."""
+        t_end = None if timeout is None else time.perf_counter() + timeout
+        with self.lock:
+            while any(self.pending[n] for n in self.pending) or self.busy:
+                left = None if t_end is None else t_end - time.perf_counter()
+                if left is not None and left <= 0:
+                    return False
+                self.lock.wait(timeout=0.05 if left is None else min(0.05, left))
+        return True
+
+    def close(self):
+        for _ in self.workers:
+            self.ready.put(None)
+        for w in self.workers:
+            w.join(timeout=30)
+        for name in list(self.handles):
+            self.handles.pop(name).close()
+
+    # -------------------------------------------------------------- reporting
+    def latencies_ms(self):
+        return sorted((r.done - r.arrival) * 1e3 for r in self.completed if r.error is None)
+
+
+def percentile(sorted_vals, q):
+    if not sorted_vals:
+        return float("nan")
+    i = min(len(sorted_vals) - 1, max(0, int(math.ceil(q * len(sorted_vals))) - 1))
+    return sorted_vals[i]

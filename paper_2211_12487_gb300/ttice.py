@@ -44,7 +44,8 @@ class ttice_update_stats(ctypes.Structure):
     _fields_ = [("skipped", c_int32), ("n_selected", c_int32), ("rel_err_before", c_double),
                 ("eps_upd", c_double), ("eps_core", c_double), ("ranks", c_int64 * 18),
                 ("new_dirs", c_int32 * 16), ("n_obs", c_int64), ("core_elems", c_int64),
-                ("eig_sweep_limit", c_int32), ("eig_sweeps", c_int32)]
+                ("eig_sweep_limit", c_int32), ("eig_sweeps", c_int32),
+                ("krylov_solves", c_int32), ("krylov_fallbacks", c_int32)]
 
 
 TTICE_NPHASES = 8

@@ -63,5 +63,5 @@ def test_defaults_and_strerror(lib):
 def test_stats_struct_layout(lib):
     from paper_2211_12487_gb300 import ttice
 
-    # int32,int32,double*3,int64[18],int32[16],int64,int64,int32,int32 with natural alignment
-    assert ctypes.sizeof(ttice.ttice_update_stats) == 8 + 24 + 144 + 64 + 16 + 8
+    # int32,int32,double*3,int64[18],int32[16],int64,int64,int32 x4 with natural alignment
+    assert ctypes.sizeof(ttice.ttice_update_stats) == 8 + 24 + 144 + 64 + 16 + 8 + 8
