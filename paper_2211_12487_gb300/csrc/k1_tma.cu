@@ -213,14 +213,22 @@ cudaError_t run(const float* Y, int b, int64_t L, int n1, int r, const T* U, int
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const size_t smem = (size_t)kStages * N1 * kTileL * sizeof(float) + 128;
-  TT_CUDA(cudaFuncSetAttribute(k1_tma_kernel<T, N1, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
-  int per_sm = 0;
-  TT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1_tma_kernel<T, N1, RM>, kThreads,
-                                                        smem));
-  int dev = 0, sms = 0;
-  TT_CUDA(cudaGetDevice(&dev));
-  TT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // one-time set-up per instantiation: shared-memory attribute, occupancy and SM count
+  static std::once_flag once;
+  static cudaError_t setup_err = cudaSuccess;
+  static int per_sm = 1, sms = 152;
+  std::call_once(once, [smem] {
+    setup_err = cudaFuncSetAttribute(k1_tma_kernel<T, N1, RM>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (setup_err == cudaSuccess)
+      setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1_tma_kernel<T, N1, RM>,
+                                                                kThreads, smem);
+    int dev = 0;
+    if (setup_err == cudaSuccess) setup_err = cudaGetDevice(&dev);
+    if (setup_err == cudaSuccess)
+      setup_err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  TT_CUDA(setup_err);
   const int64_t ntiles = ((L + kTileL - 1) / kTileL) * b;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), ntiles));
   note_launch();

@@ -148,7 +148,7 @@ constexpr int kMaxSweeps32 = 12;
 constexpr int kKryP = 8;         // block size of the Krylov eigen-solver
 constexpr int kKryBlocks = 8;    // blocks: a basis of kKry = 64 vectors
 constexpr int kKry = kKryP * kKryBlocks;
-constexpr int kKrylovMin = 1 << 30;  // mixed path: Gram matrices above this size try the Krylov solver first
+constexpr int kKrylovMin = 96;   // mixed path: Gram matrices above this size try the Krylov solver first
 
 int cu(cudaError_t e) { return e == cudaSuccess ? TTICE_OK : TTICE_ECUDA; }
 #define TT_TRY(...)                      \

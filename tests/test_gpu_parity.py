@@ -235,3 +235,10 @@ def test_fp32_projection_mode(T):
     ranks equal to the oracle's, reconstructions within FP32-level error."""
     Y = blob_video(0, 24, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=7)
     run_pair(T, Y, 4, 0.1, precision="fp32", tol=1e-4)
+
+
+def test_video_c1_prefix_fp32(T):
+    """Full-size video frames on the FP32 path (Krylov / Jacobi eigen-solves with FP64 Rayleigh-Ritz):
+    ranks and decisions equal to the oracle's, eps met on every increment."""
+    Y = blob_video(0, 32)
+    run_pair(T, Y, 8, 0.1, precision="fp32", tol=1e-4)
