@@ -103,10 +103,11 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
       for (int j = 0; j < TN; ++j) acc64[i][j] += (double)acc[i][j];
   }
 
-  double ss = 0.0;
-  double rowss[TM];
+  // squared outputs: summed per thread in the accumulator type (at most TM*TN terms), then in FP64
+  ACC ss_t = ACC(0);
+  ACC rowss[TM];
 #pragma unroll
-  for (int i = 0; i < TM; ++i) rowss[i] = 0.0;
+  for (int i = 0; i < TM; ++i) rowss[i] = ACC(0);
   TC* C = static_cast<TC*>(g.C);
   const int64_t coff = z1 * g.c_bs1 + z2 * g.c_bs2;
   const int64_t xoff = z1 * g.X.bs1 + z2 * g.X.bs2;
@@ -123,8 +124,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
         if (g.X.p) v += g.beta * (double)ld_elem<TX>(g.X.p, xoff + gm * g.X.rs + gn * g.X.cs);
         const TC cv = (TC)v;
         if (g.norm) {
-          ss += (double)cv * (double)cv;
-          rowss[i] += (double)cv * (double)cv;
+          const ACC q = (ACC)cv;
+          ss_t = fma(q, q, ss_t);
+          rowss[i] = fma(q, q, rowss[i]);
         }
         if (g.store) {
           TC* dst = C + coff + gm * g.c_rs + gn * g.c_cs;
@@ -141,13 +143,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < TM; ++i)
-      if (rowss[i] != 0.0) atomicAdd(&rsum[ty + i * (BM / TM)], rowss[i]);
+      if (rowss[i] != ACC(0)) atomicAdd(&rsum[ty + i * (BM / TM)], (double)rowss[i]);
     __syncthreads();
     for (int i = tid; i < BM; i += 256) {
       const int64_t gm = m0 + i;
       if (gm < g.M && rsum[i] != 0.0) atomicAdd(g.norm + gm, rsum[i]);
     }
   } else if (g.norm) {
+    double ss = (double)ss_t;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if ((tid & 31) == 0 && ss != 0.0) atomicAdd(g.norm + z1, ss);

@@ -128,26 +128,28 @@ __global__ void __launch_bounds__(kThreads) k1_tma_kernel(const __grid_constant_
     T w[RM];
 #pragma unroll
     for (int a = 0; a < RM; ++a) w[a] = T(0);
-    double sy = 0.0;
+    // squares of one column are summed in T (n_1 <= 32 terms), columns are combined in FP64
+    T sy_c = T(0);
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
       if (k < n1) {
         const T y = (T)tile[k * kTileL + tid];
-        sy = fma((double)y, (double)y, sy);
+        sy_c = fma(y, y, sy_c);
 #pragma unroll
         for (int a = 0; a < RM; ++a) w[a] = fma(Uk[k][a], y, w[a]);
       }
     }
-    double se = 0.0;
+    T se_c = T(0);
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
       if (k < n1) {
         T acc = (T)tile[k * kTileL + tid];
 #pragma unroll
         for (int a = 0; a < RM; ++a) acc = fma(-Uk[k][a], w[a], acc);
-        se = fma((double)acc, (double)acc, se);
+        se_c = fma(acc, acc, se_c);
       }
     }
+    double sy = (double)sy_c, se = (double)se_c;
     if (l < L) {
       T* Wz = W + (int64_t)z * r * L + l;
 #pragma unroll

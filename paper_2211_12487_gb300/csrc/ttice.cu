@@ -66,11 +66,13 @@ struct ttice_s {
   double* H = nullptr;
   double* Z = nullptr;   // kRR x kRR eigenvectors
   double* theta = nullptr;
-  double* KQ = nullptr;   // block-Krylov basis, s_max x kKry
-  double* KW = nullptr;   // s_max x kKryP
-  double* KW2 = nullptr;  // s_max x kKryP
-  double* KT = nullptr;   // kKry x kKryP
-  double* KV = nullptr;   // kKry x kKry (FP64 copy of the FP32 eigenvectors of H)
+  float* G32 = nullptr;   // FP32 copy of the Gram for the Krylov solver
+  float* KQ = nullptr;    // block-Krylov basis, s_max x kKry
+  float* KGQ = nullptr;   // G Q, s_max x kKry
+  float* KW2 = nullptr;   // s_max x kKryP
+  float* KT = nullptr;    // kKry x kKryP
+  float* KR32 = nullptr;  // kKryP x kKryP
+  double* KV = nullptr;   // s_max x kKryP (start block), also kKry x kKry eigenvectors of H
   double* res = nullptr;  // Ritz residual norms
   double* h_dbl = nullptr;  // pinned host scratch
   double* Ebuf = nullptr;  // R V for a column-side Gram (m x s)
@@ -178,7 +180,7 @@ void free_all(ttice_s* h) {
   for (int i = 0; i < kMaxD; ++i) {
     cudaFree(h->U[i]); cudaFree(h->Uf[i]); cudaFree(h->stage[i]); cudaFree(h->dstage[i]);
   }
-  void* ptrs[] = {h->KQ, h->KW, h->KW2, h->KT, h->KV, h->res,
+  void* ptrs[] = {h->G32, h->KQ, h->KGQ, h->KW2, h->KT, h->KR32, h->KV, h->res,
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
@@ -360,9 +362,10 @@ int rayleigh_ritz(ttice_s* h, int64_t s, int K, const double* d_eps, int max_new
   return TTICE_OK;
 }
 
-// CholQR2 of an s x p block X (column-major, ld s), in place; status (device int) set if the
-// block is numerically rank deficient.
-int cholqr2_block(ttice_s* h, double* X, int64_t s, int p, int* status, cudaStream_t st) {
+// CholQR2 of an FP32 s x p block X (column-major, ld s), in place: S = X^T X with FP32 products
+// accumulated in FP64, the inverse Cholesky factor in FP64, X <- X R^{-1} in FP32.  status (device
+// int) is set if the block is numerically rank deficient.
+int cholqr2_block32(ttice_s* h, float* X, int64_t s, int p, int* status, cudaStream_t st) {
   for (int pass = 0; pass < 2; ++pass) {
     TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)p * p * sizeof(double), st));
     GemmArgs g;  // S = X^T X
@@ -370,51 +373,56 @@ int cholqr2_block(ttice_s* h, double* X, int64_t s, int p, int* status, cudaStre
     g.A.p = X; g.A.rs = s; g.A.cs = 1;
     g.B.p = X; g.B.rs = 1; g.B.cs = s;
     g.C = h->Ssm; g.c_rs = 1; g.c_cs = p;
-    TT_CU((gemm<double, double, double, double, double>(g, st)));
+    TT_CU((gemm<float, float, float, double, float>(g, st)));
     TT_CU(launch_chol_inv(h->Ssm, p, h->Rinv, status, st));
+    TT_CU((launch_cast<double, float>(h->Rinv, h->KR32, (int64_t)p * p, st)));
     GemmArgs q;  // X2 = X Rinv
     q.M = s; q.N = p; q.K = p;
     q.A.p = X; q.A.rs = 1; q.A.cs = s;
-    q.B.p = h->Rinv; q.B.rs = 1; q.B.cs = p;
+    q.B.p = h->KR32; q.B.rs = 1; q.B.cs = p;
     q.C = h->KW2; q.c_rs = 1; q.c_cs = s;
-    TT_CU((gemm<double, double, double, double, double>(q, st)));
-    TT_CU(cudaMemcpyAsync(X, h->KW2, (size_t)s * p * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TT_CU((gemm<float, float, float, float, float>(q, st)));
+    TT_CU(cudaMemcpyAsync(X, h->KW2, (size_t)s * p * sizeof(float), cudaMemcpyDeviceToDevice, st));
   }
   return TTICE_OK;
 }
 
-// Candidate eigenvectors for the leading part of the Gram G (s x s, FP64) from a block Krylov
-// subspace: X_0 = orth(random s x p), X_i = orth((I - Q Q^T) G X_{i-1}) (CGS2 against the basis
-// Q = [X_0 .. X_{i-1}]), kKryBlocks blocks; H = Q^T G Q is diagonalised (FP32 Jacobi on the small
-// matrix) and its leading K eigenvectors, mapped back to R^s, are left in h->Q for the FP64
-// Rayleigh-Ritz step.  *K_out = 0 when the subspace is too small for the tolerance.
+// Candidate eigenvectors for the leading part of the Gram G (s x s) from a block Krylov subspace
+// built in FP32 (an FP32 copy of G): X_0 = orth(random s x p), X_i = orth((I - Q Q^T) G X_{i-1})
+// (CGS2 against the basis Q = [X_0 .. X_{i-1}]), kKryBlocks blocks; H = Q^T G Q (FP32 products,
+// FP64 accumulation) is diagonalised by FP32 Jacobi and its leading K eigenvectors, mapped back to
+// R^s in FP64, are left in h->Q for the FP64 Rayleigh-Ritz step, which alone decides the rank.
+// *K_out = 0 when the subspace is too small for the tolerance.
 int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStream_t st) {
   const int p = kKryP;
   *K_out = 0;
-  double* Qb = h->KQ;
+  float* Qb = h->KQ;
+  float* G32 = h->G32;
+  TT_CU((launch_cast<double, float>(h->G, G32, s * s, st)));
   TT_CU(cudaMemsetAsync(h->ibuf + 6, 0, sizeof(int), st));
-  TT_CU(launch_fill_hash(Qb, s * p, 0x5eedull + (uint64_t)s, st));
-  TT_TRY(cholqr2_block(h, Qb, s, p, h->ibuf + 6, st));
+  TT_CU(launch_fill_hash(h->KV, s * p, 0x5eedull + (uint64_t)s, st));
+  TT_CU((launch_cast<double, float>(h->KV, Qb, s * p, st)));
+  TT_TRY(cholqr2_block32(h, Qb, s, p, h->ibuf + 6, st));
   int nblk = kKryBlocks;
   for (int i = 1; i < nblk; ++i) {
-    const double* Xprev = Qb + (int64_t)(i - 1) * p * s;
-    double* Xi = Qb + (int64_t)i * p * s;
-    TT_CU(cudaMemsetAsync(Xi, 0, (size_t)s * p * sizeof(double), st));
+    const float* Xprev = Qb + (int64_t)(i - 1) * p * s;
+    float* Xi = Qb + (int64_t)i * p * s;
+    TT_CU(cudaMemsetAsync(Xi, 0, (size_t)s * p * sizeof(float), st));
     GemmArgs g;  // X_i = G X_{i-1}
     g.M = s; g.N = p; g.K = s; g.atomic = 1; g.allow_splitk = 1;
-    g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
+    g.A.p = G32; g.A.rs = s; g.A.cs = 1;
     g.B.p = Xprev; g.B.rs = 1; g.B.cs = s;
     g.C = Xi; g.c_rs = 1; g.c_cs = s;
-    TT_CU((gemm<double, double, double, double, double>(g, st)));
+    TT_CU((gemm<float, float, float, float, float>(g, st)));
     const int nq = i * p;
     for (int pass = 0; pass < 2; ++pass) {
-      TT_CU(cudaMemsetAsync(h->KT, 0, (size_t)nq * p * sizeof(double), st));
+      TT_CU(cudaMemsetAsync(h->KT, 0, (size_t)nq * p * sizeof(float), st));
       GemmArgs a;  // T = Q^T X_i
       a.M = nq; a.N = p; a.K = s; a.atomic = 1; a.allow_splitk = 1;
       a.A.p = Qb; a.A.rs = s; a.A.cs = 1;
       a.B.p = Xi; a.B.rs = 1; a.B.cs = s;
       a.C = h->KT; a.c_rs = 1; a.c_cs = nq;
-      TT_CU((gemm<double, double, double, double, double>(a, st)));
+      TT_CU((gemm<float, float, float, float, float>(a, st)));
       GemmArgs b;  // X_i -= Q T
       b.M = s; b.N = p; b.K = nq;
       b.A.p = Qb; b.A.rs = 1; b.A.cs = s;
@@ -422,26 +430,27 @@ int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStrea
       b.X.p = Xi; b.X.rs = 1; b.X.cs = s;
       b.alpha = -1.0; b.beta = 1.0;
       b.C = Xi; b.c_rs = 1; b.c_cs = s;
-      TT_CU((gemm<double, double, double, double, double>(b, st)));
+      TT_CU((gemm<float, float, float, float, float>(b, st)));
     }
-    TT_TRY(cholqr2_block(h, Xi, s, p, h->ibuf + 6, st));
+    TT_TRY(cholqr2_block32(h, Xi, s, p, h->ibuf + 6, st));
   }
   const int k = nblk * p;
-  // H = Q^T G Q
-  TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * k * sizeof(double), st));
+  // H = Q^T G Q (FP32 products, FP64 accumulation)
+  float* GQ32 = h->KGQ;
+  TT_CU(cudaMemsetAsync(GQ32, 0, (size_t)s * k * sizeof(float), st));
   GemmArgs g;
   g.M = s; g.N = k; g.K = s; g.atomic = 1; g.allow_splitk = 1;
-  g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
+  g.A.p = G32; g.A.rs = s; g.A.cs = 1;
   g.B.p = Qb; g.B.rs = 1; g.B.cs = s;
-  g.C = h->GQ; g.c_rs = 1; g.c_cs = s;
-  TT_CU((gemm<double, double, double, double, double>(g, st)));
+  g.C = GQ32; g.c_rs = 1; g.c_cs = s;
+  TT_CU((gemm<float, float, float, float, float>(g, st)));
   TT_CU(cudaMemsetAsync(h->H, 0, (size_t)k * k * sizeof(double), st));
   GemmArgs hh;
   hh.M = k; hh.N = k; hh.K = s; hh.atomic = 1; hh.allow_splitk = 1;
   hh.A.p = Qb; hh.A.rs = s; hh.A.cs = 1;
-  hh.B.p = h->GQ; hh.B.rs = 1; hh.B.cs = s;
+  hh.B.p = GQ32; hh.B.rs = 1; hh.B.cs = s;
   hh.C = h->H; hh.c_rs = k; hh.c_cs = 1;
-  TT_CU((gemm<double, double, double, double, double>(hh, st)));
+  TT_CU((gemm<float, float, float, double, float>(hh, st)));
   TT_CU(cudaMemsetAsync(h->bjflags, 0, 4 * sizeof(int), st));
   TT_CU(jacobi_eig<float>(h->H, k, k, h->w32, h->V32, h->bjw32, h->bjflags + 3, st));
   TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, k * sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -462,14 +471,14 @@ int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStrea
   }
   if (r32 < 0 || r32 + 8 > k - 8) return TTICE_OK;  // subspace too small: full solver
   const int K = std::min(k, r32 + 8);
-  // candidates Q = Q_krylov V[:, :K]
+  // candidates Q = Q_krylov V[:, :K] in FP64
   TT_CU(launch_to_f64<float>(h->V32, (int64_t)k * K, h->KV, st));
   GemmArgs c;
   c.M = s; c.N = K; c.K = k;
   c.A.p = Qb; c.A.rs = 1; c.A.cs = s;
   c.B.p = h->KV; c.B.rs = 1; c.B.cs = k;
   c.C = h->Q; c.c_rs = 1; c.c_cs = s;
-  TT_CU((gemm<double, double, double, double, double>(c, st)));
+  TT_CU((gemm<float, double, double, double, double>(c, st)));
   *K_out = K;
   return TTICE_OK;
 }
@@ -965,11 +974,13 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->bjw32, block_jacobi_work<float>((int)s));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->fro, 1);
   if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 4);
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->KQ, s * kKry);
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->KW, s * kKryP);
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->KW2, s * kKryP);
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->KT, kKry * kKryP);
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->KV, kKry * kKry);
+  if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->G32, s * s);
+  if (rc == TTICE_OK) rc = dalloc<float>(&h->KQ, s * kKry);
+  if (rc == TTICE_OK) rc = dalloc<float>(&h->KGQ, s * kKry);
+  if (rc == TTICE_OK) rc = dalloc<float>(&h->KW2, s * kKryP);
+  if (rc == TTICE_OK) rc = dalloc<float>(&h->KT, kKry * kKryP);
+  if (rc == TTICE_OK) rc = dalloc<float>(&h->KR32, kKryP * kKryP);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->KV, std::max<int64_t>(s * kKryP, kKry * kKry));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->res, kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Q, s * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Q2, s * kRR);
