@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(32 * BJ<T>::BS) bj_solve(const T* A, int sp, i
   }
   __syncthreads();
   const T teps = BJ<T>::eps();
-  const T floor_abs = (T)((double)teps * sqrt(*fro));
+  const T floor_abs = (T)((double)teps * sqrt(*fro));  // rounding level, see jacobi_kernel
   int any = 0;
   for (int round2 = 0; round2 < N2 - 1; ++round2) {
     int p, q;

@@ -9,6 +9,7 @@
 // shared memory when it fits, otherwise in global scratch.  A rotation is skipped when
 // |a_pq| <= eps_T sqrt(|a_pp a_qq|); sweeps stop when a sweep performs no rotation or after a fixed
 // sweep limit (reported through `status`, never by spinning).
+#include <algorithm>
 #include <cfloat>
 #include <mutex>
 
@@ -38,7 +39,9 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, in
   T* V = work + (use_smem ? 0 : (int64_t)s * lda);  // s x s column-major, ld s
   const int tid = threadIdx.x, nt = blockDim.x;
 
-  __shared__ double red[32];
+  __shared__ double red[33];
+  __shared__ int stall;
+  __shared__ double prev_off;
   double fro = 0.0;
   for (int64_t e = tid; e < (int64_t)s * s; e += nt) {
     const int i = (int)(e / s), j = (int)(e % s);
@@ -58,8 +61,8 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, in
   }
   __syncthreads();
   // Off-diagonal entries below eps_T ||A||_F are at the rounding level of the working precision:
-  // rotating them moves no eigenvalue beyond that level and does not settle (each rotation
-  // regenerates noise of the same size), so they end the iteration.
+  // rotating them moves no eigenvalue beyond that level.  Rotations at that level regenerate noise of
+  // the same size, so the sweeps also stop once the off-diagonal norm has stagnated (see below).
   const T floor_abs = (T)((double)Lim<T>::eps() * red[0]);
   __syncthreads();
 
@@ -121,7 +124,26 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, in
     }
     __syncthreads();
     if (nrot == 0) break;
+    // off-diagonal norm after this sweep: Jacobi converges quadratically, so a sweep that does not
+    // at least quarter it is rotating rounding noise -- stop there
+    double off = 0.0;
+    for (int64_t e = tid; e < (int64_t)s * s; e += nt) {
+      const int i = (int)(e / s), j = (int)(e % s);
+      if (i != j) { const double a = (double)A[i * lda + j]; off += a * a; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
     __syncthreads();
+    if ((tid & 31) == 0) red[1 + (tid >> 5)] = off;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nt / 32; ++w) t += red[1 + w];
+      stall = (sweep > 0 && t > 0.25 * prev_off) ? 1 : 0;
+      prev_off = t;
+    }
+    __syncthreads();
+    if (stall) break;
   }
   if (tid == 0 && status) *status = (sweep >= kMaxSweeps) ? 1 : 0;
   // sort by descending eigenvalue (ties by index) and write outputs
@@ -229,8 +251,12 @@ cudaError_t jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* V, T* work,
                                     (int)kEigSmemMax);
   });
   TT_CUDA(attr_err);
+  // threads: about four rotation-update items per thread per phase, so that small problems do not
+  // pay for 1024-thread barriers
+  const int npairs = (s + 1) / 2;
+  int threads = (int)std::min<int64_t>(kEigThreads, std::max<int64_t>(64, ((int64_t)npairs * s / 4 + 31) / 32 * 32));
   note_launch();
-  jacobi_kernel<T><<<1, kEigThreads, smem, st>>>(G, ldg, s, w, V, work, status, use_smem);
+  jacobi_kernel<T><<<1, threads, smem, st>>>(G, ldg, s, w, V, work, status, use_smem);
   return cudaGetLastError();
 }
 

@@ -188,6 +188,8 @@ cudaError_t run(const GemmArgs& g, cudaStream_t st) {
 template <typename TA, typename TB, typename TX, typename TC, typename ACC>
 cudaError_t gemm(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.nbatch <= 0) return cudaSuccess;
+  if (g.M <= 16 && g.N <= 16) return run<TA, TB, TX, TC, ACC, 16, 16, 16, 1, 1>(g, st);
+  if (g.M <= 32 && g.N <= 32) return run<TA, TB, TX, TC, ACC, 32, 32, 16, 2, 2>(g, st);
   if (g.M <= 16) return run<TA, TB, TX, TC, ACC, 16, 256, 16, 2, 8>(g, st);
   if (g.M <= 32) return run<TA, TB, TX, TC, ACC, 32, 128, 16, 4, 4>(g, st);
   if (g.N <= 16) return run<TA, TB, TX, TC, ACC, 256, 16, 16, 8, 2>(g, st);
@@ -211,6 +213,7 @@ TT_GEMM_INST(float, double, float, float, float)
 // accumulation across K-slabs
 TT_GEMM_INST(float, float, float, double, double)
 TT_GEMM_INST(float, float, float, double, float)
+TT_GEMM_INST(float, float, double, double, float)
 TT_GEMM_INST(float, double, double, double, double)
 // reconstruction into FP32 outputs
 TT_GEMM_INST(double, double, double, float, double)

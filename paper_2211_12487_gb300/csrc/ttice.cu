@@ -78,6 +78,10 @@ struct ttice_s {
   double* Ebuf = nullptr;  // R V for a column-side Gram (m x s)
   int64_t max_ms = 0;
   double* Vn = nullptr;  // new directions, max_m x kRR
+  const double* dir_src = nullptr;    // eigen / Ritz vectors of the current truncated SVD (s x K)
+  const double* dir_scale = nullptr;  // their eigenvalues (column-side Grams: 1/sqrt scaling)
+  bool dir_left = true;
+  int64_t dir_s = 0;
   double* Vn2 = nullptr;
   double* P = nullptr;   // cap x kRR projections for CGS2
   int64_t max_m = 0;
@@ -144,7 +148,7 @@ void ph_collect(ttice_s* h) {
 
 constexpr int kRR = 96;         // largest Rayleigh-Ritz subspace
 constexpr int kDirectEig = 32;  // Gram matrices up to this size are diagonalised in FP64 directly
-constexpr int kMaxEig = 1024;
+constexpr int kMaxEig = 4608;  // largest Gram side (128^3 x 4 flow: 33 x 128 = 4224)
 constexpr int kMaxSweeps64 = 15;  // block Jacobi sweep limits (quadratic convergence needs ~6-10)
 constexpr int kMaxSweeps32 = 12;
 constexpr int kKryP = 8;         // block size of the Krylov eigen-solver
@@ -512,6 +516,43 @@ int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
   return TTICE_OK;
 }
 
+// Energy of R along each eigenvector of its Gram held in h->V64 (s x s, a complete basis),
+// measured on R itself (||q_j^T R||^2 or ||R v_j||^2) into h->theta, so that the truncation tail
+// does not inherit the squared rounding of the Gram matrix.  The basis is complete, so these
+// energies sum to ||R||^2 and the tail is summed directly.
+template <typename WT>
+int measure_energies(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int64_t s, bool left,
+                     cudaStream_t st) {
+  double* e = h->theta;
+  TT_CU(cudaMemsetAsync(e, 0, s * sizeof(double), st));
+  // FP64 path: FP64 products of FP64 residuals.  Mixed path (FP32 residual): FP32 products of the
+  // FP32 residual and the FP32 eigenvectors, accumulated in FP64 (the residual itself carries FP32
+  // rounding, so FP64 products would add no accuracy and cost 64x on GB300).
+  using VT = WT;
+  const VT* V = (sizeof(WT) == 8) ? reinterpret_cast<const VT*>(h->V64) : reinterpret_cast<const VT*>(h->V32);
+  using ACC = typename std::conditional<sizeof(WT) == 8, double, float>::type;
+  if (left) {
+    GemmArgs g;  // E = V^T R, row norms
+    g.M = s; g.N = L; g.K = m;
+    g.A.p = V; g.A.rs = s; g.A.cs = 1;
+    g.B.p = R; g.B.rs = L; g.B.cs = 1; g.B.bs1 = m * L;
+    g.store = 0; g.norm = e; g.norm_rows = 1;
+    g.nbatch = nsel;
+    TT_CU((gemm<VT, WT, double, double, ACC>(g, st)));
+  } else {
+    TT_CU(cudaMemsetAsync(h->Ebuf, 0, (size_t)m * s * sizeof(double), st));
+    GemmArgs g;  // E = R V (m x s), column norms
+    g.M = m; g.N = s; g.K = L; g.atomic = 1; g.allow_splitk = 1;
+    g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
+    g.B.p = V; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
+    g.C = h->Ebuf; g.c_rs = 1; g.c_cs = m;
+    g.nbatch = nsel;
+    TT_CU((gemm<WT, VT, double, double, ACC>(g, st)));
+    TT_CU(launch_col_norms(h->Ebuf, m, (int)s, m, e, st));
+  }
+  return TTICE_OK;
+}
+
 // ---------------------------------------------------------------- truncated SVD of one residual
 // Residual R (observation-major blocks, m x L each, nsel blocks) -> new directions Vn (m x rR,
 // column-major, ld m), rR returned through *rR_out.
@@ -564,34 +605,12 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
       TT_CU(cudaMemcpyAsync(h->ibuf + 1, h->bjflags + 3, sizeof(int), cudaMemcpyDeviceToDevice, st));
       TT_CU(cudaMemcpyAsync(h->ibuf + 3, h->bjflags + 2, sizeof(int), cudaMemcpyDeviceToDevice, st));
     }
-    // Energy of R along each eigenvector, measured on R itself (||q_j^T R||^2 or ||R v_j||^2) so
-    // that the truncation tail does not inherit the squared rounding of the Gram matrix.  The
-    // eigenbasis is complete, so these energies sum to ||R||^2 and the tail is summed directly.
+    TT_TRY((measure_energies<WT>(h, R, m, L, nsel, s, left, st)));
     double* e = h->theta;
-    TT_CU(cudaMemsetAsync(e, 0, s * sizeof(double), st));
-    if (left) {
-      GemmArgs g;  // E = V^T R, row norms
-      g.M = s; g.N = L; g.K = m;
-      g.A.p = h->V64; g.A.rs = s; g.A.cs = 1;
-      g.B.p = R; g.B.rs = L; g.B.cs = 1; g.B.bs1 = m * L;
-      g.store = 0; g.norm = e; g.norm_rows = 1;
-      g.nbatch = nsel;
-      TT_CU((gemm<double, WT, double, double, double>(g, st)));
-    } else {
-      TT_CU(cudaMemsetAsync(h->Ebuf, 0, (size_t)m * s * sizeof(double), st));
-      GemmArgs g;  // E = R V (m x s), column norms
-      g.M = m; g.N = s; g.K = L; g.atomic = 1; g.allow_splitk = 1;
-      g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
-      g.B.p = h->V64; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
-      g.C = h->Ebuf; g.c_rs = 1; g.c_cs = m;
-      g.nbatch = nsel;
-      TT_CU((gemm<WT, double, double, double, double>(g, st)));
-      TT_CU(launch_col_norms(h->Ebuf, m, (int)s, m, e, st));
-    }
     TT_CU(launch_rank_rule(e, (int)s, 1, h->trace, d_eps, max_new, h->ibuf, st));
     Vdir = h->V64; thet = h->w64; K = (int)s;
   } else {
-    bool have = false;
+    bool have = false, big = false;
     if (s > kKrylovMin) {
       // block Krylov candidates + FP64 Rayleigh-Ritz, kept only if certified
       int Kk = 0;
@@ -630,11 +649,22 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
       if (std::sqrt(tail) <= eps_c) r32 = j; else break;
     }
     K = std::min<int>((int)s, std::min(r32 + 8, kRR));
-    if (r32 + 1 > kRR) return TTICE_ECAPACITY;
-    TT_CU(launch_to_f64<float>(h->V32, s * K, h->Q, st));
-    TT_TRY(rayleigh_ritz(h, s, K, d_eps, max_new, st));
+    if (r32 + 8 > kRR) {
+      // more directions than one Rayleigh-Ritz problem holds: use the whole FP32 eigenbasis, promoted
+      // to FP64, with the energy of R along each vector measured on R itself (complete basis, so the
+      // truncation tail is a direct sum, as on the FP64 path)
+      TT_CU(launch_to_f64<float>(h->V32, s * s, h->V64, st));
+      TT_CU(launch_to_f64<float>(h->w32, s, h->w64, st));
+      TT_TRY((measure_energies<WT>(h, R, m, L, nsel, s, left, st)));
+      TT_CU(launch_rank_rule(h->theta, (int)s, 1, h->trace, d_eps, max_new, h->ibuf, st));
+      Vdir = h->V64; thet = h->theta; K = (int)s;
+      have = true;
+      big = true;
     }
-    Vdir = h->Q2; thet = h->theta;
+    if (!big) TT_CU(launch_to_f64<float>(h->V32, s * K, h->Q, st));
+    if (!big) TT_TRY(rayleigh_ritz(h, s, K, d_eps, max_new, st));
+    }
+    if (!big) { Vdir = h->Q2; thet = h->theta; }
   }
   TT_CU(cudaMemcpyAsync(h->h_int, h->ibuf, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   ph_end(h, st);
@@ -645,25 +675,34 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   if (rR < 0) return TTICE_ECAPACITY;  // Rayleigh-Ritz subspace too small for the tolerance
   *rR_out = rR;
   if (rR == 0) return TTICE_OK;
-  if (rR > kRR) return TTICE_ECAPACITY;
-  // directions in R^m (part of the eigen-solve phase)
-  ph_begin(h, PH_EIG, st, 0.0, 0.0);
-  if (left) {
+  h->dir_src = Vdir;
+  h->dir_scale = thet;
+  h->dir_left = left;
+  h->dir_s = s;
+  return TTICE_OK;
+}
+
+// New directions c0 .. c0+k-1 of the current truncated SVD into Vn (m x k): the leading
+// eigenvectors themselves for a row-side Gram, u_j = R v_j / sqrt(theta_j) for a column-side one.
+template <typename WT>
+int build_dirs(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int c0, int k,
+               cudaStream_t st) {
+  const int64_t s = h->dir_s;
+  const double* Vdir = h->dir_src + (int64_t)c0 * s;
+  if (h->dir_left) {
     TT_CU(cudaMemcpy2DAsync(h->Vn, m * sizeof(double), Vdir, s * sizeof(double), m * sizeof(double),
-                            rR, cudaMemcpyDeviceToDevice, st));
+                            k, cudaMemcpyDeviceToDevice, st));
   } else {
-    // u_j = R v_j / sqrt(theta_j), v_j indexed by (observation, l)
-    TT_CU(cudaMemsetAsync(h->Vn, 0, (size_t)m * rR * sizeof(double), st));
+    TT_CU(cudaMemsetAsync(h->Vn, 0, (size_t)m * k * sizeof(double), st));
     GemmArgs g;
-    g.M = m; g.N = rR; g.K = L; g.atomic = 1; g.allow_splitk = 1;
+    g.M = m; g.N = k; g.K = L; g.atomic = 1; g.allow_splitk = 1;
     g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
     g.B.p = Vdir; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
     g.C = h->Vn; g.c_rs = 1; g.c_cs = m;
     g.nbatch = nsel;
     TT_CU((gemm<WT, double, double, double, double>(g, st)));
-    TT_CU(launch_scale_cols_rsqrt(h->Vn, m, rR, m, thet, st));
+    TT_CU(launch_scale_cols_rsqrt(h->Vn, m, k, m, h->dir_scale + c0, st));
   }
-  ph_end(h, st);
   return TTICE_OK;
 }
 
@@ -822,12 +861,19 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
         if (rc != TTICE_OK) break;
         if (rR > 0) {
           if (ri + rR > h->cap[i + 1]) { rc = TTICE_ECAPACITY; break; }
-          ph_begin(h, PH_ORTH, st, 8.0 * m * (2.0 * ri + 3.0 * rR),
-                   8.0 * m * ri * rR + 8.0 * m * (double)rR * rR);
-          rc = orthonormalize_append(h, i, m, rR, st);
-          ph_end(h, st);
+          // append in chunks of at most kRR directions; each chunk is re-orthogonalised against the
+          // core including the chunks already appended (block CGS2)
+          for (int c0 = 0; c0 < rR && rc == TTICE_OK; c0 += kRR) {
+            const int kc = std::min(kRR, rR - c0);
+            const int64_t rcur = h->r[i + 1];
+            ph_begin(h, PH_ORTH, st, 8.0 * m * (2.0 * rcur + 3.0 * kc),
+                     8.0 * m * rcur * kc + 8.0 * m * (double)kc * kc);
+            rc = build_dirs<WT>(h, R, m, L, nsel, c0, kc, st);
+            if (rc == TTICE_OK) rc = orthonormalize_append(h, i, m, kc, st);
+            ph_end(h, st);
+            if (rc == TTICE_OK) h->r[i + 1] = rcur + kc;
+          }
           if (rc != TTICE_OK) break;
-          h->r[i + 1] = ri + rR;
           grew = rR;
         }
       }
@@ -968,7 +1014,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK) rc = dalloc<float>(&h->w32, s);
   if (rc == TTICE_OK) rc = dalloc<float>(&h->V32, s * s);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->w64, std::max<int64_t>(s, kRR));
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->V64, std::max<int64_t>(s * s, (int64_t)kRR * kRR));
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->V64, std::max<int64_t>(s * s, (int64_t)kRR * kRR));  // both paths
   if (rc == TTICE_OK) rc = dalloc<double>(&h->work64, 2 * std::max<int64_t>(s, kRR) * (std::max<int64_t>(s, kRR) + 1));
   if (rc == TTICE_OK && h->wt_bytes == 8) rc = dalloc<double>(&h->bjw64, block_jacobi_work<double>((int)s));
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->bjw32, block_jacobi_work<float>((int)s));
