@@ -8,7 +8,7 @@ frames.  A step is one TT-ICE* update of one increment through the whole path (f
 per-observation errors, skip test, subselection, per-core residual / Gram / truncated eigen-solve /
 CGS2 / append / padding, final projection and last-core append).  The stream is consumed in order:
 W warm-up increments, then K timed increments, each a fresh 29.5 MB slice of a pre-generated stream
-several GB long, so no timed step reads input that is resident in L2.
+of (W + K) x 29.5 MB, so no timed step reads input that an earlier step left in L2.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
 """
@@ -152,8 +152,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--fp64-steps", type=int, default=12, help="steps of the FP64 path timed for comparison")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle work for cpu_baseline (0 leaves it out)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="open the CUDA profiler API (cudaProfilerStart/Stop) around the timed steps only, "
+                         "for ncu --profile-from-start off")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -197,14 +201,20 @@ def main():
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         l0 = T.ttice_kernel_launches()
         barrier()
+        window = profile and args.profile_window
+        if window:
+            torch.cuda.profiler.start()
         evs[0].record(st)
         stats = []
         for k in range(steps):
             i = args.warmup + k
             s = h.update(Y[i * b:(i + 1) * b])
             evs[k + 1].record(st)
-            stats.append((s.skipped, s.n_selected, list(s.ranks[:len(DIMS) + 2])))
+            stats.append((s.skipped, s.n_selected, list(s.ranks[:len(DIMS) + 2]), s.krylov_solves,
+                          s.krylov_fallbacks, s.eig_sweep_limit))
         barrier()
+        if window:
+            torch.cuda.profiler.stop()
         launches = T.ttice_kernel_launches() - l0
         lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
         total = evs[0].elapsed_time(evs[-1])
@@ -277,7 +287,7 @@ def main():
                 "avg_launch_ms": ph["ms"] / ph["count"]}
     phase_share = {n: round(prof[n]["ms"] / max(total_ms, 1e-9), 4) for n in names}
     cpu = None
-    if ws == 1 or rank == 0:
+    if (ws == 1 or rank == 0) and args.cpu_budget > 0:
         v, k, busy, threads = oracle_elements_per_s(args.cpu_budget, b)
         cpu = {"value": v, "unit": "elements/s", "cores": threads, "kind": "oracle",
                "sample": f"first {k} increments of {b} frames of the same stream ({busy:.1f} s CPU)"}
@@ -288,11 +298,15 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch": b, "precision": args.precision,
-                   "l2": "each step reads a fresh 29.5 MB slice of a multi-GB pre-generated stream",
+                   "l2": f"each step reads a fresh 29.5 MB slice of a {n_inc * b * N * 4 / 1e9:.2f} GB "
+                         "pre-generated stream (no timed step re-reads an earlier step's input)",
                    "parallelism": f"replicas{ws}"},
         "latency_ms": {"p50": statistics.median(lat), "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "max": max(lat)},
         "increments": {"timed": args.steps, "skipped": skipped, "final_ranks": stats[-1][2]},
+        "eigen_solves": {"krylov_certified": sum(x[3] for x in stats),
+                         "krylov_fallbacks": sum(x[4] for x in stats),
+                         "sweep_limit_hits": sum(x[5] for x in stats)},
         "roofline": roof,
         "dominant_phase": dom,
         "phase_share": phase_share,

@@ -22,7 +22,11 @@ template <typename T> struct Lim;
 template <> struct Lim<float> { static __device__ float eps() { return FLT_EPSILON; } };
 template <> struct Lim<double> { static __device__ double eps() { return DBL_EPSILON; } };
 
-constexpr int kMaxSweeps = 40;
+// sweep caps: quadratic convergence reaches the working precision in well under these; what
+// remains beyond them is rotation of rounding noise
+template <typename T> struct SweepCap;
+template <> struct SweepCap<float> { static constexpr int value = 14; };
+template <> struct SweepCap<double> { static constexpr int value = 30; };
 constexpr int kEigThreads = 1024;
 constexpr size_t kEigSmemMax = 200 * 1024;  // dynamic shared memory cap of jacobi_kernel
 
@@ -64,13 +68,14 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, in
   // rotating them moves no eigenvalue beyond that level.  Rotations at that level regenerate noise of
   // the same size, so the sweeps also stop once the off-diagonal norm has stagnated (see below).
   const T floor_abs = (T)((double)Lim<T>::eps() * red[0]);
+  const double off_gate = 64.0 * sqrt((double)s) * (double)Lim<T>::eps() * red[0];
   __syncthreads();
 
   const int np = (s + 1) & ~1;  // players, with a dummy when s is odd
   const int npairs = np / 2;
   const T teps = Lim<T>::eps();
   int sweep = 0;
-  for (; sweep < kMaxSweeps; ++sweep) {
+  for (; sweep < SweepCap<T>::value; ++sweep) {
     if (tid == 0) nrot = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
@@ -124,8 +129,9 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, in
     }
     __syncthreads();
     if (nrot == 0) break;
-    // off-diagonal norm after this sweep: Jacobi converges quadratically, so a sweep that does not
-    // at least quarter it is rotating rounding noise -- stop there
+    // off-diagonal norm after this sweep.  Early sweeps may shrink it by as little as ~0.6; once it
+    // is down at the rounding level (below off_gate) a sweep that does not halve it is rotating
+    // rounding noise -- stop there
     double off = 0.0;
     for (int64_t e = tid; e < (int64_t)s * s; e += nt) {
       const int i = (int)(e / s), j = (int)(e % s);
@@ -139,13 +145,13 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, in
     if (tid == 0) {
       double t = 0.0;
       for (int w = 0; w < nt / 32; ++w) t += red[1 + w];
-      stall = (sweep > 0 && t > 0.25 * prev_off) ? 1 : 0;
+      stall = (sweep > 0 && t > 0.25 * prev_off && t <= off_gate * off_gate) ? 1 : 0;
       prev_off = t;
     }
     __syncthreads();
     if (stall) break;
   }
-  if (tid == 0 && status) *status = (sweep >= kMaxSweeps) ? 1 : 0;
+  if (tid == 0 && status) *status = (sweep >= SweepCap<T>::value) ? 1 : 0;
   // sort by descending eigenvalue (ties by index) and write outputs
   for (int i = tid; i < s; i += nt) {
     const T di = A[i * lda + i];
@@ -156,6 +162,258 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, in
     }
     w[rank] = di;
     for (int r = 0; r < s; ++r) Vout[(int64_t)rank * s + r] = V[(int64_t)i * s + r];
+  }
+}
+
+// ---- small problems (s <= 128): everything in shared memory, one barrier per round ----
+//
+// The same cyclic Jacobi method and round-robin ordering as above, arranged so that a round needs a
+// single barrier.  Each thread owns one 2x2 block (pair i rows, pair j columns) of the round: it
+// forms R_i B R_j^T from the matrix before the round (A_in) into a second buffer (A_out), writing the
+// mirrored block too, and applies rotation i to the V entries of rows {p_j, q_j}, which no other
+// thread touches in that round.  The rotations of the next round are computed in the same phase by
+// re-forming, from A_in, the three entries of each next pair that this round produces (with the same
+// helper functions, so they agree with what is written), which removes the barrier between the
+// angle computation and the update.
+template <typename T>
+__device__ __forceinline__ void rr_pair(int k, int r, int m, int& p, int& q) {
+  // (r + k) mod m and (r - k) mod m for 0 <= r, k < m, without an integer division
+  if (k == 0) { p = r; q = m; }
+  else {
+    p = r + k; if (p >= m) p -= m;
+    q = r - k; if (q < 0) q += m;
+  }
+  if (p > q) { const int t = p; p = q; q = t; }
+}
+
+// pair index of player x in round r (inverse of rr_pair); m = players - 1
+__device__ __forceinline__ int rr_pair_of(int x, int r, int m) {
+  if (x == m || x == r) return 0;
+  int k = x - r;
+  if (k < 0) k += m;
+  return (2 * k <= m) ? k : m - k;
+}
+
+template <typename T>
+__device__ __forceinline__ void make_rotation(T app, T aqq, T apq, T floor_abs, T& c, T& sn, T& t) {
+  c = T(1); sn = T(0); t = T(0);
+  if (fabs(apq) > floor_abs && fabs(apq) > Lim<T>::eps() * sqrt(fabs(app * aqq))) {
+    const T tau = (aqq - app) / (T(2) * apq);
+    t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+    c = T(1) / sqrt(T(1) + t * t);
+    sn = t * c;
+  }
+}
+
+// new diagonal entries of a rotated pair: a_pp - t a_pq and a_qq + t a_pq (a_pq becomes 0)
+template <typename T>
+__device__ __forceinline__ T diag_after(T a, T t, T apq, bool is_p) {
+  return is_p ? fma(-t, apq, a) : fma(t, apq, a);
+}
+
+// R_i B R_j^T of one 2x2 block, R = [[c, -s], [s, c]]; entries of rows/columns that are the dummy
+// player are zero in B and never read from the result
+template <typename T>
+__device__ __forceinline__ void block_after(const T* A, int lda, int s, int pi, int qi, int pj, int qj,
+                                            T ci, T si, T cj, T sj, T o[4]) {
+  const bool ri = qi < s, rj = qj < s;
+  const T b00 = A[pi * lda + pj];
+  const T b01 = rj ? A[pi * lda + qj] : T(0);
+  const T b10 = ri ? A[qi * lda + pj] : T(0);
+  const T b11 = (ri && rj) ? A[qi * lda + qj] : T(0);
+  const T m00 = fma(ci, b00, -(si * b10)), m01 = fma(ci, b01, -(si * b11));
+  const T m10 = fma(si, b00, ci * b10), m11 = fma(si, b01, ci * b11);
+  o[0] = fma(cj, m00, -(sj * m01));
+  o[1] = fma(sj, m00, cj * m01);
+  o[2] = fma(cj, m10, -(sj * m11));
+  o[3] = fma(sj, m10, cj * m11);
+}
+
+constexpr int kSmallEigMax = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kEigThreads) jacobi_small_kernel(const double* G, int64_t ldg, int s,
+                                                                   T* w, T* Vout, int* status) {
+  constexpr int NP = kSmallEigMax / 2;   // most pairs of a round
+  constexpr int NA = NP * (NP + 1) / 2;  // most 2x2 blocks with i <= j
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T rc[2][NP], rs[2][NP], rt[2][NP];  // rotation of each pair: c, s, t = s / c
+  __shared__ int rpq[2][NP];                     // the pair itself: p | q << 16
+  __shared__ unsigned short ij_tab[NA];          // i << 8 | j of the blocks a thread owns
+  __shared__ double red[33];
+  __shared__ int rotated, stop;
+  __shared__ double prev_off;
+  const int lda = s + 1;
+  T* Ain = reinterpret_cast<T*>(smem_raw);
+  T* Aout = Ain + (int64_t)s * lda;
+  T* V = Aout + (int64_t)s * lda;  // s x s column-major, ld s
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  double fro = 0.0;
+  for (int e = tid; e < s * s; e += nt) {
+    const int i = e / s, j = e - i * s;
+    const double g = G[i * ldg + j];
+    fro += g * g;
+    Ain[i * lda + j] = (T)g;
+    V[j * s + i] = (i == j) ? T(1) : T(0);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+  if ((tid & 31) == 0) red[tid >> 5] = fro;
+  const int np = (s + 1) & ~1;
+  const int m = np - 1;
+  const int npairs = np / 2;
+  const int nA = npairs * (npairs + 1) / 2;
+  for (int t = tid; t < nA; t += nt) {
+    int i = 0, off = 0;
+    while (off + (npairs - i) <= t) { off += npairs - i; ++i; }
+    ij_tab[t] = (unsigned short)((i << 8) | (i + (t - off)));
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < nt / 32; ++q) t += red[q];
+    red[32] = sqrt(t);
+    rotated = 0;
+    stop = 0;
+  }
+  __syncthreads();
+  const T floor_abs = (T)((double)Lim<T>::eps() * red[32]);
+  const double off_gate = 64.0 * sqrt((double)s) * (double)Lim<T>::eps() * red[32];
+  int cur = 0;
+  for (int k = tid; k < npairs; k += nt) {
+    int p, q;
+    rr_pair<T>(k, 0, m, p, q);
+    T c = T(1), sn = T(0), t = T(0);
+    if (q < s) make_rotation(Ain[p * lda + p], Ain[q * lda + q], Ain[p * lda + q], floor_abs, c, sn, t);
+    rc[0][k] = c; rs[0][k] = sn; rt[0][k] = t;
+    rpq[0][k] = p | (q << 16);
+  }
+  __syncthreads();
+  // V items: (pair i, row x), rows fastest so that a warp touches consecutive words
+  const int vi0 = tid / s, vx0 = tid - vi0 * s, vdi = nt / s, vdx = nt - vdi * s;
+
+  int sweep = 0;
+  for (; sweep < SweepCap<T>::value; ++sweep) {
+    for (int round = 0; round < m; ++round) {
+      // A <- J^T A J, one 2x2 block (and its mirror) per item, from Ain into Aout
+      for (int t = tid; t < nA; t += nt) {
+        const int ij = ij_tab[t];
+        const int i = ij >> 8, j = ij & 255;
+        const int pqi = rpq[cur][i];
+        const int pi = pqi & 0xffff, qi = pqi >> 16;
+        const T si = rs[cur][i];
+        if (i == j) {
+          if (qi < s) {
+            const T app = Ain[pi * lda + pi], aqq = Ain[qi * lda + qi], apq = Ain[pi * lda + qi];
+            if (si != T(0)) {
+              const T tt = rt[cur][i];
+              Aout[pi * lda + pi] = diag_after(app, tt, apq, true);
+              Aout[qi * lda + qi] = diag_after(aqq, tt, apq, false);
+              Aout[pi * lda + qi] = T(0);
+              Aout[qi * lda + pi] = T(0);
+              rotated = 1;
+            } else {
+              Aout[pi * lda + pi] = app;
+              Aout[qi * lda + qi] = aqq;
+              Aout[pi * lda + qi] = apq;
+              Aout[qi * lda + pi] = apq;
+            }
+          } else {
+            Aout[pi * lda + pi] = Ain[pi * lda + pi];
+          }
+        } else {
+          const int pqj = rpq[cur][j];
+          const int pj = pqj & 0xffff, qj = pqj >> 16;
+          T o[4];
+          block_after(Ain, lda, s, pi, qi, pj, qj, rc[cur][i], si, rc[cur][j], rs[cur][j], o);
+          Aout[pi * lda + pj] = o[0];
+          Aout[pj * lda + pi] = o[0];
+          if (qj < s) { Aout[pi * lda + qj] = o[1]; Aout[qj * lda + pi] = o[1]; }
+          if (qi < s) { Aout[qi * lda + pj] = o[2]; Aout[pj * lda + qi] = o[2]; }
+          if (qi < s && qj < s) { Aout[qi * lda + qj] = o[3]; Aout[qj * lda + qi] = o[3]; }
+        }
+      }
+      // V <- V J, in place: item (i, x) owns V[x, p_i] and V[x, q_i]
+      for (int i = vi0, x = vx0; i < npairs;) {
+        const T si = rs[cur][i];
+        if (si != T(0)) {  // a rotation implies q_i < s
+          const int pqi = rpq[cur][i];
+          const int pi = pqi & 0xffff, qi = pqi >> 16;
+          const T ci = rc[cur][i];
+          const T vp = V[pi * s + x], vq = V[qi * s + x];
+          V[pi * s + x] = fma(ci, vp, -(si * vq));
+          V[qi * s + x] = fma(si, vp, ci * vq);
+        }
+        x += vdx;
+        i += vdi;
+        if (x >= s) { x -= s; ++i; }
+      }
+      // pairs and angles of the next round, from the entries this round produces
+      const int rn = (round + 1 == m) ? 0 : round + 1;
+      for (int k = tid; k < npairs; k += nt) {
+        int p, q;
+        rr_pair<T>(k, rn, m, p, q);
+        T c = T(1), sn = T(0), t = T(0);
+        if (q < s) {
+          const int a = rr_pair_of(p, round, m), b = rr_pair_of(q, round, m);
+          const int pqa = rpq[cur][a], pqb = rpq[cur][b];
+          const int pa = pqa & 0xffff, qa = pqa >> 16, pb = pqb & 0xffff, qb = pqb >> 16;
+          T app = Ain[p * lda + p], aqq = Ain[q * lda + q];
+          if (rs[cur][a] != T(0)) app = diag_after(app, rt[cur][a], Ain[pa * lda + qa], p == pa);
+          if (rs[cur][b] != T(0)) aqq = diag_after(aqq, rt[cur][b], Ain[pb * lda + qb], q == pb);
+          T apq;
+          if (a == b) {  // only when s <= 2: the same pair again
+            apq = (rs[cur][a] != T(0)) ? T(0) : Ain[p * lda + q];
+          } else {
+            const bool alo = a < b;
+            const int lo = alo ? a : b, hi = alo ? b : a;
+            const int pl = alo ? pa : pb, ql = alo ? qa : qb, ph = alo ? pb : pa, qh = alo ? qb : qa;
+            T o[4];
+            block_after(Ain, lda, s, pl, ql, ph, qh, rc[cur][lo], rs[cur][lo], rc[cur][hi], rs[cur][hi], o);
+            const int xl = alo ? p : q, xh = alo ? q : p;  // entry (xl, xh) of the block
+            apq = (xl == pl) ? ((xh == ph) ? o[0] : o[1]) : ((xh == ph) ? o[2] : o[3]);
+          }
+          make_rotation(app, aqq, apq, floor_abs, c, sn, t);
+        }
+        rc[cur ^ 1][k] = c; rs[cur ^ 1][k] = sn; rt[cur ^ 1][k] = t;
+        rpq[cur ^ 1][k] = p | (q << 16);
+      }
+      __syncthreads();
+      cur ^= 1;
+      T* tmp = Ain; Ain = Aout; Aout = tmp;
+    }
+    // stop when a sweep rotated nothing, or when the off-diagonal norm is at the rounding level
+    // (below off_gate) and the sweep did not halve it: what is left is rounding noise
+    double off = 0.0;
+    for (int e = tid; e < s * s; e += nt) {
+      const int i = e / s, j = e - i * s;
+      if (i != j) { const double a = (double)Ain[i * lda + j]; off += a * a; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+    if ((tid & 31) == 0) red[tid >> 5] = off;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int q = 0; q < nt / 32; ++q) t += red[q];
+      stop = (rotated == 0) || (sweep > 0 && t > 0.25 * prev_off && t <= off_gate * off_gate);
+      prev_off = t;
+      rotated = 0;
+    }
+    __syncthreads();
+    if (stop) break;
+  }
+  if (tid == 0 && status) *status = (sweep >= SweepCap<T>::value) ? 1 : 0;
+  for (int i = tid; i < s; i += nt) {
+    const T di = Ain[i * lda + i];
+    int rank = 0;
+    for (int j = 0; j < s; ++j) {
+      const T dj = Ain[j * lda + j];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    w[rank] = di;
+    for (int r = 0; r < s; ++r) Vout[(int64_t)rank * s + r] = V[i * s + r];
   }
 }
 
@@ -232,13 +490,136 @@ __global__ void chol_inv_kernel(const double* S, int k, double* Rinv, int* statu
   if (tid == 0 && status) *status = bad;
 }
 
+// Cholesky-QR applied twice to an s x p block X (column-major, ld s, p <= P) by one CTA of 512
+// threads.  Per pass: S = X^T X with products and per-thread / per-warp sums in T, the 16 warp
+// partials summed in FP64 in a fixed order (the result does not depend on scheduling); the upper
+// Cholesky factor R in FP64 by warp 0, one column per lane; then X <- X R^{-1} by forward
+// substitution on each row, in T.  The column count is a template parameter so the per-thread
+// Gram stays in registers.  status = 1 if S is not positive definite (the pivot is replaced so
+// the kernel still finishes).
+template <typename T, int P>
+__global__ void __launch_bounds__(512) cholqr2_small_kernel(T* X, int64_t s, int p, int* status) {
+  static_assert(P <= 32, "one lane per column");
+  constexpr int kThreads = 512, kWarps = kThreads / 32, NQ = P * (P + 1) / 2;
+  __shared__ T wpart[kWarps][NQ];
+  __shared__ double S[P * P];
+  __shared__ T Rt[P * P];   // R (upper), row-major: Rt[k * P + c] = R_kc
+  __shared__ T Rid[P];      // 1 / R_cc
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto qi = [](int a, int b) { return a * P - a * (a + 1) / 2 + b; };  // packed upper index, b >= a
+  for (int pass = 0; pass < 2; ++pass) {
+    T part[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) part[q] = T(0);
+    for (int64_t i = tid; i < s; i += kThreads) {
+      T x[P];
+#pragma unroll
+      for (int a = 0; a < P; ++a) x[a] = (a < p) ? X[(int64_t)a * s + i] : T(0);
+#pragma unroll
+      for (int a = 0; a < P; ++a)
+#pragma unroll
+        for (int b = a; b < P; ++b) part[qi(a, b)] = fma(x[a], x[b], part[qi(a, b)]);
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T v = part[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) wpart[warp][q] = v;
+    }
+    __syncthreads();
+    if (tid < NQ) {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; ++w) v += (double)wpart[w][tid];
+      int a = 0;
+      while (tid >= qi(a, P)) ++a;  // row of the packed entry
+      const int b = tid - qi(a, 0);
+      S[a * P + b] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // right-looking Cholesky; lane c keeps column c of the upper triangle: col[k] = S_kc (k <= c)
+      double col[P];
+#pragma unroll
+      for (int k = 0; k < P; ++k) col[k] = (lane < p && k <= lane) ? S[k * P + lane] : 0.0;
+      int bad = 0;
+      double my_inv = 0.0;  // 1 / R_cc of this lane's column
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        if (j < p) {
+          double d = __shfl_sync(0xffffffffu, col[j], j);
+          if (!(d > 0.0)) { bad = 1; d = 1.0; }
+          const double rjj = sqrt(d), inv = 1.0 / rjj;
+          if (lane == j) { col[j] = rjj; my_inv = inv; }
+          else if (lane > j) col[j] *= inv;  // R_jc
+#pragma unroll
+          for (int k = j + 1; k < P; ++k) {
+            const double rjk = __shfl_sync(0xffffffffu, col[j], k < 32 ? k : 0);
+            if (lane >= k && lane < p) col[k] = fma(-rjk, col[j], col[k]);
+          }
+        }
+      }
+      if (lane < P) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) Rt[k * P + lane] = (lane < p && k <= lane) ? (T)col[k] : T(0);
+        Rid[lane] = (T)my_inv;
+      }
+      if (lane == 0 && bad && status) *status = 1;
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < s; i += kThreads) {
+      T x[P];
+#pragma unroll
+      for (int a = 0; a < P; ++a) x[a] = (a < p) ? X[(int64_t)a * s + i] : T(0);
+      // solve y R = x for the row y
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        T v = x[c];
+#pragma unroll
+        for (int a = 0; a < c; ++a) v = fma(-x[a], Rt[a * P + c], v);
+        x[c] = v * Rid[c];
+      }
+#pragma unroll
+      for (int c = 0; c < P; ++c)
+        if (c < p) X[(int64_t)c * s + i] = x[c];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_cholqr2_small(T* X, int64_t s, int p, int* status, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  if (p > 8) return cudaErrorInvalidValue;
+  note_launch();
+  cholqr2_small_kernel<T, 8><<<1, 512, 0, st>>>(X, s, p, status);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cholqr2_small<float>(float*, int64_t, int, int*, cudaStream_t);
+template cudaError_t launch_cholqr2_small<double>(double*, int64_t, int, int*, cudaStream_t);
 
 template <typename T>
 cudaError_t jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* V, T* work, int* status,
                        cudaStream_t st) {
   if (s <= 0) return cudaSuccess;
   if (s > 1024) return cudaErrorInvalidValue;
+  const size_t small_need = (2 * (size_t)s * (s + 1) + (size_t)s * s) * sizeof(T);
+  if (s <= kSmallEigMax && small_need <= kEigSmemMax) {
+    static std::once_flag once_small;
+    static cudaError_t small_err = cudaSuccess;
+    std::call_once(once_small, [] {
+      small_err = cudaFuncSetAttribute(jacobi_small_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmemMax);
+    });
+    TT_CUDA(small_err);
+    const int npairs = (s + 1) / 2;
+    const int threads = std::min(kEigThreads, std::max(64, (npairs * npairs + 31) / 32 * 32));
+    note_launch();
+    jacobi_small_kernel<T><<<1, threads, small_need, st>>>(G, ldg, s, w, V, status);
+    return cudaGetLastError();
+  }
   const size_t need = (size_t)s * (s + 1) * sizeof(T);
   const int use_smem = need <= kEigSmemMax;
   const size_t smem = use_smem ? need : 0;

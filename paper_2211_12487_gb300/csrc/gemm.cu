@@ -192,6 +192,7 @@ cudaError_t gemm(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 32 && g.N <= 32) return run<TA, TB, TX, TC, ACC, 32, 32, 16, 2, 2>(g, st);
   if (g.M <= 16) return run<TA, TB, TX, TC, ACC, 16, 256, 16, 2, 8>(g, st);
   if (g.M <= 32) return run<TA, TB, TX, TC, ACC, 32, 128, 16, 4, 4>(g, st);
+  if (g.N <= 16 && g.M <= 4096) return run<TA, TB, TX, TC, ACC, 32, 16, 16, 2, 1>(g, st);
   if (g.N <= 16) return run<TA, TB, TX, TC, ACC, 256, 16, 16, 8, 2>(g, st);
   return run<TA, TB, TX, TC, ACC, 64, 64, 16, 4, 4>(g, st);
 }

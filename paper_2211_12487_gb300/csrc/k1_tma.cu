@@ -23,7 +23,7 @@ namespace ttice {
 namespace {
 
 constexpr int kTileL = 256;
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr int kThreads = kTileL;         // one column per thread
 constexpr long long kSpinLimit = 1LL << 24;
 
@@ -70,7 +70,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-template <typename T, int N1, int RM>
+template <typename T, int N1, int RM, bool NORMS>
 __global__ void __launch_bounds__(kThreads) k1_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                           int n1, int r, int64_t L, int b,
                                                           const T* __restrict__ U, int64_t ldu,
@@ -139,23 +139,34 @@ __global__ void __launch_bounds__(kThreads) k1_tma_kernel(const __grid_constant_
         for (int a = 0; a < RM; ++a) w[a] = fma(Uk[k][a], y, w[a]);
       }
     }
-    T se_c = T(0);
-#pragma unroll
-    for (int k = 0; k < N1; ++k) {
-      if (k < n1) {
-        T acc = (T)tile[k * kTileL + tid];
-#pragma unroll
-        for (int a = 0; a < RM; ++a) acc = fma(-Uk[k][a], w[a], acc);
-        se_c = fma(acc, acc, se_c);
-      }
-    }
-    double sy = (double)sy_c, se = (double)se_c;
     if (l < L) {
       T* Wz = W + (int64_t)z * r * L + l;
 #pragma unroll
       for (int a = 0; a < RM; ++a)
         if (a < r) Wz[(int64_t)a * L] = w[a];
     }
+    if constexpr (!NORMS) {
+      __syncthreads();  // every thread is done reading stage s
+      if (tid == 0) {
+        const int64_t tn = t + (int64_t)kStages * gridDim.x;
+        if (tn < ntiles) issue(tn, s);
+      }
+      continue;
+    }
+    // back-projection with one independent accumulator per row k (e_k = y_k - sum_a U(k,a) w_a)
+    T e[N1];
+#pragma unroll
+    for (int k = 0; k < N1; ++k) e[k] = (k < n1) ? (T)tile[k * kTileL + tid] : T(0);
+#pragma unroll
+    for (int a = 0; a < RM; ++a) {
+#pragma unroll
+      for (int k = 0; k < N1; ++k) e[k] = fma(-Uk[k][a], w[a], e[k]);
+    }
+    T se_c = T(0);
+#pragma unroll
+    for (int k = 0; k < N1; ++k)
+      if (k < n1) se_c = fma(e[k], e[k], se_c);
+    double sy = (double)sy_c, se = (double)se_c;
     // per-tile reduction of the two norms, one FP64 atomic each per tile
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -200,7 +211,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <typename T, int N1, int RM>
+template <typename T, int N1, int RM, bool NORMS>
 cudaError_t run(const float* Y, int b, int64_t L, int n1, int r, const T* U, int64_t ldu, T* W,
                 double* y2, double* rho2, double* part, int* status, cudaStream_t st) {
   auto enc = encode_fn();
@@ -220,10 +231,10 @@ cudaError_t run(const float* Y, int b, int64_t L, int n1, int r, const T* U, int
   static cudaError_t setup_err = cudaSuccess;
   static int per_sm = 1, sms = 152;
   std::call_once(once, [smem] {
-    setup_err = cudaFuncSetAttribute(k1_tma_kernel<T, N1, RM>,
+    setup_err = cudaFuncSetAttribute(k1_tma_kernel<T, N1, RM, NORMS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (setup_err == cudaSuccess)
-      setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1_tma_kernel<T, N1, RM>,
+      setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1_tma_kernel<T, N1, RM, NORMS>,
                                                                 kThreads, smem);
     int dev = 0;
     if (setup_err == cudaSuccess) setup_err = cudaGetDevice(&dev);
@@ -234,10 +245,11 @@ cudaError_t run(const float* Y, int b, int64_t L, int n1, int r, const T* U, int
   const int64_t ntiles = ((L + kTileL - 1) / kTileL) * b;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), ntiles));
   note_launch();
-  k1_tma_kernel<T, N1, RM><<<(unsigned)grid, kThreads, smem, st>>>(map, n1, r, L, b, U, ldu, W, part,
-                                                                    status);
+  k1_tma_kernel<T, N1, RM, NORMS><<<(unsigned)grid, kThreads, smem, st>>>(map, n1, r, L, b, U, ldu,
+                                                                           W, part, status);
   TT_CUDA(cudaGetLastError());
-  return launch_k1_reduce(part, b, (L + kTileL - 1) / kTileL, y2, rho2, st);
+  if constexpr (NORMS) return launch_k1_reduce(part, b, (L + kTileL - 1) / kTileL, y2, rho2, st);
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -250,12 +262,18 @@ bool k1_tma_supported(const void* Y, int64_t L, int n1, int r) {
 template <typename T>
 cudaError_t launch_k1_tma(const float* Y, int b, int64_t L, int n1, int r, const T* U, int64_t ldu,
                           T* W, double* y2, double* rho2, double* part, int* status, cudaStream_t st) {
-  if (n1 <= 8 && r <= 8) return run<T, 8, 8>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, status, st);
-  if (n1 <= 16 && r <= 16) return run<T, 16, 16>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, status, st);
-  if (n1 <= 24 && r <= 16) return run<T, 24, 16>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, status, st);
-  if (n1 <= 24 && r <= 24) return run<T, 24, 24>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, status, st);
-  if (n1 <= 32 && r <= 16) return run<T, 32, 16>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, status, st);
-  if (n1 <= 32 && r <= 32) return run<T, 32, 32>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, status, st);
+  // y2 == nullptr: projection only (no residual, no norms)
+  const bool nrm = y2 != nullptr;
+#define TT_K1_CASE(N1_, RM_)                                                                   \
+  return nrm ? run<T, N1_, RM_, true>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, status, st)  \
+             : run<T, N1_, RM_, false>(Y, b, L, n1, r, U, ldu, W, y2, rho2, part, status, st)
+  if (n1 <= 8 && r <= 8) TT_K1_CASE(8, 8);
+  if (n1 <= 16 && r <= 16) TT_K1_CASE(16, 16);
+  if (n1 <= 24 && r <= 16) TT_K1_CASE(24, 16);
+  if (n1 <= 24 && r <= 24) TT_K1_CASE(24, 24);
+  if (n1 <= 32 && r <= 16) TT_K1_CASE(32, 16);
+  if (n1 <= 32 && r <= 32) TT_K1_CASE(32, 32);
+#undef TT_K1_CASE
   return cudaErrorInvalidValue;
 }
 

@@ -87,6 +87,8 @@ struct ttice_s {
   int64_t max_m = 0;
   double* rho2 = nullptr;
   double* y2 = nullptr;
+  double* rn2 = nullptr;    // per-observation ||R_i(z)||^2 of the residual being truncated
+  double* h_rn2 = nullptr;  // pinned copy
   double* part = nullptr;  // per-CTA / per-tile partial norms of the first pass
   double* trace = nullptr;
   Decision* dec = nullptr;
@@ -148,6 +150,7 @@ void ph_collect(ttice_s* h) {
 
 constexpr int kRR = 96;         // largest Rayleigh-Ritz subspace
 constexpr int kDirectEig = 32;  // Gram matrices up to this size are diagonalised in FP64 directly
+constexpr int kDirectEig32 = 96;  // mixed path: FP32 Jacobi in one CTA up to this size
 constexpr int kMaxEig = 4608;  // largest Gram side (128^3 x 4 flow: 33 x 128 = 4224)
 constexpr int kMaxSweeps64 = 15;  // block Jacobi sweep limits (quadratic convergence needs ~6-10)
 constexpr int kMaxSweeps32 = 12;
@@ -188,9 +191,10 @@ void free_all(ttice_s* h) {
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->Ebuf, h->P, h->part, h->rho2, h->y2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
+  cudaFreeHost(h->h_rn2);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -297,6 +301,9 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
       } else {
         TT_CU((launch_k1<TY, WT>(X0, b, L, (int)m, (int)rn, Ui, h->ldu[i], W, h->y2, h->rho2, h->part, st)));
       }
+    } else if (i == 0 && !errors && sizeof(TY) == 4 && k1_tma_supported(X0, L, (int)m, (int)rn)) {
+      TT_CU((launch_k1_tma<WT>(reinterpret_cast<const float*>(X0), b, L, (int)m, (int)rn, Ui,
+                               h->ldu[i], W, nullptr, nullptr, nullptr, h->ibuf + 5, st)));
     } else if (i == 0) {
       TT_TRY(proj<WT, TY, WT>(Ui, h->ldu[i], X0, m, L, rn, b, W, st));
       if (errors) TT_TRY((resid<WT, WT, TY, WT>(Ui, h->ldu[i], W, X0, m, L, rn, b, nullptr, h->rho2, st)));
@@ -366,29 +373,13 @@ int rayleigh_ritz(ttice_s* h, int64_t s, int K, const double* d_eps, int max_new
   return TTICE_OK;
 }
 
-// CholQR2 of an FP32 s x p block X (column-major, ld s), in place: S = X^T X with FP32 products
-// accumulated in FP64, the inverse Cholesky factor in FP64, X <- X R^{-1} in FP32.  status (device
-// int) is set if the block is numerically rank deficient.
+// CholQR2 of an FP32 s x p block X (column-major, ld s), in place, in one CTA: S = X^T X with FP32
+// products and an FP64 sum of the warp partials, the inverse Cholesky factor in FP64,
+// X <- X R^{-1} in FP32.  status (device int) is
+// set if the block is numerically rank deficient.
 int cholqr2_block32(ttice_s* h, float* X, int64_t s, int p, int* status, cudaStream_t st) {
-  for (int pass = 0; pass < 2; ++pass) {
-    TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)p * p * sizeof(double), st));
-    GemmArgs g;  // S = X^T X
-    g.M = p; g.N = p; g.K = s; g.atomic = 1; g.allow_splitk = 1;
-    g.A.p = X; g.A.rs = s; g.A.cs = 1;
-    g.B.p = X; g.B.rs = 1; g.B.cs = s;
-    g.C = h->Ssm; g.c_rs = 1; g.c_cs = p;
-    TT_CU((gemm<float, float, float, double, float>(g, st)));
-    TT_CU(launch_chol_inv(h->Ssm, p, h->Rinv, status, st));
-    TT_CU((launch_cast<double, float>(h->Rinv, h->KR32, (int64_t)p * p, st)));
-    GemmArgs q;  // X2 = X Rinv
-    q.M = s; q.N = p; q.K = p;
-    q.A.p = X; q.A.rs = 1; q.A.cs = s;
-    q.B.p = h->KR32; q.B.rs = 1; q.B.cs = p;
-    q.C = h->KW2; q.c_rs = 1; q.c_cs = s;
-    TT_CU((gemm<float, float, float, float, float>(q, st)));
-    TT_CU(cudaMemcpyAsync(X, h->KW2, (size_t)s * p * sizeof(float), cudaMemcpyDeviceToDevice, st));
-  }
-  return TTICE_OK;
+  (void)h;
+  return cu(launch_cholqr2_small<float>(X, s, p, status, st));
 }
 
 // Candidate eigenvectors for the leading part of the Gram G (s x s) from a block Krylov subspace
@@ -496,8 +487,9 @@ int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
   TT_TRY(sync_read(h, st));
   const int rR = h->h_int[0];
   if (rR < 0) return TTICE_OK;
+  // rR = 0 is decided by the trace alone (no Ritz value enters it)
+  if (rR == 0) { *ok = true; return TTICE_OK; }
   const int jm = std::min(rR + 1, K);
-  if (jm == 0) { *ok = true; return TTICE_OK; }
   TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * jm * sizeof(double), st));
   GemmArgs g;  // GQ = G Z
   g.M = s; g.N = jm; g.K = s; g.atomic = 1; g.allow_splitk = 1;
@@ -626,7 +618,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     if (!have) {
     // FP32 Jacobi (one CTA for small matrices, block Jacobi otherwise) for approximate
     // eigenvectors, then FP64 Rayleigh-Ritz on the leading K of them.
-    if (s <= kDirectEig) {
+    if (s <= kDirectEig32) {
       TT_CU(cudaMemsetAsync(h->bjflags, 0, 4 * sizeof(int), st));
       TT_CU(jacobi_eig<float>(h->G, s, (int)s, h->w32, h->V32, h->bjw32, h->bjflags + 3, st));
     } else {
@@ -841,13 +833,23 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
           ph_begin(h, PH_RESID, st, nsel * (sx * m * L + sw * m * L + 2.0 * sw * ri * L),
                    4.0 * nsel * (double)m * L * ri);
         }
+        bool small = false;  // ||R_i||_F <= eps_c: the rank rule gives 0 without any eigenvalue
         if (ri > 0) {
-          if (i == 0) {
+          rc = cu(cudaMemsetAsync(h->rn2, 0, nsel * sizeof(double), st));
+          if (rc == TTICE_OK && i == 0) {
             rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0, m, L, ri, nsel, Wt, st);
-            if (rc == TTICE_OK) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wt, D0, m, L, ri, nsel, R, nullptr, st);
-          } else {
+            if (rc == TTICE_OK) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wt, D0, m, L, ri, nsel, R, h->rn2, st);
+          } else if (rc == TTICE_OK) {
             rc = proj<WT, WT, WT>(Ui, h->ldu[i], X, m, L, ri, nsel, Wt, st);
-            if (rc == TTICE_OK) rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wt, X, m, L, ri, nsel, R, nullptr, st);
+            if (rc == TTICE_OK) rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wt, X, m, L, ri, nsel, R, h->rn2, st);
+          }
+          if (rc == TTICE_OK) rc = cu(cudaMemcpyAsync(h->h_rn2, h->rn2, nsel * sizeof(double),
+                                                      cudaMemcpyDeviceToHost, st));
+          if (rc == TTICE_OK) rc = sync_read(h, st);
+          if (rc == TTICE_OK) {
+            double t = 0.0;
+            for (int z = 0; z < nsel; ++z) t += h->h_rn2[z];
+            small = std::sqrt(t) <= dec.eps_c;
           }
         } else {
           if (i == 0) rc = cu(launch_cast<TY, WT>(D0, R, (int64_t)nsel * m * L, st));
@@ -857,7 +859,9 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
         if (rc != TTICE_OK) break;
         const int max_new = (int)(m - ri);
         int rR = 0;
-        rc = truncated_dirs<WT>(h, i, R, m, L, nsel, dec.eps_c, max_new, &rR, st);
+        // Eq. 5 at r = 0: the tail is ||R_i||_F^2 itself, so no direction is needed and the Gram and
+        // its eigen-solve are skipped
+        if (!small) rc = truncated_dirs<WT>(h, i, R, m, L, nsel, dec.eps_c, max_new, &rR, st);
         if (rc != TTICE_OK) break;
         if (rR > 0) {
           if (ri + rR > h->cap[i + 1]) { rc = TTICE_ECAPACITY; break; }
@@ -890,7 +894,10 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
           ph_begin(h, PH_DPROJ, st, nsel * (sx * m * L + sizeof(WT) * (double)rn * L),
                    2.0 * nsel * (double)m * L * rn);
         }
-        if (i == 0) rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0, m, L, rn, nsel, Wn, st);
+        if (i == 0 && sizeof(TY) == 4 && k1_tma_supported(D0, L, (int)m, (int)rn))
+          rc = cu(launch_k1_tma<WT>(reinterpret_cast<const float*>(D0), nsel, L, (int)m, (int)rn, Ui,
+                                    h->ldu[i], Wn, nullptr, nullptr, nullptr, h->ibuf + 5, st));
+        else if (i == 0) rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0, m, L, rn, nsel, Wn, st);
         else rc = proj<WT, WT, WT>(Ui, h->ldu[i], X, m, L, rn, nsel, Wn, st);
         ph_end(h, st);
         X = Wn;
@@ -908,7 +915,9 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
   const int rd = (int)h->r[h->d];
   TT_CU(launch_append_last_t<WT>(static_cast<const WT*>(S1[h->d - 1]), b, rd, h->last, h->n_obs,
                                  h->cap[h->d], st));
+  TT_CU(cudaMemcpyAsync(h->h_int + 5, h->ibuf + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
   TT_TRY(sync_read(h, st));
+  if (h->h_int[5]) return TTICE_ETIMEOUT;  // a staged copy of a projection pass never completed
   h->n_obs += b;
   fill_stats(h);
   ph_collect(h);
@@ -1044,6 +1053,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK) rc = dalloc<double>(&h->P, maxcap * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->part, 2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rho2, B);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->rn2, B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->y2, B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->trace, 1);
   if (rc == TTICE_OK) rc = dalloc<Decision>(&h->dec, 1);
@@ -1054,6 +1064,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_int, 16 * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_w32, s * sizeof(float)) != cudaSuccess) rc = TTICE_ENOMEM;
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_dbl, 256 * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_rn2, B * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
   if (rc == TTICE_OK) rc = grow_last(h, std::max<int64_t>(h->capc.obs_reserve, 1));
   if (rc == TTICE_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TTICE_ECUDA;
   if (rc != TTICE_OK) {

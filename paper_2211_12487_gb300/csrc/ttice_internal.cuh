@@ -121,6 +121,9 @@ cudaError_t launch_canonical_sign(double* V, int64_t m, int k, int64_t ld, cudaS
 // Cholesky-QR step support: given S = V^T V (k x k, FP64, ld k), overwrite Rinv (k x k, ld k) with
 // the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  status=1 if not positive definite.
 cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st);
+// Cholesky-QR twice of an s x p block (p <= 8) in one CTA (eig.cu)
+template <typename T>
+cudaError_t launch_cholqr2_small(T* X, int64_t s, int p, int* status, cudaStream_t st);
 // scale column j of V (m x k, ld) by 1/sqrt(theta[j])
 cudaError_t launch_scale_cols_rsqrt(double* V, int64_t m, int k, int64_t ld, const double* theta,
                                     cudaStream_t st);
