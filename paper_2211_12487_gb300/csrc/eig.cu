@@ -490,115 +490,8 @@ __global__ void chol_inv_kernel(const double* S, int k, double* Rinv, int* statu
   if (tid == 0 && status) *status = bad;
 }
 
-// Cholesky-QR applied twice to an s x p block X (column-major, ld s, p <= P) by one CTA of 512
-// threads.  Per pass: S = X^T X with products and per-thread / per-warp sums in T, the 16 warp
-// partials summed in FP64 in a fixed order (the result does not depend on scheduling); the upper
-// Cholesky factor R in FP64 by warp 0, one column per lane; then X <- X R^{-1} by forward
-// substitution on each row, in T.  The column count is a template parameter so the per-thread
-// Gram stays in registers.  status = 1 if S is not positive definite (the pivot is replaced so
-// the kernel still finishes).
-template <typename T, int P>
-__global__ void __launch_bounds__(512) cholqr2_small_kernel(T* X, int64_t s, int p, int* status) {
-  static_assert(P <= 32, "one lane per column");
-  constexpr int kThreads = 512, kWarps = kThreads / 32, NQ = P * (P + 1) / 2;
-  __shared__ T wpart[kWarps][NQ];
-  __shared__ double S[P * P];
-  __shared__ T Rt[P * P];   // R (upper), row-major: Rt[k * P + c] = R_kc
-  __shared__ T Rid[P];      // 1 / R_cc
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  auto qi = [](int a, int b) { return a * P - a * (a + 1) / 2 + b; };  // packed upper index, b >= a
-  for (int pass = 0; pass < 2; ++pass) {
-    T part[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) part[q] = T(0);
-    for (int64_t i = tid; i < s; i += kThreads) {
-      T x[P];
-#pragma unroll
-      for (int a = 0; a < P; ++a) x[a] = (a < p) ? X[(int64_t)a * s + i] : T(0);
-#pragma unroll
-      for (int a = 0; a < P; ++a)
-#pragma unroll
-        for (int b = a; b < P; ++b) part[qi(a, b)] = fma(x[a], x[b], part[qi(a, b)]);
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      T v = part[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) wpart[warp][q] = v;
-    }
-    __syncthreads();
-    if (tid < NQ) {
-      double v = 0.0;
-      for (int w = 0; w < kWarps; ++w) v += (double)wpart[w][tid];
-      int a = 0;
-      while (tid >= qi(a, P)) ++a;  // row of the packed entry
-      const int b = tid - qi(a, 0);
-      S[a * P + b] = v;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      // right-looking Cholesky; lane c keeps column c of the upper triangle: col[k] = S_kc (k <= c)
-      double col[P];
-#pragma unroll
-      for (int k = 0; k < P; ++k) col[k] = (lane < p && k <= lane) ? S[k * P + lane] : 0.0;
-      int bad = 0;
-      double my_inv = 0.0;  // 1 / R_cc of this lane's column
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        if (j < p) {
-          double d = __shfl_sync(0xffffffffu, col[j], j);
-          if (!(d > 0.0)) { bad = 1; d = 1.0; }
-          const double rjj = sqrt(d), inv = 1.0 / rjj;
-          if (lane == j) { col[j] = rjj; my_inv = inv; }
-          else if (lane > j) col[j] *= inv;  // R_jc
-#pragma unroll
-          for (int k = j + 1; k < P; ++k) {
-            const double rjk = __shfl_sync(0xffffffffu, col[j], k < 32 ? k : 0);
-            if (lane >= k && lane < p) col[k] = fma(-rjk, col[j], col[k]);
-          }
-        }
-      }
-      if (lane < P) {
-#pragma unroll
-        for (int k = 0; k < P; ++k) Rt[k * P + lane] = (lane < p && k <= lane) ? (T)col[k] : T(0);
-        Rid[lane] = (T)my_inv;
-      }
-      if (lane == 0 && bad && status) *status = 1;
-    }
-    __syncthreads();
-    for (int64_t i = tid; i < s; i += kThreads) {
-      T x[P];
-#pragma unroll
-      for (int a = 0; a < P; ++a) x[a] = (a < p) ? X[(int64_t)a * s + i] : T(0);
-      // solve y R = x for the row y
-#pragma unroll
-      for (int c = 0; c < P; ++c) {
-        T v = x[c];
-#pragma unroll
-        for (int a = 0; a < c; ++a) v = fma(-x[a], Rt[a * P + c], v);
-        x[c] = v * Rid[c];
-      }
-#pragma unroll
-      for (int c = 0; c < P; ++c)
-        if (c < p) X[(int64_t)c * s + i] = x[c];
-    }
-    __syncthreads();
-  }
-}
-
 }  // namespace
 
-template <typename T>
-cudaError_t launch_cholqr2_small(T* X, int64_t s, int p, int* status, cudaStream_t st) {
-  if (p <= 0) return cudaSuccess;
-  if (p > 8) return cudaErrorInvalidValue;
-  note_launch();
-  cholqr2_small_kernel<T, 8><<<1, 512, 0, st>>>(X, s, p, status);
-  return cudaGetLastError();
-}
-template cudaError_t launch_cholqr2_small<float>(float*, int64_t, int, int*, cudaStream_t);
-template cudaError_t launch_cholqr2_small<double>(double*, int64_t, int, int*, cudaStream_t);
 
 template <typename T>
 cudaError_t jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* V, T* work, int* status,

@@ -163,7 +163,8 @@ cudaError_t run(const GemmArgs& g, cudaStream_t st) {
   const int64_t gx = (g.N + BN - 1) / BN, gy = (g.M + BM - 1) / BM;
   int ksplit = 1;
   int64_t kchunk = g.K > 0 ? g.K : 1;
-  if (g.atomic && g.allow_splitk && !g.X.p && !g.norm) {
+  const bool zero_split = !g.atomic && g.store && g.c_zero_elems > 0 && !g.X.p && !g.norm;
+  if ((g.atomic && g.allow_splitk && !g.X.p && !g.norm) || zero_split) {
     const int64_t tiles = gx * gy * g.nbatch;
     const int64_t target = 2 * 152;
     if (tiles < target && g.K > 4 * BK) {
@@ -178,6 +179,16 @@ cudaError_t run(const GemmArgs& g, cudaStream_t st) {
   if (gx == 0 || gy == 0 || g.nbatch == 0) return cudaSuccess;
   if (gy > 65535 || (int64_t)g.nbatch * ksplit > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(g.nbatch * ksplit));
+  if (zero_split && ksplit > 1) {
+    // a plain-store output split over K: zero it, then every K-chunk adds its part
+    const cudaError_t e = cudaMemsetAsync(g.C, 0, (size_t)g.c_zero_elems * sizeof(TC), st);
+    if (e != cudaSuccess) return e;
+    GemmArgs ga = g;
+    ga.atomic = 1;
+    note_launch();
+    gemm_kernel<TA, TB, TX, TC, ACC, BM, BN, BK, TM, TN><<<grid, 256, 0, st>>>(ga, ksplit, kchunk);
+    return cudaGetLastError();
+  }
   note_launch();
   gemm_kernel<TA, TB, TX, TC, ACC, BM, BN, BK, TM, TN><<<grid, 256, 0, st>>>(g, ksplit, kchunk);
   return cudaGetLastError();

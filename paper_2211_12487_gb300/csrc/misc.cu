@@ -22,20 +22,28 @@ inline unsigned grid_for(int64_t n, int per = kThreads) {
 
 // Algorithm 2: per-observation relative errors (Eq. 17), skip test (Eq. 20 or the mean surrogate),
 // subselection D = {j : eps_Y(j) > eps}, eps_upd (Eq. 18 or 19), eps = eps_upd ||D|| / sqrt(d).
-// One thread: b is small and the order of the FP64 sums is fixed (ascending j).
-__global__ void decision_kernel(const double* rho2, const double* y2, int b, double eps, int d,
-                                int skip_mode, int subselect, int eps_upd_mode, Decision* dec,
+// One thread: b is small and the order of the FP64 sums is fixed (ascending j).  rho2 holds the
+// squared residual of every observation per TT stage (stage-major, nst x b); rho2(j) is their sum,
+// taken in ascending stage order (the orthogonal decomposition of ||y_j - ~y_j||^2).
+__global__ void decision_kernel(const double* rho2s, int nst, const double* y2, int b, double eps,
+                                int d, int skip_mode, int subselect, int eps_upd_mode, Decision* dec,
                                 int* sel) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  auto rho2 = [&](int j) {
+    double v = 0.0;
+    for (int i = 0; i < nst; ++i) v += rho2s[(int64_t)i * b + j];
+    return v;
+  };
   Decision D;
   double ynorm2 = 0.0, rsum = 0.0, relsum = 0.0;
   int nonfinite = 0;
   for (int j = 0; j < b; ++j) {
     ynorm2 += y2[j];
-    rsum += rho2[j];
-    const double rel = y2[j] > 0.0 ? sqrt(rho2[j] / y2[j]) : 0.0;
+    const double rj = rho2(j);
+    rsum += rj;
+    const double rel = y2[j] > 0.0 ? sqrt(rj / y2[j]) : 0.0;
     relsum += rel;
-    if (!isfinite(y2[j]) || !isfinite(rho2[j])) nonfinite = 1;
+    if (!isfinite(y2[j]) || !isfinite(rj)) nonfinite = 1;
   }
   D.nonfinite = nonfinite;
   D.ynorm2 = ynorm2;
@@ -52,12 +60,13 @@ __global__ void decision_kernel(const double* rho2, const double* y2, int b, dou
     double rest_rho2 = 0.0, rest_rel = 0.0;
     int nsel = 0;
     for (int j = 0; j < b; ++j) {
-      const double rel = y2[j] > 0.0 ? sqrt(rho2[j] / y2[j]) : 0.0;
+      const double rj = rho2(j);
+      const double rel = y2[j] > 0.0 ? sqrt(rj / y2[j]) : 0.0;
       if (!subselect || rel > eps) {
         sel[nsel++] = j;
         D.dnorm2 += y2[j];
       } else {
-        rest_rho2 += rho2[j];
+        rest_rho2 += rj;
         rest_rel += rel;
       }
     }
@@ -258,19 +267,22 @@ __global__ void ritz_residual_kernel(const double* GQ, const double* Q, const do
   }
 }
 
-__global__ void rel_err_kernel(const double* rho2, const double* y2, int b, double* rel) {
+__global__ void rel_err_kernel(const double* rho2s, int nst, const double* y2, int b, double* rel) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < b) rel[j] = y2[j] > 0.0 ? sqrt(rho2[j] / y2[j]) : 0.0;
+  if (j >= b) return;
+  double r = 0.0;
+  for (int i = 0; i < nst; ++i) r += rho2s[(int64_t)i * b + j];
+  rel[j] = y2[j] > 0.0 ? sqrt(r / y2[j]) : 0.0;
 }
 
 }  // namespace
 
-cudaError_t launch_decision(const double* rho2, const double* y2, int b, double eps, int d,
+cudaError_t launch_decision(const double* rho2s, int nst, const double* y2, int b, double eps, int d,
                             int skip_mode, int subselect, int eps_upd_mode, Decision* dec,
                             int* sel, cudaStream_t st) {
   note_launch();
-  decision_kernel<<<1, 32, 0, st>>>(rho2, y2, b, eps, d, skip_mode, subselect, eps_upd_mode, dec,
-                                    sel);
+  decision_kernel<<<1, 32, 0, st>>>(rho2s, nst, y2, b, eps, d, skip_mode, subselect, eps_upd_mode,
+                                    dec, sel);
   return cudaGetLastError();
 }
 
@@ -400,11 +412,11 @@ cudaError_t launch_ritz_residual(const double* GQ, const double* Q, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_rel_err(const double* rho2, const double* y2, int b, double* rel,
+cudaError_t launch_rel_err(const double* rho2s, int nst, const double* y2, int b, double* rel,
                            cudaStream_t st) {
   if (b <= 0) return cudaSuccess;
   note_launch();
-  rel_err_kernel<<<(b + 127) / 128, 128, 0, st>>>(rho2, y2, b, rel);
+  rel_err_kernel<<<(b + 127) / 128, 128, 0, st>>>(rho2s, nst, y2, b, rel);
   return cudaGetLastError();
 }
 

@@ -68,10 +68,8 @@ struct ttice_s {
   double* theta = nullptr;
   float* G32 = nullptr;   // FP32 copy of the Gram for the Krylov solver
   float* KQ = nullptr;    // block-Krylov basis, s_max x kKry
-  float* KGQ = nullptr;   // G Q, s_max x kKry
-  float* KW2 = nullptr;   // s_max x kKryP
-  float* KT = nullptr;    // kKry x kKryP
-  float* KR32 = nullptr;  // kKryP x kKryP
+  float* kpart = nullptr;          // per-CTA partial sums of the fused Krylov kernel
+  unsigned int* ksync = nullptr;   // its grid-barrier state (arrivals, generation, error)
   double* KV = nullptr;   // s_max x kKryP (start block), also kKry x kKry eigenvectors of H
   double* res = nullptr;  // Ritz residual norms
   double* h_dbl = nullptr;  // pinned host scratch
@@ -85,7 +83,8 @@ struct ttice_s {
   double* Vn2 = nullptr;
   double* P = nullptr;   // cap x kRR projections for CGS2
   int64_t max_m = 0;
-  double* rho2 = nullptr;
+  double* rho2 = nullptr;    // squared residual per TT stage and observation (stage-major, d x b)
+  double* h_rho2 = nullptr;  // pinned copy (first pass of an update)
   double* y2 = nullptr;
   double* rn2 = nullptr;    // per-observation ||R_i(z)||^2 of the residual being truncated
   double* h_rn2 = nullptr;  // pinned copy
@@ -187,7 +186,7 @@ void free_all(ttice_s* h) {
   for (int i = 0; i < kMaxD; ++i) {
     cudaFree(h->U[i]); cudaFree(h->Uf[i]); cudaFree(h->stage[i]); cudaFree(h->dstage[i]);
   }
-  void* ptrs[] = {h->G32, h->KQ, h->KGQ, h->KW2, h->KT, h->KR32, h->KV, h->res,
+  void* ptrs[] = {h->G32, h->KQ, h->kpart, h->ksync, h->KV, h->res,
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
@@ -195,6 +194,7 @@ void free_all(ttice_s* h) {
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
   cudaFreeHost(h->h_rn2);
+  cudaFreeHost(h->h_rho2);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -210,6 +210,7 @@ int proj(const TU* Ui, int64_t ldu, const TX* X, int64_t m, int64_t L, int64_t r
   g.B.p = X; g.B.rs = L; g.B.cs = 1; g.B.bs1 = m * L;
   g.C = W; g.c_rs = L; g.c_cs = 1; g.c_bs1 = rnext * L;
   g.nbatch = b;
+  g.c_zero_elems = (int64_t)b * rnext * L;  // short-and-wide outputs (large m_i) split over K
   using ACC = typename std::conditional<sizeof(TW) == 8, double, float>::type;
   return cu(gemm<TU, TX, TX, TW, ACC>(g, st));
 }
@@ -239,29 +240,32 @@ int sumsq(const T* X, int b, int64_t n, double* out, cudaStream_t st) {
 
 // ---------------------------------------------------------------- chain projection
 // Project b observations of X0 (stage-0 layout) through U_1..U_d into `bufs`; with `errors`,
-// rho2[z] = sum_i ||R_i(z)||^2 (the orthogonal decomposition of ||y - ~y||^2) and y2[z] = ||y_z||^2.
+// rho2[i b + z] = ||R_i(z)||^2 for every stage i (their sum over i is ||y_z - ~y_z||^2, the orthogonal
+// decomposition) and y2[z] = ||y_z||^2.  Without `errors`, `first` > 0 starts at stage `first` from
+// the stage output already in bufs[first - 1].
 template <typename WT, typename TY>
-int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_t st) {
-  const WT* Xw = nullptr;
+int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_t st, int first = 0) {
+  if (errors) first = 0;
+  const WT* Xw = first > 0 ? static_cast<const WT*>(bufs[first - 1]) : nullptr;
   const double sw = sizeof(WT), sy = sizeof(TY);
   const bool fused_k1 = errors && h->r[1] > 0 && k1_supported<TY, WT>((int)h->n[0], (int)h->r[1]);
   if (errors) {
-    TT_CU(cudaMemsetAsync(h->rho2, 0, b * sizeof(double), st));
+    TT_CU(cudaMemsetAsync(h->rho2, 0, (size_t)h->d * b * sizeof(double), st));
     TT_CU(cudaMemsetAsync(h->y2, 0, b * sizeof(double), st));
     TT_CU(cudaMemsetAsync(h->ibuf + 5, 0, sizeof(int), st));
     const double N = (double)h->N, r1 = (double)h->r[1];
     ph_begin(h, PH_K1, st, b * (sy * N + sw * r1 * h->L[0]), b * (4.0 * N * r1 + 4.0 * N));
     if (!fused_k1) TT_TRY(sumsq<TY>(X0, b, h->N, h->y2, st));
   } else {
-    double by = sy * b * h->N, fl = 0.0;
-    for (int i = 0; i < h->d; ++i) {
+    double by = first > 0 ? sw * b * (double)h->r[first] * h->L[first - 1] : sy * b * h->N, fl = 0.0;
+    for (int i = first; i < h->d; ++i) {
       const double out = (double)b * h->r[i + 1] * h->L[i];
       by += sw * out * (i + 1 < h->d ? 2.0 : 1.0);
       fl += 2.0 * b * (double)h->r[i] * h->n[i] * h->L[i] * h->r[i + 1];
     }
     ph_begin(h, PH_FINAL, st, by, fl);
   }
-  for (int i = 0; i < h->d; ++i) {
+  for (int i = first; i < h->d; ++i) {
     const int64_t m = h->r[i] * h->n[i], rn = h->r[i + 1], L = h->L[i];
     WT* W = static_cast<WT*>(bufs[i]);
     if (errors && i == 1) {
@@ -278,7 +282,7 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
       // nothing is represented from here on: the whole remaining stage is residual
       if (errors && m > 0) {
         if (i == 0) TT_TRY(sumsq<TY>(X0, b, m * L, h->rho2, st));
-        else TT_TRY(sumsq<WT>(Xw, b, m * L, h->rho2, st));
+        else TT_TRY(sumsq<WT>(Xw, b, m * L, h->rho2 + (int64_t)i * b, st));
       }
       // zero the coefficients of the remaining stages
       for (int j = i; j < h->d; ++j) {
@@ -309,7 +313,8 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
       if (errors) TT_TRY((resid<WT, WT, TY, WT>(Ui, h->ldu[i], W, X0, m, L, rn, b, nullptr, h->rho2, st)));
     } else {
       TT_TRY(proj<WT, WT, WT>(Ui, h->ldu[i], Xw, m, L, rn, b, W, st));
-      if (errors) TT_TRY((resid<WT, WT, WT, WT>(Ui, h->ldu[i], W, Xw, m, L, rn, b, nullptr, h->rho2, st)));
+      if (errors)
+        TT_TRY((resid<WT, WT, WT, WT>(Ui, h->ldu[i], W, Xw, m, L, rn, b, nullptr, h->rho2 + (int64_t)i * b, st)));
     }
     Xw = W;
   }
@@ -373,87 +378,30 @@ int rayleigh_ritz(ttice_s* h, int64_t s, int K, const double* d_eps, int max_new
   return TTICE_OK;
 }
 
-// CholQR2 of an FP32 s x p block X (column-major, ld s), in place, in one CTA: S = X^T X with FP32
-// products and an FP64 sum of the warp partials, the inverse Cholesky factor in FP64,
-// X <- X R^{-1} in FP32.  status (device int) is
-// set if the block is numerically rank deficient.
-int cholqr2_block32(ttice_s* h, float* X, int64_t s, int p, int* status, cudaStream_t st) {
-  (void)h;
-  return cu(launch_cholqr2_small<float>(X, s, p, status, st));
-}
-
 // Candidate eigenvectors for the leading part of the Gram G (s x s) from a block Krylov subspace
-// built in FP32 (an FP32 copy of G): X_0 = orth(random s x p), X_i = orth((I - Q Q^T) G X_{i-1})
-// (CGS2 against the basis Q = [X_0 .. X_{i-1}]), kKryBlocks blocks; H = Q^T G Q (FP32 products,
-// FP64 accumulation) is diagonalised by FP32 Jacobi and its leading K eigenvectors, mapped back to
-// R^s in FP64, are left in h->Q for the FP64 Rayleigh-Ritz step, which alone decides the rank.
+// built in FP32 (an FP32 copy of G) by one cooperative kernel: X_0 = orth(random s x p),
+// X_i = orth((I - Q Q^T) G X_{i-1}) (CGS2 against the basis Q = [X_0 .. X_{i-1}]), kKryBlocks
+// blocks, and H = Q^T G Q (FP32 products, FP64 accumulation across CTAs).  H is diagonalised by FP32
+// Jacobi and its leading K eigenvectors, mapped back to R^s in FP64, are left in h->Q for the FP64
+// Rayleigh-Ritz step, which alone decides the rank.
 // *K_out = 0 when the subspace is too small for the tolerance.
 int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStream_t st) {
-  const int p = kKryP;
   *K_out = 0;
   float* Qb = h->KQ;
-  float* G32 = h->G32;
-  TT_CU((launch_cast<double, float>(h->G, G32, s * s, st)));
+  const int k = kKry;
   TT_CU(cudaMemsetAsync(h->ibuf + 6, 0, sizeof(int), st));
-  TT_CU(launch_fill_hash(h->KV, s * p, 0x5eedull + (uint64_t)s, st));
-  TT_CU((launch_cast<double, float>(h->KV, Qb, s * p, st)));
-  TT_TRY(cholqr2_block32(h, Qb, s, p, h->ibuf + 6, st));
-  int nblk = kKryBlocks;
-  for (int i = 1; i < nblk; ++i) {
-    const float* Xprev = Qb + (int64_t)(i - 1) * p * s;
-    float* Xi = Qb + (int64_t)i * p * s;
-    TT_CU(cudaMemsetAsync(Xi, 0, (size_t)s * p * sizeof(float), st));
-    GemmArgs g;  // X_i = G X_{i-1}
-    g.M = s; g.N = p; g.K = s; g.atomic = 1; g.allow_splitk = 1;
-    g.A.p = G32; g.A.rs = s; g.A.cs = 1;
-    g.B.p = Xprev; g.B.rs = 1; g.B.cs = s;
-    g.C = Xi; g.c_rs = 1; g.c_cs = s;
-    TT_CU((gemm<float, float, float, float, float>(g, st)));
-    const int nq = i * p;
-    for (int pass = 0; pass < 2; ++pass) {
-      TT_CU(cudaMemsetAsync(h->KT, 0, (size_t)nq * p * sizeof(float), st));
-      GemmArgs a;  // T = Q^T X_i
-      a.M = nq; a.N = p; a.K = s; a.atomic = 1; a.allow_splitk = 1;
-      a.A.p = Qb; a.A.rs = s; a.A.cs = 1;
-      a.B.p = Xi; a.B.rs = 1; a.B.cs = s;
-      a.C = h->KT; a.c_rs = 1; a.c_cs = nq;
-      TT_CU((gemm<float, float, float, float, float>(a, st)));
-      GemmArgs b;  // X_i -= Q T
-      b.M = s; b.N = p; b.K = nq;
-      b.A.p = Qb; b.A.rs = 1; b.A.cs = s;
-      b.B.p = h->KT; b.B.rs = 1; b.B.cs = nq;
-      b.X.p = Xi; b.X.rs = 1; b.X.cs = s;
-      b.alpha = -1.0; b.beta = 1.0;
-      b.C = Xi; b.c_rs = 1; b.c_cs = s;
-      TT_CU((gemm<float, float, float, float, float>(b, st)));
-    }
-    TT_TRY(cholqr2_block32(h, Xi, s, p, h->ibuf + 6, st));
-  }
-  const int k = nblk * p;
-  // H = Q^T G Q (FP32 products, FP64 accumulation)
-  float* GQ32 = h->KGQ;
-  TT_CU(cudaMemsetAsync(GQ32, 0, (size_t)s * k * sizeof(float), st));
-  GemmArgs g;
-  g.M = s; g.N = k; g.K = s; g.atomic = 1; g.allow_splitk = 1;
-  g.A.p = G32; g.A.rs = s; g.A.cs = 1;
-  g.B.p = Qb; g.B.rs = 1; g.B.cs = s;
-  g.C = GQ32; g.c_rs = 1; g.c_cs = s;
-  TT_CU((gemm<float, float, float, float, float>(g, st)));
-  TT_CU(cudaMemsetAsync(h->H, 0, (size_t)k * k * sizeof(double), st));
-  GemmArgs hh;
-  hh.M = k; hh.N = k; hh.K = s; hh.atomic = 1; hh.allow_splitk = 1;
-  hh.A.p = Qb; hh.A.rs = s; hh.A.cs = 1;
-  hh.B.p = GQ32; hh.B.rs = 1; hh.B.cs = s;
-  hh.C = h->H; hh.c_rs = k; hh.c_cs = 1;
-  TT_CU((gemm<float, float, float, double, float>(hh, st)));
+  TT_CU(launch_krylov(h->G, h->G32, s, Qb, h->kpart, h->H, h->ksync, h->ibuf + 6,
+                      0x5eedull + (uint64_t)s, st));
   TT_CU(cudaMemsetAsync(h->bjflags, 0, 4 * sizeof(int), st));
   TT_CU(jacobi_eig<float>(h->H, k, k, h->w32, h->V32, h->bjw32, h->bjflags + 3, st));
   TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, k * sizeof(float), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_dbl, h->trace, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_int + 6, h->ibuf + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_int + 7, h->ksync + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
   ph_end(h, st);
   TT_TRY(sync_read(h, st));
   ph_begin(h, PH_EIG, st, 0.0, 0.0);
+  if (h->h_int[7]) return TTICE_ETIMEOUT;  // a grid barrier of the Krylov kernel gave up
   if (h->h_int[6]) return TTICE_OK;  // the Krylov blocks lost rank: leave it to the full solver
   // leading part needed: smallest r with trace - sum_{j<r} theta_j <= eps^2 (sizes the RR step)
   const double tr = h->h_dbl[0];
@@ -792,11 +740,12 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
   TT_TRY(grow_last(h, h->n_obs + b));
   void** S1 = h->stage;
   TT_TRY((chain<WT, TY>(h, Y, b, S1, true, st)));
-  TT_CU(launch_decision(h->rho2, h->y2, b, h->eps, h->d, h->h.skip_mode, h->h.subselect,
+  TT_CU(launch_decision(h->rho2, h->d, h->y2, b, h->eps, h->d, h->h.skip_mode, h->h.subselect,
                         h->h.eps_upd_mode, h->dec, h->sel, st));
   TT_CU(cudaMemcpyAsync(h->h_dec, h->dec, sizeof(Decision), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_sel, h->sel, b * sizeof(int), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_int + 5, h->ibuf + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_rho2, h->rho2, (size_t)h->d * b * sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_TRY(sync_read(h, st));
   const Decision dec = *h->h_dec;
   if (h->h_int[5]) return TTICE_ETIMEOUT;  // a staged copy of the first pass never completed
@@ -818,11 +767,30 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
       D0 = static_cast<const TY*>(h->dgather);
     }
     const WT* X = nullptr;  // stage input for i >= 1
+    // While no core has grown in this update, D_i and U_i^T D_i of the selected observations are
+    // exactly what the first pass computed (same cores, same inputs): its stage outputs and per-stage
+    // residual norms are reused instead of recomputed.
+    bool pristine = true;
+    int first_grown = h->d;  // first core that gained directions
     int rc = TTICE_OK;
     for (int i = 0; i < h->d && rc == TTICE_OK; ++i) {
       const int64_t m = h->r[i] * h->n[i], L = h->L[i];
       const int64_t ri = h->r[i + 1];
       int grew = 0;
+      // pristine: the first pass's projections U_i^T D_i of the selected observations
+      const WT* Wp = nullptr;
+      if (pristine && ri > 0 && m > 0) {
+        if (nsel == b) {
+          Wp = static_cast<const WT*>(S1[i]);
+        } else {
+          WT* g = static_cast<WT*>(h->dstage[i]);
+          rc = cu(launch_gather_obs<WT>(static_cast<const WT*>(S1[i]), g, h->sel, nsel, ri * L, st));
+          if (rc != TTICE_OK) break;
+          Wp = g;
+        }
+      }
+      const TY* D0i = D0;
+      const WT* Xi = X;
       if (m > 0 && !((double)ri >= h->h.occupancy_tau * (double)m)) {
         WT* R = static_cast<WT*>(h->Rbuf);
         const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
@@ -834,14 +802,22 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
                    4.0 * nsel * (double)m * L * ri);
         }
         bool small = false;  // ||R_i||_F <= eps_c: the rank rule gives 0 without any eigenvalue
-        if (ri > 0) {
+        if (ri > 0 && pristine) {
+          double t = 0.0;
+          for (int z = 0; z < nsel; ++z) t += h->h_rho2[(int64_t)i * b + h->h_sel[z]];
+          small = std::sqrt(t) <= dec.eps_c;
+          if (!small) {
+            if (i == 0) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wp, D0i, m, L, ri, nsel, R, nullptr, st);
+            else rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wp, Xi, m, L, ri, nsel, R, nullptr, st);
+          }
+        } else if (ri > 0) {
           rc = cu(cudaMemsetAsync(h->rn2, 0, nsel * sizeof(double), st));
           if (rc == TTICE_OK && i == 0) {
-            rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0, m, L, ri, nsel, Wt, st);
-            if (rc == TTICE_OK) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wt, D0, m, L, ri, nsel, R, h->rn2, st);
+            rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0i, m, L, ri, nsel, Wt, st);
+            if (rc == TTICE_OK) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wt, D0i, m, L, ri, nsel, R, h->rn2, st);
           } else if (rc == TTICE_OK) {
-            rc = proj<WT, WT, WT>(Ui, h->ldu[i], X, m, L, ri, nsel, Wt, st);
-            if (rc == TTICE_OK) rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wt, X, m, L, ri, nsel, R, h->rn2, st);
+            rc = proj<WT, WT, WT>(Ui, h->ldu[i], Xi, m, L, ri, nsel, Wt, st);
+            if (rc == TTICE_OK) rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wt, Xi, m, L, ri, nsel, R, h->rn2, st);
           }
           if (rc == TTICE_OK) rc = cu(cudaMemcpyAsync(h->h_rn2, h->rn2, nsel * sizeof(double),
                                                       cudaMemcpyDeviceToHost, st));
@@ -852,8 +828,8 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
             small = std::sqrt(t) <= dec.eps_c;
           }
         } else {
-          if (i == 0) rc = cu(launch_cast<TY, WT>(D0, R, (int64_t)nsel * m * L, st));
-          else rc = cu(cudaMemcpyAsync(R, X, (size_t)nsel * m * L * sizeof(WT), cudaMemcpyDeviceToDevice, st));
+          if (i == 0) rc = cu(launch_cast<TY, WT>(D0i, R, (int64_t)nsel * m * L, st));
+          else rc = cu(cudaMemcpyAsync(R, Xi, (size_t)nsel * m * L * sizeof(WT), cudaMemcpyDeviceToDevice, st));
         }
         ph_end(h, st);
         if (rc != TTICE_OK) break;
@@ -882,25 +858,33 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
         }
       }
       h->stats.new_dirs[i] = grew;
+      if (grew > 0 && first_grown == h->d) first_grown = i;
       // D_{i+1} = reshape(U_i^T D_i) with the updated core
       if (i + 1 < h->d) {
         const int64_t rn = h->r[i + 1];
+        if (m == 0 || rn == 0) break;  // nothing flows to the next cores
+        if (pristine && grew == 0) {
+          X = Wp;  // U_i is unchanged: the first pass's stage output
+          continue;
+        }
+        pristine = false;
         const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
                                          : reinterpret_cast<const WT*>(h->Uf[i]);
         WT* Wn = static_cast<WT*>(h->dstage[i]);
-        if (m == 0 || rn == 0) break;  // nothing flows to the next cores
         {
           const double sx = (i == 0) ? sizeof(TY) : sizeof(WT);
           ph_begin(h, PH_DPROJ, st, nsel * (sx * m * L + sizeof(WT) * (double)rn * L),
                    2.0 * nsel * (double)m * L * rn);
         }
-        if (i == 0 && sizeof(TY) == 4 && k1_tma_supported(D0, L, (int)m, (int)rn))
-          rc = cu(launch_k1_tma<WT>(reinterpret_cast<const float*>(D0), nsel, L, (int)m, (int)rn, Ui,
+        if (i == 0 && sizeof(TY) == 4 && k1_tma_supported(D0i, L, (int)m, (int)rn))
+          rc = cu(launch_k1_tma<WT>(reinterpret_cast<const float*>(D0i), nsel, L, (int)m, (int)rn, Ui,
                                     h->ldu[i], Wn, nullptr, nullptr, nullptr, h->ibuf + 5, st));
-        else if (i == 0) rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0, m, L, rn, nsel, Wn, st);
-        else rc = proj<WT, WT, WT>(Ui, h->ldu[i], X, m, L, rn, nsel, Wn, st);
+        else if (i == 0) rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0i, m, L, rn, nsel, Wn, st);
+        else rc = proj<WT, WT, WT>(Ui, h->ldu[i], Xi, m, L, rn, nsel, Wn, st);
         ph_end(h, st);
         X = Wn;
+      } else if (grew > 0) {
+        pristine = false;
       }
     }
     if (rc != TTICE_OK) {
@@ -909,8 +893,9 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
       h->ev_used = 0;
       return rc;
     }
-    // project every observation onto the updated cores (Algorithm 2, last two steps)
-    TT_TRY((chain<WT, TY>(h, Y, b, S1, false, st)));
+    // project every observation onto the updated cores (Algorithm 2, last two steps); the stages
+    // before the first core that grew are the first pass's, unchanged
+    if (first_grown < h->d) TT_TRY((chain<WT, TY>(h, Y, b, S1, false, st, first_grown)));
   }
   const int rd = (int)h->r[h->d];
   TT_CU(launch_append_last_t<WT>(static_cast<const WT*>(S1[h->d - 1]), b, rd, h->last, h->n_obs,
@@ -930,7 +915,7 @@ int project_impl(ttice_s* h, const TY* Y, int b, double* coeffs, double* rel, cu
   TT_TRY((chain<WT, TY>(h, Y, b, h->stage, rel != nullptr, st)));
   const int rd = (int)h->r[h->d];
   if (coeffs && rd > 0) TT_CU((launch_cast<WT, double>(static_cast<const WT*>(h->stage[h->d - 1]), coeffs, (int64_t)b * rd, st)));
-  if (rel) TT_CU(launch_rel_err(h->rho2, h->y2, b, rel, st));
+  if (rel) TT_CU(launch_rel_err(h->rho2, h->d, h->y2, b, rel, st));
   return TTICE_OK;
 }
 
@@ -1031,10 +1016,8 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 4);
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->G32, s * s);
   if (rc == TTICE_OK) rc = dalloc<float>(&h->KQ, s * kKry);
-  if (rc == TTICE_OK) rc = dalloc<float>(&h->KGQ, s * kKry);
-  if (rc == TTICE_OK) rc = dalloc<float>(&h->KW2, s * kKryP);
-  if (rc == TTICE_OK) rc = dalloc<float>(&h->KT, kKry * kKryP);
-  if (rc == TTICE_OK) rc = dalloc<float>(&h->KR32, kKryP * kKryP);
+  if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->kpart, krylov_part_floats());
+  if (rc == TTICE_OK) rc = dalloc<unsigned int>(&h->ksync, 4);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->KV, std::max<int64_t>(s * kKryP, kKry * kKry));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->res, kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Q, s * kRR);
@@ -1052,7 +1035,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   for (int i = 1; i <= d; ++i) maxcap = std::max(maxcap, h->cap[i]);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->P, maxcap * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->part, 2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)));
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->rho2, B);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->rho2, (int64_t)h->d * B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rn2, B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->y2, B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->trace, 1);
@@ -1065,6 +1048,8 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_w32, s * sizeof(float)) != cudaSuccess) rc = TTICE_ENOMEM;
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_dbl, 256 * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_rn2, B * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_rho2, (size_t)h->d * B * sizeof(double)) != cudaSuccess)
+    rc = TTICE_ENOMEM;
   if (rc == TTICE_OK) rc = grow_last(h, std::max<int64_t>(h->capc.obs_reserve, 1));
   if (rc == TTICE_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TTICE_ECUDA;
   if (rc != TTICE_OK) {

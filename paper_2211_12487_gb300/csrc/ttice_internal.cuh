@@ -37,6 +37,8 @@ struct GemmArgs {
   double* norm = nullptr; // optional: += sum of squares of the C(z) entries into norm[z1]
   int norm_rows = 0;      // with norm: accumulate per output row instead (norm[row])
   int allow_splitk = 0;   // with atomic: split K across CTAs when the tile grid is small
+  int64_t c_zero_elems = 0;  // without atomic: C spans this many elements from C; if the tile grid
+                             // is small, zero them and split K with atomic adds instead of stores
 };
 
 template <typename TA, typename TB, typename TX, typename TC, typename ACC>
@@ -73,7 +75,8 @@ struct Decision {
   int nonfinite;
 };
 
-cudaError_t launch_decision(const double* rho2, const double* y2, int b, double eps, int d,
+// rho2s: squared residuals per TT stage and observation (stage-major, nst x b)
+cudaError_t launch_decision(const double* rho2s, int nst, const double* y2, int b, double eps, int d,
                             int skip_mode, int subselect, int eps_upd_mode, Decision* dec,
                             int* sel, cudaStream_t st);
 
@@ -121,9 +124,13 @@ cudaError_t launch_canonical_sign(double* V, int64_t m, int k, int64_t ld, cudaS
 // Cholesky-QR step support: given S = V^T V (k x k, FP64, ld k), overwrite Rinv (k x k, ld k) with
 // the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  status=1 if not positive definite.
 cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st);
-// Cholesky-QR twice of an s x p block (p <= 8) in one CTA (eig.cu)
-template <typename T>
-cudaError_t launch_cholqr2_small(T* X, int64_t s, int p, int* status, cudaStream_t st);
+// Block-Krylov basis Q (s x 64, FP32) of the Gram G and H = Q^T G Q (64 x 64, FP64) in one
+// cooperative launch (krylov.cu).  G32: s x s FP32 scratch; part: krylov_part_floats() floats;
+// sync: 3 words (zeroed by the launcher; sync[2] != 0 afterwards means a grid barrier timed out);
+// *lost is set if a block lost rank.  Requires s >= 64.
+int64_t krylov_part_floats();
+cudaError_t launch_krylov(const double* G, float* G32, int64_t s, float* Q, float* part, double* H,
+                          unsigned int* sync, int* lost, uint64_t seed, cudaStream_t st);
 // scale column j of V (m x k, ld) by 1/sqrt(theta[j])
 cudaError_t launch_scale_cols_rsqrt(double* V, int64_t m, int k, int64_t ld, const double* theta,
                                     cudaStream_t st);
@@ -144,8 +151,8 @@ cudaError_t launch_fill_hash(double* x, int64_t n, uint64_t seed, cudaStream_t s
 // res[j] = ||GQ[:,j] - theta[j] Q[:,j]|| for j < k (column-major, ld s)
 cudaError_t launch_ritz_residual(const double* GQ, const double* Q, const double* theta, int64_t s,
                                  int k, double* res, cudaStream_t st);
-// rel[j] = sqrt(rho2[j]/y2[j]) (0 when y2 = 0)
-cudaError_t launch_rel_err(const double* rho2, const double* y2, int b, double* rel,
+// rel[j] = sqrt(sum_i rho2s[i b + j] / y2[j]) (0 when y2 = 0); rho2s stage-major, nst x b
+cudaError_t launch_rel_err(const double* rho2s, int nst, const double* y2, int b, double* rel,
                            cudaStream_t st);
 // gather top-K eigenvector columns of a float/double s x s column-major matrix into FP64 Q (s x K)
 template <typename T>

@@ -47,8 +47,9 @@ def _interface_projectors(cores, max_rows=2048):
 
 
 def run_pair(T, frames, batch, eps, *, precision="fp64", tol=1e-10, check_eps=True,
-             oracle_kw=None, gpu_kw=None):
-    """Stream `frames` through the GPU and the oracle; compare after every increment."""
+             oracle_kw=None, gpu_kw=None, stats_out=None):
+    """Stream `frames` through the GPU and the oracle; compare after every increment.  With
+    `stats_out` (a list), the GPU's per-update statistics are appended to it."""
     dims = frames.shape[1:]
     in_dtype = frames.dtype
     g = T.TTICE(dims, eps, precision=precision, input_dtype=in_dtype, max_batch=batch,
@@ -58,6 +59,8 @@ def run_pair(T, frames, batch, eps, *, precision="fp64", tol=1e-10, check_eps=Tr
     for k in range(0, frames.shape[0], batch):
         Yk = frames[k:k + batch]
         st = g.update(dev[k:k + batch])
+        if stats_out is not None:
+            stats_out.append((st.krylov_solves, st.krylov_fallbacks, list(st.new_dirs[:len(dims)])))
         so = o.update(Yk.double().numpy(), check_error=check_eps)
         assert list(st.ranks[:len(dims) + 1]) == so.ranks[:len(dims) + 1], (k, list(st.ranks[:len(dims) + 2]), so.ranks)
         assert bool(st.skipped) == so.skipped, k
@@ -239,6 +242,9 @@ def test_fp32_projection_mode(T):
 
 def test_video_c1_prefix_fp32(T):
     """Full-size video frames on the FP32 path (Krylov / Jacobi eigen-solves with FP64 Rayleigh-Ritz):
-    ranks and decisions equal to the oracle's, eps met on every increment."""
+    ranks and decisions equal to the oracle's, eps met on every increment, and the block-Krylov
+    solver (Gram sides above 96) both runs and certifies its result."""
     Y = blob_video(0, 32)
-    run_pair(T, Y, 8, 0.1, precision="fp32", tol=1e-4)
+    stats = []
+    run_pair(T, Y, 8, 0.1, precision="fp32", tol=1e-4, stats_out=stats)
+    assert sum(x[0] for x in stats) >= 1, stats
