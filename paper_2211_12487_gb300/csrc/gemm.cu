@@ -21,8 +21,9 @@ __device__ __forceinline__ T ld_elem(const void* p, int64_t off) {
 
 template <typename TA, typename TB, typename TX, typename TC, typename ACC, int BM, int BN, int BK,
           int TM, int TN>
-__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64_t kchunk) {
-  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) gemm_kernel(GemmArgs g, int ksplit, int64_t kchunk) {
+  constexpr int NT = (BM / TM) * (BN / TN);  // threads: one per TM x TN block of outputs
+  static_assert(NT % 32 == 0 && NT <= 256, "whole warps, at most 256 threads");
   __shared__ ACC As[BK][BM + 1];
   __shared__ ACC Bs[BK][BN + 1];
   const int z = blockIdx.z;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
   int slab = 0;
 
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += 256) {
+    for (int e = tid; e < BM * BK; e += NT) {
       int mm, kk;
       if (a_kfast) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
       const int64_t gm = m0 + mm, gk = k0 + kk;
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
       if (gm < g.M && gk < kend) v = (ACC)ld_elem<TA>(g.A.p, aoff + gm * g.A.rs + gk * g.A.cs);
       As[kk][mm] = v;
     }
-    for (int e = tid; e < BN * BK; e += 256) {
+    for (int e = tid; e < BN * BK; e += NT) {
       int nn, kk;
       if (b_nfast) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
       const int64_t gn = n0 + nn, gk = k0 + kk;
@@ -139,13 +140,13 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
   if (g.norm && g.norm_rows) {
     // reduce each tile row over the BN/TN threads that share it, then one atomic per row per CTA
     __shared__ double rsum[BM];
-    for (int i = tid; i < BM; i += 256) rsum[i] = 0.0;
+    for (int i = tid; i < BM; i += NT) rsum[i] = 0.0;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < TM; ++i)
       if (rowss[i] != ACC(0)) atomicAdd(&rsum[ty + i * (BM / TM)], (double)rowss[i]);
     __syncthreads();
-    for (int i = tid; i < BM; i += 256) {
+    for (int i = tid; i < BM; i += NT) {
       const int64_t gm = m0 + i;
       if (gm < g.M && rsum[i] != 0.0) atomicAdd(g.norm + gm, rsum[i]);
     }
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g, int ksplit, int64
 template <typename TA, typename TB, typename TX, typename TC, typename ACC, int BM, int BN, int BK,
           int TM, int TN>
 cudaError_t run(const GemmArgs& g, cudaStream_t st) {
+  constexpr int NT = (BM / TM) * (BN / TN);
   const int64_t gx = (g.N + BN - 1) / BN, gy = (g.M + BM - 1) / BM;
   int ksplit = 1;
   int64_t kchunk = g.K > 0 ? g.K : 1;
@@ -186,11 +188,11 @@ cudaError_t run(const GemmArgs& g, cudaStream_t st) {
     GemmArgs ga = g;
     ga.atomic = 1;
     note_launch();
-    gemm_kernel<TA, TB, TX, TC, ACC, BM, BN, BK, TM, TN><<<grid, 256, 0, st>>>(ga, ksplit, kchunk);
+    gemm_kernel<TA, TB, TX, TC, ACC, BM, BN, BK, TM, TN><<<grid, NT, 0, st>>>(ga, ksplit, kchunk);
     return cudaGetLastError();
   }
   note_launch();
-  gemm_kernel<TA, TB, TX, TC, ACC, BM, BN, BK, TM, TN><<<grid, 256, 0, st>>>(g, ksplit, kchunk);
+  gemm_kernel<TA, TB, TX, TC, ACC, BM, BN, BK, TM, TN><<<grid, NT, 0, st>>>(g, ksplit, kchunk);
   return cudaGetLastError();
 }
 
@@ -203,6 +205,9 @@ cudaError_t gemm(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 32 && g.N <= 32) return run<TA, TB, TX, TC, ACC, 32, 32, 16, 2, 2>(g, st);
   if (g.M <= 16) return run<TA, TB, TX, TC, ACC, 16, 256, 16, 2, 8>(g, st);
   if (g.M <= 32) return run<TA, TB, TX, TC, ACC, 32, 128, 16, 4, 4>(g, st);
+  // a few columns (new directions, last stages): narrow tiles, no padding of N, many CTAs (which
+  // matters most for FP64, at 1/64 of the FP32 rate per SM)
+  if (g.N <= 4) return run<TA, TB, TX, TC, ACC, 32, 4, 16, 1, 1>(g, st);
   if (g.N <= 16 && g.M <= 4096) return run<TA, TB, TX, TC, ACC, 32, 16, 16, 2, 1>(g, st);
   if (g.N <= 16) return run<TA, TB, TX, TC, ACC, 256, 16, 16, 8, 2>(g, st);
   return run<TA, TB, TX, TC, ACC, 64, 64, 16, 4, 4>(g, st);

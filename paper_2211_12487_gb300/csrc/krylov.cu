@@ -1,26 +1,35 @@
-// Block-Krylov basis of a residual Gram matrix in one cooperative launch (the candidate step of the
-// mixed-precision truncated eigen-solve of Eq. 9; the FP64 Rayleigh-Ritz step and its certification
-// follow on the host side).
+// Block-Krylov basis of a residual Gram matrix in one thread-block cluster (the candidate step of
+// the mixed-precision truncated eigen-solve of Eq. 9; the FP64 Rayleigh-Ritz step and its
+// certification follow on the host side).
 //
 // Q = [X_0, ..., X_7] (s x 64, column-major, ld s): X_0 a fixed pseudo-random block, X_i = G X_{i-1}
 // projected out of the earlier blocks twice (block classical Gram-Schmidt, CGS2) and orthonormalised
-// by Cholesky-QR applied twice; then H = Q^T G Q (64 x 64, FP64 output).  G is the FP64 Gram; the
-// kernel keeps an FP32 copy (products and per-CTA sums in FP32, cross-CTA sums in FP64).
+// by Cholesky-QR applied twice; H = Q^T G Q (64 x 64, FP64).  Products and per-CTA sums in FP32,
+// sums across CTAs in FP64.
 //
-// Layout of the work: P CTAs, CTA c owns the rows [c nr, (c+1) nr) of every basis column, so every
-// update of the basis is row-local.  Each reduction over rows (the projections Q^T X_i, the block
-// Grams X_i^T X_i, H) writes one partial per CTA into a ping-pong buffer; after a grid barrier every
-// CTA sums the P partials itself, in CTA order, so all CTAs hold bit-identical sums (and apply the
-// same Cholesky factor) and the result does not depend on scheduling.  G X_{i-1} stages X_{i-1} in
-// shared memory and reads G rows from L2.
+// One cluster of C CTAs (16 where the device allows it, else 8), all on one GPC: CTA c owns the rows
+// [c nr, (c+1) nr) of every basis column and keeps them in shared memory, so every update of the
+// basis is local.  Reductions over rows (the projections Q^T X_i, the block Grams, H's last block
+// column) write one partial per CTA into shared memory; after a cluster barrier every CTA reads the C
+// partials through distributed shared memory and sums them in rank order, so all CTAs hold
+// bit-identical sums (and apply the same Cholesky factor).  G X_{i-1} reads X_{i-1} from the owners'
+// shared memory in chunks, and the CTA's rows of G from shared memory when they fit (else from an
+// FP32 copy in global memory that only this CTA reads).
 //
-// Grid barriers are bounded: a CTA that waits longer than kSpinLimit polls (or sees the error flag
-// another CTA raised) sets the flag and returns; the host reports TTICE_ETIMEOUT.  The launch is
-// cooperative, so all CTAs are resident.
+// H needs no G Q product: with G X_c = Q_{<=c} Ttot + X_{c+1} Rtot (the two CGS2 coefficient blocks
+// summed, and R2 R1 of the two Cholesky-QR passes), block column c of H is Ttot over the earlier
+// blocks (its diagonal block symmetrised), Rtot below it, and zero further down (the block-Lanczos
+// structure).  Only the last block column uses an explicit G X_7.
+//
+// Cluster barriers are hardware barriers; the kernel has no spin loop and no early exit.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <mutex>
 
 #include "ttice_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ttice {
 namespace {
@@ -31,9 +40,9 @@ constexpr int kBP = 8;            // block width
 constexpr int kNBk = 8;           // blocks
 constexpr int kKB = kBP * kNBk;   // basis size
 constexpr int kNQ = kBP * (kBP + 1) / 2;
-constexpr int kSlot = kKB * kKB;  // floats per CTA in a partial buffer (the largest partial is H's)
-constexpr int kMaxP = 128;
-constexpr long long kSpinLimit = 1ll << 22;
+constexpr int kPartMax = kKB * kBP;  // the largest per-CTA partial (H's last block column)
+constexpr int kChunk = 1024;         // rows of X_{i-1} staged at a time
+constexpr size_t kSmemCap = 208 * 1024;
 
 __device__ __forceinline__ double hash_uniform(uint64_t seed, int64_t i) {
   // splitmix64 of (seed, index), mapped to [-1, 1)
@@ -44,58 +53,42 @@ __device__ __forceinline__ double hash_uniform(uint64_t seed, int64_t i) {
   return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-// Sense-free counting barrier over the whole grid.  sync[0] = arrivals, sync[1] = generation,
-// sync[2] = error flag.  Returns false (in every thread of the CTA) on timeout or error.
-__device__ bool grid_barrier(unsigned int* sync, unsigned int nblocks) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = sync + 1;
-    volatile int* verr = reinterpret_cast<volatile int*>(sync + 2);
-    int ok = 1;
-    const unsigned int g = *vgen;
-    __threadfence();
-    if (atomicAdd(sync, 1u) == nblocks - 1) {
-      atomicExch(sync, 0u);
-      __threadfence();
-      atomicAdd(sync + 1, 1u);
-    } else {
-      long long it = 0;
-      while (*vgen == g) {
-        if (*verr != 0) { ok = 0; break; }
-        if (++it > kSpinLimit) { atomicExch(reinterpret_cast<int*>(sync + 2), 1); ok = 0; break; }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (*verr != 0) ok = 0;
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
+__host__ __device__ inline int krylov_ldq(int nr) { return nr | 1; }
 
-struct Rows {
-  int r0, r1;
+// This CTA's rows [r0, r0 + nloc) of the basis: q[col * ldq + rl] (odd ldq: conflict-free columns).
+struct Loc {
+  int r0, nloc, nr, ldq;
+  float* q;
 };
 
-// Cholesky-QR twice of the block columns [col0, col0 + kBP) restricted to this CTA's rows, with the
-// block Gram summed over all CTAs.  Rtot (8 x 8, row-major, upper) receives R2 R1, the factor with
-// X_before = X_after Rtot.  Returns false if a barrier failed.
-__device__ bool block_cholqr2(float* Q, int s, int col0, Rows rw, float* part, int& pp, unsigned int* sync,
-                              int* lost, float* wsum, double* S, float* Rt, float* Rid, float* R1,
-                              float* Rtot) {
+// Sum over the cluster's CTAs of entries [0, n) of the partial buffer `part` (same offset in every
+// CTA's shared memory), in rank order, in FP64.  put(e, v) is called by the thread that owns e.
+template <typename F>
+__device__ void cluster_sum(cg::cluster_group& cl, float* part, int n, F put) {
+  const unsigned int C = cl.num_blocks();
+  for (int e = threadIdx.x; e < n; e += kKT) {
+    double v = 0.0;
+#pragma unroll 4
+    for (unsigned int c = 0; c < C; ++c) v += (double)cl.map_shared_rank(part, c)[e];
+    put(e, v);
+  }
+}
+
+// Cholesky-QR twice of the block columns [col0, col0 + kBP) of the local rows, with the block Gram
+// summed over the cluster.  Rtot (8 x 8, row-major, upper) receives R2 R1, the factor with
+// X_before = X_after Rtot.
+__device__ void block_cholqr2(cg::cluster_group& cl, Loc L, int col0, float* part2, int& pp, int* lost,
+                              float* wsum, double* S, float* Rt, float* Rid, float* R1, float* Rtot) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned int P = gridDim.x;
   auto qi = [](int a, int b) { return a * kBP - a * (a + 1) / 2 + b; };
   for (int pass = 0; pass < 2; ++pass) {
     float acc[kNQ];
 #pragma unroll
     for (int q = 0; q < kNQ; ++q) acc[q] = 0.f;
-    for (int r = rw.r0 + tid; r < rw.r1; r += kKT) {
+    for (int rl = tid; rl < L.nloc; rl += kKT) {
       float x[kBP];
 #pragma unroll
-      for (int a = 0; a < kBP; ++a) x[a] = Q[(int64_t)(col0 + a) * s + r];
+      for (int a = 0; a < kBP; ++a) x[a] = L.q[(col0 + a) * L.ldq + rl];
 #pragma unroll
       for (int a = 0; a < kBP; ++a)
 #pragma unroll
@@ -109,22 +102,19 @@ __device__ bool block_cholqr2(float* Q, int s, int col0, Rows rw, float* part, i
       if (lane == 0) wsum[warp * kNQ + q] = v;
     }
     __syncthreads();
-    float* mine = part + ((int64_t)pp * P + blockIdx.x) * kSlot;
+    float* mine = part2 + pp * kPartMax;
     if (tid < kNQ) {
       float v = 0.f;
       for (int w = 0; w < kKW; ++w) v += wsum[w * kNQ + tid];
       mine[tid] = v;
     }
-    if (!grid_barrier(sync, P)) return false;
-    const float* all = part + (int64_t)pp * P * kSlot;
-    pp ^= 1;
-    if (tid < kNQ) {
-      double v = 0.0;
-      for (unsigned int c = 0; c < P; ++c) v += (double)__ldcg(all + (int64_t)c * kSlot + tid);
+    cl.sync();
+    cluster_sum(cl, mine, kNQ, [&](int e, double v) {
       int a = 0;
-      while (tid >= qi(a, kBP)) ++a;
-      S[a * kBP + (tid - qi(a, 0))] = v;
-    }
+      while (e >= qi(a, kBP)) ++a;
+      S[a * kBP + (e - qi(a, 0))] = v;
+    });
+    pp ^= 1;
     __syncthreads();
     if (warp == 0) {
       // right-looking Cholesky, lane c keeps column c of the upper triangle
@@ -151,7 +141,7 @@ __device__ bool block_cholqr2(float* Q, int s, int col0, Rows rw, float* part, i
         for (int k = 0; k < kBP; ++k) Rt[k * kBP + lane] = (k <= lane) ? (float)col[k] : 0.f;
         Rid[lane] = (float)my_inv;
       }
-      if (lane == 0 && bad && blockIdx.x == 0) atomicOr(lost, 1);
+      if (lane == 0 && bad && cl.block_rank() == 0) atomicOr(lost, 1);
     }
     __syncthreads();
     if (pass == 0) {
@@ -162,10 +152,10 @@ __device__ bool block_cholqr2(float* Q, int s, int col0, Rows rw, float* part, i
       for (int k = i; k <= j; ++k) v = fmaf(Rt[i * kBP + k], R1[k * kBP + j], v);
       Rtot[tid] = v;
     }
-    for (int r = rw.r0 + tid; r < rw.r1; r += kKT) {
+    for (int rl = tid; rl < L.nloc; rl += kKT) {
       float x[kBP];
 #pragma unroll
-      for (int a = 0; a < kBP; ++a) x[a] = Q[(int64_t)(col0 + a) * s + r];
+      for (int a = 0; a < kBP; ++a) x[a] = L.q[(col0 + a) * L.ldq + rl];
 #pragma unroll
       for (int c = 0; c < kBP; ++c) {
         float v = x[c];
@@ -174,135 +164,155 @@ __device__ bool block_cholqr2(float* Q, int s, int col0, Rows rw, float* part, i
         x[c] = v * Rid[c];
       }
 #pragma unroll
-      for (int c = 0; c < kBP; ++c) Q[(int64_t)(col0 + c) * s + r] = x[c];
+      for (int c = 0; c < kBP; ++c) L.q[(col0 + c) * L.ldq + rl] = x[c];
     }
     __syncthreads();
   }
-  return true;
 }
 
-// Y[rl, a] = sum_k G[r0 + rl, k] X[k, a] for this CTA's rows (X staged in xs, s x kBP column-major),
-// four rows per warp so that every staged X value feeds four rows.  G rows come from the shared slab
-// (ld gld) or from the FP32 copy in global memory.  out(rl, a, v) stores the result.
-template <typename Out>
-__device__ void g_times_block(const float* gbase, int64_t gld, const float* xs, int s, int nloc, Out out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int rb = warp * 4; rb < nloc; rb += kKW * 4) {
-    float acc[4][kBP];
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-      for (int a = 0; a < kBP; ++a) acc[t][a] = 0.f;
-    const float* g[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) g[t] = gbase + (int64_t)min(rb + t, nloc - 1) * gld;
-#pragma unroll 2
-    for (int k = lane; k < s; k += 32) {
-      float x[kBP];
-#pragma unroll
-      for (int a = 0; a < kBP; ++a) x[a] = xs[a * s + k];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const float gv = g[t][k];
-#pragma unroll
-        for (int a = 0; a < kBP; ++a) acc[t][a] = fmaf(gv, x[a], acc[t][a]);
-      }
+// out[a * ldo + rl] = sum_k G[r0 + rl, k] X[k, a] for this CTA's rows, with X = the block columns
+// [cprev, cprev + kBP) of the basis, read from the owners' shared memory in chunks of kChunk rows.
+// Four rows per warp, so that every staged X value feeds four rows.
+__device__ void g_times_block(cg::cluster_group& cl, Loc L, int s, int cprev, const float* gbase, int64_t gld,
+                              float* xs, float* out, int ldo) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < L.nloc * kBP; e += kKT) {
+    const int a = e / L.nloc, rl = e - a * L.nloc;
+    out[a * ldo + rl] = 0.f;
+  }
+  for (int k0 = 0; k0 < s; k0 += kChunk) {
+    const int kc = min(kChunk, s - k0);
+    __syncthreads();
+    for (int e = tid; e < kc * kBP; e += kKT) {
+      const int a = e / kc, k = e - a * kc;
+      const int row = k0 + k, owner = row / L.nr;
+      const float* rq = cl.map_shared_rank(L.q, (unsigned int)owner);
+      xs[a * kc + k] = rq[(cprev + a) * L.ldq + (row - owner * L.nr)];
     }
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-      for (int a = 0; a < kBP; ++a) {
-        float v = acc[t][a];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[t][a] = v;
-      }
-    if (lane == 0) {
+    __syncthreads();
+    for (int rb = warp * 4; rb < L.nloc; rb += kKW * 4) {
+      float acc[4][kBP];
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        if (rb + t < nloc) {
 #pragma unroll
-          for (int a = 0; a < kBP; ++a) out(rb + t, a, acc[t][a]);
+        for (int a = 0; a < kBP; ++a) acc[t][a] = 0.f;
+      const float* g[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) g[t] = gbase + (int64_t)min(rb + t, L.nloc - 1) * gld + k0;
+#pragma unroll 2
+      for (int k = lane; k < kc; k += 32) {
+        float x[kBP];
+#pragma unroll
+        for (int a = 0; a < kBP; ++a) x[a] = xs[a * kc + k];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float gv = g[t][k];
+#pragma unroll
+          for (int a = 0; a < kBP; ++a) acc[t][a] = fmaf(gv, x[a], acc[t][a]);
         }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int a = 0; a < kBP; ++a) {
+          float v = acc[t][a];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          acc[t][a] = v;
+        }
+      if (lane == 0) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (rb + t < L.nloc) {
+#pragma unroll
+            for (int a = 0; a < kBP; ++a) out[a * ldo + rb + t] += acc[t][a];
+          }
+      }
     }
   }
+  __syncthreads();
 }
 
-// gslab != 0: this CTA's rows of G are kept in shared memory (ld s + 4) for the whole kernel;
-// otherwise they are streamed from the FP32 copy G32 (written here, read only by the same CTA).
+// Shared memory (floats): xs min(s, kChunk)*kBP | q kKB*ldq | gx kBP*ldq | part 2*kPartMax |
+// gslab nr*(s+4)
+struct KrylovShape {
+  int C;
+  int nr;
+  int gslab;
+  size_t smem;
+};
+
+size_t krylov_base_floats(int s, int nr) {
+  const int kc = s < kChunk ? s : kChunk;
+  return (size_t)kc * kBP + (size_t)(kKB + kBP) * krylov_ldq(nr) + 2 * (size_t)kPartMax;
+}
+
 __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32, int s, float* Q,
-                                                     float* part, double* H, unsigned int* sync,
-                                                     int* lost, uint64_t seed, int gslab) {
+                                                     double* H, int* lost, uint64_t seed, int gslab) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float wsum[kKW * kNQ];
   __shared__ double S[kBP * kBP];
   __shared__ float Rt[kBP * kBP], Rid[kBP], R1[kBP * kBP], Rtot[kBP * kBP];
   __shared__ float T[(kKB - kBP) * kBP], Ttot[kKB * kBP];
+  cg::cluster_group cl = cg::this_cluster();
   const int tid = threadIdx.x;
-  const unsigned int P = gridDim.x;
-  const int nr = (s + (int)P - 1) / (int)P;
-  Rows rw;
-  rw.r0 = min(s, (int)blockIdx.x * nr);
-  rw.r1 = min(s, rw.r0 + nr);
-  const int nloc = rw.r1 - rw.r0;
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  Loc L;
+  L.nr = (s + C - 1) / C;
+  L.r0 = min(s, rank * L.nr);
+  L.nloc = min(s, L.r0 + L.nr) - L.r0;
+  L.ldq = krylov_ldq(L.nr);
+  const int kcmax = min(s, kChunk);
+  float* xs = sm;                                   // kChunk x kBP staging
+  L.q = xs + (size_t)kcmax * kBP;                   // kKB x ldq local rows of Q
+  float* gx = L.q + (size_t)kKB * L.ldq;            // kBP x ldq local rows of G X_7
+  float* part2 = gx + (size_t)kBP * L.ldq;          // 2 x kPartMax partial sums (ping-pong)
+  float* gs = part2 + 2 * kPartMax;                 // nr x (s + 4) rows of G (gslab)
+  const int nloc = L.nloc;
   int pp = 0;
-  float* xs = sm;                          // s x kBP staging of the previous block
-  float* gs = sm + (int64_t)s * kBP;       // nr x (s + 4) slab of G rows (gslab)
   const int64_t gld = gslab ? (int64_t)s + 4 : (int64_t)s;
-  const float* gbase = gslab ? gs : G32 + (int64_t)rw.r0 * s;
-  const bool writer = blockIdx.x == 0;     // every CTA holds the same coefficients; CTA 0 writes H
+  const float* gbase = gslab ? gs : G32 + (int64_t)L.r0 * s;
+  const bool writer = rank == 0;  // every CTA holds the same coefficients; rank 0 writes H
 
   // FP32 rows of G; this CTA's rows of the start block
   for (int64_t e = tid; e < (int64_t)nloc * s; e += kKT) {
     const int rl = (int)(e / s), k = (int)(e - (int64_t)rl * s);
-    const float v = (float)G[(int64_t)(rw.r0 + rl) * s + k];
+    const float v = (float)G[(int64_t)(L.r0 + rl) * s + k];
     if (gslab) gs[rl * gld + k] = v;
-    else G32[(int64_t)(rw.r0 + rl) * s + k] = v;
+    else G32[(int64_t)(L.r0 + rl) * s + k] = v;
   }
   for (int e = tid; e < nloc * kBP; e += kKT) {
-    const int r = rw.r0 + e % nloc, a = e / nloc;
-    const int64_t i = (int64_t)a * s + r;
-    Q[i] = (float)hash_uniform(seed, i);
+    const int a = e / nloc, rl = e - a * nloc;
+    L.q[a * L.ldq + rl] = (float)hash_uniform(seed, (int64_t)a * s + L.r0 + rl);
   }
   if (writer)
     for (int e = tid; e < kKB * kKB; e += kKT) H[e] = 0.0;
   __syncthreads();
-  if (!block_cholqr2(Q, s, 0, rw, part, pp, sync, lost, wsum, S, Rt, Rid, R1, Rtot)) return;
+  block_cholqr2(cl, L, 0, part2, pp, lost, wsum, S, Rt, Rid, R1, Rtot);
 
   for (int blk = 1; blk <= kNBk; ++blk) {
-    // every CTA's rows of X_{blk-1} are final
-    if (!grid_barrier(sync, P)) return;
+    cl.sync();  // every CTA's rows of X_{blk-1} are final
     const int cprev = (blk - 1) * kBP, ccur = blk * kBP;
-    for (int e = tid; e < s * kBP; e += kKT) {
-      const int a = e / s, k = e - a * s;
-      xs[e] = __ldcg(Q + (int64_t)(cprev + a) * s + k);
-    }
-    __syncthreads();
     if (blk == kNBk) {
       // last block column of H: X_j^T (G X_7) for every block j, from an explicit G X_7
-      float* gx = xs + (int64_t)s * kBP;  // nloc x kBP after the staging (gslab: reuse the tail)
-      if (gslab) gx = gs + (int64_t)nr * gld;
-      g_times_block(gbase, gld, xs, s, nloc, [&](int rl, int a, float v) { gx[rl * kBP + a] = v; });
-      __syncthreads();
-      float* mine = part + ((int64_t)pp * P + blockIdx.x) * kSlot;
+      g_times_block(cl, L, s, cprev, gbase, gld, xs, gx, L.ldq);
+      float* mine = part2 + pp * kPartMax;
       for (int e = tid; e < kKB * kBP; e += kKT) {
         const int a = e / kBP, j = e - a * kBP;
-        const float* qa = Q + (int64_t)a * s + rw.r0;
+        const float* qa = L.q + a * L.ldq;
+        const float* gj = gx + j * L.ldq;
         float v = 0.f;
-        for (int rl = 0; rl < nloc; ++rl) v = fmaf(qa[rl], gx[rl * kBP + j], v);
+        for (int rl = 0; rl < nloc; ++rl) v = fmaf(qa[rl], gj[rl], v);
         mine[e] = v;
       }
-      if (!grid_barrier(sync, P)) return;
+      cl.sync();
       if (writer) {
-        const float* all = part + (int64_t)pp * P * kSlot;
-        for (int e = tid; e < kKB * kBP; e += kKT) {
+        cluster_sum(cl, mine, kKB * kBP, [&](int e, double v) {
           const int a = e / kBP, j = e - a * kBP;
-          double v = 0.0;
-          for (unsigned int c = 0; c < P; ++c) v += (double)__ldcg(all + (int64_t)c * kSlot + e);
           const int col = cprev + j;
           if (a < cprev) { H[a * kKB + col] = v; H[col * kKB + a] = v; }
           else Ttot[(a - cprev) * kBP + j] = (float)v;
-        }
+        });
         __syncthreads();
         for (int e = tid; e < kBP * kBP; e += kKT) {  // symmetrised diagonal block
           const int a = e / kBP, j = e - a * kBP;
@@ -312,42 +322,36 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
       break;
     }
     // X_blk = G X_{blk-1} on this CTA's rows
-    g_times_block(gbase, gld, xs, s, nloc, [&](int rl, int a, float v) {
-      Q[(int64_t)(ccur + a) * s + rw.r0 + rl] = v;
-    });
-    __syncthreads();
+    g_times_block(cl, L, s, cprev, gbase, gld, xs, L.q + ccur * L.ldq, L.ldq);
     // X_blk -= Q_prev (Q_prev^T X_blk), twice; Ttot accumulates the two coefficient blocks
     const int nq = ccur;
     for (int e = tid; e < nq * kBP; e += kKT) Ttot[e] = 0.f;
     for (int pass = 0; pass < 2; ++pass) {
-      float* mine = part + ((int64_t)pp * P + blockIdx.x) * kSlot;
+      float* mine = part2 + pp * kPartMax;
       for (int e = tid; e < nq * kBP; e += kKT) {
         const int a = e / kBP, j = e - a * kBP;
-        const float* qa = Q + (int64_t)a * s + rw.r0;
-        const float* xj = Q + (int64_t)(ccur + j) * s + rw.r0;
+        const float* qa = L.q + a * L.ldq;
+        const float* xj = L.q + (ccur + j) * L.ldq;
         float v = 0.f;
         for (int rl = 0; rl < nloc; ++rl) v = fmaf(qa[rl], xj[rl], v);
         mine[e] = v;
       }
-      if (!grid_barrier(sync, P)) return;
-      const float* all = part + (int64_t)pp * P * kSlot;
-      pp ^= 1;
-      for (int e = tid; e < nq * kBP; e += kKT) {
-        double v = 0.0;
-        for (unsigned int c = 0; c < P; ++c) v += (double)__ldcg(all + (int64_t)c * kSlot + e);
+      cl.sync();
+      cluster_sum(cl, mine, nq * kBP, [&](int e, double v) {
         T[e] = (float)v;
         Ttot[e] += (float)v;
-      }
+      });
+      pp ^= 1;
       __syncthreads();
       for (int e = tid; e < nloc * kBP; e += kKT) {
-        const int j = e / nloc, r = rw.r0 + (e - j * nloc);
-        float v = Q[(int64_t)(ccur + j) * s + r];
-        for (int a = 0; a < nq; ++a) v = fmaf(-Q[(int64_t)a * s + r], T[a * kBP + j], v);
-        Q[(int64_t)(ccur + j) * s + r] = v;
+        const int j = e / nloc, rl = e - j * nloc;
+        float v = L.q[(ccur + j) * L.ldq + rl];
+        for (int a = 0; a < nq; ++a) v = fmaf(-L.q[a * L.ldq + rl], T[a * kBP + j], v);
+        L.q[(ccur + j) * L.ldq + rl] = v;
       }
       __syncthreads();
     }
-    if (!block_cholqr2(Q, s, ccur, rw, part, pp, sync, lost, wsum, S, Rt, Rid, R1, Rtot)) return;
+    block_cholqr2(cl, L, ccur, part2, pp, lost, wsum, S, Rt, Rid, R1, Rtot);
     // block column blk-1 of H (G X_{blk-1} = Q_prev Ttot + X_blk Rtot): rows of the earlier blocks from
     // Ttot (diagonal block symmetrised), block blk from Rtot, zero below
     if (writer) {
@@ -369,67 +373,72 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
       }
     }
   }
+  // the basis for the host; no CTA leaves while another may still read its shared memory
+  for (int e = tid; e < nloc * kKB; e += kKT) {
+    const int a = e / nloc, rl = e - a * nloc;
+    Q[(int64_t)a * s + L.r0 + rl] = L.q[a * L.ldq + rl];
+  }
+  cl.sync();
 }
 
-int krylov_ctas(int s) { return std::min(kMaxP, std::max(4, (s + 31) / 32)); }
-
-// launch shape: P CTAs and whether the G slab fits in shared memory (with the block staging and
-// the explicit G X_7 rows)
-struct KrylovShape {
-  int P;
-  int gslab;
-  size_t smem;
-};
-
-KrylovShape krylov_shape(int s) {
-  constexpr size_t kCap = 200 * 1024 / sizeof(float);
+KrylovShape krylov_shape(int s, int C) {
   KrylovShape k;
-  const size_t stage = (size_t)s * kBP;
-  for (int P = krylov_ctas(s); P <= kMaxP; ++P) {
-    const size_t nr = (size_t)(s + P - 1) / P;
-    const size_t need = stage + nr * ((size_t)s + 4) + nr * kBP;
-    if (need <= kCap) {
-      k.P = P; k.gslab = 1; k.smem = need * sizeof(float);
-      return k;
-    }
-  }
-  k.P = krylov_ctas(s);
-  const size_t nr = (size_t)(s + k.P - 1) / k.P;
-  k.gslab = 0;
-  k.smem = (stage + nr * kBP) * sizeof(float);
+  k.C = C;
+  k.nr = (s + C - 1) / C;
+  const size_t base = krylov_base_floats(s, k.nr);
+  const size_t slab = (size_t)k.nr * ((size_t)s + 4);
+  k.gslab = (base + slab) * sizeof(float) <= kSmemCap;
+  k.smem = (base + (k.gslab ? slab : 0)) * sizeof(float);
   return k;
 }
 
 }  // namespace
 
-int64_t krylov_part_floats() { return 2ll * kMaxP * kSlot; }
-
-cudaError_t launch_krylov(const double* G, float* G32, int64_t s, float* Q, float* part, double* H,
-                          unsigned int* sync, int* lost, uint64_t seed, cudaStream_t st) {
+cudaError_t launch_krylov(const double* G, float* G32, int64_t s, float* Q, double* H, int* lost,
+                          uint64_t seed, cudaStream_t st) {
   static_assert(kKB == 64, "the caller's buffers hold a 64-vector basis");
   if (s < kKB) return cudaErrorInvalidValue;
-  const KrylovShape ks = krylov_shape((int)s);
-  if (ks.smem > 200 * 1024) return cudaErrorInvalidValue;
+  // cluster size: 16 CTAs where the device allows that many (non-portable), else 8
   static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  static int max_resident = 0;
+  static cudaError_t setup_err = cudaSuccess;
+  static int cluster = 8;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(krylov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    int dev = 0, sms = 0, per_sm = 0;
-    if (attr_err == cudaSuccess) attr_err = cudaGetDevice(&dev);
-    if (attr_err == cudaSuccess) attr_err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, krylov_kernel, kKT, 200 * 1024);
-    max_resident = sms * per_sm;
+    setup_err = cudaFuncSetAttribute(krylov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    if (setup_err != cudaSuccess) return;
+    if (cudaFuncSetAttribute(krylov_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 16;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(kKT);
+      cfg.dynamicSmemBytes = kSmemCap;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, krylov_kernel, &cfg) == cudaSuccess && n >= 1) cluster = 16;
+    }
+    (void)cudaGetLastError();  // a refused query leaves no error behind
   });
-  TT_CUDA(attr_err);
-  if (ks.P > max_resident) return cudaErrorCooperativeLaunchTooLarge;
-  TT_CUDA(cudaMemsetAsync(sync, 0, 3 * sizeof(unsigned int), st));
-  int si = (int)s, slab = ks.gslab;
-  void* args[] = {(void*)&G, (void*)&G32, (void*)&si, (void*)&Q, (void*)&part, (void*)&H,
-                  (void*)&sync, (void*)&lost, (void*)&seed, (void*)&slab};
+  TT_CUDA(setup_err);
+  const KrylovShape ks = krylov_shape((int)s, cluster);
+  if (ks.smem > kSmemCap) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ks.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)ks.C);
+  cfg.blockDim = dim3(kKT);
+  cfg.dynamicSmemBytes = ks.smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
   note_launch();
-  return cudaLaunchCooperativeKernel((const void*)krylov_kernel, dim3(ks.P), dim3(kKT), args, ks.smem, st);
+  return cudaLaunchKernelEx(&cfg, krylov_kernel, G, G32, (int)s, Q, H, lost, seed, ks.gslab);
 }
 
 }  // namespace ttice

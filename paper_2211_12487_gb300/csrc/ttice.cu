@@ -68,8 +68,6 @@ struct ttice_s {
   double* theta = nullptr;
   float* G32 = nullptr;   // FP32 copy of the Gram for the Krylov solver
   float* KQ = nullptr;    // block-Krylov basis, s_max x kKry
-  float* kpart = nullptr;          // per-CTA partial sums of the fused Krylov kernel
-  unsigned int* ksync = nullptr;   // its grid-barrier state (arrivals, generation, error)
   double* KV = nullptr;   // s_max x kKryP (start block), also kKry x kKry eigenvectors of H
   double* res = nullptr;  // Ritz residual norms
   double* h_dbl = nullptr;  // pinned host scratch
@@ -186,7 +184,7 @@ void free_all(ttice_s* h) {
   for (int i = 0; i < kMaxD; ++i) {
     cudaFree(h->U[i]); cudaFree(h->Uf[i]); cudaFree(h->stage[i]); cudaFree(h->dstage[i]);
   }
-  void* ptrs[] = {h->G32, h->KQ, h->kpart, h->ksync, h->KV, h->res,
+  void* ptrs[] = {h->G32, h->KQ, h->KV, h->res,
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
@@ -379,7 +377,7 @@ int rayleigh_ritz(ttice_s* h, int64_t s, int K, const double* d_eps, int max_new
 }
 
 // Candidate eigenvectors for the leading part of the Gram G (s x s) from a block Krylov subspace
-// built in FP32 (an FP32 copy of G) by one cooperative kernel: X_0 = orth(random s x p),
+// built in FP32 (an FP32 copy of G) by one thread-block cluster: X_0 = orth(random s x p),
 // X_i = orth((I - Q Q^T) G X_{i-1}) (CGS2 against the basis Q = [X_0 .. X_{i-1}]), kKryBlocks
 // blocks, and H = Q^T G Q (FP32 products, FP64 accumulation across CTAs).  H is diagonalised by FP32
 // Jacobi and its leading K eigenvectors, mapped back to R^s in FP64, are left in h->Q for the FP64
@@ -390,18 +388,15 @@ int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStrea
   float* Qb = h->KQ;
   const int k = kKry;
   TT_CU(cudaMemsetAsync(h->ibuf + 6, 0, sizeof(int), st));
-  TT_CU(launch_krylov(h->G, h->G32, s, Qb, h->kpart, h->H, h->ksync, h->ibuf + 6,
-                      0x5eedull + (uint64_t)s, st));
+  TT_CU(launch_krylov(h->G, h->G32, s, Qb, h->H, h->ibuf + 6, 0x5eedull + (uint64_t)s, st));
   TT_CU(cudaMemsetAsync(h->bjflags, 0, 4 * sizeof(int), st));
   TT_CU(jacobi_eig<float>(h->H, k, k, h->w32, h->V32, h->bjw32, h->bjflags + 3, st));
   TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, k * sizeof(float), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_dbl, h->trace, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_int + 6, h->ibuf + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TT_CU(cudaMemcpyAsync(h->h_int + 7, h->ksync + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
   ph_end(h, st);
   TT_TRY(sync_read(h, st));
   ph_begin(h, PH_EIG, st, 0.0, 0.0);
-  if (h->h_int[7]) return TTICE_ETIMEOUT;  // a grid barrier of the Krylov kernel gave up
   if (h->h_int[6]) return TTICE_OK;  // the Krylov blocks lost rank: leave it to the full solver
   // leading part needed: smallest r with trace - sum_{j<r} theta_j <= eps^2 (sizes the RR step)
   const double tr = h->h_dbl[0];
@@ -1016,8 +1011,6 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 4);
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->G32, s * s);
   if (rc == TTICE_OK) rc = dalloc<float>(&h->KQ, s * kKry);
-  if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->kpart, krylov_part_floats());
-  if (rc == TTICE_OK) rc = dalloc<unsigned int>(&h->ksync, 4);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->KV, std::max<int64_t>(s * kKryP, kKry * kKry));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->res, kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Q, s * kRR);

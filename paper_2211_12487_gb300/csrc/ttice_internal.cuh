@@ -125,12 +125,10 @@ cudaError_t launch_canonical_sign(double* V, int64_t m, int k, int64_t ld, cudaS
 // the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  status=1 if not positive definite.
 cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st);
 // Block-Krylov basis Q (s x 64, FP32) of the Gram G and H = Q^T G Q (64 x 64, FP64) in one
-// cooperative launch (krylov.cu).  G32: s x s FP32 scratch; part: krylov_part_floats() floats;
-// sync: 3 words (zeroed by the launcher; sync[2] != 0 afterwards means a grid barrier timed out);
-// *lost is set if a block lost rank.  Requires s >= 64.
-int64_t krylov_part_floats();
-cudaError_t launch_krylov(const double* G, float* G32, int64_t s, float* Q, float* part, double* H,
-                          unsigned int* sync, int* lost, uint64_t seed, cudaStream_t st);
+// thread-block cluster (krylov.cu).  G32: s x s FP32 scratch (used when a CTA's rows of G do not fit
+// in shared memory); *lost is set if a block lost rank.  Requires s >= 64.
+cudaError_t launch_krylov(const double* G, float* G32, int64_t s, float* Q, double* H, int* lost,
+                          uint64_t seed, cudaStream_t st);
 // scale column j of V (m x k, ld) by 1/sqrt(theta[j])
 cudaError_t launch_scale_cols_rsqrt(double* V, int64_t m, int k, int64_t ld, const double* theta,
                                     cudaStream_t st);
