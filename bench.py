@@ -33,6 +33,23 @@ WORKLOAD = "video 480x640x3 as 20x24x20x32x3, fp32 input, eps=0.1, 12 blobs, noi
 METRIC = "increment elements/s"
 
 
+# DRAM bytes (read + write) of one first-pass launch (k1_tma_kernel, 8 frames of this workload) from
+# the ncu capture summarised in profiles/, valid for the kernel source with this SHA-1; reported as
+# the roofline's `traffic` only while csrc/k1_tma.cu is unchanged.
+K1_TRAFFIC = {"sha1": None, "bytes": None}
+
+
+def _k1_traffic():
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "paper_2211_12487_gb300", "csrc", "k1_tma.cu"), "rb") as f:
+            h = hashlib.sha1(f.read()).hexdigest()
+    except OSError:
+        return None
+    return K1_TRAFFIC["bytes"] if K1_TRAFFIC["sha1"] == h else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -86,6 +103,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def replica_seed(rank: int) -> int:
+    """Seed of the stream replica `rank` runs (independent streams: weak scaling, no collective on
+    the data path)."""
+    return 1001 + 7919 * rank
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The slowest rank's value of a timed region (identity for one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
+    """Units processed by all ranks over the slowest rank's time."""
+    return ws * units_per_rank / seconds
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -113,6 +152,131 @@ def oracle_elements_per_s(budget_s: float, batch: int):
         k += 1
     threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
     return n_el / t_busy, k, t_busy, int(threads)
+
+
+def run_serving(seconds: float, n_streams: int = 64, rate: float = 2000.0, slots: int = 8, seed: int = 1003):
+    """Continuous batching over many streams (the serving workload): stream shapes drawn from
+    {16^4 cosine stream, the 20x24x20x32x3 video view, 64^3 x 4 flow, 32^4 cosine stream}, batch
+    sizes from {1, 4, 16, 32}, eps from {0.05, 0.1, 0.3}; Poisson arrivals at `rate` increments/s over
+    all streams for `seconds`.  Each stream cycles through a pool of pre-generated device-resident
+    increments (at most ~192 MB per stream), so later requests of a stream are mostly represented
+    already and take the skip path.  Latency = arrival -> completion of the update."""
+    import random
+
+    import torch
+
+    from paper_2211_12487_gb300 import serving as S
+    from tt_streams import blob_video, cp_cosine, fourier_flow
+
+    rng = random.Random(seed)
+    kinds = [("cosine16", (16, 16, 16, 16)), ("video", DIMS), ("flow64", (64, 64, 64, 4)),
+             ("cosine32", (32, 32, 32, 32))]
+    specs, pools = [], {}
+    for i in range(n_streams):
+        kind, dims = kinds[rng.randrange(len(kinds))]
+        b = rng.choice([1, 4, 16, 32])
+        eps = rng.choice([0.05, 0.1, 0.3])
+        name = f"{kind}_{i}"
+        specs.append(S.StreamSpec(name, dims, eps, b))
+        n_el = b * math.prod(dims)
+        npool = max(2, min(16, (192 << 20) // (4 * n_el)))
+        frames = npool * b
+        if kind.startswith("cosine"):
+            y = cp_cosine(0, frames, dims=dims, seed=seed + i).to(torch.float32).cuda()
+        elif kind == "video":
+            y = blob_video(0, frames, seed=seed + i, device="cuda")
+        else:
+            y = fourier_flow(0, frames, grid=64, seed=seed + i, device="cuda")
+        pools[name] = [y[k * b:(k + 1) * b] for k in range(npool)]
+    torch.cuda.synchronize()
+    eng = S.ServingEngine(specs, slots=slots)
+    try:
+        # warm-up: one increment per stream (creates every handle, first update from empty cores)
+        for sp in specs:
+            eng.submit(S.Request(sp.name, pools[sp.name][0]))
+        eng.drain(timeout=600)
+        eng.completed.clear()
+        count = {sp.name: 1 for sp in specs}
+        t0 = time.perf_counter()
+        t_next = t0
+        n_sub = 0
+        elements = 0
+        while True:
+            t_next += rng.expovariate(rate)
+            if t_next - t0 > seconds:
+                break
+            now = time.perf_counter()
+            if t_next > now:
+                time.sleep(t_next - now)
+            sp = specs[rng.randrange(n_streams)]
+            k = count[sp.name]
+            count[sp.name] = k + 1
+            y = pools[sp.name][k % len(pools[sp.name])]
+            eng.submit(S.Request(sp.name, y, arrival=t_next))
+            n_sub += 1
+            elements += y.numel()
+        ok = eng.drain(timeout=600)
+        wall = time.perf_counter() - t0
+        lat = eng.latencies_ms()
+        skipped = sum(1 for r in eng.completed if r.stats is not None and r.stats.skipped)
+        errors = sum(1 for r in eng.completed if r.error is not None)
+        return {"streams": n_streams, "slots": slots, "arrival_rate_per_s": rate, "seconds": seconds,
+                "requests": n_sub, "completed": len(lat), "errors": errors, "drained": ok,
+                "skipped_fraction": skipped / max(len(eng.completed), 1),
+                "p50_ms": S.percentile(lat, 0.50), "p99_ms": S.percentile(lat, 0.99),
+                "max_ms": lat[-1] if lat else None,
+                "throughput_elements_per_s": elements / wall, "throughput_updates_per_s": len(lat) / wall}
+    finally:
+        eng.close()
+
+
+def run_flow(steps: int, warmup: int = 3, b: int = 16, eps: float = 0.05, seed: int = 1002):
+    """The simulation-shaped stream (128^3 grid, 4 fields: 4-way 128x128x128x4, FP32, 64 Fourier modes
+    per field with |k|^(-5/3) amplitudes advected at (0.3, 0.1, 0.2) cells/snapshot), batches of b,
+    eps.  After warm-up the stream is represented and increments mostly take the skip path: one
+    read of the 537 MB batch plus the chain.  Reports throughput, latency and the update's fraction of
+    the HBM roofline (input bytes / step time against the measured copy bandwidth)."""
+    import torch
+
+    from paper_2211_12487_gb300 import ttice as T
+    from tt_streams import fourier_flow
+
+    dims = (128, 128, 128, 4)
+    n = warmup + steps
+    Y = torch.empty((n * b,) + dims, dtype=torch.float32, device="cuda")
+    for k in range(0, n * b, b):
+        Y[k:k + b] = fourier_flow(k, b, seed=seed, device="cuda")
+    h = T.TTICE(dims, eps, precision="fp32", input_dtype=torch.float32, max_batch=b, max_rank=1024)
+    for k in range(warmup):
+        h.update(Y[k * b:(k + 1) * b])
+    st = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(st)
+    skipped = 0
+    for k in range(steps):
+        i = warmup + k
+        s_ = h.update(Y[i * b:(i + 1) * b])
+        skipped += int(s_.skipped)
+        evs[k + 1].record(st)
+    torch.cuda.synchronize()
+    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    total = evs[0].elapsed_time(evs[-1])
+    ranks = h.ranks()
+    h.close()
+    del Y
+    torch.cuda.empty_cache()
+    peaks, kind = _peaks()
+    n_el = b * math.prod(dims)
+    gbs = 4.0 * n_el / (total / steps / 1e3) / 1e9
+    return {"workload": "flow 128^3 x 4 (4-way 128x128x128x4), fp32 input, eps=0.05, 64 modes/field",
+            "batch": b, "steps": steps, "warmup": warmup, "value": steps * n_el / (total / 1e3),
+            "unit": "elements/s", "ms_per_step": total / steps,
+            "latency_ms": {"p50": statistics.median(lat), "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},
+            "skipped": skipped, "final_ranks": ranks,
+            "roofline_step": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": gbs / peaks["hbm_gbs"], "bytes_per_step": 4.0 * n_el,
+                              "bytes": "input batch read once (the bare lower bound)", "peak_kind": kind}}
 
 
 def run_reference(args):
@@ -155,6 +319,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle work for cpu_baseline (0 leaves it out)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--flow-steps", type=int, default=8,
+                    help="timed steps of the 128^3 x 4 simulation-shaped stream reported under `flow` (0 leaves it out)")
+    ap.add_argument("--serving-seconds", type=float, default=5.0,
+                    help="length of the many-stream serving run reported under `serving` (0 leaves it out)")
     ap.add_argument("--profile-window", action="store_true",
                     help="open the CUDA profiler API (cudaProfilerStart/Stop) around the timed steps only, "
                          "for ncu --profile-from-start off")
@@ -179,7 +347,7 @@ def main():
     b = args.batch
     n_inc = args.warmup + args.steps
     N = math.prod(DIMS)
-    seed = 1001 + 7919 * rank  # independent replicas per rank (weak scaling)
+    seed = replica_seed(rank)  # independent replicas per rank (weak scaling)
     Y = torch.empty((n_inc * b,) + DIMS, dtype=torch.float32, device=dev)
     for k in range(0, n_inc * b, 64):
         c = min(64, n_inc * b - k)
@@ -224,11 +392,8 @@ def main():
 
     with ClockSampler(local) as clk:
         total_ms, lat, stats, prof, launches = timed_run(args.precision, args.steps, True)
-    t = torch.tensor([total_ms], device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = ws * args.steps * b * N / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, ws, dev)
+    value = whole_job_rate(ws, args.steps * b * N, total_ms / 1e3)
 
     # FP64 path on the same stream (the plain FP64 GPU TT-ICE), shorter
     fp64 = None
@@ -258,12 +423,22 @@ def main():
             d2h += coeffs.nbytes
         barrier()
         dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], device=dev)
-        if ws > 1:
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": ws * args.steps * b * N / float(tt.item()), "unit": "elements/s",
+        e2e = {"value": whole_job_rate(ws, args.steps * b * N, max_over_ranks(dt, ws, dev)), "unit": "elements/s",
                "h2d_bytes_per_step": b * N * 4, "d2h_bytes_per_step": int(d2h / args.steps)}
         h.close()
+
+    flow = None
+    if args.flow_steps > 0 and rank == 0:
+        try:
+            flow = run_flow(args.flow_steps)
+        except Exception as e:
+            flow = {"error": f"{type(e).__name__}: {e}"}
+    serving = None
+    if args.serving_seconds > 0 and rank == 0:
+        try:
+            serving = run_serving(args.serving_seconds)
+        except Exception as e:  # reported in the line; the headline numbers above stand
+            serving = {"error": f"{type(e).__name__}: {e}"}
 
     if rank != 0:
         if ws > 1:
@@ -282,9 +457,15 @@ def main():
         per_launch_s = ph["ms"] / ph["count"] / 1e3
         achieved = ph["bytes"] / ph["count"] / per_launch_s / 1e9
         roof = {"bound": "hbm", "kernel": pick, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": _k1_traffic(),
                 "peak_kind": peak_kind, "bytes_per_launch": ph["bytes"] / ph["count"],
                 "avg_launch_ms": ph["ms"] / ph["count"]}
+    # the whole update against the same bound: algorithmic bytes of every phase per update / step time
+    step_bytes = sum(prof[n]["bytes"] for n in names) / max(prof["updates"], 1)
+    step_gbs = step_bytes / (total_ms / args.steps / 1e3) / 1e9
+    roof_step = {"bound": "hbm", "achieved": step_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": step_gbs / peaks["hbm_gbs"], "bytes_per_step": step_bytes,
+                 "note": "latency-bound: the truncated eigen-solves dominate (see phase_share)"}
     phase_share = {n: round(prof[n]["ms"] / max(total_ms, 1e-9), 4) for n in names}
     cpu = None
     if (ws == 1 or rank == 0) and args.cpu_budget > 0:
@@ -308,9 +489,12 @@ def main():
                          "krylov_fallbacks": sum(x[4] for x in stats),
                          "sweep_limit_hits": sum(x[5] for x in stats)},
         "roofline": roof,
+        "roofline_step": roof_step,
         "dominant_phase": dom,
         "phase_share": phase_share,
         "fp64_path": fp64,
+        "flow": flow,
+        "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

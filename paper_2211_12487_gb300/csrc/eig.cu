@@ -296,14 +296,19 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_small_kernel(const double*
     rpq[0][k] = p | (q << 16);
   }
   __syncthreads();
-  // V items: (pair i, row x), rows fastest so that a warp touches consecutive words
-  const int vi0 = tid / s, vx0 = tid - vi0 * s, vdi = nt / s, vdx = nt - vdi * s;
+  // The last warp computes the next round's angles while the others update A and V, so a round's
+  // critical path is the longer of the two, not their sum.  V items: (pair i, row x), rows fastest
+  // so that a warp touches consecutive words.
+  const int nwork = nt - 32;
+  const bool angle_warp = tid >= nwork;
+  const int vi0 = angle_warp ? npairs : tid / s, vx0 = angle_warp ? 0 : tid - (tid / s) * s;
+  const int vdi = nwork / s, vdx = nwork - vdi * s;
 
   int sweep = 0;
   for (; sweep < SweepCap<T>::value; ++sweep) {
     for (int round = 0; round < m; ++round) {
       // A <- J^T A J, one 2x2 block (and its mirror) per item, from Ain into Aout
-      for (int t = tid; t < nA; t += nt) {
+      for (int t = angle_warp ? nA : tid; t < nA; t += nwork) {
         const int ij = ij_tab[t];
         const int i = ij >> 8, j = ij & 255;
         const int pqi = rpq[cur][i];
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_small_kernel(const double*
       }
       // pairs and angles of the next round, from the entries this round produces
       const int rn = (round + 1 == m) ? 0 : round + 1;
-      for (int k = tid; k < npairs; k += nt) {
+      for (int k = angle_warp ? tid - nwork : npairs; k < npairs; k += 32) {
         int p, q;
         rr_pair<T>(k, rn, m, p, q);
         T c = T(1), sn = T(0), t = T(0);

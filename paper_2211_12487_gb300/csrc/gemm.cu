@@ -56,24 +56,64 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) gemm_kernel(GemmArgs g,
   }
   int slab = 0;
 
+  // register double buffering: the next K-slab is loaded from global memory while the current one
+  // is multiplied out of shared memory
+  constexpr int NA = (BM * BK + NT - 1) / NT, NB = (BN * BK + NT - 1) / NT;
+  ACC ra[NA], rb[NB];
+  auto load_slab = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + q * NT;
+      ACC v = ACC(0);
+      if (e < BM * BK) {
+        int mm, kk;
+        if (a_kfast) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
+        const int64_t gm = m0 + mm, gk = k0 + kk;
+        if (gm < g.M && gk < kend) v = (ACC)ld_elem<TA>(g.A.p, aoff + gm * g.A.rs + gk * g.A.cs);
+      }
+      ra[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + q * NT;
+      ACC v = ACC(0);
+      if (e < BN * BK) {
+        int nn, kk;
+        if (b_nfast) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
+        const int64_t gn = n0 + nn, gk = k0 + kk;
+        if (gn < g.N && gk < kend) v = (ACC)ld_elem<TB>(g.B.p, boff + gk * g.B.rs + gn * g.B.cs);
+      }
+      rb[q] = v;
+    }
+  };
+  auto store_slab = [&]() {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + q * NT;
+      if (e < BM * BK) {
+        int mm, kk;
+        if (a_kfast) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
+        As[kk][mm] = ra[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + q * NT;
+      if (e < BN * BK) {
+        int nn, kk;
+        if (b_nfast) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
+        Bs[kk][nn] = rb[q];
+      }
+    }
+  };
+  if (kbeg < kend) {
+    load_slab(kbeg);
+    store_slab();
+  }
+  __syncthreads();
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += NT) {
-      int mm, kk;
-      if (a_kfast) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
-      const int64_t gm = m0 + mm, gk = k0 + kk;
-      ACC v = ACC(0);
-      if (gm < g.M && gk < kend) v = (ACC)ld_elem<TA>(g.A.p, aoff + gm * g.A.rs + gk * g.A.cs);
-      As[kk][mm] = v;
-    }
-    for (int e = tid; e < BN * BK; e += NT) {
-      int nn, kk;
-      if (b_nfast) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
-      const int64_t gn = n0 + nn, gk = k0 + kk;
-      ACC v = ACC(0);
-      if (gn < g.N && gk < kend) v = (ACC)ld_elem<TB>(g.B.p, boff + gk * g.B.rs + gn * g.B.cs);
-      Bs[kk][nn] = v;
-    }
-    __syncthreads();
+    const bool more = k0 + BK < kend;
+    if (more) load_slab(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       ACC a[TM], b[TN];
@@ -87,6 +127,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) gemm_kernel(GemmArgs g,
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
+    if (more) {
+      store_slab();
+      __syncthreads();
+    }
     if constexpr (kMix) {
       if (++slab == kMixSlabs) {
         slab = 0;

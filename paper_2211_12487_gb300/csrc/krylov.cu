@@ -2,9 +2,10 @@
 // the mixed-precision truncated eigen-solve of Eq. 9; the FP64 Rayleigh-Ritz step and its
 // certification follow on the host side).
 //
-// Q = [X_0, ..., X_7] (s x 64, column-major, ld s): X_0 a fixed pseudo-random block, X_i = G X_{i-1}
+// Q = [X_0, ..., X_{nblk-1}] (s x 8 nblk, column-major, ld s; nblk <= 8): X_0 a fixed pseudo-random
+// block, X_i = G X_{i-1}
 // projected out of the earlier blocks twice (block classical Gram-Schmidt, CGS2) and orthonormalised
-// by Cholesky-QR applied twice; H = Q^T G Q (64 x 64, FP64).  Products and per-CTA sums in FP32,
+// by Cholesky-QR applied twice; H = Q^T G Q (8 nblk x 8 nblk, FP64).  Products and per-CTA sums in FP32,
 // sums across CTAs in FP64.
 //
 // One cluster of C CTAs (16 where the device allows it, else 8), all on one GPC: CTA c owns the rows
@@ -19,7 +20,7 @@
 // H needs no G Q product: with G X_c = Q_{<=c} Ttot + X_{c+1} Rtot (the two CGS2 coefficient blocks
 // summed, and R2 R1 of the two Cholesky-QR passes), block column c of H is Ttot over the earlier
 // blocks (its diagonal block symmetrised), Rtot below it, and zero further down (the block-Lanczos
-// structure).  Only the last block column uses an explicit G X_7.
+// structure).  Only the last block column uses an explicit G X_{nblk-1}.
 //
 // Cluster barriers are hardware barriers; the kernel has no spin loop and no early exit.
 #include <cooperative_groups.h>
@@ -74,47 +75,60 @@ __device__ void cluster_sum(cg::cluster_group& cl, float* part, int n, F put) {
   }
 }
 
+__device__ __forceinline__ int packed_upper(int a, int b) { return a * kBP - a * (a + 1) / 2 + b; }
+
+// Block Gram X^T X of the block columns [col0, col0 + kBP) over this CTA's rows, packed upper
+// triangle (kNQ entries), written to out[0 .. kNQ) by threads 0 .. kNQ-1.
+__device__ void local_block_gram(Loc L, int col0, float* wsum, float* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float acc[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) acc[q] = 0.f;
+  for (int rl = tid; rl < L.nloc; rl += kKT) {
+    float x[kBP];
+#pragma unroll
+    for (int a = 0; a < kBP; ++a) x[a] = L.q[(col0 + a) * L.ldq + rl];
+#pragma unroll
+    for (int a = 0; a < kBP; ++a)
+#pragma unroll
+      for (int b = a; b < kBP; ++b) acc[packed_upper(a, b)] = fmaf(x[a], x[b], acc[packed_upper(a, b)]);
+  }
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) {
+    float v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[warp * kNQ + q] = v;
+  }
+  __syncthreads();
+  if (tid < kNQ) {
+    float v = 0.f;
+    for (int w = 0; w < kKW; ++w) v += wsum[w * kNQ + tid];
+    out[tid] = v;
+  }
+}
+
 // Cholesky-QR twice of the block columns [col0, col0 + kBP) of the local rows, with the block Gram
 // summed over the cluster.  Rtot (8 x 8, row-major, upper) receives R2 R1, the factor with
-// X_before = X_after Rtot.
+// X_before = X_after Rtot.  With gram_ready the first pass takes its Gram from S (upper triangle,
+// S[a * kBP + b], a <= b) instead of forming and summing it.
 __device__ void block_cholqr2(cg::cluster_group& cl, Loc L, int col0, float* part2, int& pp, int* lost,
-                              float* wsum, double* S, float* Rt, float* Rid, float* R1, float* Rtot) {
+                              float* wsum, double* S, float* Rt, float* Rid, float* R1, float* Rtot,
+                              bool gram_ready) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  auto qi = [](int a, int b) { return a * kBP - a * (a + 1) / 2 + b; };
+  auto qi = [](int a, int b) { return packed_upper(a, b); };
   for (int pass = 0; pass < 2; ++pass) {
-    float acc[kNQ];
-#pragma unroll
-    for (int q = 0; q < kNQ; ++q) acc[q] = 0.f;
-    for (int rl = tid; rl < L.nloc; rl += kKT) {
-      float x[kBP];
-#pragma unroll
-      for (int a = 0; a < kBP; ++a) x[a] = L.q[(col0 + a) * L.ldq + rl];
-#pragma unroll
-      for (int a = 0; a < kBP; ++a)
-#pragma unroll
-        for (int b = a; b < kBP; ++b) acc[qi(a, b)] = fmaf(x[a], x[b], acc[qi(a, b)]);
+    if (!(pass == 0 && gram_ready)) {
+      float* mine = part2 + pp * kPartMax;
+      local_block_gram(L, col0, wsum, mine);
+      cl.sync();
+      cluster_sum(cl, mine, kNQ, [&](int e, double v) {
+        int a = 0;
+        while (e >= qi(a, kBP)) ++a;
+        S[a * kBP + (e - qi(a, 0))] = v;
+      });
+      pp ^= 1;
     }
-#pragma unroll
-    for (int q = 0; q < kNQ; ++q) {
-      float v = acc[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) wsum[warp * kNQ + q] = v;
-    }
-    __syncthreads();
-    float* mine = part2 + pp * kPartMax;
-    if (tid < kNQ) {
-      float v = 0.f;
-      for (int w = 0; w < kKW; ++w) v += wsum[w * kNQ + tid];
-      mine[tid] = v;
-    }
-    cl.sync();
-    cluster_sum(cl, mine, kNQ, [&](int e, double v) {
-      int a = 0;
-      while (e >= qi(a, kBP)) ++a;
-      S[a * kBP + (e - qi(a, 0))] = v;
-    });
-    pp ^= 1;
     __syncthreads();
     if (warp == 0) {
       // right-looking Cholesky, lane c keeps column c of the upper triangle
@@ -247,13 +261,16 @@ size_t krylov_base_floats(int s, int nr) {
   return (size_t)kc * kBP + (size_t)(kKB + kBP) * krylov_ldq(nr) + 2 * (size_t)kPartMax;
 }
 
+// nblk (1 .. kNBk) blocks: a basis of kk = nblk kBP vectors and H of kk x kk (row-major, ld kk).
 __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32, int s, float* Q,
-                                                     double* H, int* lost, uint64_t seed, int gslab) {
+                                                     double* H, int* lost, uint64_t seed, int gslab,
+                                                     int nblk) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float wsum[kKW * kNQ];
   __shared__ double S[kBP * kBP];
   __shared__ float Rt[kBP * kBP], Rid[kBP], R1[kBP * kBP], Rtot[kBP * kBP];
   __shared__ float T[(kKB - kBP) * kBP], Ttot[kKB * kBP];
+  __shared__ double Td[(kKB - kBP) * kBP], Sp[kNQ];  // second-pass coefficients, Gram before it
   cg::cluster_group cl = cg::this_cluster();
   const int tid = threadIdx.x;
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
@@ -273,6 +290,7 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
   const int64_t gld = gslab ? (int64_t)s + 4 : (int64_t)s;
   const float* gbase = gslab ? gs : G32 + (int64_t)L.r0 * s;
   const bool writer = rank == 0;  // every CTA holds the same coefficients; rank 0 writes H
+  const int kk = nblk * kBP;      // basis size; H is kk x kk with leading dimension kk
 
   // FP32 rows of G; this CTA's rows of the start block
   for (int64_t e = tid; e < (int64_t)nloc * s; e += kKT) {
@@ -286,18 +304,18 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
     L.q[a * L.ldq + rl] = (float)hash_uniform(seed, (int64_t)a * s + L.r0 + rl);
   }
   if (writer)
-    for (int e = tid; e < kKB * kKB; e += kKT) H[e] = 0.0;
+    for (int e = tid; e < kk * kk; e += kKT) H[e] = 0.0;
   __syncthreads();
-  block_cholqr2(cl, L, 0, part2, pp, lost, wsum, S, Rt, Rid, R1, Rtot);
+  block_cholqr2(cl, L, 0, part2, pp, lost, wsum, S, Rt, Rid, R1, Rtot, false);
 
-  for (int blk = 1; blk <= kNBk; ++blk) {
+  for (int blk = 1; blk <= nblk; ++blk) {
     cl.sync();  // every CTA's rows of X_{blk-1} are final
     const int cprev = (blk - 1) * kBP, ccur = blk * kBP;
-    if (blk == kNBk) {
-      // last block column of H: X_j^T (G X_7) for every block j, from an explicit G X_7
+    if (blk == nblk) {
+      // last block column of H: X_j^T (G X_last) for every block j, from an explicit G X_last
       g_times_block(cl, L, s, cprev, gbase, gld, xs, gx, L.ldq);
       float* mine = part2 + pp * kPartMax;
-      for (int e = tid; e < kKB * kBP; e += kKT) {
+      for (int e = tid; e < kk * kBP; e += kKT) {
         const int a = e / kBP, j = e - a * kBP;
         const float* qa = L.q + a * L.ldq;
         const float* gj = gx + j * L.ldq;
@@ -307,23 +325,27 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
       }
       cl.sync();
       if (writer) {
-        cluster_sum(cl, mine, kKB * kBP, [&](int e, double v) {
+        cluster_sum(cl, mine, kk * kBP, [&](int e, double v) {
           const int a = e / kBP, j = e - a * kBP;
           const int col = cprev + j;
-          if (a < cprev) { H[a * kKB + col] = v; H[col * kKB + a] = v; }
+          if (a < cprev) { H[a * kk + col] = v; H[col * kk + a] = v; }
           else Ttot[(a - cprev) * kBP + j] = (float)v;
         });
         __syncthreads();
         for (int e = tid; e < kBP * kBP; e += kKT) {  // symmetrised diagonal block
           const int a = e / kBP, j = e - a * kBP;
-          H[(cprev + a) * kKB + cprev + j] = 0.5 * ((double)Ttot[a * kBP + j] + (double)Ttot[j * kBP + a]);
+          H[(cprev + a) * kk + cprev + j] = 0.5 * ((double)Ttot[a * kBP + j] + (double)Ttot[j * kBP + a]);
         }
       }
       break;
     }
     // X_blk = G X_{blk-1} on this CTA's rows
     g_times_block(cl, L, s, cprev, gbase, gld, xs, L.q + ccur * L.ldq, L.ldq);
-    // X_blk -= Q_prev (Q_prev^T X_blk), twice; Ttot accumulates the two coefficient blocks
+    // X_blk -= Q_prev (Q_prev^T X_blk), twice; Ttot accumulates the two coefficient blocks.  The
+    // second pass's sum also carries the block Gram of X_blk before that pass, from which the Gram
+    // after it follows exactly (Q_prev orthonormal): X''^T X'' = X'^T X' - T2^T T2.  T2 is the
+    // second pass's small correction, so the difference loses nothing, and the first Cholesky-QR
+    // pass needs no sum of its own.
     const int nq = ccur;
     for (int e = tid; e < nq * kBP; e += kKT) Ttot[e] = 0.f;
     for (int pass = 0; pass < 2; ++pass) {
@@ -336,13 +358,27 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
         for (int rl = 0; rl < nloc; ++rl) v = fmaf(qa[rl], xj[rl], v);
         mine[e] = v;
       }
+      if (pass == 1) local_block_gram(L, ccur, wsum, mine + nq * kBP);
       cl.sync();
-      cluster_sum(cl, mine, nq * kBP, [&](int e, double v) {
-        T[e] = (float)v;
-        Ttot[e] += (float)v;
+      cluster_sum(cl, mine, nq * kBP + (pass == 1 ? kNQ : 0), [&](int e, double v) {
+        if (e < nq * kBP) {
+          T[e] = (float)v;
+          Ttot[e] += (float)v;
+          Td[e] = v;
+        } else {
+          Sp[e - nq * kBP] = v;
+        }
       });
       pp ^= 1;
       __syncthreads();
+      if (pass == 1 && tid < kNQ) {
+        int a = 0;
+        while (tid >= packed_upper(a, kBP)) ++a;
+        const int b = tid - packed_upper(a, 0);
+        double v = Sp[tid];
+        for (int c = 0; c < nq; ++c) v -= Td[c * kBP + a] * Td[c * kBP + b];
+        S[a * kBP + b] = v;
+      }
       for (int e = tid; e < nloc * kBP; e += kKT) {
         const int j = e / nloc, rl = e - j * nloc;
         float v = L.q[(ccur + j) * L.ldq + rl];
@@ -351,7 +387,7 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
       }
       __syncthreads();
     }
-    block_cholqr2(cl, L, ccur, part2, pp, lost, wsum, S, Rt, Rid, R1, Rtot);
+    block_cholqr2(cl, L, ccur, part2, pp, lost, wsum, S, Rt, Rid, R1, Rtot, true);
     // block column blk-1 of H (G X_{blk-1} = Q_prev Ttot + X_blk Rtot): rows of the earlier blocks from
     // Ttot (diagonal block symmetrised), block blk from Rtot, zero below
     if (writer) {
@@ -359,22 +395,22 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
         const int a = e / kBP, j = e - a * kBP;
         const int col = cprev + j;
         if (a < cprev) {
-          H[a * kKB + col] = (double)Ttot[e];
-          H[col * kKB + a] = (double)Ttot[e];
+          H[a * kk + col] = (double)Ttot[e];
+          H[col * kk + a] = (double)Ttot[e];
         } else {
           const int aa = a - cprev;
-          H[a * kKB + col] = 0.5 * ((double)Ttot[e] + (double)Ttot[(cprev + j) * kBP + aa]);
+          H[a * kk + col] = 0.5 * ((double)Ttot[e] + (double)Ttot[(cprev + j) * kBP + aa]);
         }
       }
       for (int e = tid; e < kBP * kBP; e += kKT) {
         const int a = e / kBP, j = e - a * kBP;  // X_blk^T G X_{blk-1} = Rtot
-        H[(ccur + a) * kKB + cprev + j] = (double)Rtot[e];
-        H[(cprev + j) * kKB + ccur + a] = (double)Rtot[e];
+        H[(ccur + a) * kk + cprev + j] = (double)Rtot[e];
+        H[(cprev + j) * kk + ccur + a] = (double)Rtot[e];
       }
     }
   }
   // the basis for the host; no CTA leaves while another may still read its shared memory
-  for (int e = tid; e < nloc * kKB; e += kKT) {
+  for (int e = tid; e < nloc * kk; e += kKT) {
     const int a = e / nloc, rl = e - a * nloc;
     Q[(int64_t)a * s + L.r0 + rl] = L.q[a * L.ldq + rl];
   }
@@ -394,10 +430,10 @@ KrylovShape krylov_shape(int s, int C) {
 
 }  // namespace
 
-cudaError_t launch_krylov(const double* G, float* G32, int64_t s, float* Q, double* H, int* lost,
-                          uint64_t seed, cudaStream_t st) {
-  static_assert(kKB == 64, "the caller's buffers hold a 64-vector basis");
-  if (s < kKB) return cudaErrorInvalidValue;
+cudaError_t launch_krylov(const double* G, float* G32, int64_t s, int nblk, float* Q, double* H,
+                          int* lost, uint64_t seed, cudaStream_t st) {
+  static_assert(kKB == 64, "the caller's buffers hold up to a 64-vector basis");
+  if (s < kKB || nblk < 2 || nblk > kNBk) return cudaErrorInvalidValue;
   // cluster size: 16 CTAs where the device allows that many (non-portable), else 8
   static std::once_flag once;
   static cudaError_t setup_err = cudaSuccess;
@@ -438,7 +474,7 @@ cudaError_t launch_krylov(const double* G, float* G32, int64_t s, float* Q, doub
   cfg.attrs = at;
   cfg.numAttrs = 1;
   note_launch();
-  return cudaLaunchKernelEx(&cfg, krylov_kernel, G, G32, (int)s, Q, H, lost, seed, ks.gslab);
+  return cudaLaunchKernelEx(&cfg, krylov_kernel, G, G32, (int)s, Q, H, lost, seed, ks.gslab, nblk);
 }
 
 }  // namespace ttice

@@ -383,12 +383,12 @@ int rayleigh_ritz(ttice_s* h, int64_t s, int K, const double* d_eps, int max_new
 // Jacobi and its leading K eigenvectors, mapped back to R^s in FP64, are left in h->Q for the FP64
 // Rayleigh-Ritz step, which alone decides the rank.
 // *K_out = 0 when the subspace is too small for the tolerance.
-int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStream_t st) {
+int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int nblk, int* K_out, cudaStream_t st) {
   *K_out = 0;
   float* Qb = h->KQ;
-  const int k = kKry;
+  const int k = nblk * kKryP;
   TT_CU(cudaMemsetAsync(h->ibuf + 6, 0, sizeof(int), st));
-  TT_CU(launch_krylov(h->G, h->G32, s, Qb, h->H, h->ibuf + 6, 0x5eedull + (uint64_t)s, st));
+  TT_CU(launch_krylov(h->G, h->G32, s, nblk, Qb, h->H, h->ibuf + 6, 0x5eedull + (uint64_t)s, st));
   TT_CU(cudaMemsetAsync(h->bjflags, 0, 4 * sizeof(int), st));
   TT_CU(jacobi_eig<float>(h->H, k, k, h->w32, h->V32, h->bjw32, h->bjflags + 3, st));
   TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, k * sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -421,9 +421,11 @@ int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStrea
   return TTICE_OK;
 }
 
-// After rayleigh_ritz: accept the Krylov result iff every Ritz pair the rank rule used (the
-// leading rR + 1) has a residual ||G z - theta z|| <= 1e-6 theta_1, i.e. the Ritz values are
-// converged far below the truncation threshold (errors are second order in the residual).
+// After rayleigh_ritz: accept the Krylov result iff every Ritz pair the rank rule used has a
+// residual ||G z - theta z|| <= 1e-6 theta_1, i.e. the Ritz values are converged far below the
+// truncation threshold (errors are second order in the residual).  The rule at rank rR reads
+// theta_1 .. theta_rR only (tail(rR) <= eps^2 < tail(rR - 1)), and those are also the directions
+// appended, so the leading rR pairs are checked.
 int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
   *ok = false;
   TT_CU(cudaMemcpyAsync(h->h_int, h->ibuf, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -432,7 +434,7 @@ int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
   if (rR < 0) return TTICE_OK;
   // rR = 0 is decided by the trace alone (no Ritz value enters it)
   if (rR == 0) { *ok = true; return TTICE_OK; }
-  const int jm = std::min(rR + 1, K);
+  const int jm = std::min(rR, K);
   TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * jm * sizeof(double), st));
   GemmArgs g;  // GQ = G Z
   g.M = s; g.N = jm; g.K = s; g.atomic = 1; g.allow_splitk = 1;
@@ -547,14 +549,17 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   } else {
     bool have = false, big = false;
     if (s > kKrylovMin) {
-      // block Krylov candidates + FP64 Rayleigh-Ritz, kept only if certified
-      int Kk = 0;
-      TT_TRY(krylov_candidates(h, s, eps_c, &Kk, st));
-      if (Kk > 0) {
-        TT_TRY(rayleigh_ritz(h, s, Kk, d_eps, max_new, st));
-        bool ok = false;
-        TT_TRY(krylov_certify(h, s, Kk, &ok, st));
-        if (ok) { have = true; K = Kk; h->stats.krylov_solves += 1; }
+      // block Krylov candidates + FP64 Rayleigh-Ritz, kept only if certified: a 32-vector basis
+      // first (enough for a few new directions, and an 8x smaller Ritz problem), then 64
+      for (int nblk : {kKryBlocks / 2, kKryBlocks}) {
+        int Kk = 0;
+        TT_TRY(krylov_candidates(h, s, eps_c, nblk, &Kk, st));
+        if (Kk > 0) {
+          TT_TRY(rayleigh_ritz(h, s, Kk, d_eps, max_new, st));
+          bool ok = false;
+          TT_TRY(krylov_certify(h, s, Kk, &ok, st));
+          if (ok) { have = true; K = Kk; h->stats.krylov_solves += 1; break; }
+        }
       }
       if (!have) h->stats.krylov_fallbacks += 1;
     }

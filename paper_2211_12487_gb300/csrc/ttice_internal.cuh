@@ -124,11 +124,12 @@ cudaError_t launch_canonical_sign(double* V, int64_t m, int k, int64_t ld, cudaS
 // Cholesky-QR step support: given S = V^T V (k x k, FP64, ld k), overwrite Rinv (k x k, ld k) with
 // the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  status=1 if not positive definite.
 cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st);
-// Block-Krylov basis Q (s x 64, FP32) of the Gram G and H = Q^T G Q (64 x 64, FP64) in one
-// thread-block cluster (krylov.cu).  G32: s x s FP32 scratch (used when a CTA's rows of G do not fit
-// in shared memory); *lost is set if a block lost rank.  Requires s >= 64.
-cudaError_t launch_krylov(const double* G, float* G32, int64_t s, float* Q, double* H, int* lost,
-                          uint64_t seed, cudaStream_t st);
+// Block-Krylov basis Q (s x 8 nblk, FP32, nblk in 2..8) of the Gram G and H = Q^T G Q
+// (8 nblk x 8 nblk, FP64, ld 8 nblk) in one thread-block cluster (krylov.cu).  G32: s x s FP32
+// scratch (used when a CTA's rows of G do not fit in shared memory); *lost is set if a block lost
+// rank.  Requires s >= 64.
+cudaError_t launch_krylov(const double* G, float* G32, int64_t s, int nblk, float* Q, double* H,
+                          int* lost, uint64_t seed, cudaStream_t st);
 // scale column j of V (m x k, ld) by 1/sqrt(theta[j])
 cudaError_t launch_scale_cols_rsqrt(double* V, int64_t m, int k, int64_t ld, const double* theta,
                                     cudaStream_t st);
