@@ -36,7 +36,7 @@ METRIC = "increment elements/s"
 # DRAM bytes (read + write) of one first-pass launch (k1_tma_kernel, 8 frames of this workload) from
 # the ncu capture summarised in profiles/, valid for the kernel source with this SHA-1; reported as
 # the roofline's `traffic` only while csrc/k1_tma.cu is unchanged.
-K1_TRAFFIC = {"sha1": None, "bytes": None}
+K1_TRAFFIC = {"sha1": "342797728611206cc646a954d4e427099f184dbc", "bytes": 29539328 + 42240}
 
 
 def _k1_traffic():
@@ -154,13 +154,16 @@ def oracle_elements_per_s(budget_s: float, batch: int):
     return n_el / t_busy, k, t_busy, int(threads)
 
 
-def run_serving(seconds: float, n_streams: int = 64, rate: float = 2000.0, slots: int = 8, seed: int = 1003):
+def run_serving(seconds: float, n_streams: int = 64, rate: float = 400.0, slots: int = 16, seed: int = 1003,
+                drain_s: float = 60.0):
     """Continuous batching over many streams (the serving workload): stream shapes drawn from
     {16^4 cosine stream, the 20x24x20x32x3 video view, 64^3 x 4 flow, 32^4 cosine stream}, batch
     sizes from {1, 4, 16, 32}, eps from {0.05, 0.1, 0.3}; Poisson arrivals at `rate` increments/s over
     all streams for `seconds`.  Each stream cycles through a pool of pre-generated device-resident
     increments (at most ~192 MB per stream), so later requests of a stream are mostly represented
-    already and take the skip path.  Latency = arrival -> completion of the update."""
+    already and take the skip path.  Latency = arrival -> completion of the update.  Requests still
+    queued `drain_s` after the last arrival are dropped and counted (the load was above capacity)."""
+    import collections
     import random
 
     import torch
@@ -215,19 +218,22 @@ def run_serving(seconds: float, n_streams: int = 64, rate: float = 2000.0, slots
             eng.submit(S.Request(sp.name, y, arrival=t_next))
             n_sub += 1
             elements += y.numel()
-        ok = eng.drain(timeout=600)
+        ok = eng.drain(timeout=drain_s)
         wall = time.perf_counter() - t0
-        lat = eng.latencies_ms()
-        skipped = sum(1 for r in eng.completed if r.stats is not None and r.stats.skipped)
-        errors = sum(1 for r in eng.completed if r.error is not None)
+        with eng.lock:
+            done = list(eng.completed)
+        lat = sorted((r.done - r.arrival) * 1e3 for r in done if r.error is None)
+        skipped = sum(1 for r in done if r.stats is not None and r.stats.skipped)
+        errors = collections.Counter(str(r.error)[:80] for r in done if r.error is not None)
         return {"streams": n_streams, "slots": slots, "arrival_rate_per_s": rate, "seconds": seconds,
-                "requests": n_sub, "completed": len(lat), "errors": errors, "drained": ok,
-                "skipped_fraction": skipped / max(len(eng.completed), 1),
+                "requests": n_sub, "completed": len(lat), "errors": dict(errors), "drained": ok,
+                "dropped": n_sub - len(done),
+                "skipped_fraction": skipped / max(len(done), 1),
                 "p50_ms": S.percentile(lat, 0.50), "p99_ms": S.percentile(lat, 0.99),
                 "max_ms": lat[-1] if lat else None,
                 "throughput_elements_per_s": elements / wall, "throughput_updates_per_s": len(lat) / wall}
     finally:
-        eng.close()
+        eng.close(cancel_pending=True)
 
 
 def run_flow(steps: int, warmup: int = 3, b: int = 16, eps: float = 0.05, seed: int = 1002):
@@ -321,7 +327,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--flow-steps", type=int, default=8,
                     help="timed steps of the 128^3 x 4 simulation-shaped stream reported under `flow` (0 leaves it out)")
-    ap.add_argument("--serving-seconds", type=float, default=5.0,
+    ap.add_argument("--serving-seconds", type=float, default=2.0,
                     help="length of the many-stream serving run reported under `serving` (0 leaves it out)")
     ap.add_argument("--profile-window", action="store_true",
                     help="open the CUDA profiler API (cudaProfilerStart/Stop) around the timed steps only, "

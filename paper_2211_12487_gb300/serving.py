@@ -139,6 +139,10 @@ class ServingEngine:
             if name is None:
                 return
             with self.lock:
+                if not self.pending[name] or name not in self.handles:  # cancelled by close()
+                    self.busy.discard(name)
+                    self.lock.notify_all()
+                    continue
                 req = self.pending[name].popleft()
                 h = self.handles[name]
             try:
@@ -165,7 +169,13 @@ class ServingEngine:
                 self.lock.wait(timeout=0.05 if left is None else min(0.05, left))
         return True
 
-    def close(self):
+    def close(self, cancel_pending: bool = False):
+        """Stop the slots.  With cancel_pending, requests not yet started are dropped (the slots
+        finish only the updates already running) instead of being run first."""
+        if cancel_pending:
+            with self.lock:
+                for dq in self.pending.values():
+                    dq.clear()
         for _ in self.workers:
             self.ready.put(None)
         for w in self.workers:
