@@ -9,7 +9,9 @@
 //   rows:  A[I u J, :] <- Q^T A[I u J, :] for every pair (disjoint row sets), tiled over columns;
 //   cols:  A[:, I u J] <- A[:, I u J] Q and V[:, I u J] <- V[:, I u J] Q, tiled over rows.
 // A sweep is nb-1 rounds; a flag raised by any significant rotation keeps the next sweep alive, and
-// every kernel returns at once after a sweep without one, so a fixed launch sequence costs almost
+// a sweep that leaves the off-diagonal norm at the working precision's rounding level without
+// halving it ends the solve too (rotations of rounding noise would otherwise run to the sweep cap);
+// every kernel returns at once after the solve has ended, so a fixed launch sequence costs almost
 // nothing once converged.  Padding to nb*BS adds zero rows/columns, which no rotation touches (their
 // off-diagonal entries are exactly zero), so the first s coordinates carry the eigenpairs.
 #include <algorithm>
@@ -194,12 +196,35 @@ __global__ void __launch_bounds__(kThreads) bj_cols(T* A, T* V, int sp, int nb, 
   }
 }
 
-__global__ void bj_sweep_end(int* flags, int max_sweeps) {
+// Squared off-diagonal norm of A after a sweep, accumulated into *off.
+template <typename T>
+__global__ void bj_offnorm(const T* A, int sp, double* off, const int* flags) {
   if (flags[1]) return;
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)sp * sp;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / sp), j = (int)(e % sp);
+    if (i != j) { const double a = (double)A[e]; acc += a * a; }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(off, acc);
+}
+
+// End of a sweep.  norms: [0] ||A||_F^2, [1] off-diagonal^2 after this sweep (reset here), [2] after
+// the previous sweep.  The solve has converged when a sweep rotated nothing, or when the
+// off-diagonal norm is at the rounding level of T (below 64 sqrt(s) eps_T ||A||_F) and the sweep
+// did not halve it: the rotations left are rotating rounding noise (the rule of jacobi_kernel).
+template <typename T>
+__global__ void bj_sweep_end(int* flags, int max_sweeps, double* norms, int s) {
+  if (flags[1]) return;
+  const double gate = 64.0 * sqrt((double)s) * (double)BJ<T>::eps() * sqrt(norms[0]);
+  const bool stalled = flags[2] >= 1 && norms[1] > 0.25 * norms[2] && norms[1] <= gate * gate;
   flags[2] += 1;
-  if (flags[0] == 0) flags[1] = 1;
+  if (flags[0] == 0 || stalled) flags[1] = 1;
   else if (flags[2] >= max_sweeps) flags[3] = 1;  // sweep limit reached while still rotating
   flags[0] = 0;
+  norms[2] = norms[1];
+  norms[1] = 0.0;
 }
 
 // eigenvalues = diag(A)[0..s), sorted descending (ties by index); eigenvectors follow.
@@ -243,7 +268,7 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
   T* V = work + (int64_t)sp * sp;
   T* Qb = V + (int64_t)sp * sp;
   const int npairs = nb / 2;
-  TT_CUDA(cudaMemsetAsync(fro, 0, sizeof(double), st));
+  TT_CUDA(cudaMemsetAsync(fro, 0, 3 * sizeof(double), st));
   TT_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
   {
     int64_t n = (int64_t)sp * sp;
@@ -261,8 +286,14 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
       note_launch();
       bj_cols<T><<<dim3(npairs, tiles), kThreads, 0, st>>>(A, V, sp, nb, round, Qb, flags);
     }
+    {
+      const int64_t n = (int64_t)sp * sp;
+      const int grid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 2);
+      note_launch();
+      bj_offnorm<T><<<grid, kThreads, 0, st>>>(A, sp, fro + 1, flags);
+    }
     note_launch();
-    bj_sweep_end<<<1, 1, 0, st>>>(flags, max_sweeps);
+    bj_sweep_end<T><<<1, 1, 0, st>>>(flags, max_sweeps, fro, s);
   }
   note_launch();
   bj_finish<T><<<(s + 127) / 128, 128, 0, st>>>(A, V, sp, s, w, Vout);

@@ -2,8 +2,8 @@
 // the mixed-precision truncated eigen-solve of Eq. 9; the FP64 Rayleigh-Ritz step and its
 // certification follow on the host side).
 //
-// Q = [X_0, ..., X_{nblk-1}] (s x 8 nblk, column-major, ld s; nblk <= 8): X_0 a fixed pseudo-random
-// block, X_i = G X_{i-1}
+// Q = [X_0, ..., X_{nblk-1}] (s x 8 nblk, column-major, ld s; nblk <= 8): X_0 a given start block (a
+// restart from earlier Ritz vectors) or a fixed pseudo-random one, X_i = G X_{i-1}
 // projected out of the earlier blocks twice (block classical Gram-Schmidt, CGS2) and orthonormalised
 // by Cholesky-QR applied twice; H = Q^T G Q (8 nblk x 8 nblk, FP64).  Products and per-CTA sums in FP32,
 // sums across CTAs in FP64.
@@ -262,9 +262,10 @@ size_t krylov_base_floats(int s, int nr) {
 }
 
 // nblk (1 .. kNBk) blocks: a basis of kk = nblk kBP vectors and H of kk x kk (row-major, ld kk).
+// X_0 is start (s x kBP, column-major, ld s) when given, else the pseudo-random block of `seed`.
 __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32, int s, float* Q,
                                                      double* H, int* lost, uint64_t seed, int gslab,
-                                                     int nblk) {
+                                                     int nblk, const float* start) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float wsum[kKW * kNQ];
   __shared__ double S[kBP * kBP];
@@ -301,7 +302,8 @@ __global__ void __launch_bounds__(kKT) krylov_kernel(const double* G, float* G32
   }
   for (int e = tid; e < nloc * kBP; e += kKT) {
     const int a = e / nloc, rl = e - a * nloc;
-    L.q[a * L.ldq + rl] = (float)hash_uniform(seed, (int64_t)a * s + L.r0 + rl);
+    const int64_t i = (int64_t)a * s + L.r0 + rl;
+    L.q[a * L.ldq + rl] = start ? start[i] : (float)hash_uniform(seed, i);
   }
   if (writer)
     for (int e = tid; e < kk * kk; e += kKT) H[e] = 0.0;
@@ -431,7 +433,7 @@ KrylovShape krylov_shape(int s, int C) {
 }  // namespace
 
 cudaError_t launch_krylov(const double* G, float* G32, int64_t s, int nblk, float* Q, double* H,
-                          int* lost, uint64_t seed, cudaStream_t st) {
+                          int* lost, uint64_t seed, const float* start, cudaStream_t st) {
   static_assert(kKB == 64, "the caller's buffers hold up to a 64-vector basis");
   if (s < kKB || nblk < 2 || nblk > kNBk) return cudaErrorInvalidValue;
   // cluster size: 16 CTAs where the device allows that many (non-portable), else 8
@@ -474,7 +476,7 @@ cudaError_t launch_krylov(const double* G, float* G32, int64_t s, int nblk, floa
   cfg.attrs = at;
   cfg.numAttrs = 1;
   note_launch();
-  return cudaLaunchKernelEx(&cfg, krylov_kernel, G, G32, (int)s, Q, H, lost, seed, ks.gslab, nblk);
+  return cudaLaunchKernelEx(&cfg, krylov_kernel, G, G32, (int)s, Q, H, lost, seed, ks.gslab, nblk, start);
 }
 
 }  // namespace ttice

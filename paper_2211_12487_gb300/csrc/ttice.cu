@@ -68,6 +68,7 @@ struct ttice_s {
   double* theta = nullptr;
   float* G32 = nullptr;   // FP32 copy of the Gram for the Krylov solver
   float* KQ = nullptr;    // block-Krylov basis, s_max x kKry
+  float* kstart = nullptr;  // start block of a restarted Krylov solve, s_max x kKryP
   double* KV = nullptr;   // s_max x kKryP (start block), also kKry x kKry eigenvectors of H
   double* res = nullptr;  // Ritz residual norms
   double* h_dbl = nullptr;  // pinned host scratch
@@ -184,7 +185,7 @@ void free_all(ttice_s* h) {
   for (int i = 0; i < kMaxD; ++i) {
     cudaFree(h->U[i]); cudaFree(h->Uf[i]); cudaFree(h->stage[i]); cudaFree(h->dstage[i]);
   }
-  void* ptrs[] = {h->G32, h->KQ, h->KV, h->res,
+  void* ptrs[] = {h->G32, h->KQ, h->kstart, h->KV, h->res,
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
@@ -383,12 +384,13 @@ int rayleigh_ritz(ttice_s* h, int64_t s, int K, const double* d_eps, int max_new
 // Jacobi and its leading K eigenvectors, mapped back to R^s in FP64, are left in h->Q for the FP64
 // Rayleigh-Ritz step, which alone decides the rank.
 // *K_out = 0 when the subspace is too small for the tolerance.
-int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int nblk, int* K_out, cudaStream_t st) {
+int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int nblk, const float* start, int* K_out,
+                       cudaStream_t st) {
   *K_out = 0;
   float* Qb = h->KQ;
   const int k = nblk * kKryP;
   TT_CU(cudaMemsetAsync(h->ibuf + 6, 0, sizeof(int), st));
-  TT_CU(launch_krylov(h->G, h->G32, s, nblk, Qb, h->H, h->ibuf + 6, 0x5eedull + (uint64_t)s, st));
+  TT_CU(launch_krylov(h->G, h->G32, s, nblk, Qb, h->H, h->ibuf + 6, 0x5eedull + (uint64_t)s, start, st));
   TT_CU(cudaMemsetAsync(h->bjflags, 0, 4 * sizeof(int), st));
   TT_CU(jacobi_eig<float>(h->H, k, k, h->w32, h->V32, h->bjw32, h->bjflags + 3, st));
   TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, k * sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -550,15 +552,21 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     bool have = false, big = false;
     if (s > kKrylovMin) {
       // block Krylov candidates + FP64 Rayleigh-Ritz, kept only if certified: a 32-vector basis
-      // first (enough for a few new directions, and an 8x smaller Ritz problem), then 64
+      // first (enough for a few new directions, and an 8x smaller Ritz problem), then 64 — restarted
+      // from the first attempt's leading Ritz vectors when it got as far as Rayleigh-Ritz
+      bool restart = false;
       for (int nblk : {kKryBlocks / 2, kKryBlocks}) {
         int Kk = 0;
-        TT_TRY(krylov_candidates(h, s, eps_c, nblk, &Kk, st));
+        TT_TRY(krylov_candidates(h, s, eps_c, nblk, restart ? h->kstart : nullptr, &Kk, st));
         if (Kk > 0) {
           TT_TRY(rayleigh_ritz(h, s, Kk, d_eps, max_new, st));
           bool ok = false;
           TT_TRY(krylov_certify(h, s, Kk, &ok, st));
           if (ok) { have = true; K = Kk; h->stats.krylov_solves += 1; break; }
+          if (Kk >= kKryP) {  // Ritz vectors h->Q2 (s x Kk, FP64): the leading 8 seed the retry
+            TT_CU((launch_cast<double, float>(h->Q2, h->kstart, s * kKryP, st)));
+            restart = true;
+          }
         }
       }
       if (!have) h->stats.krylov_fallbacks += 1;
@@ -1012,10 +1020,11 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK) rc = dalloc<double>(&h->work64, 2 * std::max<int64_t>(s, kRR) * (std::max<int64_t>(s, kRR) + 1));
   if (rc == TTICE_OK && h->wt_bytes == 8) rc = dalloc<double>(&h->bjw64, block_jacobi_work<double>((int)s));
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->bjw32, block_jacobi_work<float>((int)s));
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->fro, 1);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->fro, 3);  // ||A||^2, off-norm^2 now and one sweep back
   if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 4);
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->G32, s * s);
   if (rc == TTICE_OK) rc = dalloc<float>(&h->KQ, s * kKry);
+  if (rc == TTICE_OK) rc = dalloc<float>(&h->kstart, s * kKryP);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->KV, std::max<int64_t>(s * kKryP, kKry * kKry));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->res, kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Q, s * kRR);

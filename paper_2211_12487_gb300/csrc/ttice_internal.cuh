@@ -55,8 +55,9 @@ cudaError_t jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* V, T* work,
                        cudaStream_t st);
 
 // Multi-CTA block Jacobi (see bjacobi.cu): same outputs as jacobi_eig.  work: block_jacobi_work<T>(s)
-// elements; fro: device double scratch; flags: device int[4] ([3] = 1 if the sweep limit was hit
-// while rotations were still significant).
+// elements; fro: device double[3] scratch (the Frobenius and off-diagonal norms the stopping rule
+// reads); flags: device int[4] ([3] = 1 if the sweep limit was hit while rotations were still
+// significant).
 template <typename T>
 int64_t block_jacobi_work(int s);
 template <typename T>
@@ -127,9 +128,10 @@ cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, c
 // Block-Krylov basis Q (s x 8 nblk, FP32, nblk in 2..8) of the Gram G and H = Q^T G Q
 // (8 nblk x 8 nblk, FP64, ld 8 nblk) in one thread-block cluster (krylov.cu).  G32: s x s FP32
 // scratch (used when a CTA's rows of G do not fit in shared memory); *lost is set if a block lost
-// rank.  Requires s >= 64.
+// rank.  start: X_0 (s x 8, column-major) or nullptr for a fixed pseudo-random block.  Requires
+// s >= 64.
 cudaError_t launch_krylov(const double* G, float* G32, int64_t s, int nblk, float* Q, double* H,
-                          int* lost, uint64_t seed, cudaStream_t st);
+                          int* lost, uint64_t seed, const float* start, cudaStream_t st);
 // scale column j of V (m x k, ld) by 1/sqrt(theta[j])
 cudaError_t launch_scale_cols_rsqrt(double* V, int64_t m, int k, int64_t ld, const double* theta,
                                     cudaStream_t st);
