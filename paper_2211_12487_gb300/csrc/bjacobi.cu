@@ -2,12 +2,13 @@
 //
 // Two-sided cyclic block Jacobi (Golub & Van Loan, Sec. 8.5, block variant): the matrix is split
 // into nb blocks of BS rows/columns; the block pairs (I, J) of one round come from the round-robin
-// ordering on block indices, so the nb/2 pairs of a round are disjoint.  One round is three kernels:
-//   solve: one CTA per pair loads the 2BS x 2BS submatrix A[I u J, I u J] into shared memory and
-//          applies one cyclic sweep of scalar Jacobi rotations to it, accumulating the orthogonal
-//          Q (2BS x 2BS) of the sweep;
-//   rows:  A[I u J, :] <- Q^T A[I u J, :] for every pair (disjoint row sets), tiled over columns;
-//   cols:  A[:, I u J] <- A[:, I u J] Q and V[:, I u J] <- V[:, I u J] Q, tiled over rows.
+// ordering on block indices, so the nb/2 pairs of a round are disjoint.  One round is two kernels:
+//   solve:  one CTA per pair loads the 2BS x 2BS submatrix A[I u J, I u J] into shared memory and
+//           applies one cyclic sweep of scalar Jacobi rotations to it, accumulating the orthogonal
+//           Q (2BS x 2BS) of the sweep;
+//   update: A_out[P_a, P_b] = Q_a^T A_in[P_a, P_b] Q_b for every pair of index sets (one 2BS x 2BS
+//           block per CTA; A is double-buffered, so rows and columns are combined in one pass), and
+//           V[:, P_a] <- V[:, P_a] Q_a in 64-row tiles.
 // A sweep is nb-1 rounds; a flag raised by any significant rotation keeps the next sweep alive, and
 // a sweep that leaves the off-diagonal norm at the working precision's rounding level without
 // halving it ends the solve too (rotations of rounding noise would otherwise run to the sweep cap);
@@ -92,9 +93,13 @@ __global__ void __launch_bounds__(32 * BJ<T>::BS) bj_solve(const T* A, int sp, i
     if (lane == 0) {
       const T apq = S[p][q], app = S[p][p], aqq = S[q][q];
       if (fabs(apq) > floor_abs && fabs(apq) > teps * sqrt(fabs(app * aqq))) {
-        const T tau = (aqq - app) / (T(2) * apq);
-        const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-        c = T(1) / sqrt(T(1) + t * t);
+        // t = sgn(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 a_pq), multiplied
+        // through by |2 a_pq|: one hypot, one division, one reciprocal square root
+        const T th = aqq - app, ph = T(2) * apq;
+        const bool pos = (th == T(0)) || ((th > T(0)) == (ph > T(0)));
+        const T mag = fabs(ph) / (fabs(th) + hypot(th, ph));
+        const T t = pos ? mag : -mag;
+        c = rsqrt(T(1) + t * t);
         sn = t * c;
         any = 1;
       }
@@ -122,77 +127,88 @@ __global__ void __launch_bounds__(32 * BJ<T>::BS) bj_solve(const T* A, int sp, i
   if (__syncthreads_or(any) && tid == 0) atomicOr(flags, 1);
 }
 
-// A[I u J, tile] <- Q^T A[I u J, tile]
+// One round's update of A and V with the pairs' orthogonal factors Q (2BS x 2BS each):
+//   A_out[P_a, P_b] = Q_a^T A_in[P_a, P_b] Q_b  for every pair of index sets P_a = I_a u J_a, and
+//   V[:, P_a] <- V[:, P_a] Q_a                  (in place: the column sets are disjoint).
+// CTAs [0, npairs^2) take the A blocks (those below the diagonal exit; each block above it also
+// writes its mirror, so A stays exactly symmetric); the CTAs after them take 64-row tiles of V.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) bj_rows(T* A, int sp, int nb, int round, const T* Qb,
-                                                    const int* flags) {
+__global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* V, int sp, int nb, int round,
+                                                      const T* Qb, const int* flags) {
   constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
   if (flags[1]) return;
-  __shared__ T Q[N2][N2 + 1];
-  __shared__ T X[N2][kTile + 1];
-  int bi, bj;
-  circle_pair(nb, round, blockIdx.x, &bi, &bj);
-  const int c0 = blockIdx.y * kTile;
+  __shared__ T Qa[N2][N2 + 1];
+  __shared__ T Qc[N2][N2 + 1];
+  __shared__ T X[kTile][N2 + 1];  // A block (N2 x N2), then the product; or a V tile (kTile x N2)
+  const int npairs = nb / 2;
   const int tid = threadIdx.x;
-  const T* Qi = Qb + (int64_t)blockIdx.x * N2 * N2;
-  auto gidx = [&](int a) { return a < BS ? bi * BS + a : bj * BS + (a - BS); };
-  for (int e = tid; e < N2 * N2; e += kThreads) Q[e / N2][e % N2] = Qi[e];
-  for (int e = tid; e < N2 * kTile; e += kThreads) {
-    const int a = e / kTile, c = e % kTile;
-    X[a][c] = (c0 + c < sp) ? A[(int64_t)gidx(a) * sp + c0 + c] : T(0);
-  }
-  __syncthreads();
-  for (int e = tid; e < N2 * kTile; e += kThreads) {
-    const int a = e / kTile, c = e % kTile;
-    if (c0 + c >= sp) continue;
-    T acc = T(0);
+  const int64_t nA = (int64_t)npairs * npairs;
+  if ((int64_t)blockIdx.x < nA) {
+    const int a = (int)(blockIdx.x / npairs), b = (int)(blockIdx.x % npairs);
+    if (a > b) return;
+    int ai, aj, bi, bj;
+    circle_pair(nb, round, a, &ai, &aj);
+    circle_pair(nb, round, b, &bi, &bj);
+    auto ga = [&](int t) { return t < BS ? ai * BS + t : aj * BS + (t - BS); };
+    auto gb = [&](int t) { return t < BS ? bi * BS + t : bj * BS + (t - BS); };
+    const T* Qa_g = Qb + (int64_t)a * N2 * N2;
+    const T* Qb_g = Qb + (int64_t)b * N2 * N2;
+    for (int e = tid; e < N2 * N2; e += kThreads) {
+      const int r = e / N2, c = e % N2;
+      Qa[r][c] = Qa_g[e];
+      Qc[r][c] = Qb_g[e];
+      X[r][c] = Ain[(int64_t)ga(r) * sp + gb(c)];
+    }
+    __syncthreads();
+    // M = Qa^T X  (4 outputs per thread), then O = M Qb
+    T m[N2 * N2 / kThreads];
+#pragma unroll
+    for (int q = 0; q < N2 * N2 / kThreads; ++q) {
+      const int e = tid + q * kThreads, r = e / N2, c = e % N2;
+      T v = T(0);
 #pragma unroll 8
-    for (int b = 0; b < N2; ++b) acc = fma(Q[b][a], X[b][c], acc);
-    A[(int64_t)gidx(a) * sp + c0 + c] = acc;
+      for (int k = 0; k < N2; ++k) v = fma(Qa[k][r], X[k][c], v);
+      m[q] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N2 * N2 / kThreads; ++q) {
+      const int e = tid + q * kThreads;
+      X[e / N2][e % N2] = m[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N2 * N2 / kThreads; ++q) {
+      const int e = tid + q * kThreads, r = e / N2, c = e % N2;
+      T v = T(0);
+#pragma unroll 8
+      for (int k = 0; k < N2; ++k) v = fma(X[r][k], Qc[k][c], v);
+      Aout[(int64_t)ga(r) * sp + gb(c)] = v;
+      if (a != b) Aout[(int64_t)gb(c) * sp + ga(r)] = v;
+    }
+    return;
   }
-}
-
-// A[tile, I u J] <- A[tile, I u J] Q ; V[tile, I u J] <- V[tile, I u J] Q (V column-major)
-template <typename T>
-__global__ void __launch_bounds__(kThreads) bj_cols(T* A, T* V, int sp, int nb, int round,
-                                                    const T* Qb, const int* flags) {
-  constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
-  if (flags[1]) return;
-  __shared__ T Q[N2][N2 + 1];
-  __shared__ T X[kTile][N2 + 1];  // the A tile, then the V tile (both as [row][pair column])
-  int bi, bj;
-  circle_pair(nb, round, blockIdx.x, &bi, &bj);
-  const int r0 = blockIdx.y * kTile;
-  const int tid = threadIdx.x;
-  const T* Qi = Qb + (int64_t)blockIdx.x * N2 * N2;
-  auto gidx = [&](int a) { return a < BS ? bi * BS + a : bj * BS + (a - BS); };
-  for (int e = tid; e < N2 * N2; e += kThreads) Q[e / N2][e % N2] = Qi[e];
-  for (int e = tid; e < kTile * N2; e += kThreads) {
-    const int i = e / N2, a = e % N2;
-    X[i][a] = (r0 + i < sp) ? A[(int64_t)(r0 + i) * sp + gidx(a)] : T(0);
+  // V tile: rows [r0, r0 + kTile) of the columns P_a
+  const int64_t vt = blockIdx.x - nA;
+  const int tiles = (sp + kTile - 1) / kTile;
+  const int a = (int)(vt / tiles), r0 = (int)(vt % tiles) * kTile;
+  int ai, aj;
+  circle_pair(nb, round, a, &ai, &aj);
+  auto ga = [&](int t) { return t < BS ? ai * BS + t : aj * BS + (t - BS); };
+  const T* Qa_g = Qb + (int64_t)a * N2 * N2;
+  for (int e = tid; e < N2 * N2; e += kThreads) Qa[e / N2][e % N2] = Qa_g[e];
+  for (int e = tid; e < N2 * kTile; e += kThreads) {
+    const int c = e / kTile, i = e % kTile;
+    X[i][c] = (r0 + i < sp) ? V[(int64_t)ga(c) * sp + r0 + i] : T(0);
   }
   __syncthreads();
-  for (int e = tid; e < kTile * N2; e += kThreads) {
-    const int i = e / N2, a = e % N2;
+  for (int e = tid; e < N2 * kTile; e += kThreads) {
+    const int c = e / kTile, i = e % kTile;
     if (r0 + i >= sp) continue;
-    T acc = T(0);
+    T v = T(0);
 #pragma unroll 8
-    for (int b = 0; b < N2; ++b) acc = fma(X[i][b], Q[b][a], acc);
-    A[(int64_t)(r0 + i) * sp + gidx(a)] = acc;
-  }
-  __syncthreads();
-  for (int e = tid; e < N2 * kTile; e += kThreads) {
-    const int a = e / kTile, i = e % kTile;
-    X[i][a] = (r0 + i < sp) ? V[(int64_t)gidx(a) * sp + r0 + i] : T(0);
-  }
-  __syncthreads();
-  for (int e = tid; e < N2 * kTile; e += kThreads) {
-    const int a = e / kTile, i = e % kTile;
-    if (r0 + i >= sp) continue;
-    T acc = T(0);
-#pragma unroll 8
-    for (int b = 0; b < N2; ++b) acc = fma(X[i][b], Q[b][a], acc);
-    V[(int64_t)gidx(a) * sp + r0 + i] = acc;
+    for (int k = 0; k < N2; ++k) v = fma(X[i][k], Qa[k][c], v);
+    V[(int64_t)ga(c) * sp + r0 + i] = v;
   }
 }
 
@@ -214,12 +230,15 @@ __global__ void bj_offnorm(const T* A, int sp, double* off, const int* flags) {
 // the previous sweep.  The solve has converged when a sweep rotated nothing, or when the
 // off-diagonal norm is at the rounding level of T (below 64 sqrt(s) eps_T ||A||_F) and the sweep
 // did not halve it: the rotations left are rotating rounding noise (the rule of jacobi_kernel).
+// `cur` is the buffer (0 or 1) that holds A after this sweep; it is recorded in flags[4] when the
+// solve ends here, since the launches after that return at once and swap nothing.
 template <typename T>
-__global__ void bj_sweep_end(int* flags, int max_sweeps, double* norms, int s) {
+__global__ void bj_sweep_end(int* flags, int max_sweeps, double* norms, int s, int cur) {
   if (flags[1]) return;
   const double gate = 64.0 * sqrt((double)s) * (double)BJ<T>::eps() * sqrt(norms[0]);
   const bool stalled = flags[2] >= 1 && norms[1] > 0.25 * norms[2] && norms[1] <= gate * gate;
   flags[2] += 1;
+  flags[4] = cur;
   if (flags[0] == 0 || stalled) flags[1] = 1;
   else if (flags[2] >= max_sweeps) flags[3] = 1;  // sweep limit reached while still rotating
   flags[0] = 0;
@@ -227,9 +246,12 @@ __global__ void bj_sweep_end(int* flags, int max_sweeps, double* norms, int s) {
   norms[1] = 0.0;
 }
 
-// eigenvalues = diag(A)[0..s), sorted descending (ties by index); eigenvectors follow.
+// eigenvalues = diag(A)[0..s), sorted descending (ties by index); eigenvectors follow.  A is the
+// buffer flags[4] names.
 template <typename T>
-__global__ void bj_finish(const T* A, const T* V, int sp, int s, T* w, T* Vout) {
+__global__ void bj_finish(const T* A0, const T* A1, const T* V, int sp, int s, T* w, T* Vout,
+                          const int* flags) {
+  const T* A = flags[4] ? A1 : A0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
     const T di = A[(int64_t)i * sp + i];
     int rank = 0;
@@ -252,7 +274,7 @@ int64_t block_jacobi_work(int s) {
   int nb = (s + BS - 1) / BS;
   nb += nb & 1;
   const int64_t sp = (int64_t)nb * BS;
-  return 2 * sp * sp + (int64_t)(nb / 2) * N2 * N2 + 16;
+  return 3 * sp * sp + (int64_t)(nb / 2) * N2 * N2 + 16;
 }
 
 template <typename T>
@@ -264,39 +286,43 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
   nb += nb & 1;
   if (nb < 2) nb = 2;
   const int sp = nb * BS;
-  T* A = work;
-  T* V = work + (int64_t)sp * sp;
+  T* A0 = work;                       // A, double-buffered: each round reads one, writes the other
+  T* A1 = work + (int64_t)sp * sp;
+  T* V = A1 + (int64_t)sp * sp;
   T* Qb = V + (int64_t)sp * sp;
   const int npairs = nb / 2;
   TT_CUDA(cudaMemsetAsync(fro, 0, 3 * sizeof(double), st));
-  TT_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+  TT_CUDA(cudaMemsetAsync(flags, 0, 5 * sizeof(int), st));
   {
     int64_t n = (int64_t)sp * sp;
     int grid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8);
     note_launch();
-    bj_init<T><<<grid, kThreads, 0, st>>>(G, ldg, s, sp, A, V, fro, flags);
+    bj_init<T><<<grid, kThreads, 0, st>>>(G, ldg, s, sp, A0, V, fro, flags);
   }
   const int tiles = (sp + kTile - 1) / kTile;
+  const int64_t upd_ctas = (int64_t)npairs * npairs + (int64_t)npairs * tiles;
+  int cur = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int round = 0; round < nb - 1; ++round) {
+      T* Ain = cur ? A1 : A0;
+      T* Aout = cur ? A0 : A1;
       note_launch();
-      bj_solve<T><<<npairs, 32 * BS, 0, st>>>(A, sp, nb, round, Qb, fro, flags);
+      bj_solve<T><<<npairs, 32 * BS, 0, st>>>(Ain, sp, nb, round, Qb, fro, flags);
       note_launch();
-      bj_rows<T><<<dim3(npairs, tiles), kThreads, 0, st>>>(A, sp, nb, round, Qb, flags);
-      note_launch();
-      bj_cols<T><<<dim3(npairs, tiles), kThreads, 0, st>>>(A, V, sp, nb, round, Qb, flags);
+      bj_update<T><<<(unsigned)upd_ctas, kThreads, 0, st>>>(Ain, Aout, V, sp, nb, round, Qb, flags);
+      cur ^= 1;
     }
     {
       const int64_t n = (int64_t)sp * sp;
       const int grid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 2);
       note_launch();
-      bj_offnorm<T><<<grid, kThreads, 0, st>>>(A, sp, fro + 1, flags);
+      bj_offnorm<T><<<grid, kThreads, 0, st>>>(cur ? A1 : A0, sp, fro + 1, flags);
     }
     note_launch();
-    bj_sweep_end<T><<<1, 1, 0, st>>>(flags, max_sweeps, fro, s);
+    bj_sweep_end<T><<<1, 1, 0, st>>>(flags, max_sweeps, fro, s, cur);
   }
   note_launch();
-  bj_finish<T><<<(s + 127) / 128, 128, 0, st>>>(A, V, sp, s, w, Vout);
+  bj_finish<T><<<(s + 127) / 128, 128, 0, st>>>(A0, A1, V, sp, s, w, Vout, flags);
   (void)N2;
   return cudaGetLastError();
 }

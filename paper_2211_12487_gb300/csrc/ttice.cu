@@ -437,14 +437,15 @@ int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
   // rR = 0 is decided by the trace alone (no Ritz value enters it)
   if (rR == 0) { *ok = true; return TTICE_OK; }
   const int jm = std::min(rR, K);
-  TT_CU(cudaMemsetAsync(h->GQ, 0, (size_t)s * jm * sizeof(double), st));
-  GemmArgs g;  // GQ = G Z
-  g.M = s; g.N = jm; g.K = s; g.atomic = 1; g.allow_splitk = 1;
-  g.A.p = h->G; g.A.rs = s; g.A.cs = 1;
-  g.B.p = h->Q2; g.B.rs = 1; g.B.cs = s;
-  g.C = h->GQ; g.c_rs = 1; g.c_cs = s;
+  // G z_j for the Ritz vectors z = Q Z: (G Q) Z from the G Q the Rayleigh-Ritz step formed, an
+  // s x K x jm product instead of s x s x jm (the two differ by FP64 rounding)
+  GemmArgs g;
+  g.M = s; g.N = jm; g.K = K;
+  g.A.p = h->GQ; g.A.rs = 1; g.A.cs = s;
+  g.B.p = h->Z; g.B.rs = 1; g.B.cs = K;
+  g.C = h->Vn2; g.c_rs = 1; g.c_cs = s;
   TT_CU((gemm<double, double, double, double, double>(g, st)));
-  TT_CU(launch_ritz_residual(h->GQ, h->Q2, h->theta, s, jm, h->res, st));
+  TT_CU(launch_ritz_residual(h->Vn2, h->Q2, h->theta, s, jm, h->res, st));
   TT_CU(cudaMemcpyAsync(h->h_dbl, h->res, jm * sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_dbl + 128, h->theta, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_TRY(sync_read(h, st));
@@ -553,17 +554,23 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     if (s > kKrylovMin) {
       // block Krylov candidates + FP64 Rayleigh-Ritz, kept only if certified: a 32-vector basis
       // first (enough for a few new directions, and an 8x smaller Ritz problem), then 64 — restarted
-      // from the first attempt's leading Ritz vectors when it got as far as Rayleigh-Ritz
-      bool restart = false;
-      for (int nblk : {kKryBlocks / 2, kKryBlocks}) {
+      // from the first attempt's leading Ritz vectors when it got as far as Rayleigh-Ritz, and from a
+      // fresh block if that restart fails too (well-converged start vectors span a nearly invariant
+      // subspace, so the restarted recurrence can break down)
+      bool restart = false, restarted = false;
+      for (int attempt = 0; attempt < 3; ++attempt) {
+        const int nblk = attempt == 0 ? kKryBlocks / 2 : kKryBlocks;
+        if (attempt == 2 && !restarted) break;
+        const bool from_ritz = attempt == 1 && restart;
         int Kk = 0;
-        TT_TRY(krylov_candidates(h, s, eps_c, nblk, restart ? h->kstart : nullptr, &Kk, st));
+        TT_TRY(krylov_candidates(h, s, eps_c, nblk, from_ritz ? h->kstart : nullptr, &Kk, st));
+        restarted = restarted || from_ritz;
         if (Kk > 0) {
           TT_TRY(rayleigh_ritz(h, s, Kk, d_eps, max_new, st));
           bool ok = false;
           TT_TRY(krylov_certify(h, s, Kk, &ok, st));
           if (ok) { have = true; K = Kk; h->stats.krylov_solves += 1; break; }
-          if (Kk >= kKryP) {  // Ritz vectors h->Q2 (s x Kk, FP64): the leading 8 seed the retry
+          if (attempt == 0 && Kk >= kKryP) {  // Ritz vectors h->Q2 (s x Kk, FP64): the leading 8 seed the retry
             TT_CU((launch_cast<double, float>(h->Q2, h->kstart, s * kKryP, st)));
             restart = true;
           }
@@ -1021,7 +1028,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK && h->wt_bytes == 8) rc = dalloc<double>(&h->bjw64, block_jacobi_work<double>((int)s));
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->bjw32, block_jacobi_work<float>((int)s));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->fro, 3);  // ||A||^2, off-norm^2 now and one sweep back
-  if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 4);
+  if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 8);
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->G32, s * s);
   if (rc == TTICE_OK) rc = dalloc<float>(&h->KQ, s * kKry);
   if (rc == TTICE_OK) rc = dalloc<float>(&h->kstart, s * kKryP);

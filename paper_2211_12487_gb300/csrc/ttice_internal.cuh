@@ -56,8 +56,8 @@ cudaError_t jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* V, T* work,
 
 // Multi-CTA block Jacobi (see bjacobi.cu): same outputs as jacobi_eig.  work: block_jacobi_work<T>(s)
 // elements; fro: device double[3] scratch (the Frobenius and off-diagonal norms the stopping rule
-// reads); flags: device int[4] ([3] = 1 if the sweep limit was hit while rotations were still
-// significant).
+// reads); flags: device int[5] ([2] = sweeps, [3] = 1 if the sweep limit was hit while rotations
+// were still significant, [4] = internal).
 template <typename T>
 int64_t block_jacobi_work(int s);
 template <typename T>
