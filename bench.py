@@ -154,15 +154,16 @@ def oracle_elements_per_s(budget_s: float, batch: int):
     return n_el / t_busy, k, t_busy, int(threads)
 
 
-def run_serving(seconds: float, n_streams: int = 64, rate: float = 400.0, slots: int = 16, seed: int = 1003,
+def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots: int = 16, seed: int = 1003,
                 drain_s: float = 60.0):
     """Continuous batching over many streams (the serving workload): stream shapes drawn from
     {16^4 cosine stream, the 20x24x20x32x3 video view, 64^3 x 4 flow, 32^4 cosine stream}, batch
-    sizes from {1, 4, 16, 32}, eps from {0.05, 0.1, 0.3}; Poisson arrivals at `rate` increments/s over
-    all streams for `seconds`.  Each stream cycles through a pool of pre-generated device-resident
+    sizes from {1, 4, 16, 32}, eps from {0.05, 0.1, 0.3}; Poisson arrivals over all streams for
+    `seconds` at each rate in `rates` (a nominal load, then a saturating one), the streams continuing
+    from one phase to the next.  Each stream cycles through a pool of pre-generated device-resident
     increments (at most ~192 MB per stream), so later requests of a stream are mostly represented
     already and take the skip path.  Latency = arrival -> completion of the update.  Requests still
-    queued `drain_s` after the last arrival are dropped and counted (the load was above capacity)."""
+    queued `drain_s` after the last arrival are dropped and counted."""
     import collections
     import random
 
@@ -193,45 +194,53 @@ def run_serving(seconds: float, n_streams: int = 64, rate: float = 400.0, slots:
         pools[name] = [y[k * b:(k + 1) * b] for k in range(npool)]
     torch.cuda.synchronize()
     eng = S.ServingEngine(specs, slots=slots)
+    phases = []
     try:
         # warm-up: one increment per stream (creates every handle, first update from empty cores)
         for sp in specs:
             eng.submit(S.Request(sp.name, pools[sp.name][0]))
         eng.drain(timeout=600)
-        eng.completed.clear()
         count = {sp.name: 1 for sp in specs}
-        t0 = time.perf_counter()
-        t_next = t0
-        n_sub = 0
-        elements = 0
-        while True:
-            t_next += rng.expovariate(rate)
-            if t_next - t0 > seconds:
-                break
-            now = time.perf_counter()
-            if t_next > now:
-                time.sleep(t_next - now)
-            sp = specs[rng.randrange(n_streams)]
-            k = count[sp.name]
-            count[sp.name] = k + 1
-            y = pools[sp.name][k % len(pools[sp.name])]
-            eng.submit(S.Request(sp.name, y, arrival=t_next))
-            n_sub += 1
-            elements += y.numel()
-        ok = eng.drain(timeout=drain_s)
-        wall = time.perf_counter() - t0
-        with eng.lock:
-            done = list(eng.completed)
-        lat = sorted((r.done - r.arrival) * 1e3 for r in done if r.error is None)
-        skipped = sum(1 for r in done if r.stats is not None and r.stats.skipped)
-        errors = collections.Counter(str(r.error)[:80] for r in done if r.error is not None)
-        return {"streams": n_streams, "slots": slots, "arrival_rate_per_s": rate, "seconds": seconds,
-                "requests": n_sub, "completed": len(lat), "errors": dict(errors), "drained": ok,
-                "dropped": n_sub - len(done),
-                "skipped_fraction": skipped / max(len(done), 1),
-                "p50_ms": S.percentile(lat, 0.50), "p99_ms": S.percentile(lat, 0.99),
-                "max_ms": lat[-1] if lat else None,
-                "throughput_elements_per_s": elements / wall, "throughput_updates_per_s": len(lat) / wall}
+        for rate in rates:
+            with eng.lock:
+                eng.completed.clear()
+            t0 = time.perf_counter()
+            t_next = t0
+            n_sub = 0
+            elements = 0
+            while True:
+                t_next += rng.expovariate(rate)
+                if t_next - t0 > seconds:
+                    break
+                now = time.perf_counter()
+                if t_next > now:
+                    time.sleep(t_next - now)
+                sp = specs[rng.randrange(n_streams)]
+                k = count[sp.name]
+                count[sp.name] = k + 1
+                y = pools[sp.name][k % len(pools[sp.name])]
+                eng.submit(S.Request(sp.name, y, arrival=t_next))
+                n_sub += 1
+                elements += y.numel()
+            ok = eng.drain(timeout=drain_s)
+            wall = time.perf_counter() - t0
+            with eng.lock:
+                done = list(eng.completed)
+            if not ok:  # drop what is still queued so that the next phase starts empty
+                with eng.lock:
+                    for dq in eng.pending.values():
+                        dq.clear()
+                eng.drain(timeout=drain_s)
+            lat = sorted((r.done - r.arrival) * 1e3 for r in done if r.error is None)
+            skipped = sum(1 for r in done if r.stats is not None and r.stats.skipped)
+            errors = collections.Counter(str(r.error)[:80] for r in done if r.error is not None)
+            phases.append({"arrival_rate_per_s": rate, "seconds": seconds, "requests": n_sub,
+                           "completed": len(lat), "errors": dict(errors), "drained": ok,
+                           "dropped": n_sub - len(done), "skipped_fraction": skipped / max(len(done), 1),
+                           "p50_ms": S.percentile(lat, 0.50), "p99_ms": S.percentile(lat, 0.99),
+                           "throughput_elements_per_s": elements / wall,
+                           "throughput_updates_per_s": len(lat) / wall})
+        return {"streams": n_streams, "slots": slots, "phases": phases}
     finally:
         eng.close(cancel_pending=True)
 

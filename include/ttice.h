@@ -49,13 +49,15 @@ extern "C" {
 #define TTICE_EPSUPD_EXACT 0  /* Eq. 18 (default) */
 #define TTICE_EPSUPD_APPROX 1 /* Eq. 19, count-weighted */
 
-/* Arithmetic of the projections / contractions (the Gram, eigen-solve, CGS2 and all norms and
- * thresholds are FP64 in every mode). */
+/* Arithmetic of the path.  In every mode the cores are stored in FP64 and the rank decision (the
+ * Ritz values it reads), the re-orthogonalisation of new directions (CGS2, Cholesky-QR) and all
+ * norms and thresholds are FP64. */
 #define TTICE_FP64 0 /* FP64 everywhere: the plain FP64 GPU TT-ICE */
-#define TTICE_FP32 1 /* FP32 projections with FP32 accumulation (SIMT) */
-#define TTICE_TF32 2 /* TF32 tensor-core projections, FP32 accumulation */
-#define TTICE_BF16 3 /* BF16 tensor-core projections, FP32 accumulation */
-#define TTICE_SPLIT_BF16 4 /* three-term split-BF16 projections (~16 mantissa bits) */
+#define TTICE_FP32 1 /* FP32 projections and residuals (SIMT, FP32 accumulation), Gram as FP32
+                        products summed in FP64, FP32 eigen-solve candidates + FP64 Rayleigh-Ritz */
+#define TTICE_TF32 2 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
+#define TTICE_BF16 3 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
+#define TTICE_SPLIT_BF16 4 /* reserved (split-BF16 projections): ttice_create returns TTICE_EINVAL */
 
 /* Element type of increments passed to ttice_update / ttice_project, and of reconstructions. */
 #define TTICE_F32 0
