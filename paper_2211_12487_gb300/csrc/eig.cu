@@ -463,6 +463,57 @@ __global__ void chol_inv_kernel(const double* S, int k, double* Rinv, int* statu
   double* R = sm;          // k x k, column-major
   double* Ri = sm + k * k; // k x k
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (k <= 32) {
+    // one warp (the launch is 32 threads): lane c keeps column c of the upper triangle in
+    // registers; right-looking Cholesky with shuffles, then lane c forms column c of R^{-1} by back
+    // substitution with the reciprocal diagonal
+    __shared__ double dinv[32];
+    const int lane = tid;
+    double col[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) col[r] = (lane < k && r <= lane) ? S[r + lane * k] : 0.0;
+    int bad = 0;
+    double my_inv = 1.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j < k) {
+        double d = __shfl_sync(0xffffffffu, col[j], j);
+        if (!(d > 0.0)) { bad = 1; d = 1.0; }
+        const double rjj = sqrt(d), inv = 1.0 / rjj;
+        if (lane == j) { col[j] = rjj; my_inv = inv; }
+        else if (lane > j) col[j] *= inv;
+#pragma unroll
+        for (int c2 = j + 1; c2 < 32; ++c2) {
+          if (c2 < k) {
+            const double rjc = __shfl_sync(0xffffffffu, col[j], c2);
+            if (lane >= c2 && lane < k) col[c2] = fma(-rjc, col[j], col[c2]);
+          }
+        }
+      }
+    }
+    if (lane < k) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (r <= lane) R[r + lane * k] = col[r];
+      dinv[lane] = my_inv;
+    }
+    __syncwarp();
+    if (lane < k) {
+      const int c = lane;
+      for (int i = c; i >= 0; --i) {
+        double v = (i == c) ? 1.0 : 0.0;
+        for (int l = i + 1; l <= c; ++l) v = fma(-R[i + l * k], Ri[l + c * k], v);
+        Ri[i + c * k] = v * dinv[i];
+      }
+    }
+    __syncwarp();
+    for (int e = lane; e < k * k; e += 32) {
+      const int i = e % k, c = e / k;
+      Rinv[e] = (i <= c) ? Ri[e] : 0.0;
+    }
+    if (lane == 0 && status) *status = bad;
+    return;
+  }
   for (int e = tid; e < k * k; e += nt) { R[e] = S[e]; Ri[e] = 0.0; }
   __syncthreads();
   __shared__ int bad;
@@ -569,7 +620,7 @@ cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, c
   });
   TT_CUDA(attr_err);
   note_launch();
-  chol_inv_kernel<<<1, 256, smem, st>>>(S, k, Rinv, status);
+  chol_inv_kernel<<<1, k <= 32 ? 32 : 256, smem, st>>>(S, k, Rinv, status);
   return cudaGetLastError();
 }
 

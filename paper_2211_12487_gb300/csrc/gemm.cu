@@ -36,6 +36,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) gemm_kernel(GemmArgs g,
   const int64_t kend = min(g.K, kbeg + kchunk);
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  // symmetric Gram: global row/column offsets of this batch's block; tiles wholly below the
+  // diagonal are left to the mirror writes of their transposes
+  const int64_t sym_r = (g.sym == 2) ? (int64_t)z1 * g.M : 0, sym_c = (g.sym == 2) ? (int64_t)z2 * g.N : 0;
+  if (g.sym && sym_r + m0 > sym_c + n0 + BN - 1) return;
   const bool a_kfast = (g.A.cs == 1);
   const bool b_nfast = (g.B.cs == 1);
 
@@ -173,7 +177,19 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) gemm_kernel(GemmArgs g,
           ss_t = fma(q, q, ss_t);
           rowss[i] = fma(q, q, rowss[i]);
         }
-        if (g.store) {
+        if (g.store && g.sym) {
+          const int64_t R = sym_r + gm, Cc = sym_c + gn;  // position in the symmetric matrix
+          if (R <= Cc) {
+            TC* dst = C + R * g.c_rs + Cc;
+            if (g.atomic) atomicAdd(dst, cv);
+            else *dst = cv;
+            if (R < Cc) {
+              TC* mir = C + Cc * g.c_rs + R;
+              if (g.atomic) atomicAdd(mir, cv);
+              else *mir = cv;
+            }
+          }
+        } else if (g.store) {
           TC* dst = C + coff + gm * g.c_rs + gn * g.c_cs;
           if (g.atomic) atomicAdd(dst, cv);
           else *dst = cv;

@@ -510,18 +510,21 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     GemmArgs g;
     g.atomic = 1; g.allow_splitk = 1;
     g.C = h->G;
+    // symmetric: only the upper triangle of G is formed (and mirrored)
     if (left) {
       g.M = m; g.N = m; g.K = L;
       g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
       g.B.p = R; g.B.rs = 1; g.B.cs = L; g.B.bs1 = m * L;
       g.c_rs = s; g.c_cs = 1;
       g.nbatch = nsel;
+      g.sym = 1;
     } else {
       g.M = L; g.N = L; g.K = m;
       g.A.p = R; g.A.rs = 1; g.A.cs = L; g.A.bs1 = m * L;
       g.B.p = R; g.B.rs = L; g.B.cs = 1; g.B.bs2 = m * L;
       g.c_rs = s; g.c_cs = 1; g.c_bs1 = L * s; g.c_bs2 = L;
       g.nbatch = nsel * nsel; g.bdiv = nsel;
+      g.sym = 2;
     }
     if constexpr (sizeof(WT) == 8) TT_CU((gemm<WT, WT, WT, double, double>(g, st)));
     else TT_CU((gemm<WT, WT, WT, double, float>(g, st)));  // FP32 products, FP64 accumulation

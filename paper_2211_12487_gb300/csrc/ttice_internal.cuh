@@ -39,6 +39,9 @@ struct GemmArgs {
   int allow_splitk = 0;   // with atomic: split K across CTAs when the tile grid is small
   int64_t c_zero_elems = 0;  // without atomic: C spans this many elements from C; if the tile grid
                              // is small, zero them and split K with atomic adds instead of stores
+  int sym = 0;  // C is a symmetric Gram (c_cs = 1, leading dimension c_rs): only its upper triangle
+                // is formed and mirrored.  1: one M x M matrix (every batch adds into it);
+                // 2: batch zb is the block (zb / bdiv, zb % bdiv) of size M x N of a larger one
 };
 
 template <typename TA, typename TB, typename TX, typename TC, typename ACC>
