@@ -17,6 +17,9 @@
 // off-diagonal entries are exactly zero), so the first s coordinates carry the eigenpairs.
 #include <algorithm>
 #include <cfloat>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "ttice_internal.cuh"
 
@@ -240,7 +243,7 @@ __global__ void bj_sweep_end(int* flags, int max_sweeps, double* norms, int s, i
   flags[2] += 1;
   flags[4] = cur;
   if (flags[0] == 0 || stalled) flags[1] = 1;
-  else if (flags[2] >= max_sweeps) flags[3] = 1;  // sweep limit reached while still rotating
+  else if (flags[2] >= max_sweeps) { flags[3] = 1; flags[1] = 1; }  // sweep limit reached while still rotating
   flags[0] = 0;
   norms[2] = norms[1];
   norms[1] = 0.0;
@@ -301,25 +304,58 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
   }
   const int tiles = (sp + kTile - 1) / kTile;
   const int64_t upd_ctas = (int64_t)npairs * npairs + (int64_t)npairs * tiles;
-  int cur = 0;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int round = 0; round < nb - 1; ++round) {
-      T* Ain = cur ? A1 : A0;
-      T* Aout = cur ? A0 : A1;
-      note_launch();
-      bj_solve<T><<<npairs, 32 * BS, 0, st>>>(Ain, sp, nb, round, Qb, fro, flags);
-      note_launch();
-      bj_update<T><<<(unsigned)upd_ctas, kThreads, 0, st>>>(Ain, Aout, V, sp, nb, round, Qb, flags);
-      cur ^= 1;
-    }
-    {
+  // Two sweeps of rounds (the buffer parity repeats after two, since a sweep has nb - 1 rounds, an
+  // odd count) are captured once into a CUDA graph per (buffers, size) and replayed until the sweep
+  // cap; every kernel returns at once after the solve has ended.  Capture goes to a private stream
+  // of the calling thread: nothing runs there, the graph is launched on st.
+  auto enqueue_two_sweeps = [&](cudaStream_t cs) {
+    int cur = 0;
+    for (int sweep = 0; sweep < 2; ++sweep) {
+      for (int round = 0; round < nb - 1; ++round) {
+        T* Ain = cur ? A1 : A0;
+        T* Aout = cur ? A0 : A1;
+        bj_solve<T><<<npairs, 32 * BS, 0, cs>>>(Ain, sp, nb, round, Qb, fro, flags);
+        bj_update<T><<<(unsigned)upd_ctas, kThreads, 0, cs>>>(Ain, Aout, V, sp, nb, round, Qb, flags);
+        cur ^= 1;
+      }
       const int64_t n = (int64_t)sp * sp;
       const int grid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 2);
-      note_launch();
-      bj_offnorm<T><<<grid, kThreads, 0, st>>>(cur ? A1 : A0, sp, fro + 1, flags);
+      bj_offnorm<T><<<grid, kThreads, 0, cs>>>(cur ? A1 : A0, sp, fro + 1, flags);
+      bj_sweep_end<T><<<1, 1, 0, cs>>>(flags, max_sweeps, fro, s, cur);
     }
-    note_launch();
-    bj_sweep_end<T><<<1, 1, 0, st>>>(flags, max_sweeps, fro, s, cur);
+  };
+  using Key = std::tuple<const void*, const void*, const void*, int, int>;
+  static std::mutex mu;
+  static std::map<Key, cudaGraphExec_t> cache;
+  const Key key{work, fro, flags, s, max_sweeps};
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) exec = it->second;
+  }
+  if (!exec) {
+    thread_local cudaStream_t cs = nullptr;
+    if (!cs) TT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    TT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    enqueue_two_sweeps(cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) return ce;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return ie;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.size() >= 512) {  // bound the cache: drop everything (graphs are cheap to rebuild)
+      for (auto& kv : cache) cudaGraphExecDestroy(kv.second);
+      cache.clear();
+    }
+    cache[key] = exec;
+  }
+  const int per_graph = 2 * (2 * (nb - 1) + 2);  // kernels in one replay
+  for (int g = 0; g < (max_sweeps + 1) / 2; ++g) {
+    for (int k = 0; k < per_graph; ++k) note_launch();
+    TT_CUDA(cudaGraphLaunch(exec, st));
   }
   note_launch();
   bj_finish<T><<<(s + 127) / 128, 128, 0, st>>>(A0, A1, V, sp, s, w, Vout, flags);
