@@ -430,25 +430,25 @@ int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int nblk, const float
 // appended, so the leading rR pairs are checked.
 int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
   *ok = false;
+  // G z_j for all K Ritz vectors z = Q Z: (G Q) Z from the G Q the Rayleigh-Ritz step formed, an
+  // s x K x K product instead of s x s x K (the two differ by FP64 rounding); their residuals are
+  // read together with the rank the rule chose, in one host round trip
+  GemmArgs g;
+  g.M = s; g.N = K; g.K = K;
+  g.A.p = h->GQ; g.A.rs = 1; g.A.cs = s;
+  g.B.p = h->Z; g.B.rs = 1; g.B.cs = K;
+  g.C = h->Vn2; g.c_rs = 1; g.c_cs = s;
+  TT_CU((gemm<double, double, double, double, double>(g, st)));
+  TT_CU(launch_ritz_residual(h->Vn2, h->Q2, h->theta, s, K, h->res, st));
   TT_CU(cudaMemcpyAsync(h->h_int, h->ibuf, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_dbl, h->res, K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_dbl + 128, h->theta, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_TRY(sync_read(h, st));
   const int rR = h->h_int[0];
   if (rR < 0) return TTICE_OK;
   // rR = 0 is decided by the trace alone (no Ritz value enters it)
   if (rR == 0) { *ok = true; return TTICE_OK; }
   const int jm = std::min(rR, K);
-  // G z_j for the Ritz vectors z = Q Z: (G Q) Z from the G Q the Rayleigh-Ritz step formed, an
-  // s x K x jm product instead of s x s x jm (the two differ by FP64 rounding)
-  GemmArgs g;
-  g.M = s; g.N = jm; g.K = K;
-  g.A.p = h->GQ; g.A.rs = 1; g.A.cs = s;
-  g.B.p = h->Z; g.B.rs = 1; g.B.cs = K;
-  g.C = h->Vn2; g.c_rs = 1; g.c_cs = s;
-  TT_CU((gemm<double, double, double, double, double>(g, st)));
-  TT_CU(launch_ritz_residual(h->Vn2, h->Q2, h->theta, s, jm, h->res, st));
-  TT_CU(cudaMemcpyAsync(h->h_dbl, h->res, jm * sizeof(double), cudaMemcpyDeviceToHost, st));
-  TT_CU(cudaMemcpyAsync(h->h_dbl + 128, h->theta, sizeof(double), cudaMemcpyDeviceToHost, st));
-  TT_TRY(sync_read(h, st));
   const double tol = 1e-6 * std::max(h->h_dbl[128], 0.0);
   bool good = true;
   for (int j = 0; j < jm; ++j) good = good && (h->h_dbl[j] <= tol);
