@@ -13,7 +13,7 @@
 // a sweep that leaves the off-diagonal norm at the working precision's rounding level without
 // halving it ends the solve too (rotations of rounding noise would otherwise run to the sweep cap);
 // every kernel returns at once after the solve has ended, so a fixed launch sequence costs almost
-// nothing once converged.  Padding to nb*BS adds zero rows/columns, which no rotation touches (their
+// nothing once converged.  Two sweeps of launches are captured once into a CUDA graph and replayed.  Padding to nb*BS adds zero rows/columns, which no rotation touches (their
 // off-diagonal entries are exactly zero), so the first s coordinates carry the eigenpairs.
 #include <algorithm>
 #include <cfloat>

@@ -13,10 +13,17 @@
 #include <cfloat>
 #include <mutex>
 
+#include "jacobi_rot.cuh"
 #include "ttice_internal.cuh"
 
 namespace ttice {
 namespace {
+
+using jrot::block_after;
+using jrot::diag_after;
+using jrot::make_rotation;
+using jrot::rr_pair;
+using jrot::rr_pair_of;
 
 template <typename T> struct Lim;
 template <> struct Lim<float> { static __device__ float eps() { return FLT_EPSILON; } };
@@ -175,66 +182,6 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_kernel(const double* G, in
 // re-forming, from A_in, the three entries of each next pair that this round produces (with the same
 // helper functions, so they agree with what is written), which removes the barrier between the
 // angle computation and the update.
-template <typename T>
-__device__ __forceinline__ void rr_pair(int k, int r, int m, int& p, int& q) {
-  // (r + k) mod m and (r - k) mod m for 0 <= r, k < m, without an integer division
-  if (k == 0) { p = r; q = m; }
-  else {
-    p = r + k; if (p >= m) p -= m;
-    q = r - k; if (q < 0) q += m;
-  }
-  if (p > q) { const int t = p; p = q; q = t; }
-}
-
-// pair index of player x in round r (inverse of rr_pair); m = players - 1
-__device__ __forceinline__ int rr_pair_of(int x, int r, int m) {
-  if (x == m || x == r) return 0;
-  int k = x - r;
-  if (k < 0) k += m;
-  return (2 * k <= m) ? k : m - k;
-}
-
-// The rotation that zeroes a_pq: t = sgn(tau) / (|tau| + sqrt(1 + tau^2)) with
-// tau = (a_qq - a_pp) / (2 a_pq), evaluated as sgn(tau) |2 a_pq| / (|a_qq - a_pp| + hypot(.)) (the
-// same value multiplied through by |2 a_pq|: one hypot, one division and one reciprocal square root
-// instead of three square roots and three divisions, which matters for FP64 at 1/64 rate).
-template <typename T>
-__device__ __forceinline__ void make_rotation(T app, T aqq, T apq, T floor_abs, T& c, T& sn, T& t) {
-  c = T(1); sn = T(0); t = T(0);
-  if (fabs(apq) > floor_abs && fabs(apq) > Lim<T>::eps() * sqrt(fabs(app * aqq))) {
-    const T th = aqq - app, ph = T(2) * apq;
-    const bool pos = (th == T(0)) || ((th > T(0)) == (ph > T(0)));  // tau >= 0
-    const T mag = fabs(ph) / (fabs(th) + hypot(th, ph));
-    t = pos ? mag : -mag;
-    c = rsqrt(T(1) + t * t);
-    sn = t * c;
-  }
-}
-
-// new diagonal entries of a rotated pair: a_pp - t a_pq and a_qq + t a_pq (a_pq becomes 0)
-template <typename T>
-__device__ __forceinline__ T diag_after(T a, T t, T apq, bool is_p) {
-  return is_p ? fma(-t, apq, a) : fma(t, apq, a);
-}
-
-// R_i B R_j^T of one 2x2 block, R = [[c, -s], [s, c]]; entries of rows/columns that are the dummy
-// player are zero in B and never read from the result
-template <typename T>
-__device__ __forceinline__ void block_after(const T* A, int lda, int s, int pi, int qi, int pj, int qj,
-                                            T ci, T si, T cj, T sj, T o[4]) {
-  const bool ri = qi < s, rj = qj < s;
-  const T b00 = A[pi * lda + pj];
-  const T b01 = rj ? A[pi * lda + qj] : T(0);
-  const T b10 = ri ? A[qi * lda + pj] : T(0);
-  const T b11 = (ri && rj) ? A[qi * lda + qj] : T(0);
-  const T m00 = fma(ci, b00, -(si * b10)), m01 = fma(ci, b01, -(si * b11));
-  const T m10 = fma(si, b00, ci * b10), m11 = fma(si, b01, ci * b11);
-  o[0] = fma(cj, m00, -(sj * m01));
-  o[1] = fma(sj, m00, cj * m01);
-  o[2] = fma(cj, m10, -(sj * m11));
-  o[3] = fma(sj, m10, cj * m11);
-}
-
 constexpr int kSmallEigMax = 128;
 
 template <typename T>
@@ -463,57 +410,6 @@ __global__ void chol_inv_kernel(const double* S, int k, double* Rinv, int* statu
   double* R = sm;          // k x k, column-major
   double* Ri = sm + k * k; // k x k
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (k <= 32) {
-    // one warp (the launch is 32 threads): lane c keeps column c of the upper triangle in
-    // registers; right-looking Cholesky with shuffles, then lane c forms column c of R^{-1} by back
-    // substitution with the reciprocal diagonal
-    __shared__ double dinv[32];
-    const int lane = tid;
-    double col[32];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) col[r] = (lane < k && r <= lane) ? S[r + lane * k] : 0.0;
-    int bad = 0;
-    double my_inv = 1.0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j < k) {
-        double d = __shfl_sync(0xffffffffu, col[j], j);
-        if (!(d > 0.0)) { bad = 1; d = 1.0; }
-        const double rjj = sqrt(d), inv = 1.0 / rjj;
-        if (lane == j) { col[j] = rjj; my_inv = inv; }
-        else if (lane > j) col[j] *= inv;
-#pragma unroll
-        for (int c2 = j + 1; c2 < 32; ++c2) {
-          if (c2 < k) {
-            const double rjc = __shfl_sync(0xffffffffu, col[j], c2);
-            if (lane >= c2 && lane < k) col[c2] = fma(-rjc, col[j], col[c2]);
-          }
-        }
-      }
-    }
-    if (lane < k) {
-#pragma unroll
-      for (int r = 0; r < 32; ++r)
-        if (r <= lane) R[r + lane * k] = col[r];
-      dinv[lane] = my_inv;
-    }
-    __syncwarp();
-    if (lane < k) {
-      const int c = lane;
-      for (int i = c; i >= 0; --i) {
-        double v = (i == c) ? 1.0 : 0.0;
-        for (int l = i + 1; l <= c; ++l) v = fma(-R[i + l * k], Ri[l + c * k], v);
-        Ri[i + c * k] = v * dinv[i];
-      }
-    }
-    __syncwarp();
-    for (int e = lane; e < k * k; e += 32) {
-      const int i = e % k, c = e / k;
-      Rinv[e] = (i <= c) ? Ri[e] : 0.0;
-    }
-    if (lane == 0 && status) *status = bad;
-    return;
-  }
   for (int e = tid; e < k * k; e += nt) { R[e] = S[e]; Ri[e] = 0.0; }
   __syncthreads();
   __shared__ int bad;
@@ -536,12 +432,16 @@ __global__ void chol_inv_kernel(const double* S, int k, double* Rinv, int* statu
     }
     __syncthreads();
   }
-  // invert the upper triangular R column by column (each thread one column of Ri)
+  // invert the upper triangular R column by column (each thread one column of Ri), multiplying by
+  // the reciprocal diagonal (k FP64 divisions in parallel instead of k^2/2 on the critical path)
+  __shared__ double dinv[112];
+  for (int i = tid; i < k; i += nt) dinv[i] = 1.0 / R[i + i * k];
+  __syncthreads();
   for (int c = tid; c < k; c += nt) {
     for (int i = c; i >= 0; --i) {
       double v = (i == c) ? 1.0 : 0.0;
-      for (int l = i + 1; l <= c; ++l) v -= R[i + l * k] * Ri[l + c * k];
-      Ri[i + c * k] = v / R[i + i * k];
+      for (int l = i + 1; l <= c; ++l) v = fma(-R[i + l * k], Ri[l + c * k], v);
+      Ri[i + c * k] = v * dinv[i];
     }
   }
   __syncthreads();
@@ -620,7 +520,7 @@ cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, c
   });
   TT_CUDA(attr_err);
   note_launch();
-  chol_inv_kernel<<<1, k <= 32 ? 32 : 256, smem, st>>>(S, k, Rinv, status);
+  chol_inv_kernel<<<1, 256, smem, st>>>(S, k, Rinv, status);
   return cudaGetLastError();
 }
 
