@@ -133,15 +133,6 @@ __global__ void sum_squares_kernel(const T* x, int64_t N, double* out) {
   }
 }
 
-template <typename T>
-__global__ void check_finite_kernel(const T* x, int64_t n, int* flag) {
-  int bad = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    bad |= !isfinite((double)x[i]);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
-}
-
 __global__ void trace_kernel(const double* G, int64_t ldg, int s, double* out) {
   double t = 0.0;
   for (int i = threadIdx.x; i < s; i += blockDim.x) t += G[i * ldg + i];
@@ -234,17 +225,6 @@ __global__ void col_norms_kernel(const double* V, int64_t m, int64_t ld, double*
 
 // Deterministic pseudo-random numbers in [-1, 1) (splitmix64 of seed + index): start blocks of the
 // Krylov eigen-solver; the solver's result does not depend on them once converged.
-__global__ void fill_hash_kernel(double* x, int64_t n, uint64_t seed) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z = z ^ (z >> 31);
-    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
-  }
-}
-
 // res[j] = || GQ[:, j] - theta[j] Q[:, j] ||  (Ritz residual norms), one CTA per column.
 __global__ void ritz_residual_kernel(const double* GQ, const double* Q, const double* theta,
                                      int64_t s, double* res) {
@@ -330,16 +310,6 @@ cudaError_t launch_sum_squares(const T* x, int b, int64_t N, double* out, cudaSt
 template cudaError_t launch_sum_squares<float>(const float*, int, int64_t, double*, cudaStream_t);
 template cudaError_t launch_sum_squares<double>(const double*, int, int64_t, double*, cudaStream_t);
 
-template <typename T>
-cudaError_t launch_check_finite(const T* x, int64_t n, int* flag, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  note_launch();
-  check_finite_kernel<T><<<grid_for(n), kThreads, 0, st>>>(x, n, flag);
-  return cudaGetLastError();
-}
-template cudaError_t launch_check_finite<float>(const float*, int64_t, int*, cudaStream_t);
-template cudaError_t launch_check_finite<double>(const double*, int64_t, int*, cudaStream_t);
-
 cudaError_t launch_trace(const double* G, int64_t ldg, int s, double* out, cudaStream_t st) {
   note_launch();
   trace_kernel<<<1, 1024, 0, st>>>(G, ldg, s, out);
@@ -394,13 +364,6 @@ cudaError_t launch_col_norms(const double* V, int64_t m, int k, int64_t ld, doub
   if (k <= 0) return cudaSuccess;
   note_launch();
   col_norms_kernel<<<k, kThreads, 0, st>>>(V, m, ld, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fill_hash(double* x, int64_t n, uint64_t seed, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  note_launch();
-  fill_hash_kernel<<<grid_for(n), kThreads, 0, st>>>(x, n, seed);
   return cudaGetLastError();
 }
 

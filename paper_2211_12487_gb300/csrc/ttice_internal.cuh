@@ -119,8 +119,6 @@ cudaError_t launch_gather_obs(const T* Y, T* out, const int* sel, int nsel, int6
                               cudaStream_t st);
 template <typename T>
 cudaError_t launch_sum_squares(const T* x, int b, int64_t N, double* out, cudaStream_t st);
-template <typename T>
-cudaError_t launch_check_finite(const T* x, int64_t n, int* flag, cudaStream_t st);
 // diag sum of an FP64 s x s matrix into *out
 cudaError_t launch_trace(const double* G, int64_t ldg, int s, double* out, cudaStream_t st);
 // columns of V (m x k, ld m): flip each so that its largest-|.| entry (lowest index on ties) is > 0
@@ -150,8 +148,6 @@ cudaError_t launch_append_last_t(const TC* coef, int b, int r, double* last, int
 // out[j] = sum_i V[j*ld + i]^2 for the k columns of an m x k column-major matrix
 cudaError_t launch_col_norms(const double* V, int64_t m, int k, int64_t ld, double* out,
                              cudaStream_t st);
-// deterministic pseudo-random fill in [-1, 1)
-cudaError_t launch_fill_hash(double* x, int64_t n, uint64_t seed, cudaStream_t st);
 // res[j] = ||GQ[:,j] - theta[j] Q[:,j]|| for j < k (column-major, ld s)
 cudaError_t launch_ritz_residual(const double* GQ, const double* Q, const double* theta, int64_t s,
                                  int k, double* res, cudaStream_t st);
