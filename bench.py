@@ -33,17 +33,17 @@ WORKLOAD = "video 480x640x3 as 20x24x20x32x3, fp32 input, eps=0.1, 12 blobs, noi
 METRIC = "increment elements/s"
 
 
-# DRAM bytes (read + write) of one first-pass launch (k1_tma_kernel, 8 frames of this workload) from
+# DRAM bytes (read + write) of one first-pass launch (k1_tc_kernel, 8 frames of this workload) from
 # the ncu capture summarised in profiles/, valid for the kernel source with this SHA-1; reported as
-# the roofline's `traffic` only while csrc/k1_tma.cu is unchanged.
-K1_TRAFFIC = {"sha1": "342797728611206cc646a954d4e427099f184dbc", "bytes": 29539328 + 42240}
+# the roofline's `traffic` only while that source file is unchanged.
+K1_TRAFFIC = {"file": "k1_tc.cu", "sha1": None, "bytes": None}
 
 
 def _k1_traffic():
     import hashlib
 
     try:
-        with open(os.path.join(ROOT, "paper_2211_12487_gb300", "csrc", "k1_tma.cu"), "rb") as f:
+        with open(os.path.join(ROOT, "paper_2211_12487_gb300", "csrc", K1_TRAFFIC["file"]), "rb") as f:
             h = hashlib.sha1(f.read()).hexdigest()
     except OSError:
         return None
@@ -240,7 +240,8 @@ def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots:
                            "p50_ms": S.percentile(lat, 0.50), "p99_ms": S.percentile(lat, 0.99),
                            "throughput_elements_per_s": elements / wall,
                            "throughput_updates_per_s": len(lat) / wall})
-        return {"streams": n_streams, "slots": slots, "phases": phases}
+        return {"streams": n_streams, "slots": slots, "phases": phases,
+                "capacity_grows": eng.grow_events, "device_gb": eng.mem_used / 1e9}
     finally:
         eng.close(cancel_pending=True)
 
@@ -264,31 +265,45 @@ def run_flow(steps: int, warmup: int = 3, b: int = 16, eps: float = 0.05, seed: 
     h = T.TTICE(dims, eps, precision="fp32", input_dtype=torch.float32, max_batch=b, max_rank=1024)
     for k in range(warmup):
         h.update(Y[k * b:(k + 1) * b])
+    h.profile(True)
     st = torch.cuda.current_stream()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     torch.cuda.synchronize()
     evs[0].record(st)
-    skipped = 0
+    skip_flags = []
     for k in range(steps):
         i = warmup + k
         s_ = h.update(Y[i * b:(i + 1) * b])
-        skipped += int(s_.skipped)
+        skip_flags.append(bool(s_.skipped))
         evs[k + 1].record(st)
     torch.cuda.synchronize()
     lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
     total = evs[0].elapsed_time(evs[-1])
     ranks = h.ranks()
+    prof = h.profile_read()
     h.close()
     del Y
     torch.cuda.empty_cache()
     peaks, kind = _peaks()
     n_el = b * math.prod(dims)
     gbs = 4.0 * n_el / (total / steps / 1e3) / 1e9
+    skip_lat = [x for x, f in zip(lat, skip_flags) if f]
+    upd_lat = [x for x, f in zip(lat, skip_flags) if not f]
+    k1 = prof["k1_stage1"]
+    k1_roof = None
+    if k1["count"]:
+        k1_gbs = k1["bytes"] / k1["count"] / (k1["ms"] / k1["count"] / 1e3) / 1e9
+        k1_roof = {"bound": "hbm", "kernel": "k1_stage1", "achieved": k1_gbs, "peak": peaks["hbm_gbs"],
+                   "unit": "GB/s", "frac": k1_gbs / peaks["hbm_gbs"], "peak_kind": kind,
+                   "bytes_per_launch": k1["bytes"] / k1["count"], "avg_launch_ms": k1["ms"] / k1["count"]}
     return {"workload": "flow 128^3 x 4 (4-way 128x128x128x4), fp32 input, eps=0.05, 64 modes/field",
             "batch": b, "steps": steps, "warmup": warmup, "value": steps * n_el / (total / 1e3),
             "unit": "elements/s", "ms_per_step": total / steps,
             "latency_ms": {"p50": statistics.median(lat), "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},
-            "skipped": skipped, "final_ranks": ranks,
+            "skipped": len(skip_lat), "final_ranks": ranks,
+            "skip_path_ms": {"p50": statistics.median(skip_lat), "min": min(skip_lat)} if skip_lat else None,
+            "update_path_ms": {"p50": statistics.median(upd_lat)} if upd_lat else None,
+            "roofline_k1": k1_roof,
             "roofline_step": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": gbs / peaks["hbm_gbs"], "bytes_per_step": 4.0 * n_el,
                               "bytes": "input batch read once (the bare lower bound)", "peak_kind": kind}}
@@ -336,6 +351,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--flow-steps", type=int, default=8,
                     help="timed steps of the 128^3 x 4 simulation-shaped stream reported under `flow` (0 leaves it out)")
+    ap.add_argument("--flow-warmup", type=int, default=3,
+                    help="untimed increments of the flow stream before its timed ones")
     ap.add_argument("--serving-seconds", type=float, default=2.0,
                     help="length of the many-stream serving run reported under `serving` (0 leaves it out)")
     ap.add_argument("--profile-window", action="store_true",
@@ -445,7 +462,7 @@ def main():
     flow = None
     if args.flow_steps > 0 and rank == 0:
         try:
-            flow = run_flow(args.flow_steps)
+            flow = run_flow(args.flow_steps, warmup=args.flow_warmup)
         except Exception as e:
             flow = {"error": f"{type(e).__name__}: {e}"}
     serving = None

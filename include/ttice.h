@@ -34,7 +34,7 @@ extern "C" {
 #define TTICE_OK 0
 #define TTICE_EINVAL (-1)     /* bad argument (null pointer, size, mode) */
 #define TTICE_ENOMEM (-2)     /* device allocation failed */
-#define TTICE_ECAPACITY (-3)  /* a rank would exceed the capacity fixed at ttice_create */
+#define TTICE_ECAPACITY (-3)  /* a rank would exceed its capacity (see ttice_reserve_rank) */
 #define TTICE_ENONFINITE (-4) /* the increment holds NaN or Inf */
 #define TTICE_ETIMEOUT (-5)   /* an iterative device solve hit its iteration limit */
 #define TTICE_ECUDA (-6)      /* a CUDA runtime call failed */
@@ -145,6 +145,31 @@ int ttice_get_last_core(ttice_t h, double* host, int64_t* n_obs, int64_t* rd);
  * Used to resume from stored cores (the cores are the compressed format) and by lockstep tests. */
 int ttice_load(ttice_t h, const int64_t* ranks, const double* const* cores, const double* last,
                int64_t n_obs);
+
+/* Capacity.  The method itself bounds no rank: each update appends as many directions as the
+ * residual needs (Eq. 9, Eq. 10), so a rank can outgrow the capacity chosen at ttice_create.  An
+ * update that would do so returns TTICE_ECAPACITY and leaves the decomposition as it was;
+ * ttice_capacity_miss names the rank and the size it needed, ttice_reserve_rank raises that rank's
+ * capacity, and the update can then be repeated.  (The library's own solver limit, a Gram side
+ * above 4608, also returns TTICE_ECAPACITY, with *k = 0.) */
+
+/* Rank capacities cap_0 .. cap_d (host, d+1 entries, cap_0 = 1). */
+int ttice_capacities(ttice_t h, int64_t* caps);
+
+/* Device memory held by h in bytes (cores at capacity, work buffers, last core). */
+int ttice_device_bytes(ttice_t h, int64_t* bytes);
+
+/* After an update that returned TTICE_ECAPACITY: *k = the rank index (1 <= k <= d) whose capacity
+ * it needed to exceed and *need = the rank r_k it needed; *k = 0 otherwise (also after a successful
+ * update). */
+int ttice_capacity_miss(ttice_t h, int* k, int64_t* need);
+
+/* Raise the capacity of rank r_k (1 <= k <= d) to at least cap (clipped to cap_{k-1} n_k, the
+ * largest rank the unfolding allows).  Re-allocates the cores and work buffers that the capacity
+ * sizes on the current device and moves the decomposition into them, device to device; ranks, cores,
+ * last core and statistics are unchanged.  Synchronises the device: no work of h may be in flight.
+ * A capacity already at least cap is a no-op.  On TTICE_ENOMEM the handle is left unchanged. */
+int ttice_reserve_rank(ttice_t h, int k, int64_t cap);
 
 /* Device-time profile of ttice_update, by phase of Algorithm 2.  Times come from CUDA events
  * recorded on the update's stream around each phase; bytes and flops are the algorithmic amounts

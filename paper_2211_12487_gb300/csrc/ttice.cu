@@ -97,6 +97,9 @@ struct ttice_s {
   int* h_int = nullptr;       // pinned
   float* h_w32 = nullptr;     // pinned, s_max
   ttice_update_stats stats{};
+  int64_t dev_bytes = 0;  // device memory held by this handle
+  int miss_k = 0;         // rank index k whose capacity the last failed update needed to exceed (0: none)
+  int64_t miss_need = 0;  // ... and the rank it needed
   // phase profiling
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -165,6 +168,9 @@ int cu(cudaError_t e) { return e == cudaSuccess ? TTICE_OK : TTICE_ECUDA; }
   } while (0)
 #define TT_CU(...) TT_TRY(cu(__VA_ARGS__))
 
+// Device allocations made while a handle is being built are added to *g_alloc_sink.
+thread_local int64_t* g_alloc_sink = nullptr;
+
 template <typename T>
 int dalloc(T** p, int64_t count) {
   *p = nullptr;
@@ -174,6 +180,7 @@ int dalloc(T** p, int64_t count) {
     *p = nullptr;
     return TTICE_ENOMEM;
   }
+  if (g_alloc_sink) *g_alloc_sink += count * (int64_t)sizeof(T);
   if (cudaMemset(*p, 0, (size_t)count * sizeof(T)) != cudaSuccess) return TTICE_ECUDA;
   return TTICE_OK;
 }
@@ -247,7 +254,11 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
   if (errors) first = 0;
   const WT* Xw = first > 0 ? static_cast<const WT*>(bufs[first - 1]) : nullptr;
   const double sw = sizeof(WT), sy = sizeof(TY);
-  const bool fused_k1 = errors && h->r[1] > 0 && k1_supported<TY, WT>((int)h->n[0], (int)h->r[1]);
+  // stage 1 of the mixed path on the tensor cores (FP32 increment and cores)
+  const bool tc_k1 = sizeof(TY) == 4 && sizeof(WT) == 4 && first == 0 && h->r[1] > 0 &&
+                     k1_tc_supported(X0, h->L[0], (int)h->n[0], (int)h->r[1]);
+  const bool fused_k1 =
+      errors && h->r[1] > 0 && (tc_k1 || k1_supported<TY, WT>((int)h->n[0], (int)h->r[1]));
   if (errors) {
     TT_CU(cudaMemsetAsync(h->rho2, 0, (size_t)h->d * b * sizeof(double), st));
     TT_CU(cudaMemsetAsync(h->y2, 0, b * sizeof(double), st));
@@ -293,7 +304,11 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
     }
     const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
                                      : reinterpret_cast<const WT*>(h->Uf[i]);
-    if (i == 0 && fused_k1) {
+    if (i == 0 && tc_k1) {
+      TT_CU(launch_k1_tc(reinterpret_cast<const float*>(X0), b, L, (int)m, (int)rn,
+                         reinterpret_cast<const float*>(Ui), h->ldu[i], reinterpret_cast<float*>(W),
+                         errors ? h->y2 : nullptr, errors ? h->rho2 : nullptr, h->part, h->ibuf + 5, st));
+    } else if (i == 0 && fused_k1) {
       if constexpr (sizeof(TY) == 4) {
         if (k1_tma_supported(X0, L, (int)m, (int)rn)) {
           TT_CU((launch_k1_tma<WT>(reinterpret_cast<const float*>(X0), b, L, (int)m, (int)rn, Ui,
@@ -538,6 +553,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   const double* Vdir = nullptr;  // s x K Ritz / eigen vectors (column-major, ld s)
   const double* thet = nullptr;
   int K = 0;
+  bool rr_on_jacobi = false;  // mixed path: rank decided by Rayleigh-Ritz on the FP32 Jacobi basis
   if (sizeof(WT) == 8) {
     // FP64 eigen-solve: one CTA for small Gram matrices, the multi-CTA block Jacobi otherwise.
     if (s <= kDirectEig) {
@@ -621,6 +637,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     }
     if (!big) TT_CU(launch_to_f64<float>(h->V32, s * K, h->Q, st));
     if (!big) TT_TRY(rayleigh_ritz(h, s, K, d_eps, max_new, st));
+    rr_on_jacobi = !big;
     }
     if (!big) { Vdir = h->Q2; thet = h->theta; }
   }
@@ -630,7 +647,22 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   int rR = h->h_int[0];
   if (h->h_int[1] != 0) h->stats.eig_sweep_limit += 1;  // unconverged sweeps: energies are still measured
   if (sizeof(WT) == 8 && s > kDirectEig) h->stats.eig_sweeps += h->h_int[3];
-  if (rR < 0) return TTICE_ECAPACITY;  // Rayleigh-Ritz subspace too small for the tolerance
+  if (rR < 0 && rr_on_jacobi) {
+    // the FP32 spectrum placed the rank more than 8 below what the FP64 Ritz values need: decide on
+    // the complete FP32 eigenbasis instead, with the energies measured on R (as for a rank beyond
+    // one Rayleigh-Ritz problem)
+    ph_begin(h, PH_EIG, st, 0.0, 0.0);
+    TT_CU(launch_to_f64<float>(h->V32, s * s, h->V64, st));
+    TT_TRY((measure_energies<WT>(h, R, m, L, nsel, s, left, st)));
+    TT_CU(launch_rank_rule(h->theta, (int)s, 1, h->trace, d_eps, max_new, h->ibuf, st));
+    TT_CU(cudaMemcpyAsync(h->h_int, h->ibuf, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ph_end(h, st);
+    TT_TRY(sync_read(h, st));
+    rR = h->h_int[0];
+    Vdir = h->V64;
+    thet = h->theta;
+  }
+  if (rR < 0) return TTICE_ECAPACITY;  // no subspace holds the tolerance (not reached in practice)
   *rR_out = rR;
   if (rR == 0) return TTICE_OK;
   h->dir_src = Vdir;
@@ -714,7 +746,11 @@ int grow_last(ttice_s* h, int64_t need) {
   if (need <= h->last_cap) return TTICE_OK;
   int64_t nc = std::max<int64_t>(h->last_cap * 2, need);
   double* p = nullptr;
-  TT_TRY(dalloc<double>(&p, nc * h->cap[h->d]));
+  int64_t* sink = g_alloc_sink;  // counted below, as the net change
+  g_alloc_sink = nullptr;
+  const int arc = dalloc<double>(&p, nc * h->cap[h->d]);
+  g_alloc_sink = sink;
+  TT_TRY(arc);
   if (h->last) {
     if (cudaMemcpy(p, h->last, (size_t)h->last_cap * h->cap[h->d] * sizeof(double),
                    cudaMemcpyDeviceToDevice) != cudaSuccess) {
@@ -723,6 +759,7 @@ int grow_last(ttice_s* h, int64_t need) {
     }
     cudaFree(h->last);
   }
+  h->dev_bytes += (nc - h->last_cap) * h->cap[h->d] * (int64_t)sizeof(double);
   h->last = p;
   h->last_cap = nc;
   return TTICE_OK;
@@ -755,6 +792,8 @@ void rollback(ttice_s* h, const int64_t* r_old, cudaStream_t st) {
 
 template <typename WT, typename TY>
 int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
+  h->miss_k = 0;
+  h->miss_need = 0;
   TT_TRY(grow_last(h, h->n_obs + b));
   void** S1 = h->stage;
   TT_TRY((chain<WT, TY>(h, Y, b, S1, true, st)));
@@ -858,7 +897,12 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
         if (!small) rc = truncated_dirs<WT>(h, i, R, m, L, nsel, dec.eps_c, max_new, &rR, st);
         if (rc != TTICE_OK) break;
         if (rR > 0) {
-          if (ri + rR > h->cap[i + 1]) { rc = TTICE_ECAPACITY; break; }
+          if (ri + rR > h->cap[i + 1]) {
+            h->miss_k = i + 1;
+            h->miss_need = ri + rR;
+            rc = TTICE_ECAPACITY;
+            break;
+          }
           // append in chunks of at most kRR directions; each chunk is re-orthogonalised against the
           // core including the chunks already appended (block CGS2)
           for (int c0 = 0; c0 < rR && rc == TTICE_OK; c0 += kRR) {
@@ -894,7 +938,11 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
           ph_begin(h, PH_DPROJ, st, nsel * (sx * m * L + sizeof(WT) * (double)rn * L),
                    2.0 * nsel * (double)m * L * rn);
         }
-        if (i == 0 && sizeof(TY) == 4 && k1_tma_supported(D0i, L, (int)m, (int)rn))
+        if (i == 0 && sizeof(TY) == 4 && sizeof(WT) == 4 && k1_tc_supported(D0i, L, (int)m, (int)rn))
+          rc = cu(launch_k1_tc(reinterpret_cast<const float*>(D0i), nsel, L, (int)m, (int)rn,
+                               reinterpret_cast<const float*>(Ui), h->ldu[i], reinterpret_cast<float*>(Wn),
+                               nullptr, nullptr, nullptr, h->ibuf + 5, st));
+        else if (i == 0 && sizeof(TY) == 4 && k1_tma_supported(D0i, L, (int)m, (int)rn))
           rc = cu(launch_k1_tma<WT>(reinterpret_cast<const float*>(D0i), nsel, L, (int)m, (int)rn, Ui,
                                     h->ldu[i], Wn, nullptr, nullptr, nullptr, h->ibuf + 5, st));
         else if (i == 0) rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0i, m, L, rn, nsel, Wn, st);
@@ -972,8 +1020,14 @@ const char* ttice_strerror(int code) {
   }
 }
 
-int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics* hp,
-                 const ttice_capacity* cp, ttice_t* out) {
+}  // extern "C"
+
+namespace {
+
+// Build a handle.  caps (host, d+1 entries, caps[0] ignored) overrides the rank capacities of the
+// default rule cap_i = min(max_rank, cap_{i-1} n_{i-1}); each is still clipped to cap_{i-1} n_{i-1}.
+int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics* hp,
+                  const ttice_capacity* cp, const int64_t* caps, ttice_t* out) {
   if (!dims || !out || d < 1 || d > kMaxD || !(eps > 0.0) || !(eps < 1.0)) return TTICE_EINVAL;
   *out = nullptr;
   ttice_s* h = new (std::nothrow) ttice_s();
@@ -1000,7 +1054,12 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   }
   h->cap[0] = 1;
   h->r[0] = 1;
-  for (int i = 1; i <= d; ++i) h->cap[i] = std::min<int64_t>(h->capc.max_rank, h->cap[i - 1] * h->n[i - 1]);
+  for (int i = 1; i <= d; ++i) {
+    const int64_t want = caps ? caps[i] : h->capc.max_rank;
+    if (want < 1) { delete h; return TTICE_EINVAL; }
+    h->cap[i] = std::min<int64_t>(want, h->cap[i - 1] * h->n[i - 1]);
+  }
+  g_alloc_sink = &h->dev_bytes;
   h->wt_bytes = (h->h.precision == TTICE_FP64) ? 8 : 4;
   const int64_t B = h->capc.max_batch;
   int rc = TTICE_OK;
@@ -1051,7 +1110,9 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   int64_t maxcap = 1;
   for (int i = 1; i <= d; ++i) maxcap = std::max(maxcap, h->cap[i]);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->P, maxcap * kRR);
-  if (rc == TTICE_OK) rc = dalloc<double>(&h->part, 2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)));
+  if (rc == TTICE_OK)
+    rc = dalloc<double>(&h->part, std::max<int64_t>(2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)),
+                                                    k1_tc_part_elems((int)B, h->L[0])));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rho2, (int64_t)h->d * B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rn2, B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->y2, B);
@@ -1068,6 +1129,7 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_rho2, (size_t)h->d * B * sizeof(double)) != cudaSuccess)
     rc = TTICE_ENOMEM;
   if (rc == TTICE_OK) rc = grow_last(h, std::max<int64_t>(h->capc.obs_reserve, 1));
+  g_alloc_sink = nullptr;
   if (rc == TTICE_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TTICE_ECUDA;
   if (rc != TTICE_OK) {
     free_all(h);
@@ -1076,6 +1138,87 @@ int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics*
   }
   fill_stats(h);
   *out = h;
+  return TTICE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ttice_create(const int64_t* dims, int d, double eps, const ttice_heuristics* hp,
+                 const ttice_capacity* cp, ttice_t* out) {
+  return create_handle(dims, d, eps, hp, cp, nullptr, out);
+}
+
+int ttice_capacities(ttice_t h, int64_t* caps) {
+  if (!h || !caps) return TTICE_EINVAL;
+  for (int i = 0; i <= h->d; ++i) caps[i] = h->cap[i];
+  return TTICE_OK;
+}
+
+int ttice_device_bytes(ttice_t h, int64_t* bytes) {
+  if (!h || !bytes) return TTICE_EINVAL;
+  *bytes = h->dev_bytes;
+  return TTICE_OK;
+}
+
+int ttice_capacity_miss(ttice_t h, int* k, int64_t* need) {
+  if (!h || !k || !need) return TTICE_EINVAL;
+  *k = h->miss_k;
+  *need = h->miss_need;
+  return TTICE_OK;
+}
+
+int ttice_reserve_rank(ttice_t h, int k, int64_t cap) {
+  if (!h || k < 1 || k > h->d || cap < 1) return TTICE_EINVAL;
+  const int64_t want = std::min<int64_t>(cap, h->cap[k - 1] * h->n[k - 1]);
+  if (want <= h->cap[k]) return TTICE_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) return TTICE_ECUDA;
+  int64_t caps[kMaxD + 1];
+  for (int i = 0; i <= h->d; ++i) caps[i] = h->cap[i];
+  caps[k] = want;
+  ttice_capacity c = h->capc;
+  c.obs_reserve = std::max<int64_t>(h->last_cap, 1);
+  int64_t dims[kMaxD];
+  for (int i = 0; i < h->d; ++i) dims[i] = h->n[i];
+  ttice_t g = nullptr;
+  TT_TRY(create_handle(dims, h->d, h->eps, &h->h, &c, caps, &g));
+  // the decomposition: the leading (r_i n_i) x r_{i+1} block of every core (its row and column
+  // layout does not depend on the capacities, only the leading dimension does) and the last core
+  int rc = TTICE_OK;
+  for (int i = 0; i < h->d && rc == TTICE_OK; ++i) {
+    const int64_t rows = h->r[i] * h->n[i], cols = h->r[i + 1];
+    if (rows == 0 || cols == 0) continue;
+    if (cudaMemcpy2D(g->U[i], g->ldu[i] * sizeof(double), h->U[i], h->ldu[i] * sizeof(double),
+                     rows * sizeof(double), cols, cudaMemcpyDeviceToDevice) != cudaSuccess)
+      rc = TTICE_ECUDA;
+    if (rc == TTICE_OK && h->Uf[i] &&
+        cudaMemcpy2D(g->Uf[i], g->ldu[i] * sizeof(float), h->Uf[i], h->ldu[i] * sizeof(float),
+                     rows * sizeof(float), cols, cudaMemcpyDeviceToDevice) != cudaSuccess)
+      rc = TTICE_ECUDA;
+  }
+  const int64_t rd = h->r[h->d];
+  if (rc == TTICE_OK && h->n_obs > 0 && rd > 0 &&
+      cudaMemcpy2D(g->last, g->cap[g->d] * sizeof(double), h->last, h->cap[h->d] * sizeof(double),
+                   rd * sizeof(double), h->n_obs, cudaMemcpyDeviceToDevice) != cudaSuccess)
+    rc = TTICE_ECUDA;
+  if (rc == TTICE_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TTICE_ECUDA;
+  if (rc != TTICE_OK) {
+    cudaGetLastError();
+    free_all(g);
+    delete g;
+    return rc;
+  }
+  for (int i = 0; i <= h->d; ++i) g->r[i] = h->r[i];
+  g->n_obs = h->n_obs;
+  g->stats = h->stats;
+  g->prof_on = h->prof_on;
+  g->prof = h->prof;
+  std::swap(g->ev_pool, h->ev_pool);
+  std::swap(*h, *g);  // h now holds the new buffers, g the old ones
+  free_all(g);
+  delete g;
+  fill_stats(h);
   return TTICE_OK;
 }
 

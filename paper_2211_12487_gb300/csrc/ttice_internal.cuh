@@ -110,6 +110,16 @@ template <typename T>
 cudaError_t launch_k1_tma(const float* Y, int b, int64_t L, int n1, int r, const T* U, int64_t ldu,
                           T* W, double* y2, double* rho2, double* part, int* status, cudaStream_t st);
 
+// K1 on the tensor cores (k1_tc.cu), FP32 increments and FP32 cores: the same outputs as
+// launch_k1_tma (y2 == nullptr: projection only), with the projection as TF32 tcgen05 MMAs on a
+// three-product hi/lo split (FP32 accuracy) and the residual norm as ||y||^2 - ||w||^2.  Supported for
+// n_1 <= 128 and 1 <= r_1 <= 64.  part: k1_tc_part_elems(b, L) doubles.  status becomes nonzero if a
+// wait of the kernel expired.
+bool k1_tc_supported(const void* Y, int64_t L, int n1, int r);
+int64_t k1_tc_part_elems(int b, int64_t L);
+cudaError_t launch_k1_tc(const float* Y, int b, int64_t L, int n1, int r, const float* U, int64_t ldu,
+                         float* W, double* y2, double* rho2, double* part, int* status, cudaStream_t st);
+
 // Misc kernels.
 cudaError_t launch_fill(double* p, int64_t n, double v, cudaStream_t st);
 template <typename TI, typename TO>

@@ -7,6 +7,9 @@ stream and host worker thread, runs whichever ready streams come next, so update
 streams overlap on the device.  A new stream is admitted only when its projected core memory (the
 capacity its handle allocates) fits in the memory budget left by the admitted streams; otherwise it
 waits in the admission queue and is admitted as soon as a finished stream releases its memory.
+Ranks are not bounded by the method: when an update needs a rank above its handle's capacity, the
+capacity is raised in place (device to device) if the grown handle still fits in the budget, and the
+update is repeated.
 
 All arithmetic stays in libttice: this module only schedules calls to `ttice_update` (ctypes
 releases the GIL during the call, so slots run concurrently).
@@ -46,20 +49,36 @@ class Request:
     error: Exception | None = None
 
 
-def projected_core_bytes(spec: StreamSpec) -> int:
-    """Device bytes a handle for `spec` allocates (cores at capacity, stage buffers, last core),
-    computed from the same capacity rule the library uses (cap_i = min(max_rank, cap_{i-1} n_{i-1}))."""
+def default_caps(spec: StreamSpec) -> list[int]:
+    """Rank capacities cap_0..cap_d of a new handle: cap_i = min(max_rank, cap_{i-1} n_{i-1})."""
+    cap = [1]
+    for n in spec.dims:
+        cap.append(min(spec.max_rank, cap[-1] * n))
+    return cap
+
+
+def projected_core_bytes(spec: StreamSpec, caps: list[int] | None = None) -> int:
+    """Device bytes a handle for `spec` with rank capacities `caps` (default: the creation rule)
+    allocates, following the library's allocations: cores at capacity (FP64, plus an FP32 mirror on
+    the mixed path), stage and residual buffers, the Gram matrix and eigen-solver work for the largest
+    Gram side s (at most 4608), the column-side products R V, and the last core's initial reserve."""
     dims = list(spec.dims)
     d = len(dims)
-    cap = [1]
-    for i in range(1, d + 1):
-        cap.append(min(spec.max_rank, cap[i - 1] * dims[i - 1]))
+    cap = caps if caps is not None else default_caps(spec)
+    B = spec.max_batch
     L = [math.prod(dims[i + 1:]) for i in range(d)]
     wt = 8 if spec.precision == "fp64" else 4
-    cores = sum(cap[i] * dims[i] * cap[i + 1] * (8 + (0 if wt == 8 else 4)) for i in range(d))
-    stages = sum(2 * spec.max_batch * cap[i + 1] * L[i] * wt for i in range(d))
-    resid = spec.max_batch * max(cap[i] * dims[i] * L[i] for i in range(d)) * wt
-    return int(cores + stages + resid + spec.max_batch * math.prod(dims) * 8 + 64 * 2 ** 20)
+    ldu = [cap[i] * dims[i] for i in range(d)]
+    cores = sum(ldu[i] * cap[i + 1] * (8 + (0 if wt == 8 else 4)) for i in range(d))
+    stages = sum(2 * B * cap[i + 1] * L[i] * wt for i in range(d))
+    resid = B * max(ldu[i] * L[i] for i in range(d)) * wt
+    s = min(4608, max(min(ldu[i], L[i] * B) for i in range(d)))
+    eig = s * s * (60 if wt == 8 else 52)
+    ebuf = 8 * max(ldu[i] * min(ldu[i], L[i] * B, 4608) for i in range(d))
+    dirs = 8 * 96 * (2 * max(ldu) + max(cap) + 4 * s)
+    gather = B * math.prod(dims) * (4 if spec.input_dtype == torch.float32 else 8)
+    last = 8 * 1024 * cap[d]
+    return int(cores + stages + resid + eig + ebuf + dirs + gather + last + (4 << 20))
 
 
 class ServingEngine:
@@ -73,6 +92,8 @@ class ServingEngine:
             mem_budget = int(free * 0.8)
         self.mem_budget = mem_budget
         self.mem_used = 0
+        self.mem_of: dict[str, int] = {}
+        self.grow_events = 0  # rank capacities raised after an update needed more
         self.handles: dict[str, T.TTICE] = {}
         self.pending: dict[str, collections.deque] = collections.defaultdict(collections.deque)
         self.busy: set[str] = set()
@@ -98,10 +119,12 @@ class ServingEngine:
             self.waiting_admission.popleft()
             spec = self.specs[name]
             with torch.cuda.device(self.device):
-                self.handles[name] = T.TTICE(spec.dims, spec.eps, precision=spec.precision,
-                                             input_dtype=spec.input_dtype, max_batch=spec.max_batch,
-                                             max_rank=spec.max_rank)
-            self.mem_used += need
+                h = T.TTICE(spec.dims, spec.eps, precision=spec.precision,
+                            input_dtype=spec.input_dtype, max_batch=spec.max_batch,
+                            max_rank=spec.max_rank)
+            self.handles[name] = h
+            self.mem_of[name] = h.device_bytes()  # what the handle actually holds
+            self.mem_used += self.mem_of[name]
             if self.pending[name]:
                 self._schedule(name)
 
@@ -127,7 +150,7 @@ class ServingEngine:
             h = self.handles.pop(name, None)
             if h is not None:
                 h.close()
-                self.mem_used -= projected_core_bytes(self.specs[name])
+                self.mem_used -= self.mem_of.pop(name, 0)
             self.finished_streams.add(name)
             self._try_admit()
 
@@ -148,7 +171,7 @@ class ServingEngine:
             try:
                 with torch.cuda.device(self.device), torch.cuda.stream(cuda_stream):
                     cuda_stream.wait_stream(torch.cuda.default_stream(self.device))
-                    req.stats = h.update(req.data, stream=cuda_stream)
+                    req.stats = self._update(name, h, req.data, cuda_stream)
             except Exception as e:  # the error is reported with the request
                 req.error = e
             req.done = time.perf_counter()
@@ -157,6 +180,40 @@ class ServingEngine:
                 self.busy.discard(name)
                 self._schedule(name)
                 self.lock.notify_all()
+
+    def _update(self, name: str, h: T.TTICE, Y: torch.Tensor, cuda_stream):
+        """ttice_update; when the increment needs a rank above its capacity (TTICE_ECAPACITY with the
+        rank named), raise that capacity -- to the rank needed, at least doubling it -- if the grown
+        handle fits in the memory budget, and repeat the update (a failed update leaves the
+        decomposition as it was)."""
+        while True:
+            try:
+                return h.update(Y, stream=cuda_stream)
+            except T.TTICEError as e:
+                if e.code != T.TTICE_ECAPACITY:
+                    raise
+                k, need = h.capacity_miss()
+                if k == 0:
+                    raise
+                caps = h.capacities()
+                new_caps = list(caps)
+                new_caps[k] = max(need, 2 * caps[k])
+                grown = projected_core_bytes(self.specs[name], new_caps)
+                with self.lock:
+                    # the old and the new buffers coexist while the cores are moved
+                    if self.mem_used + grown > self.mem_budget:
+                        raise
+                    self.mem_used += grown
+                ok = False
+                try:
+                    h.reserve_rank(k, new_caps[k])
+                    ok = True
+                finally:
+                    with self.lock:
+                        now = h.device_bytes()
+                        self.mem_used += now - self.mem_of[name] - grown
+                        self.mem_of[name] = now
+                        self.grow_events += int(ok)
 
     def drain(self, timeout: float | None = None) -> bool:
         """Wait until every submitted request has completed."""

@@ -82,6 +82,10 @@ def _load():
         "ttice_get_core": (c_int, [c_void_p, c_int, c_void_p, P(c_int64), P(c_int64)]),
         "ttice_get_last_core": (c_int, [c_void_p, c_void_p, P(c_int64), P(c_int64)]),
         "ttice_load": (c_int, [c_void_p, P(c_int64), P(c_void_p), c_void_p, c_int64]),
+        "ttice_capacities": (c_int, [c_void_p, P(c_int64)]),
+        "ttice_device_bytes": (c_int, [c_void_p, P(c_int64)]),
+        "ttice_capacity_miss": (c_int, [c_void_p, P(c_int), P(c_int64)]),
+        "ttice_reserve_rank": (c_int, [c_void_p, c_int, c_int64]),
         "ttice_profile_enable": (c_int, [c_void_p, c_int]),
         "ttice_profile_read": (c_int, [c_void_p, P(ttice_profile)]),
         "ttice_kernel_launches": (c_int64, []),
@@ -209,6 +213,28 @@ def ttice_load(h: int, ranks, cores, last: np.ndarray) -> None:
            "ttice_load")
 
 
+def ttice_capacities(h: int, d: int) -> list[int]:
+    arr = (c_int64 * (d + 1))()
+    _check(_lib.ttice_capacities(h, arr), "ttice_capacities")
+    return list(arr)
+
+
+def ttice_device_bytes(h: int) -> int:
+    v = c_int64()
+    _check(_lib.ttice_device_bytes(h, ctypes.byref(v)), "ttice_device_bytes")
+    return int(v.value)
+
+
+def ttice_capacity_miss(h: int) -> tuple[int, int]:
+    k, need = c_int(), c_int64()
+    _check(_lib.ttice_capacity_miss(h, ctypes.byref(k), ctypes.byref(need)), "ttice_capacity_miss")
+    return int(k.value), int(need.value)
+
+
+def ttice_reserve_rank(h: int, k: int, cap: int) -> None:
+    _check(_lib.ttice_reserve_rank(h, int(k), int(cap)), "ttice_reserve_rank")
+
+
 def ttice_profile_enable(h: int, on: bool = True) -> None:
     _check(_lib.ttice_profile_enable(h, int(bool(on))), "ttice_profile_enable")
 
@@ -281,6 +307,19 @@ class TTICE:
 
     def load(self, ranks, cores, last) -> None:
         ttice_load(self.h, ranks, cores, last)
+
+    def capacities(self) -> list[int]:
+        return ttice_capacities(self.h, self.d)
+
+    def device_bytes(self) -> int:
+        return ttice_device_bytes(self.h)
+
+    def capacity_miss(self) -> tuple[int, int]:
+        """(k, need) after an update that failed with TTICE_ECAPACITY: rank r_k needed `need`."""
+        return ttice_capacity_miss(self.h)
+
+    def reserve_rank(self, k: int, cap: int) -> None:
+        ttice_reserve_rank(self.h, k, cap)
 
     def profile(self, on: bool = True) -> None:
         ttice_profile_enable(self.h, on)

@@ -215,6 +215,49 @@ def test_capacity_exceeded_rolls_back(T):
         assert g.core(i).size == 0
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_capacity_growth_matches_roomy_handle(T, precision, tol):
+    """A handle created with rank capacity 2, grown by ttice_reserve_rank to the rank that each
+    failed update names, ends in the state of a handle created with room to spare: the failed
+    update leaves ranks and cores as they were, the repeated one gives the same ranks, and the
+    reconstructions agree (up to the order of FP64 atomic additions)."""
+    Y = blob_video(0, 16, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=7)
+    dims = Y.shape[1:]
+    roomy = T.TTICE(dims, 0.05, precision=precision, input_dtype=torch.float32, max_batch=4)
+    g = T.TTICE(dims, 0.05, precision=precision, input_dtype=torch.float32, max_batch=4, max_rank=2,
+                obs_reserve=2)
+    bytes0 = g.device_bytes()
+    assert bytes0 > 0 and g.capacities() == [1, 2, 2, 2, 2, 2]
+    grown = 0
+    for k in range(0, 16, 4):
+        Yk = Y[k:k + 4].cuda()
+        roomy.update(Yk)
+        while True:
+            r_before = g.ranks()
+            core_before = g.core(1)
+            try:
+                g.update(Yk)
+                break
+            except T.TTICEError as e:
+                assert e.code == T.TTICE_ECAPACITY
+                assert g.ranks() == r_before
+                kk, need = g.capacity_miss()
+                caps = g.capacities()
+                assert 1 <= kk <= len(dims) and need > caps[kk]
+                g.reserve_rank(kk, need)
+                assert g.capacities()[kk] == need
+                assert g.ranks() == r_before
+                np.testing.assert_array_equal(g.core(1), core_before)
+                grown += 1
+        assert g.capacity_miss() == (0, 0)
+        assert g.ranks() == roomy.ranks(), k
+    assert grown >= 3 and g.device_bytes() > bytes0
+    g.reserve_rank(1, 1)  # below the current capacity: no-op
+    assert _relmax(g.reconstruct(0, 16).cpu().numpy(), roomy.reconstruct(0, 16).cpu().numpy()) < tol
+    g.close()
+    roomy.close()
+
+
 def test_lockstep_load(T):
     """Load the oracle's state mid-stream, apply one increment on both sides, compare."""
     Y = blob_video(0, 16, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=12)

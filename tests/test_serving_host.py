@@ -1,0 +1,81 @@
+"""Host logic of the serving loop, on CPU with a stand-in handle (no kernel runs): an update that
+needs a rank above its capacity grows that capacity within the memory budget and is repeated, and
+the memory accounting follows what the handles hold."""
+import pytest
+import torch
+
+from paper_2211_12487_gb300 import serving as S
+from paper_2211_12487_gb300 import ttice as T
+
+
+class FakeHandle:
+    """Fails with TTICE_ECAPACITY while the capacity of rank 2 is below `needs[i]`."""
+
+    def __init__(self, needs):
+        self.caps = [1, 4, 16, 16, 3]
+        self.needs = list(needs)
+        self.reserved = []
+        self.updates = 0
+
+    def device_bytes(self):
+        return 1000 * sum(self.caps)
+
+    def capacities(self):
+        return list(self.caps)
+
+    def capacity_miss(self):
+        return (2, self.needs[0]) if self.needs and self.needs[0] > self.caps[2] else (0, 0)
+
+    def reserve_rank(self, k, cap):
+        self.reserved.append((k, cap))
+        self.caps[k] = max(self.caps[k], cap)
+
+    def update(self, Y, stream=None):
+        while self.needs and self.needs[0] <= self.caps[2]:
+            self.needs.pop(0)
+        if self.needs:
+            raise T.TTICEError(T.TTICE_ECAPACITY, "ttice_update")
+        self.updates += 1
+        return "stats"
+
+
+def _engine(budget):
+    spec = S.StreamSpec("s", (8, 8, 8, 3), 0.1, 4)
+    eng = S.ServingEngine([spec], slots=0, mem_budget=budget, device="cpu")
+    return eng
+
+
+def test_growth_repeats_the_update():
+    eng = _engine(1 << 40)
+    h = FakeHandle([40, 90])
+    eng.handles["s"] = h
+    eng.mem_of["s"] = h.device_bytes()
+    eng.mem_used = h.device_bytes()
+    assert eng._update("s", h, None, None) == "stats"
+    # each growth reaches the rank needed and at least doubles the capacity
+    assert h.reserved == [(2, 40), (2, 90)]
+    assert h.updates == 1 and eng.grow_events == 2
+    assert eng.mem_used == h.device_bytes() == eng.mem_of["s"]
+
+
+def test_growth_refused_over_budget():
+    h = FakeHandle([40])
+    eng = _engine(h.device_bytes() + 10)
+    eng.handles["s"] = h
+    eng.mem_of["s"] = h.device_bytes()
+    eng.mem_used = h.device_bytes()
+    with pytest.raises(T.TTICEError) as ei:
+        eng._update("s", h, None, None)
+    assert ei.value.code == T.TTICE_ECAPACITY
+    assert h.reserved == [] and eng.mem_used == h.device_bytes() and eng.grow_events == 0
+
+
+def test_projection_grows_with_capacity():
+    spec = S.StreamSpec("v", (20, 24, 20, 32, 3), 0.05, 32)
+    caps = S.default_caps(spec)
+    assert caps == [1, 20, 480, 512, 512, 512]
+    base = S.projected_core_bytes(spec)
+    assert base == S.projected_core_bytes(spec, caps)
+    bigger = list(caps)
+    bigger[3] = 1024
+    assert S.projected_core_bytes(spec, bigger) > base
