@@ -246,12 +246,14 @@ def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots:
         eng.close(cancel_pending=True)
 
 
-def run_flow(steps: int, warmup: int = 3, b: int = 16, eps: float = 0.05, seed: int = 1002):
+def run_flow(steps: int, warmup: int = 40, b: int = 16, eps: float = 0.05, seed: int = 1002):
     """The simulation-shaped stream (128^3 grid, 4 fields: 4-way 128x128x128x4, FP32, 64 Fourier modes
     per field with |k|^(-5/3) amplitudes advected at (0.3, 0.1, 0.2) cells/snapshot), batches of b,
-    eps.  After warm-up the stream is represented and increments mostly take the skip path: one
-    read of the 537 MB batch plus the chain.  Reports throughput, latency and the update's fraction of
-    the HBM roofline (input bytes / step time against the measured copy bandwidth)."""
+    eps, timed after `warmup` increments (the early ones grow core 2 to a Gram side of 4224 and cost up
+    to a second each).  Reports throughput, latency (skip-path increments, which read the 537 MB batch
+    once and run the chain, separately from updating ones), the first pass's own roofline, and the
+    update's fraction of the HBM roofline (input bytes / step time against the measured copy
+    bandwidth)."""
     import torch
 
     from paper_2211_12487_gb300 import ttice as T
@@ -349,9 +351,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle work for cpu_baseline (0 leaves it out)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--flow-steps", type=int, default=8,
+    ap.add_argument("--flow-steps", type=int, default=16,
                     help="timed steps of the 128^3 x 4 simulation-shaped stream reported under `flow` (0 leaves it out)")
-    ap.add_argument("--flow-warmup", type=int, default=3,
+    ap.add_argument("--flow-warmup", type=int, default=40,
                     help="untimed increments of the flow stream before its timed ones")
     ap.add_argument("--serving-seconds", type=float, default=2.0,
                     help="length of the many-stream serving run reported under `serving` (0 leaves it out)")

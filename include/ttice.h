@@ -53,8 +53,11 @@ extern "C" {
  * Ritz values it reads), the re-orthogonalisation of new directions (CGS2, Cholesky-QR) and all
  * norms and thresholds are FP64. */
 #define TTICE_FP64 0 /* FP64 everywhere: the plain FP64 GPU TT-ICE */
-#define TTICE_FP32 1 /* FP32 projections and residuals (SIMT, FP32 accumulation), Gram as FP32
-                        products summed in FP64, FP32 eigen-solve candidates + FP64 Rayleigh-Ritz */
+#define TTICE_FP32 1 /* FP32 projections and residuals, Gram as FP32 products summed in FP64, FP32
+                        eigen-solve candidates + FP64 Rayleigh-Ritz.  The first pass over an FP32
+                        increment (n_1 <= 128, r_1 <= 64) runs on the tensor cores in TF32 with each
+                        operand split into a TF32 head and an FP32 tail (three products), which keeps
+                        FP32 accuracy; the other projections are FP32 SIMT. */
 #define TTICE_TF32 2 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_BF16 3 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_SPLIT_BF16 4 /* reserved (split-BF16 projections): ttice_create returns TTICE_EINVAL */

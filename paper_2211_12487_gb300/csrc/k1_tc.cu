@@ -17,7 +17,8 @@
 // rows beyond n_1 are zero.
 //
 // Roles (6 warps, one persistent CTA per SM):
-//   warp 4, one lane:  TMA loads of raw 32 x 128 FP32 chunks (row-major, no swizzle) into a ring;
+//   warp 4, one lane:  TMA loads of raw 32 x 128 FP32 chunks (row-major, no swizzle; n_1 rounded up
+//                      to 8 rows when n_1 < 32) into a ring;
 //   warps 0-3:         each thread owns one column of the tile: it reads its 32 values of a chunk,
 //                      writes x_hi and x_lo into the K-major, 128-byte-swizzled A operand (one row
 //                      per column) and sums y^2; after the last chunk it reads its row of the
@@ -87,15 +88,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase of `bar` with the given parity to complete, for at most kWaitNs; gives up early
-// once another thread has raised *abort, and raises it on expiry.
+// Wait for the phase of `bar` with the given parity to complete, for at most about kWaitNs; gives up
+// early once another thread has raised *abort, and raises it on expiry.  The clock is first read
+// after 128 unsuccessful polls, so a wait on a completed phase costs one try_wait.
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  const unsigned long long t0 = now_ns();
+  unsigned long long t0 = 0;
   for (uint32_t i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 127u) == 127u) {
       if (*abort) return false;
-      if (now_ns() - t0 > kWaitNs) {
+      const unsigned long long t = now_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > kWaitNs) {
         *abort = 1;
         return false;
       }
@@ -174,8 +179,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 template <int RP, bool NORMS>
 __global__ void __launch_bounds__(kThreads, 1)
-    k1_tc_kernel(const __grid_constant__ CUtensorMap tmap, int n1, int r, int64_t L, int b,
-                 const float* __restrict__ U, int64_t ldu, float* __restrict__ W, double* part,
+    k1_tc_kernel(const __grid_constant__ CUtensorMap tmap, int n1, int box_rows, int r, int64_t L,
+                 int b, const float* __restrict__ U, int64_t ldu, float* __restrict__ W, double* part,
                  int* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_expect_tx(&raw_full[s], kRawBytes);
+          mbar_expect_tx(&raw_full[s], (uint32_t)box_rows * kTile * 4);
           tma_load_2d(smem_u32(raw + (size_t)s * kRawBytes), &tmap, x, z * n1 + c * kChunk, &raw_full[s]);
         }
       }
@@ -471,7 +476,9 @@ cudaError_t run(const float* Y, int b, int64_t L, int n1, int r, const float* U,
   CUtensorMap map;
   const cuuint64_t gdim[2] = {(cuuint64_t)L, (cuuint64_t)b * n1};
   const cuuint64_t gstride[1] = {(cuuint64_t)L * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)kChunk};
+  // rows per copy: a whole chunk, or n_1 rounded up to 8 when one chunk covers mode 1
+  const int box_rows = n1 >= kChunk ? kChunk : (n1 + 7) / 8 * 8;
+  const cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)box_rows};
   const cuuint32_t estride[2] = {1, 1};
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Y), gdim, gstride, box, estride,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -493,7 +500,8 @@ cudaError_t run(const float* Y, int b, int64_t L, int n1, int r, const float* U,
   const int64_t ntiles = ((L + kTile - 1) / kTile) * b;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(sms, ntiles));
   note_launch();
-  k1_tc_kernel<RP, NORMS><<<(unsigned)grid, kThreads, smem, st>>>(map, n1, r, L, b, U, ldu, W, part, status);
+  k1_tc_kernel<RP, NORMS><<<(unsigned)grid, kThreads, smem, st>>>(map, n1, box_rows, r, L, b, U, ldu, W,
+                                                                   part, status);
   TT_CUDA(cudaGetLastError());
   if constexpr (NORMS) {
     note_launch();
