@@ -170,8 +170,10 @@ int ttice_capacity_miss(ttice_t h, int* k, int64_t* need);
 /* Raise the capacity of rank r_k (1 <= k <= d) to at least cap (clipped to cap_{k-1} n_k, the
  * largest rank the unfolding allows).  Re-allocates the cores and work buffers that the capacity
  * sizes on the current device and moves the decomposition into them, device to device; ranks, cores,
- * last core and statistics are unchanged.  Synchronises the device: no work of h may be in flight.
- * A capacity already at least cap is a no-op.  On TTICE_ENOMEM the handle is left unchanged. */
+ * last core and statistics are unchanged.  No work of h may be in flight (a failed ttice_update has
+ * already finished its work when it returns); work of other handles is neither waited for nor
+ * ordered against.  A capacity already at least cap is a no-op.  On TTICE_ENOMEM the handle is
+ * left unchanged. */
 int ttice_reserve_rank(ttice_t h, int k, int64_t cap);
 
 /* Device-time profile of ttice_update, by phase of Algorithm 2.  Times come from CUDA events
@@ -223,6 +225,9 @@ int ttice_reconstruct_noalloc(ttice_t h, int64_t first, int64_t count, void* out
 
 void ttice_destroy(ttice_t h);
 const char* ttice_strerror(int code);
+/* Name of the CUDA runtime error behind the last TTICE_ECUDA or TTICE_ENOMEM that a call returned
+ * to the calling thread ("cudaSuccess" if none). */
+const char* ttice_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -160,7 +160,14 @@ constexpr int kKryBlocks = 8;    // blocks: a basis of kKry = 64 vectors
 constexpr int kKry = kKryP * kKryBlocks;
 constexpr int kKrylovMin = 96;   // mixed path: Gram matrices above this size try the Krylov solver first
 
-int cu(cudaError_t e) { return e == cudaSuccess ? TTICE_OK : TTICE_ECUDA; }
+// The CUDA error behind the last TTICE_ECUDA returned to this thread (ttice_last_cuda_error).
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+int cu(cudaError_t e) {
+  if (e == cudaSuccess) return TTICE_OK;
+  g_last_cuda_error = e;
+  return TTICE_ECUDA;
+}
 #define TT_TRY(...)                      \
   do {                                   \
     int rc__ = (__VA_ARGS__);            \
@@ -171,18 +178,34 @@ int cu(cudaError_t e) { return e == cudaSuccess ? TTICE_OK : TTICE_ECUDA; }
 // Device allocations made while a handle is being built are added to *g_alloc_sink.
 thread_local int64_t* g_alloc_sink = nullptr;
 
+// A non-blocking stream private to the calling thread for the library's own set-up copies and
+// fills (zeroing new buffers, moving cores to grown buffers), synchronised on its own: building or
+// growing one handle never waits for, nor orders against, work that other threads have in flight.
+cudaStream_t setup_stream() {
+  thread_local cudaStream_t s = nullptr;
+  if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s = nullptr;
+  }
+  return s;
+}
+
 template <typename T>
 int dalloc(T** p, int64_t count) {
   *p = nullptr;
   if (count <= 0) return TTICE_OK;
-  if (cudaMalloc((void**)p, (size_t)count * sizeof(T)) != cudaSuccess) {
+  const cudaError_t me = cudaMalloc((void**)p, (size_t)count * sizeof(T));
+  if (me != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
+    g_last_cuda_error = me;
     return TTICE_ENOMEM;
   }
   if (g_alloc_sink) *g_alloc_sink += count * (int64_t)sizeof(T);
-  if (cudaMemset(*p, 0, (size_t)count * sizeof(T)) != cudaSuccess) return TTICE_ECUDA;
-  return TTICE_OK;
+  cudaStream_t fs = setup_stream();
+  if (!fs) return cu(cudaErrorNotReady);
+  TT_TRY(cu(cudaMemsetAsync(*p, 0, (size_t)count * sizeof(T), fs)));
+  return cu(cudaStreamSynchronize(fs));
 }
 int dalloc_bytes(void** p, int64_t bytes) {
   return dalloc<unsigned char>(reinterpret_cast<unsigned char**>(p), bytes);
@@ -752,10 +775,14 @@ int grow_last(ttice_s* h, int64_t need) {
   g_alloc_sink = sink;
   TT_TRY(arc);
   if (h->last) {
-    if (cudaMemcpy(p, h->last, (size_t)h->last_cap * h->cap[h->d] * sizeof(double),
-                   cudaMemcpyDeviceToDevice) != cudaSuccess) {
+    cudaStream_t fs = setup_stream();
+    int rc = fs ? cu(cudaMemcpyAsync(p, h->last, (size_t)h->last_cap * h->cap[h->d] * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, fs))
+                : cu(cudaErrorNotReady);
+    if (rc == TTICE_OK) rc = cu(cudaStreamSynchronize(fs));
+    if (rc != TTICE_OK) {
       cudaFree(p);
-      return TTICE_ECUDA;
+      return rc;
     }
     cudaFree(h->last);
   }
@@ -1020,6 +1047,8 @@ const char* ttice_strerror(int code) {
   }
 }
 
+const char* ttice_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
+
 }  // extern "C"
 
 namespace {
@@ -1130,7 +1159,6 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
     rc = TTICE_ENOMEM;
   if (rc == TTICE_OK) rc = grow_last(h, std::max<int64_t>(h->capc.obs_reserve, 1));
   g_alloc_sink = nullptr;
-  if (rc == TTICE_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TTICE_ECUDA;
   if (rc != TTICE_OK) {
     free_all(h);
     delete h;
@@ -1173,7 +1201,6 @@ int ttice_reserve_rank(ttice_t h, int k, int64_t cap) {
   if (!h || k < 1 || k > h->d || cap < 1) return TTICE_EINVAL;
   const int64_t want = std::min<int64_t>(cap, h->cap[k - 1] * h->n[k - 1]);
   if (want <= h->cap[k]) return TTICE_OK;
-  if (cudaDeviceSynchronize() != cudaSuccess) return TTICE_ECUDA;
   int64_t caps[kMaxD + 1];
   for (int i = 0; i <= h->d; ++i) caps[i] = h->cap[i];
   caps[k] = want;
@@ -1185,24 +1212,22 @@ int ttice_reserve_rank(ttice_t h, int k, int64_t cap) {
   TT_TRY(create_handle(dims, h->d, h->eps, &h->h, &c, caps, &g));
   // the decomposition: the leading (r_i n_i) x r_{i+1} block of every core (its row and column
   // layout does not depend on the capacities, only the leading dimension does) and the last core
-  int rc = TTICE_OK;
+  cudaStream_t fs = setup_stream();
+  int rc = fs ? TTICE_OK : cu(cudaErrorNotReady);
   for (int i = 0; i < h->d && rc == TTICE_OK; ++i) {
     const int64_t rows = h->r[i] * h->n[i], cols = h->r[i + 1];
     if (rows == 0 || cols == 0) continue;
-    if (cudaMemcpy2D(g->U[i], g->ldu[i] * sizeof(double), h->U[i], h->ldu[i] * sizeof(double),
-                     rows * sizeof(double), cols, cudaMemcpyDeviceToDevice) != cudaSuccess)
-      rc = TTICE_ECUDA;
-    if (rc == TTICE_OK && h->Uf[i] &&
-        cudaMemcpy2D(g->Uf[i], g->ldu[i] * sizeof(float), h->Uf[i], h->ldu[i] * sizeof(float),
-                     rows * sizeof(float), cols, cudaMemcpyDeviceToDevice) != cudaSuccess)
-      rc = TTICE_ECUDA;
+    rc = cu(cudaMemcpy2DAsync(g->U[i], g->ldu[i] * sizeof(double), h->U[i], h->ldu[i] * sizeof(double),
+                              rows * sizeof(double), cols, cudaMemcpyDeviceToDevice, fs));
+    if (rc == TTICE_OK && h->Uf[i])
+      rc = cu(cudaMemcpy2DAsync(g->Uf[i], g->ldu[i] * sizeof(float), h->Uf[i], h->ldu[i] * sizeof(float),
+                                rows * sizeof(float), cols, cudaMemcpyDeviceToDevice, fs));
   }
   const int64_t rd = h->r[h->d];
-  if (rc == TTICE_OK && h->n_obs > 0 && rd > 0 &&
-      cudaMemcpy2D(g->last, g->cap[g->d] * sizeof(double), h->last, h->cap[h->d] * sizeof(double),
-                   rd * sizeof(double), h->n_obs, cudaMemcpyDeviceToDevice) != cudaSuccess)
-    rc = TTICE_ECUDA;
-  if (rc == TTICE_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TTICE_ECUDA;
+  if (rc == TTICE_OK && h->n_obs > 0 && rd > 0)
+    rc = cu(cudaMemcpy2DAsync(g->last, g->cap[g->d] * sizeof(double), h->last, h->cap[h->d] * sizeof(double),
+                              rd * sizeof(double), h->n_obs, cudaMemcpyDeviceToDevice, fs));
+  if (rc == TTICE_OK) rc = cu(cudaStreamSynchronize(fs));
   if (rc != TTICE_OK) {
     cudaGetLastError();
     free_all(g);

@@ -17,6 +17,7 @@ releases the GIL during the call, so slots run concurrently).
 from __future__ import annotations
 
 import collections
+import contextlib
 import math
 import queue
 import threading
@@ -99,6 +100,7 @@ class ServingEngine:
         self.busy: set[str] = set()
         self.waiting_admission: collections.deque = collections.deque()
         self.finished_streams: set[str] = set()
+        self.failed_streams: dict[str, Exception] = {}  # streams whose handle could not be created
         self.lock = threading.Condition()
         self.ready: queue.Queue = queue.Queue()
         self.completed: list[Request] = []
@@ -118,10 +120,24 @@ class ServingEngine:
                 return
             self.waiting_admission.popleft()
             spec = self.specs[name]
-            with torch.cuda.device(self.device):
-                h = T.TTICE(spec.dims, spec.eps, precision=spec.precision,
-                            input_dtype=spec.input_dtype, max_batch=spec.max_batch,
-                            max_rank=spec.max_rank)
+            try:
+                # an explicit device index is made current for the creation; none: the current one
+                ctx = (torch.cuda.device(self.device.index) if self.device.index is not None
+                       else contextlib.nullcontext())
+                with ctx:
+                    h = T.TTICE(spec.dims, spec.eps, precision=spec.precision,
+                                input_dtype=spec.input_dtype, max_batch=spec.max_batch,
+                                max_rank=spec.max_rank)
+            except T.TTICEError as e:
+                # the stream cannot be served: its requests complete with the error
+                now = time.perf_counter()
+                while self.pending[name]:
+                    req = self.pending[name].popleft()
+                    req.error, req.done = e, now
+                    self.completed.append(req)
+                self.failed_streams[name] = e
+                self.lock.notify_all()
+                continue
             self.handles[name] = h
             self.mem_of[name] = h.device_bytes()  # what the handle actually holds
             self.mem_used += self.mem_of[name]
@@ -137,6 +153,10 @@ class ServingEngine:
         with self.lock:
             if not req.arrival:
                 req.arrival = time.perf_counter()
+            if req.stream in self.failed_streams:
+                req.error, req.done = self.failed_streams[req.stream], time.perf_counter()
+                self.completed.append(req)
+                return
             self.pending[req.stream].append(req)
             if req.stream not in self.handles and req.stream not in self.waiting_admission:
                 self.waiting_admission.append(req.stream)

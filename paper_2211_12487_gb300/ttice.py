@@ -60,7 +60,10 @@ class ttice_profile(ctypes.Structure):
 
 class TTICEError(RuntimeError):
     def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {ttice_strerror(code)} ({code})")
+        msg = f"{what}: {ttice_strerror(code)} ({code})"
+        if code in (TTICE_ECUDA, TTICE_ENOMEM):
+            msg += f" [{ttice_last_cuda_error()}]"
+        super().__init__(msg)
         self.code = code
 
 
@@ -92,6 +95,7 @@ def _load():
         "ttice_reconstruct_noalloc": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int, c_void_p]),
         "ttice_destroy": (None, [c_void_p]),
         "ttice_strerror": (ctypes.c_char_p, [c_int]),
+        "ttice_last_cuda_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -105,6 +109,10 @@ _lib = _load()
 
 def ttice_strerror(code: int) -> str:
     return _lib.ttice_strerror(int(code)).decode()
+
+
+def ttice_last_cuda_error() -> str:
+    return _lib.ttice_last_cuda_error().decode()
 
 
 def _check(code: int, what: str):

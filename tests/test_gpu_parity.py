@@ -13,7 +13,7 @@ import pytest
 import torch
 
 from oracle import ttice_oracle as O
-from tt_streams import blob_video, cp_cosine, random_tt
+from tt_streams import blob_video, cp_cosine, fourier_flow, random_tt
 
 pytestmark = pytest.mark.gpu
 
@@ -157,6 +157,30 @@ def test_project_matches_oracle(T):
     c_o, rho2, y2 = o.errors(Z.double().numpy())
     assert _relmax(coeffs.cpu().numpy(), c_o) < 1e-10
     np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho2 / y2), rtol=1e-9)
+
+
+@pytest.mark.parametrize("grid", [64, 128])
+def test_first_pass_tensor_cores_flow(T, grid):
+    """FP32 path whose first pass runs on the tensor cores at n_1 = 64 and 128 (four 32-row chunks,
+    r_1 = 33): new snapshots projected onto cores loaded from the oracle give the oracle's
+    coefficients to FP32 accuracy, and per-observation relative errors (stage-1 residual by
+    Pythagoras) within 2e-4 relative."""
+    b = 2
+    Y = fourier_flow(0, 2 * b, grid=grid, seed=21)
+    o = O.TTICEOracle(Y.shape[1:], 0.05)
+    o.update(Y[:b].double().numpy())
+    assert 32 < o.ranks[1] <= 64
+    g = T.TTICE(Y.shape[1:], 0.05, precision="fp32", input_dtype=torch.float32, max_batch=b)
+    last = np.zeros((len(o.last), o.ranks[-1]))
+    for j, c in enumerate(o.last):
+        last[j, :c.shape[0]] = c
+    g.load(o.ranks, o.U, last)
+    Z = Y[b:]
+    coeffs, rel = g.project(Z.cuda())
+    c_o, rho2, y2 = o.errors(Z.double().numpy())
+    assert _relmax(coeffs.cpu().numpy(), c_o) < 1e-5
+    np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho2 / y2), rtol=2e-4)
+    g.close()
 
 
 def test_subselect_golden_gpu(T):

@@ -79,3 +79,20 @@ def test_projection_grows_with_capacity():
     bigger = list(caps)
     bigger[3] = 1024
     assert S.projected_core_bytes(spec, bigger) > base
+
+
+def test_stream_that_cannot_be_created_fails_alone():
+    """Admission of a stream whose handle cannot be created (here: no GPU in the process, so the
+    first device allocation fails) completes that stream's requests with the error, names the CUDA
+    error behind it, and leaves the engine usable for the other streams."""
+    if torch.cuda.is_available():
+        pytest.skip("needs a process without a GPU")
+    spec = S.StreamSpec("s", (8, 8, 8, 3), 0.1, 4)
+    eng = S.ServingEngine([spec], slots=0, mem_budget=1 << 40, device="cuda")
+    eng.submit(S.Request("s", None))
+    eng.submit(S.Request("s", None))
+    assert len(eng.completed) == 2 and "s" in eng.failed_streams and "s" not in eng.handles
+    for r in eng.completed:
+        assert isinstance(r.error, T.TTICEError) and r.error.code in (T.TTICE_ENOMEM, T.TTICE_ECUDA)
+        assert "[cuda" in str(r.error)
+    assert eng.mem_used == 0 and not any(eng.pending.values())
