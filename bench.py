@@ -36,7 +36,7 @@ METRIC = "increment elements/s"
 # DRAM bytes (read + write) of one first-pass launch (k1_tc_kernel, 8 frames of this workload) from
 # the ncu capture summarised in profiles/, valid for the kernel source with this SHA-1; reported as
 # the roofline's `traffic` only while that source file is unchanged.
-K1_TRAFFIC = {"file": "k1_tc.cu", "sha1": None, "bytes": None}
+K1_TRAFFIC = {"file": "k1_tc.cu", "sha1": "c62fd6edf3548fdc8d64535d88aa5b0758e9e67e", "bytes": 29539840 + 91904}
 
 
 def _k1_traffic():
