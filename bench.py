@@ -246,6 +246,88 @@ def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots:
         eng.close(cancel_pending=True)
 
 
+def run_project(built: dict, precision: str, batches: int, b: int = 32, seed: int = 1001):
+    """Projection of unseen frames onto the cores the timed stream built (Algorithm 2 'project'; the
+    relative prediction error workload of Sec. 5.1): `batches` calls of ttice_project on b frames
+    each, frames 100000 onwards of the same generator, after 3 untimed calls.  The projection reads
+    each batch once and runs the chain, so it is reported against the HBM bound (input bytes read
+    once, the bare lower bound) beside the mean per-frame relative error."""
+    import torch
+
+    from paper_2211_12487_gb300 import ttice as T
+    from tt_streams import blob_video
+
+    N = math.prod(DIMS)
+    hp = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=b)
+    hp.load(built["ranks"], built["cores"], built["last"])
+    Z = torch.empty((batches * b,) + DIMS, dtype=torch.float32, device="cuda")
+    for k in range(0, batches * b, 64):
+        c = min(64, batches * b - k)
+        Z[k:k + c] = blob_video(100000 + k, c, seed=seed, device="cuda")
+    rd = built["ranks"][len(DIMS)]
+    coeffs = torch.empty((b, max(rd, 1)), dtype=torch.float64, device="cuda")
+    rel = torch.empty((batches, b), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    for k in range(3):
+        T.ttice_project(hp.h, Z[k * b:(k + 1) * b], coeffs, rel[k], st)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(batches + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(st)
+    for k in range(batches):
+        T.ttice_project(hp.h, Z[k * b:(k + 1) * b], coeffs, rel[k], st)
+        evs[k + 1].record(st)
+    torch.cuda.synchronize()
+    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(batches)]
+    total = evs[0].elapsed_time(evs[-1])
+    hp.close()
+    peaks, kind = _peaks()
+    gbs = 4.0 * b * N / (total / batches / 1e3) / 1e9
+    r = rel.cpu()
+    return {"workload": f"ttice_project of unseen frames, {b} per call, onto ranks {built['ranks']}",
+            "batch": b, "calls": batches, "value": batches * b * N / (total / 1e3), "unit": "elements/s",
+            "ms_per_call": total / batches, "p50_ms": statistics.median(lat),
+            "rel_err_mean": float(r.mean()), "rel_err_max": float(r.max()),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / peaks["hbm_gbs"], "bytes_per_call": 4.0 * b * N,
+                         "bytes": "input batch read once (the bare lower bound)", "peak_kind": kind}}
+
+
+def run_variants(Y, b: int, precision: str, steps: int):
+    """The stream run twice from empty cores: with the exact defaults (skip on the batch error of
+    Eq. 20, eps_upd of Eq. 18, tau = 1) and with the paper's heuristics (skip on mean(eps_Y), eps_upd
+    of Eq. 19, occupancy tau = 0.8).  After every increment the batch is reconstructed and its
+    relative error compared with eps: the defaults keep it within eps (Theorem 1 with the exact
+    decisions); the heuristics may exceed it, and the rate at which they do is reported with the
+    time and the core sizes they save."""
+    import torch
+
+    from paper_2211_12487_gb300 import ttice as T
+
+    out = {}
+    for name, kw in (("exact", {}), ("paper", {"skip_mode": "mean", "eps_upd": "approx", "tau": 0.8})):
+        h = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=b, **kw)
+        errs, skipped, ms = [], 0, 0.0
+        for k in range(steps):
+            Yk = Y[k * b:(k + 1) * b]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = h.update(Yk)
+            e1.record()
+            rec = h.reconstruct(k * b, b, dtype=torch.float64)
+            d = (Yk.double() - rec).reshape(-1)
+            errs.append(float(d.norm() / Yk.double().reshape(-1).norm()))
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            skipped += int(st.skipped)
+        viol = [e for e in errs if e > EPS * (1 + 1e-9)]
+        out[name] = {"increments": steps, "skipped": skipped, "update_ms_total": ms,
+                     "eps_violations": len(viol), "violation_rate": len(viol) / steps,
+                     "max_rel_err": max(errs), "mean_rel_err": sum(errs) / steps,
+                     "final_ranks": h.ranks(), "core_elems": int(h.stats().core_elems)}
+        h.close()
+    return out
+
+
 def run_flow(steps: int, warmup: int = 40, b: int = 16, eps: float = 0.05, seed: int = 1002):
     """The simulation-shaped stream (128^3 grid, 4 fields: 4-way 128x128x128x4, FP32, 64 Fourier modes
     per field with |k|^(-5/3) amplitudes advected at (0.3, 0.1, 0.2) cells/snapshot), batches of b,
@@ -353,6 +435,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--flow-steps", type=int, default=16,
                     help="timed steps of the 128^3 x 4 simulation-shaped stream reported under `flow` (0 leaves it out)")
+    ap.add_argument("--project-batches", type=int, default=16,
+                    help="timed ttice_project calls (32 unseen frames each) onto the built cores, reported "
+                         "under `project` (0 leaves it out)")
+    ap.add_argument("--variant-steps", type=int, default=44,
+                    help="increments of the stream run with the paper's heuristics (mean skip, Eq. 19, "
+                         "tau = 0.8) and with the exact defaults, reported under `paper_variants` (0 leaves it out)")
     ap.add_argument("--flow-warmup", type=int, default=40,
                     help="untimed increments of the flow stream before its timed ones")
     ap.add_argument("--serving-seconds", type=float, default=2.0,
@@ -393,6 +481,8 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    built = {}
+
     def timed_run(precision: str, steps: int, profile: bool):
         h = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=b, max_rank=512)
         for k in range(args.warmup):
@@ -421,6 +511,10 @@ def main():
         lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
         total = evs[0].elapsed_time(evs[-1])
         prof = h.profile_read() if profile else None
+        if profile:  # the cores the stream built, for the projection leg
+            rk = h.ranks()
+            built.update(ranks=rk[:len(DIMS) + 1], cores=[h.core(i) for i in range(1, len(DIMS) + 1)],
+                         last=h.last_core())
         h.close()
         return total, lat, stats, prof, launches
 
@@ -460,6 +554,19 @@ def main():
         e2e = {"value": whole_job_rate(ws, args.steps * b * N, max_over_ranks(dt, ws, dev)), "unit": "elements/s",
                "h2d_bytes_per_step": b * N * 4, "d2h_bytes_per_step": int(d2h / args.steps)}
         h.close()
+
+    project = None
+    if args.project_batches > 0 and rank == 0 and built:
+        try:
+            project = run_project(built, args.precision, args.project_batches, seed=seed)
+        except Exception as e:
+            project = {"error": f"{type(e).__name__}: {e}"}
+    variants = None
+    if args.variant_steps > 0 and rank == 0:
+        try:
+            variants = run_variants(Y, b, args.precision, min(args.variant_steps, n_inc))
+        except Exception as e:
+            variants = {"error": f"{type(e).__name__}: {e}"}
 
     flow = None
     if args.flow_steps > 0 and rank == 0:
@@ -528,6 +635,8 @@ def main():
         "phase_share": phase_share,
         "fp64_path": fp64,
         "flow": flow,
+        "project": project,
+        "paper_variants": variants,
         "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
