@@ -176,6 +176,36 @@ int ttice_capacity_miss(ttice_t h, int* k, int64_t* need);
  * left unchanged. */
 int ttice_reserve_rank(ttice_t h, int k, int64_t cap);
 
+/* Checkpoint / resume.  The cores are the compressed form of the accumulation (Sec. 5.3): a
+ * checkpoint file holds the decomposition and what is needed to continue it, nothing else.  Layout,
+ * all values little-endian, no padding:
+ *   char[8] "TTICECK1" | int32 version = 1 | int32 d | int64 n_1..n_d | float64 eps |
+ *   int32 skip_mode | int32 subselect | int32 eps_upd_mode | float64 occupancy_tau |
+ *   int32 precision | int32 input_dtype | int64 r_0..r_d | int64 n_obs |
+ *   U_1..U_d, each row-major (r_{i-1} n_i) x r_i float64 | last core, row-major n_obs x r_d float64 |
+ *   uint64 FNV-1a (64-bit) of every preceding byte.
+ * Readers reject a wrong magic or version, shapes that violate r_0 = 1 and r_i <= r_{i-1} n_i, a
+ * checksum mismatch, a short file and trailing bytes, with TTICE_EINVAL. */
+
+/* Write a checkpoint from host data (cores and last core as in ttice_load).  Host only. */
+int ttice_checkpoint_write(const char* path, int d, const int64_t* dims, double eps,
+                           const ttice_heuristics* heur, const int64_t* ranks,
+                           const double* const* cores, const double* last, int64_t n_obs);
+
+/* Read a checkpoint into host memory.  With cores == NULL only the header is read (d, dims[<=16],
+ * eps, heur, ranks[d+1], n_obs), to size the buffers; then call again with cores[i] holding
+ * (r_i n_{i+1}) x r_{i+1} doubles and last n_obs x r_d doubles.  Host only. */
+int ttice_checkpoint_read(const char* path, int* d, int64_t* dims, double* eps, ttice_heuristics* heur,
+                          int64_t* ranks, int64_t* n_obs, double* const* cores, double* last);
+
+/* Save the state of h (synchronous; no work of h may be in flight). */
+int ttice_save(ttice_t h, const char* path);
+
+/* Create a handle on the current device from a checkpoint: its mode sizes, eps and heuristics, and
+ * its decomposition; `cap` (NULL: defaults) sets the batch size and the capacities, each rank's
+ * capacity being raised to at least its saved rank.  Updates then continue the stream. */
+int ttice_open(const char* path, const ttice_capacity* cap, ttice_t* out);
+
 /* Device-time profile of ttice_update, by phase of Algorithm 2.  Times come from CUDA events
  * recorded on the update's stream around each phase; bytes and flops are the algorithmic amounts
  * (what the method must read, write and compute for the sizes involved, not what the kernels

@@ -1418,6 +1418,63 @@ int ttice_load(ttice_t h, const int64_t* ranks, const double* const* cores, cons
   return TTICE_OK;
 }
 
+int ttice_save(ttice_t h, const char* path) {
+  if (!h || !path) return TTICE_EINVAL;
+  const int d = h->d;
+  std::vector<std::vector<double>> cores(d);
+  std::vector<const double*> ptrs(d, nullptr);
+  for (int i = 1; i <= d; ++i) {
+    int64_t rows = 0, cols = 0;
+    TT_TRY(ttice_get_core(h, i, nullptr, &rows, &cols));
+    cores[i - 1].resize((size_t)(rows * cols));
+    if (rows * cols > 0) TT_TRY(ttice_get_core(h, i, cores[i - 1].data(), &rows, &cols));
+    ptrs[i - 1] = cores[i - 1].data();
+  }
+  int64_t n_obs = 0, rd = 0;
+  TT_TRY(ttice_get_last_core(h, nullptr, &n_obs, &rd));
+  std::vector<double> last((size_t)(n_obs * rd));
+  if (!last.empty()) TT_TRY(ttice_get_last_core(h, last.data(), &n_obs, &rd));
+  int64_t ranks[kMaxD + 1];
+  for (int i = 0; i <= d; ++i) ranks[i] = h->r[i];
+  return ttice_checkpoint_write(path, d, h->n, h->eps, &h->h, ranks, ptrs.data(), last.data(), n_obs);
+}
+
+int ttice_open(const char* path, const ttice_capacity* cp, ttice_t* out) {
+  if (!path || !out) return TTICE_EINVAL;
+  *out = nullptr;
+  int d = 0;
+  int64_t dims[kMaxD], ranks[kMaxD + 1], n_obs = 0;
+  double eps = 0.0;
+  ttice_heuristics heur{};
+  TT_TRY(ttice_checkpoint_read(path, &d, dims, &eps, &heur, ranks, &n_obs, nullptr, nullptr));
+  std::vector<std::vector<double>> cores(d);
+  std::vector<double*> ptrs(d);
+  std::vector<const double*> cptrs(d);
+  for (int i = 0; i < d; ++i) {
+    cores[i].resize((size_t)(ranks[i] * dims[i] * ranks[i + 1]) + 1);
+    ptrs[i] = cores[i].data();
+    cptrs[i] = cores[i].data();
+  }
+  std::vector<double> last((size_t)(n_obs * ranks[d]) + 1);
+  TT_TRY(ttice_checkpoint_read(path, &d, dims, &eps, &heur, ranks, &n_obs, ptrs.data(), last.data()));
+  ttice_capacity c;
+  ttice_default_capacity(&c);
+  if (cp) c = *cp;
+  c.obs_reserve = std::max<int64_t>(c.obs_reserve, n_obs);
+  int64_t caps[kMaxD + 1];
+  caps[0] = 1;
+  for (int i = 1; i <= d; ++i) caps[i] = std::max<int64_t>(c.max_rank, std::max<int64_t>(ranks[i], 1));
+  ttice_t h = nullptr;
+  TT_TRY(create_handle(dims, d, eps, &heur, &c, caps, &h));
+  const int rc = ttice_load(h, ranks, cptrs.data(), last.data(), n_obs);
+  if (rc != TTICE_OK) {
+    ttice_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return TTICE_OK;
+}
+
 }  // extern "C"
 
 // ================================================================== allocation-free reconstruction

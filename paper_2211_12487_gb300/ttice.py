@@ -89,6 +89,12 @@ def _load():
         "ttice_device_bytes": (c_int, [c_void_p, P(c_int64)]),
         "ttice_capacity_miss": (c_int, [c_void_p, P(c_int), P(c_int64)]),
         "ttice_reserve_rank": (c_int, [c_void_p, c_int, c_int64]),
+        "ttice_checkpoint_write": (c_int, [ctypes.c_char_p, c_int, P(c_int64), c_double, P(ttice_heuristics),
+                                           P(c_int64), P(c_void_p), c_void_p, c_int64]),
+        "ttice_checkpoint_read": (c_int, [ctypes.c_char_p, P(c_int), P(c_int64), P(c_double),
+                                          P(ttice_heuristics), P(c_int64), P(c_int64), P(c_void_p), c_void_p]),
+        "ttice_save": (c_int, [c_void_p, ctypes.c_char_p]),
+        "ttice_open": (c_int, [ctypes.c_char_p, P(ttice_capacity), P(c_void_p)]),
         "ttice_profile_enable": (c_int, [c_void_p, c_int]),
         "ttice_profile_read": (c_int, [c_void_p, P(ttice_profile)]),
         "ttice_kernel_launches": (c_int64, []),
@@ -221,6 +227,67 @@ def ttice_load(h: int, ranks, cores, last: np.ndarray) -> None:
            "ttice_load")
 
 
+def ttice_checkpoint_write(path: str, dims, eps: float, heuristics: ttice_heuristics, ranks, cores,
+                           last: np.ndarray) -> None:
+    d = len(dims)
+    dm = (c_int64 * d)(*[int(n) for n in dims])
+    rk = (c_int64 * (d + 1))(*[int(r) for r in ranks])
+    keep = [np.ascontiguousarray(c, dtype=np.float64) for c in cores]
+    ptrs = (c_void_p * d)(*[k.ctypes.data if k.size else None for k in keep])
+    lastc = np.ascontiguousarray(last, dtype=np.float64)
+    _check(_lib.ttice_checkpoint_write(os.fsencode(path), d, dm, float(eps), ctypes.byref(heuristics), rk, ptrs,
+                                       lastc.ctypes.data if lastc.size else None, int(lastc.shape[0])),
+           "ttice_checkpoint_write")
+
+
+def ttice_checkpoint_read(path: str) -> dict:
+    d = c_int()
+    dims = (c_int64 * 16)()
+    eps = c_double()
+    heur = ttice_heuristics()
+    ranks = (c_int64 * 17)()
+    n_obs = c_int64()
+    args = (os.fsencode(path), ctypes.byref(d), dims, ctypes.byref(eps), ctypes.byref(heur), ranks,
+            ctypes.byref(n_obs))
+    _check(_lib.ttice_checkpoint_read(*args, None, None), "ttice_checkpoint_read")
+    dd = d.value
+    rk = [int(ranks[i]) for i in range(dd + 1)]
+    dm = [int(dims[i]) for i in range(dd)]
+    cores = [np.zeros((rk[i] * dm[i], rk[i + 1])) for i in range(dd)]
+    last = np.zeros((n_obs.value, rk[dd]))
+    ptrs = (c_void_p * dd)(*[c.ctypes.data if c.size else None for c in cores])
+    _check(_lib.ttice_checkpoint_read(*args, ptrs, last.ctypes.data if last.size else None),
+           "ttice_checkpoint_read")
+    return {"dims": dm, "eps": eps.value, "heuristics": heur, "ranks": rk, "cores": cores, "last": last}
+
+
+def ttice_checkpoint_read_header(path: str) -> dict:
+    """dims, eps, heuristics, ranks and n_obs of a checkpoint, without its arrays."""
+    d = c_int()
+    dims = (c_int64 * 16)()
+    eps = c_double()
+    heur = ttice_heuristics()
+    ranks = (c_int64 * 17)()
+    n_obs = c_int64()
+    _check(_lib.ttice_checkpoint_read(os.fsencode(path), ctypes.byref(d), dims, ctypes.byref(eps),
+                                      ctypes.byref(heur), ranks, ctypes.byref(n_obs), None, None),
+           "ttice_checkpoint_read")
+    dd = d.value
+    return {"dims": [int(dims[i]) for i in range(dd)], "eps": eps.value, "heuristics": heur,
+            "ranks": [int(ranks[i]) for i in range(dd + 1)], "n_obs": int(n_obs.value)}
+
+
+def ttice_save(h: int, path: str) -> None:
+    _check(_lib.ttice_save(h, os.fsencode(path)), "ttice_save")
+
+
+def ttice_open(path: str, capacity: ttice_capacity | None = None) -> int:
+    out = c_void_p()
+    _check(_lib.ttice_open(os.fsencode(path), ctypes.byref(capacity) if capacity is not None else None,
+                           ctypes.byref(out)), "ttice_open")
+    return out.value
+
+
 def ttice_capacities(h: int, d: int) -> list[int]:
     arr = (c_int64 * (d + 1))()
     _check(_lib.ttice_capacities(h, arr), "ttice_capacities")
@@ -315,6 +382,23 @@ class TTICE:
 
     def load(self, ranks, cores, last) -> None:
         ttice_load(self.h, ranks, cores, last)
+
+    def save(self, path: str) -> None:
+        ttice_save(self.h, path)
+
+    @classmethod
+    def open(cls, path: str, *, max_batch: int = 32, max_rank: int = 512, obs_reserve: int = 1024) -> "TTICE":
+        """A decomposition resumed from a checkpoint written by save() (its dims, eps, heuristics
+        and state); capacities as in the constructor, each rank's at least its saved rank."""
+        hdr = ttice_checkpoint_read_header(path)
+        c = ttice_default_capacity()
+        c.max_batch, c.max_rank, c.obs_reserve = int(max_batch), int(max_rank), int(obs_reserve)
+        self = cls.__new__(cls)
+        self.dims = hdr["dims"]
+        self.d = len(self.dims)
+        self.input_dtype = torch.float32 if hdr["heuristics"].input_dtype == TTICE_F32 else torch.float64
+        self.h = ttice_open(path, c)
+        return self
 
     def capacities(self) -> list[int]:
         return ttice_capacities(self.h, self.d)

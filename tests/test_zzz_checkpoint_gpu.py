@@ -1,0 +1,45 @@
+"""Checkpoint / resume of a GPU decomposition through the C ABI: ttice_save writes the state,
+ttice_open recreates it on the device, and the resumed handle continues the stream exactly as the
+uninterrupted one does (same decisions and ranks; reconstructions equal up to the order of FP64
+atomic additions, which on the FP32 path can move FP32 roundings)."""
+import numpy as np
+import pytest
+import torch
+
+from tt_streams import blob_video
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2211_12487_gb300 import ttice
+
+    return ttice
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_save_open_resume(T, tmp_path, precision, tol):
+    Y = blob_video(0, 16, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=9).cuda()
+    g = T.TTICE(Y.shape[1:], 0.1, precision=precision, input_dtype=torch.float32, max_batch=4)
+    for k in range(0, 8, 4):
+        g.update(Y[k:k + 4])
+    path = str(tmp_path / "s.ttck")
+    g.save(path)
+    r = T.TTICE.open(path, max_batch=4)
+    assert r.ranks() == g.ranks() and r.dims == g.dims
+    np.testing.assert_array_equal(r.last_core(), g.last_core())
+    for i in range(1, len(g.dims) + 1):
+        np.testing.assert_array_equal(r.core(i), g.core(i))
+    np.testing.assert_array_equal(r.reconstruct(0, 8).cpu().numpy(), g.reconstruct(0, 8).cpu().numpy())
+    for k in range(8, 16, 4):
+        s1 = g.update(Y[k:k + 4])
+        s2 = r.update(Y[k:k + 4])
+        assert list(s1.ranks[:7]) == list(s2.ranks[:7])
+        assert (s1.skipped, s1.n_selected) == (s2.skipped, s2.n_selected)
+    a, b = g.reconstruct(0, 16).cpu().numpy(), r.reconstruct(0, 16).cpu().numpy()
+    assert np.abs(a - b).max() <= tol * np.abs(a).max()
+    g.close()
+    r.close()
