@@ -21,6 +21,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ttice_internal.cuh"
 
 using namespace ttice;
@@ -102,6 +104,7 @@ struct ttice_s {
   int64_t miss_need = 0;  // ... and the rank it needed
   // phase profiling
   bool prof_on = false;
+  bool nvtx_open = false;  // a phase's NVTX range is open on this handle
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<int, size_t>> marks;  // (phase, index of the start event; end = +1)
@@ -125,7 +128,22 @@ cudaEvent_t next_event(ttice_s* h) {
 }
 
 // Record the start of a phase and add its algorithmic bytes / flops.
+// NVTX ranges name the phases on the host thread for profilers (ncu --nvtx --nvtx-include
+// "ttice:eig/", nsys); they cost nothing measurable when no tool is attached.  At most one is open
+// per handle: a phase closes the one an error path may have left open.
+const char* const kPhaseNames[] = {"ttice:first_pass", "ttice:chain",      "ttice:residual",
+                                   "ttice:gram",       "ttice:eig",        "ttice:orth_append",
+                                   "ttice:d_project",  "ttice:final"};
+void nvtx_close(ttice_s* h) {
+  if (h->nvtx_open) {
+    nvtxRangePop();
+    h->nvtx_open = false;
+  }
+}
 void ph_begin(ttice_s* h, int ph, cudaStream_t st, double bytes, double flops) {
+  nvtx_close(h);
+  nvtxRangePushA(kPhaseNames[ph]);
+  h->nvtx_open = true;
   if (!h->prof_on) return;
   h->marks.push_back({ph, h->ev_used});
   cudaEventRecord(next_event(h), st);
@@ -134,6 +152,7 @@ void ph_begin(ttice_s* h, int ph, cudaStream_t st, double bytes, double flops) {
   h->prof.count[ph] += 1;
 }
 void ph_end(ttice_s* h, cudaStream_t st) {
+  nvtx_close(h);
   if (!h->prof_on) return;
   cudaEventRecord(next_event(h), st);
 }
@@ -819,6 +838,7 @@ void rollback(ttice_s* h, const int64_t* r_old, cudaStream_t st) {
 
 template <typename WT, typename TY>
 int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
+  nvtx_close(h);
   h->miss_k = 0;
   h->miss_need = 0;
   TT_TRY(grow_last(h, h->n_obs + b));
@@ -1005,6 +1025,7 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
 
 template <typename WT, typename TY>
 int project_impl(ttice_s* h, const TY* Y, int b, double* coeffs, double* rel, cudaStream_t st) {
+  nvtx_close(h);
   TT_TRY((chain<WT, TY>(h, Y, b, h->stage, rel != nullptr, st)));
   const int rd = (int)h->r[h->d];
   if (coeffs && rd > 0) TT_CU((launch_cast<WT, double>(static_cast<const WT*>(h->stage[h->d - 1]), coeffs, (int64_t)b * rd, st)));
