@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) k1_tma_kernel(const __grid_constant_
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
     const int s = it % kStages;
     const uint32_t parity = (uint32_t)((it / kStages) & 1);
-    // One thread waits (bounded) and the verdict is shared, so that the whole CTA takes the same
+    // One thread waits (bounded) and the outcome is shared, so that the whole CTA takes the same
     // branch; then every thread observes the completed phase (acquiring the tile's bytes).
     if (tid == 0) stage_ok = mbar_wait_bounded(&full[s], parity) ? 1 : 0;
     __syncthreads();
