@@ -162,6 +162,13 @@ int ttice_capacities(ttice_t h, int64_t* caps);
 /* Device memory held by h in bytes (cores at capacity, work buffers, last core). */
 int ttice_device_bytes(ttice_t h, int64_t* bytes);
 
+/* Device bytes that ttice_create(dims, d, *, h, cap) would allocate, with the rank capacities
+ * caps[1..d] (host, d+1 entries; NULL: the default rule cap_i = min(max_rank, cap_{i-1} n_{i-1})),
+ * computed by the creation code itself without allocating anything and without a GPU.  What
+ * admission by projected memory needs; equal to ttice_device_bytes of the created handle. */
+int ttice_projected_bytes(const int64_t* dims, int d, const ttice_heuristics* h, const ttice_capacity* cap,
+                          const int64_t* caps, int64_t* bytes);
+
 /* After an update that returned TTICE_ECAPACITY: *k = the rank index (1 <= k <= d) whose capacity
  * it needed to exceed and *need = the rank r_k it needed; *k = 0 otherwise (also after a successful
  * update). */

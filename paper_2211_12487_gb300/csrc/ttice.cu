@@ -196,6 +196,8 @@ int cu(cudaError_t e) {
 
 // Device allocations made while a handle is being built are added to *g_alloc_sink.
 thread_local int64_t* g_alloc_sink = nullptr;
+// Dry run (ttice_projected_bytes): allocations are counted but not made, the pointers stay null.
+thread_local bool g_dry_run = false;
 
 // A non-blocking stream private to the calling thread for the library's own set-up copies and
 // fills (zeroing new buffers, moving cores to grown buffers), synchronised on its own: building or
@@ -213,6 +215,10 @@ template <typename T>
 int dalloc(T** p, int64_t count) {
   *p = nullptr;
   if (count <= 0) return TTICE_OK;
+  if (g_dry_run) {
+    if (g_alloc_sink) *g_alloc_sink += count * (int64_t)sizeof(T);
+    return TTICE_OK;
+  }
   const cudaError_t me = cudaMalloc((void**)p, (size_t)count * sizeof(T));
   if (me != cudaSuccess) {
     cudaGetLastError();
@@ -1170,13 +1176,13 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
   if (rc == TTICE_OK) rc = dalloc<Decision>(&h->dec, 1);
   if (rc == TTICE_OK) rc = dalloc<int>(&h->sel, B);
   if (rc == TTICE_OK) rc = dalloc<int>(&h->ibuf, 16);
-  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_dec, sizeof(Decision)) != cudaSuccess) rc = TTICE_ENOMEM;
-  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_sel, B * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
-  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_int, 16 * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
-  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_w32, s * sizeof(float)) != cudaSuccess) rc = TTICE_ENOMEM;
-  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_dbl, 256 * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
-  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_rn2, B * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
-  if (rc == TTICE_OK && cudaMallocHost((void**)&h->h_rho2, (size_t)h->d * B * sizeof(double)) != cudaSuccess)
+  if (rc == TTICE_OK && !g_dry_run && cudaMallocHost((void**)&h->h_dec, sizeof(Decision)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && !g_dry_run && cudaMallocHost((void**)&h->h_sel, B * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && !g_dry_run && cudaMallocHost((void**)&h->h_int, 16 * sizeof(int)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && !g_dry_run && cudaMallocHost((void**)&h->h_w32, s * sizeof(float)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && !g_dry_run && cudaMallocHost((void**)&h->h_dbl, 256 * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && !g_dry_run && cudaMallocHost((void**)&h->h_rn2, B * sizeof(double)) != cudaSuccess) rc = TTICE_ENOMEM;
+  if (rc == TTICE_OK && !g_dry_run && cudaMallocHost((void**)&h->h_rho2, (size_t)h->d * B * sizeof(double)) != cudaSuccess)
     rc = TTICE_ENOMEM;
   if (rc == TTICE_OK) rc = grow_last(h, std::max<int64_t>(h->capc.obs_reserve, 1));
   g_alloc_sink = nullptr;
@@ -1208,6 +1214,20 @@ int ttice_capacities(ttice_t h, int64_t* caps) {
 int ttice_device_bytes(ttice_t h, int64_t* bytes) {
   if (!h || !bytes) return TTICE_EINVAL;
   *bytes = h->dev_bytes;
+  return TTICE_OK;
+}
+
+int ttice_projected_bytes(const int64_t* dims, int d, const ttice_heuristics* hp, const ttice_capacity* cp,
+                          const int64_t* caps, int64_t* bytes) {
+  if (!bytes) return TTICE_EINVAL;
+  *bytes = 0;
+  ttice_t h = nullptr;
+  g_dry_run = true;
+  const int rc = create_handle(dims, d, 0.5, hp, cp, caps, &h);
+  g_dry_run = false;
+  if (rc != TTICE_OK) return rc;
+  *bytes = h->dev_bytes;
+  delete h;  // a dry run holds no device or pinned memory
   return TTICE_OK;
 }
 

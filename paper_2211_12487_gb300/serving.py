@@ -60,26 +60,14 @@ def default_caps(spec: StreamSpec) -> list[int]:
 
 def projected_core_bytes(spec: StreamSpec, caps: list[int] | None = None) -> int:
     """Device bytes a handle for `spec` with rank capacities `caps` (default: the creation rule)
-    allocates, following the library's allocations: cores at capacity (FP64, plus an FP32 mirror on
-    the mixed path), stage and residual buffers, the Gram matrix and eigen-solver work for the largest
-    Gram side s (at most 4608), the column-side products R V, and the last core's initial reserve."""
-    dims = list(spec.dims)
-    d = len(dims)
-    cap = caps if caps is not None else default_caps(spec)
-    B = spec.max_batch
-    L = [math.prod(dims[i + 1:]) for i in range(d)]
-    wt = 8 if spec.precision == "fp64" else 4
-    ldu = [cap[i] * dims[i] for i in range(d)]
-    cores = sum(ldu[i] * cap[i + 1] * (8 + (0 if wt == 8 else 4)) for i in range(d))
-    stages = sum(2 * B * cap[i + 1] * L[i] * wt for i in range(d))
-    resid = B * max(ldu[i] * L[i] for i in range(d)) * wt
-    s = min(4608, max(min(ldu[i], L[i] * B) for i in range(d)))
-    eig = s * s * (60 if wt == 8 else 52)
-    ebuf = 8 * max(ldu[i] * min(ldu[i], L[i] * B, 4608) for i in range(d))
-    dirs = 8 * 96 * (2 * max(ldu) + max(cap) + 4 * s)
-    gather = B * math.prod(dims) * (4 if spec.input_dtype == torch.float32 else 8)
-    last = 8 * 1024 * cap[d]
-    return int(cores + stages + resid + eig + ebuf + dirs + gather + last + (4 << 20))
+    allocates: computed by the library's own creation code in a dry run (ttice_projected_bytes), so
+    it is what ttice_device_bytes reports once the handle exists."""
+    h = T.ttice_default_heuristics()
+    h.precision = T.PRECISIONS[spec.precision]
+    h.input_dtype = T.TTICE_F32 if spec.input_dtype == torch.float32 else T.TTICE_F64
+    c = T.ttice_default_capacity()
+    c.max_batch, c.max_rank = int(spec.max_batch), int(spec.max_rank)
+    return T.ttice_projected_bytes(spec.dims, h, c, caps)
 
 
 class ServingEngine:

@@ -88,6 +88,8 @@ def _load():
         "ttice_capacities": (c_int, [c_void_p, P(c_int64)]),
         "ttice_device_bytes": (c_int, [c_void_p, P(c_int64)]),
         "ttice_capacity_miss": (c_int, [c_void_p, P(c_int), P(c_int64)]),
+        "ttice_projected_bytes": (c_int, [P(c_int64), c_int, P(ttice_heuristics), P(ttice_capacity), P(c_int64),
+                                          P(c_int64)]),
         "ttice_reserve_rank": (c_int, [c_void_p, c_int, c_int64]),
         "ttice_checkpoint_write": (c_int, [ctypes.c_char_p, c_int, P(c_int64), c_double, P(ttice_heuristics),
                                            P(c_int64), P(c_void_p), c_void_p, c_int64]),
@@ -297,6 +299,18 @@ def ttice_capacities(h: int, d: int) -> list[int]:
 def ttice_device_bytes(h: int) -> int:
     v = c_int64()
     _check(_lib.ttice_device_bytes(h, ctypes.byref(v)), "ttice_device_bytes")
+    return int(v.value)
+
+
+def ttice_projected_bytes(dims, heuristics: ttice_heuristics | None = None,
+                          capacity: ttice_capacity | None = None, caps=None) -> int:
+    d = len(dims)
+    dm = (c_int64 * d)(*[int(n) for n in dims])
+    cp = (c_int64 * (d + 1))(*[int(c) for c in caps]) if caps is not None else None
+    v = c_int64()
+    _check(_lib.ttice_projected_bytes(dm, d, ctypes.byref(heuristics) if heuristics is not None else None,
+                                      ctypes.byref(capacity) if capacity is not None else None, cp,
+                                      ctypes.byref(v)), "ttice_projected_bytes")
     return int(v.value)
 
 

@@ -96,3 +96,27 @@ def test_stream_that_cannot_be_created_fails_alone():
         assert isinstance(r.error, T.TTICEError) and r.error.code in (T.TTICE_ENOMEM, T.TTICE_ECUDA)
         assert "[cuda" in str(r.error)
     assert eng.mem_used == 0 and not any(eng.pending.values())
+
+
+def test_projected_bytes_from_the_creation_code():
+    """ttice_projected_bytes runs the library's creation code without allocating (no GPU here): it
+    grows with the batch size and with each rank's capacity, and a capacity above what the unfolding
+    allows is clipped like in ttice_create."""
+    dims = (20, 24, 20, 32, 3)
+    c8, c32 = T.ttice_default_capacity(), T.ttice_default_capacity()
+    c8.max_batch, c32.max_batch = 8, 32
+    b8, b32 = T.ttice_projected_bytes(dims, None, c8), T.ttice_projected_bytes(dims, None, c32)
+    assert 0 < b8 < b32
+    caps = [1, 20, 480, 512, 512, 512]
+    assert T.ttice_projected_bytes(dims, None, c32, caps) == b32
+    grown = list(caps)
+    grown[3] = 1024
+    assert T.ttice_projected_bytes(dims, None, c32, grown) > b32
+    clipped = list(caps)
+    clipped[1] = 10 ** 6  # r_1 <= n_1 = 20
+    assert T.ttice_projected_bytes(dims, None, c32, clipped) == b32
+    h = T.ttice_default_heuristics()
+    h.precision = T.TTICE_FP32
+    assert T.ttice_projected_bytes(dims, h, c32) != b32  # FP32 mirrors and FP32 stage buffers
+    with pytest.raises(T.TTICEError):
+        T.ttice_projected_bytes((4, 0, 3))

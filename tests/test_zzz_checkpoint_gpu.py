@@ -1,7 +1,8 @@
-"""Checkpoint / resume of a GPU decomposition through the C ABI: ttice_save writes the state,
-ttice_open recreates it on the device, and the resumed handle continues the stream exactly as the
-uninterrupted one does (same decisions and ranks; reconstructions equal up to the order of FP64
-atomic additions, which on the FP32 path can move FP32 roundings)."""
+"""Checkpoint / resume of a GPU decomposition through the C ABI, and the memory projection of a
+handle.  ttice_save writes the state, ttice_open recreates it on the device, and the resumed handle
+continues the stream exactly as the uninterrupted one does (same decisions and ranks;
+reconstructions equal up to the order of FP64 atomic additions, which on the FP32 path can move FP32
+roundings).  ttice_projected_bytes, a dry run of the creation code, equals what a handle holds."""
 import numpy as np
 import pytest
 import torch
@@ -43,3 +44,19 @@ def test_save_open_resume(T, tmp_path, precision, tol):
     assert np.abs(a - b).max() <= tol * np.abs(a).max()
     g.close()
     r.close()
+
+
+def test_projected_bytes_equal_device_bytes(T):
+    """The dry run of the creation code counts exactly what a handle allocates, also after growth."""
+    dims = (6, 8, 8, 8, 3)
+    for precision in ("fp64", "fp32"):
+        g = T.TTICE(dims, 0.1, precision=precision, input_dtype=torch.float32, max_batch=4, max_rank=8)
+        h = T.ttice_default_heuristics()
+        h.precision = T.PRECISIONS[precision]
+        c = T.ttice_default_capacity()
+        c.max_batch, c.max_rank = 4, 8
+        assert g.device_bytes() == T.ttice_projected_bytes(dims, h, c)
+        g.reserve_rank(2, 40)
+        assert g.capacities()[2] == 40
+        assert g.device_bytes() == T.ttice_projected_bytes(dims, h, c, g.capacities())
+        g.close()
