@@ -94,6 +94,29 @@ def test_d1_is_eckart_young():
         assert np.abs(P - P_true).max() < 1e-10
 
 
+def test_d1_stream_spans_the_concatenation():
+    """d = 1 as a stream: TT-ICE is an incremental truncated SVD of the matrix whose columns are the
+    observations.  On a stream of rank-5 columns (n = 30) arriving 4 at a time, with eps far below
+    every singular value, the final U_1 spans exactly the column space of the concatenation (its
+    leading left singular vectors), r_1 = 5, no increment after the span is complete updates the
+    core, and every increment meets eps (Theorem 1 with d = 1)."""
+    rng = np.random.default_rng(7)
+    n, r, cols = 30, 5, 40
+    B, _ = np.linalg.qr(rng.normal(size=(n, r)))
+    M = B @ (rng.normal(size=(r, cols)) * np.array([[8.0], [4.0], [2.0], [1.0], [0.5]]))
+    o = O.TTICEOracle((n,), 1e-6)
+    for k in range(0, cols, 4):
+        st = o.update(M[:, k:k + 4].T, check_error=True)
+        assert st.rel_err_after <= 1e-6
+        if k >= 8:
+            assert st.skipped
+    assert o.ranks == [1, r]
+    U, _, _ = np.linalg.svd(M, full_matrices=False)
+    P_true = U[:, :r] @ U[:, :r].T
+    assert np.abs(o.U[0] @ o.U[0].T - P_true).max() < 1e-10
+    assert np.abs(o.U[0].T @ o.U[0] - np.eye(r)).max() < 1e-12
+
+
 # ---------------------------------------------------------------- independent algorithm
 def test_first_increment_equals_tt_svd():
     """From empty cores, one increment equals TT-SVD of the (d+1)-way batch (Sec. 2.1) with
@@ -187,9 +210,10 @@ def test_zero_observation():
 
 # ---------------------------------------------------------------- exact low rank (Appendix B)
 @pytest.mark.parametrize("ranks", [(1, 2, 3, 5, 1), (1, 4, 10, 30, 1)])
-@pytest.mark.parametrize("seed", [11, 12])
+@pytest.mark.parametrize("seed", list(range(11, 31)))
 def test_appendix_b_rank_recovery(ranks, seed):
-    """TT-ICE* with eps = 1e-8 recovers the TT-ranks of an exactly low-rank 10x15x20x500 stream."""
+    """TT-ICE* with eps = 1e-8 recovers the TT-ranks of an exactly low-rank 10x15x20x500 stream
+    (Appendix B: 20 seeded streams per rank set)."""
     Y = random_tt(0, 500, ranks=ranks, seed=seed).numpy()
     o = O.TTICEOracle((10, 15, 20), 1e-8)
     for k in range(500):
