@@ -266,6 +266,12 @@ const char* ttice_strerror(int code);
  * to the calling thread ("cudaSuccess" if none). */
 const char* ttice_last_cuda_error(void);
 
+/* Test hook for the out-of-memory paths (failures are injected on the host, never provoked on the
+ * device): the n-th device allocation of the library from now on (process-wide) fails with
+ * TTICE_ENOMEM as if the device were full, and ttice_last_cuda_error names
+ * cudaErrorMemoryAllocation.  n <= 0 disarms it. */
+void ttice_test_fail_alloc(int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

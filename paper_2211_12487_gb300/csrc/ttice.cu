@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -198,6 +199,8 @@ int cu(cudaError_t e) {
 thread_local int64_t* g_alloc_sink = nullptr;
 // Dry run (ttice_projected_bytes): allocations are counted but not made, the pointers stay null.
 thread_local bool g_dry_run = false;
+// Test hook (ttice_test_fail_alloc): the allocation that takes this count from 1 to 0 fails.
+std::atomic<long long> g_fail_alloc{0};
 
 // A non-blocking stream private to the calling thread for the library's own set-up copies and
 // fills (zeroing new buffers, moving cores to grown buffers), synchronised on its own: building or
@@ -218,6 +221,10 @@ int dalloc(T** p, int64_t count) {
   if (g_dry_run) {
     if (g_alloc_sink) *g_alloc_sink += count * (int64_t)sizeof(T);
     return TTICE_OK;
+  }
+  if (g_fail_alloc.load(std::memory_order_relaxed) > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+    g_last_cuda_error = cudaErrorMemoryAllocation;  // injected: as if the device were full
+    return TTICE_ENOMEM;
   }
   const cudaError_t me = cudaMalloc((void**)p, (size_t)count * sizeof(T));
   if (me != cudaSuccess) {
@@ -1075,6 +1082,8 @@ const char* ttice_strerror(int code) {
 }
 
 const char* ttice_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
+
+void ttice_test_fail_alloc(int64_t n) { g_fail_alloc.store(n > 0 ? n : 0); }
 
 }  // extern "C"
 

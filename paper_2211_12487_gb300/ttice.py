@@ -104,6 +104,7 @@ def _load():
         "ttice_destroy": (None, [c_void_p]),
         "ttice_strerror": (ctypes.c_char_p, [c_int]),
         "ttice_last_cuda_error": (ctypes.c_char_p, []),
+        "ttice_test_fail_alloc": (None, [c_int64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -121,6 +122,10 @@ def ttice_strerror(code: int) -> str:
 
 def ttice_last_cuda_error() -> str:
     return _lib.ttice_last_cuda_error().decode()
+
+
+def ttice_test_fail_alloc(n: int) -> None:
+    _lib.ttice_test_fail_alloc(int(n))
 
 
 def _check(code: int, what: str):

@@ -120,3 +120,22 @@ def test_projected_bytes_from_the_creation_code():
     assert T.ttice_projected_bytes(dims, h, c32) != b32  # FP32 mirrors and FP32 stage buffers
     with pytest.raises(T.TTICEError):
         T.ttice_projected_bytes((4, 0, 3))
+
+
+def test_injected_allocation_failure_hook():
+    """ttice_test_fail_alloc(1) makes the next device allocation fail as out of memory (named
+    cudaErrorMemoryAllocation), once; the dry run of ttice_projected_bytes allocates nothing and
+    leaves the hook armed."""
+    if torch.cuda.is_available():
+        pytest.skip("needs a process without a GPU")
+    T.ttice_test_fail_alloc(1)
+    try:
+        assert T.ttice_projected_bytes((4, 4)) > 0
+        with pytest.raises(T.TTICEError) as ei:
+            T.ttice_create([4, 4], 0.1)
+        assert ei.value.code == T.TTICE_ENOMEM and "cudaErrorMemoryAllocation" in str(ei.value)
+        with pytest.raises(T.TTICEError) as ei:
+            T.ttice_create([4, 4], 0.1)  # the hook fired once: now the machine's own failure
+        assert "cudaErrorMemoryAllocation" not in str(ei.value)
+    finally:
+        T.ttice_test_fail_alloc(0)
