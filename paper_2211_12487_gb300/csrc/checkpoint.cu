@@ -35,6 +35,7 @@ bool host_little_endian() {
 }
 
 struct Writer {
+  explicit Writer(FILE* file) : f(file) {}
   FILE* f;
   Hash hash;
   bool ok = true;
@@ -48,6 +49,7 @@ struct Writer {
 };
 
 struct Reader {
+  explicit Reader(FILE* file) : f(file) {}
   FILE* f;
   Hash hash;
   bool ok = true;
@@ -88,7 +90,7 @@ int ttice_checkpoint_write(const char* path, int d, const int64_t* dims, double 
   if (n_obs * ranks[d] > 0 && !last) return TTICE_EINVAL;
   FILE* f = fopen(path, "wb");
   if (!f) return TTICE_EINVAL;
-  Writer w{f};
+  Writer w(f);
   w.put(kMagic, sizeof(kMagic));
   w.val<int32_t>(kVersion);
   w.val<int32_t>(d);
@@ -116,7 +118,7 @@ int ttice_checkpoint_read(const char* path, int* d, int64_t* dims, double* eps, 
     return TTICE_EINVAL;
   FILE* f = fopen(path, "rb");
   if (!f) return TTICE_EINVAL;
-  Reader r{f};
+  Reader r(f);
   char magic[8];
   r.get(magic, sizeof(magic));
   const int32_t version = r.val<int32_t>();
