@@ -144,6 +144,16 @@ int ttice_checkpoint_read(const char* path, int* d, int64_t* dims, double* eps, 
     nob = r.val<int64_t>();
     if (!r.ok || !valid_shape(dd, dm, rk, nob) || !(e > 0.0 && e < 1.0)) rc = TTICE_EINVAL;
   }
+  // the file must be exactly as long as its header says, checked before anything is sized from it
+  if (rc == TTICE_OK) {
+    unsigned __int128 total = 8 + 4 + 4 + 8 * (unsigned)dd + 8 + 3 * 4 + 8 + 2 * 4 + 8 * (unsigned)(dd + 1) + 8;
+    for (int i = 0; i < dd; ++i) total += (unsigned __int128)rk[i] * dm[i] * rk[i + 1] * 8;
+    total += (unsigned __int128)nob * rk[dd] * 8 + 8;
+    const long pos = ftell(f);
+    long size = -1;
+    if (pos >= 0 && fseek(f, 0, SEEK_END) == 0) size = ftell(f);
+    if (size < 0 || fseek(f, pos, SEEK_SET) != 0 || total != (unsigned __int128)size) rc = TTICE_EINVAL;
+  }
   if (rc == TTICE_OK) {
     *d = dd;
     for (int i = 0; i < dd; ++i) dims[i] = dm[i];

@@ -1468,8 +1468,41 @@ int ttice_load(ttice_t h, const int64_t* ranks, const double* const* cores, cons
   return TTICE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+int save_impl(ttice_t h, const char* path);
+int open_impl(const char* path, const ttice_capacity* cp, ttice_t* out);
+}  // namespace
+
+extern "C" {
+
+// Checkpoints build host copies of the cores: an allocation failure there is reported, not thrown
+// across the C ABI.
 int ttice_save(ttice_t h, const char* path) {
   if (!h || !path) return TTICE_EINVAL;
+  try {
+    return save_impl(h, path);
+  } catch (const std::bad_alloc&) {
+    return TTICE_ENOMEM;
+  }
+}
+
+int ttice_open(const char* path, const ttice_capacity* cp, ttice_t* out) {
+  if (!path || !out) return TTICE_EINVAL;
+  *out = nullptr;
+  try {
+    return open_impl(path, cp, out);
+  } catch (const std::bad_alloc&) {
+    return TTICE_ENOMEM;
+  }
+}
+
+}  // extern "C"
+
+namespace {
+
+int save_impl(ttice_t h, const char* path) {
   const int d = h->d;
   std::vector<std::vector<double>> cores(d);
   std::vector<const double*> ptrs(d, nullptr);
@@ -1489,9 +1522,7 @@ int ttice_save(ttice_t h, const char* path) {
   return ttice_checkpoint_write(path, d, h->n, h->eps, &h->h, ranks, ptrs.data(), last.data(), n_obs);
 }
 
-int ttice_open(const char* path, const ttice_capacity* cp, ttice_t* out) {
-  if (!path || !out) return TTICE_EINVAL;
-  *out = nullptr;
+int open_impl(const char* path, const ttice_capacity* cp, ttice_t* out) {
   int d = 0;
   int64_t dims[kMaxD], ranks[kMaxD + 1], n_obs = 0;
   double eps = 0.0;
@@ -1525,7 +1556,7 @@ int ttice_open(const char* path, const ttice_capacity* cp, ttice_t* out) {
   return TTICE_OK;
 }
 
-}  // extern "C"
+}  // namespace
 
 // ================================================================== allocation-free reconstruction
 // ttice_reconstruct obtains its two intermediate buffers from cudaMallocAsync on every call.  Some

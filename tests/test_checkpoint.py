@@ -144,3 +144,20 @@ def test_resume_continues_the_stream(tmp_path):
         assert s1.ranks == s2.ranks and s1.skipped == s2.skipped and s1.n_selected == s2.n_selected
     n = len(o.last)
     np.testing.assert_allclose(r.reconstruct(0, n), o.reconstruct(0, n), rtol=0, atol=1e-13)
+
+
+def test_header_claiming_more_than_the_file_holds(tmp_path):
+    """A header whose sizes disagree with the file's length (here n_obs set to 2^40) is rejected when
+    the header is read, before any buffer is sized from it."""
+    _, o, last = _oracle_state()
+    path = tmp_path / "g.ttck"
+    _write(path, o, last)
+    raw = bytearray(path.read_bytes())
+    d = len(o.dims)
+    off_nobs = 8 + 4 + 4 + 8 * d + 8 + 12 + 8 + 8 + 8 * (d + 1)
+    assert struct.unpack_from("<q", raw, off_nobs)[0] == last.shape[0]
+    struct.pack_into("<q", raw, off_nobs, 1 << 40)
+    path.write_bytes(bytes(raw))
+    with pytest.raises(T.TTICEError) as ei:
+        T.ttice_checkpoint_read_header(str(path))
+    assert ei.value.code == T.TTICE_EINVAL
