@@ -128,9 +128,16 @@ int ttice_project(ttice_t h, const void* Y, int64_t batch, double* coeffs, doubl
 int ttice_ranks(ttice_t h, int64_t* ranks);
 
 /* Reconstruct stored observations first .. first+count-1 (Eq. 14): out is a device array of
- * count observations in the increment layout, element type out_dtype (TTICE_F32/F64). Asynchronous. */
+ * count observations in the increment layout, element type out_dtype (TTICE_F32/F64), at least
+ * count * n_1 ... n_d elements.  Any count works (ranges above 65535 observations run in chunks).
+ * Its two intermediate buffers come from cudaMallocAsync on `stream`.  Asynchronous. */
 int ttice_reconstruct(ttice_t h, int64_t first, int64_t count, void* out, int out_dtype,
                       void* stream);
+
+/* Shape and placement of h: *d = number of modes, dims[0..d) = n_1..n_d (room for 16), *device =
+ * the CUDA device its buffers live on (the current device at ttice_create / ttice_open).  Any
+ * argument may be NULL.  Host only. */
+int ttice_info(ttice_t h, int* d, int64_t* dims, int* device);
 
 /* Statistics of the last update. */
 int ttice_stats(ttice_t h, ttice_update_stats* st);
@@ -252,7 +259,9 @@ int64_t ttice_kernel_launches(void);
  *  - Limit: count * (n_1 ... n_d) must not exceed TTICE_NOALLOC_MAX_ELEMS (and count <= 65535);
  *    larger requests return TTICE_EINVAL without doing any work.
  *  - The first call on a device looks up the array's device address with that device current (the
- *    caller's current device); make that first call before any stream capture.
+ *    caller's current device); make that first call before any stream capture.  The address is kept
+ *    for the life of the process: after cudaDeviceReset on that device (which also ends every
+ *    handle there) the entry point must not be called again in this process.
  *  - All calls share the array.  Calls whose work overlaps on the GPU (different streams, or
  *    different handles, at the same time) race on it: serialise them.
  *  - Asynchronous on `stream`, like ttice_reconstruct. */
@@ -260,6 +269,8 @@ int64_t ttice_kernel_launches(void);
 int ttice_reconstruct_noalloc(ttice_t h, int64_t first, int64_t count, void* out, int out_dtype,
                               void* stream);
 
+/* Free h.  Synchronises the device first (cudaFree would as well), so no work of h may be left
+ * running; work of other handles is waited for too. */
 void ttice_destroy(ttice_t h);
 const char* ttice_strerror(int code);
 /* Name of the CUDA runtime error behind the last TTICE_ECUDA or TTICE_ENOMEM that a call returned

@@ -67,13 +67,17 @@ struct Reader {
 };
 
 // Shape checks shared by the writer and the reader: 1 <= d <= 16, positive mode sizes, r_0 = 1,
-// 0 <= r_i <= r_{i-1} n_i, n_obs >= 0.
+// 0 <= r_i <= r_{i-1} n_i, n_obs >= 0, and every array size (elements and bytes) representable in
+// int64 (checked products: a crafted header cannot make a size wrap around).
 bool valid_shape(int d, const int64_t* dims, const int64_t* ranks, int64_t n_obs) {
   if (d < 1 || d > ttice::kMaxD || n_obs < 0 || ranks[0] != 1) return false;
   for (int i = 0; i < d; ++i) {
-    if (dims[i] < 1 || ranks[i + 1] < 0 || ranks[i + 1] > ranks[i] * dims[i]) return false;
+    int64_t bound = 0;
+    if (dims[i] < 1 || ranks[i + 1] < 0 || __builtin_mul_overflow(ranks[i], dims[i], &bound) ||
+        ranks[i + 1] > bound)
+      return false;
   }
-  return true;
+  return ttice::checked_shape_elems(d, dims, ranks, n_obs, nullptr, nullptr, nullptr);
 }
 
 }  // namespace
@@ -85,9 +89,11 @@ int ttice_checkpoint_write(const char* path, int d, const int64_t* dims, double 
                            const double* const* cores, const double* last, int64_t n_obs) {
   if (!path || !dims || !heur || !ranks || !host_little_endian()) return TTICE_EINVAL;
   if (!valid_shape(d, dims, ranks, n_obs) || !(eps > 0.0 && eps < 1.0)) return TTICE_EINVAL;
+  int64_t ce[ttice::kMaxD] = {}, le = 0;
+  ttice::checked_shape_elems(d, dims, ranks, n_obs, ce, &le, nullptr);  // valid_shape checked it
   for (int i = 0; i < d; ++i)
-    if (ranks[i] * dims[i] * ranks[i + 1] > 0 && (!cores || !cores[i])) return TTICE_EINVAL;
-  if (n_obs * ranks[d] > 0 && !last) return TTICE_EINVAL;
+    if (ce[i] > 0 && (!cores || !cores[i])) return TTICE_EINVAL;
+  if (le > 0 && !last) return TTICE_EINVAL;
   FILE* f = fopen(path, "wb");
   if (!f) return TTICE_EINVAL;
   Writer w(f);
@@ -104,8 +110,8 @@ int ttice_checkpoint_write(const char* path, int d, const int64_t* dims, double 
   w.val<int32_t>(heur->input_dtype);
   for (int i = 0; i <= d; ++i) w.val<int64_t>(ranks[i]);
   w.val<int64_t>(n_obs);
-  for (int i = 0; i < d; ++i) w.put(cores[i], (size_t)(ranks[i] * dims[i] * ranks[i + 1]) * sizeof(double));
-  w.put(last, (size_t)(n_obs * ranks[d]) * sizeof(double));
+  for (int i = 0; i < d; ++i) w.put(cores[i], (size_t)ce[i] * sizeof(double));
+  w.put(last, (size_t)le * sizeof(double));
   const uint64_t sum = w.hash.h;
   if (w.ok) w.ok = fwrite(&sum, 1, sizeof(sum), f) == sizeof(sum);
   const bool closed = fclose(f) == 0;
@@ -145,14 +151,17 @@ int ttice_checkpoint_read(const char* path, int* d, int64_t* dims, double* eps, 
     if (!r.ok || !valid_shape(dd, dm, rk, nob) || !(e > 0.0 && e < 1.0)) rc = TTICE_EINVAL;
   }
   // the file must be exactly as long as its header says, checked before anything is sized from it
+  // (valid_shape has checked that the element counts and their byte count fit in int64)
+  int64_t ce[ttice::kMaxD] = {}, le = 0;
   if (rc == TTICE_OK) {
-    unsigned __int128 total = 8 + 4 + 4 + 8 * (unsigned)dd + 8 + 3 * 4 + 8 + 2 * 4 + 8 * (unsigned)(dd + 1) + 8;
-    for (int i = 0; i < dd; ++i) total += (unsigned __int128)rk[i] * dm[i] * rk[i + 1] * 8;
-    total += (unsigned __int128)nob * rk[dd] * 8 + 8;
+    int64_t elems = 0;
+    ttice::checked_shape_elems(dd, dm, rk, nob, ce, &le, &elems);
+    const int64_t header = 8 + 4 + 4 + 8 * (int64_t)dd + 8 + 3 * 4 + 8 + 2 * 4 + 8 * (int64_t)(dd + 1) + 8;
+    const int64_t total = header + 8 * elems + 8;  // < INT64_MAX: elems <= INT64_MAX / 8 - 1 by then
     const long pos = ftell(f);
     long size = -1;
     if (pos >= 0 && fseek(f, 0, SEEK_END) == 0) size = ftell(f);
-    if (size < 0 || fseek(f, pos, SEEK_SET) != 0 || total != (unsigned __int128)size) rc = TTICE_EINVAL;
+    if (size < 0 || fseek(f, pos, SEEK_SET) != 0 || total != (int64_t)size) rc = TTICE_EINVAL;
   }
   if (rc == TTICE_OK) {
     *d = dd;
@@ -168,11 +177,11 @@ int ttice_checkpoint_read(const char* path, int* d, int64_t* dims, double* eps, 
     return rc;
   }
   for (int i = 0; i < dd && rc == TTICE_OK; ++i) {
-    const size_t n = (size_t)(rk[i] * dm[i] * rk[i + 1]);
+    const size_t n = (size_t)ce[i];
     if (n > 0 && !cores[i]) rc = TTICE_EINVAL;
     else r.get(cores[i], n * sizeof(double));
   }
-  const size_t nl = (size_t)(nob * rk[dd]);
+  const size_t nl = (size_t)le;
   if (rc == TTICE_OK) {
     if (nl > 0 && !last) rc = TTICE_EINVAL;
     else r.get(last, nl * sizeof(double));

@@ -30,6 +30,7 @@ using namespace ttice;
 
 struct ttice_s {
   int d = 0;
+  int device = 0;  // CUDA device the handle's buffers live on (current at creation)
   int64_t n[kMaxD] = {};
   int64_t L[kMaxD] = {};  // L[i] = n[i+1] * ... * n[d-1]
   int64_t N = 0;
@@ -179,6 +180,7 @@ constexpr int kKryP = 8;         // block size of the Krylov eigen-solver
 constexpr int kKryBlocks = 8;    // blocks: a basis of kKry = 64 vectors
 constexpr int kKry = kKryP * kKryBlocks;
 constexpr int kKrylovMin = 96;   // mixed path: Gram matrices above this size try the Krylov solver first
+constexpr int64_t kMaxGridZ = 65535;  // batch (grid z) limit of one contraction launch
 
 // The CUDA error behind the last TTICE_ECUDA returned to this thread (ttice_last_cuda_error).
 thread_local cudaError_t g_last_cuda_error = cudaSuccess;
@@ -1107,6 +1109,8 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
   h->d = d;
   h->eps = eps;
   h->N = 1;
+  // the current device (without one, the first allocation below fails and reports why)
+  if (!g_dry_run && cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); h->device = 0; }
   for (int i = 0; i < d; ++i) {
     if (dims[i] < 1) { delete h; return TTICE_EINVAL; }
     h->n[i] = dims[i];
@@ -1350,47 +1354,62 @@ int ttice_reconstruct(ttice_t h, int64_t first, int64_t count, void* out, int ou
   cudaStream_t st = S(stream);
   const int d = h->d;
   const int64_t rd = h->r[d];
-  if (rd == 0) {
-    return cu(cudaMemsetAsync(out, 0, (size_t)count * h->N * (out_dtype == TTICE_F32 ? 4 : 8), st));
-  }
+  const size_t esize = out_dtype == TTICE_F32 ? 4 : 8;
+  if (rd == 0) return cu(cudaMemsetAsync(out, 0, (size_t)count * h->N * esize, st));
+  // observations are a grid dimension of the contractions (at most 65535 per launch): long ranges
+  // are reconstructed in chunks through the same two intermediate buffers
+  const int64_t chunk = std::min<int64_t>(count, kMaxGridZ);
   double *bufA = nullptr, *bufB = nullptr;
   if (d > 1) {
-    if (cudaMallocAsync((void**)&bufA, (size_t)count * h->N * sizeof(double), st) != cudaSuccess) return TTICE_ENOMEM;
-    if (cudaMallocAsync((void**)&bufB, (size_t)count * h->N * sizeof(double), st) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&bufA, (size_t)chunk * h->N * sizeof(double), st) != cudaSuccess) return TTICE_ENOMEM;
+    if (cudaMallocAsync((void**)&bufB, (size_t)chunk * h->N * sizeof(double), st) != cudaSuccess) {
       cudaFreeAsync(bufA, st);
       return TTICE_ENOMEM;
     }
   }
-  // X (per observation r_{i+1} x rest) -> U_i X (per observation (r_i n_i) x rest)
-  const double* X = h->last + first * h->cap[d];
-  int64_t x_bs = h->cap[d];  // observation stride of X
-  int64_t rest = 1;
-  int rc = TTICE_OK;
   double* bufs[2] = {bufA, bufB};
-  for (int i = d - 1; i >= 0 && rc == TTICE_OK; --i) {
-    const int64_t m = h->r[i] * h->n[i], rn = h->r[i + 1];
-    GemmArgs g;
-    g.M = m; g.N = rest; g.K = rn;
-    g.A.p = h->U[i]; g.A.rs = 1; g.A.cs = h->ldu[i];
-    g.B.p = X; g.B.rs = rest; g.B.cs = 1; g.B.bs1 = x_bs;
-    g.nbatch = (int)count;
-    g.c_rs = rest; g.c_cs = 1; g.c_bs1 = m * rest;
-    if (i == 0) {
-      g.C = out;
-      if (out_dtype == TTICE_F64) rc = cu(gemm<double, double, double, double, double>(g, st));
-      else rc = cu(gemm<double, double, double, float, double>(g, st));
-    } else {
-      double* dst = bufs[i & 1];
-      g.C = dst;
-      rc = cu(gemm<double, double, double, double, double>(g, st));
-      X = dst;
-      x_bs = m * rest;
+  int rc = TTICE_OK;
+  for (int64_t c0 = 0; c0 < count && rc == TTICE_OK; c0 += chunk) {
+    const int64_t cnt = std::min(chunk, count - c0);
+    void* outc = static_cast<char*>(out) + (size_t)c0 * h->N * esize;
+    // X (per observation r_{i+1} x rest) -> U_i X (per observation (r_i n_i) x rest)
+    const double* X = h->last + (first + c0) * h->cap[d];
+    int64_t x_bs = h->cap[d];  // observation stride of X
+    int64_t rest = 1;
+    for (int i = d - 1; i >= 0 && rc == TTICE_OK; --i) {
+      const int64_t m = h->r[i] * h->n[i], rn = h->r[i + 1];
+      GemmArgs g;
+      g.M = m; g.N = rest; g.K = rn;
+      g.A.p = h->U[i]; g.A.rs = 1; g.A.cs = h->ldu[i];
+      g.B.p = X; g.B.rs = rest; g.B.cs = 1; g.B.bs1 = x_bs;
+      g.nbatch = (int)cnt;
+      g.c_rs = rest; g.c_cs = 1; g.c_bs1 = m * rest;
+      if (i == 0) {
+        g.C = outc;
+        if (out_dtype == TTICE_F64) rc = cu(gemm<double, double, double, double, double>(g, st));
+        else rc = cu(gemm<double, double, double, float, double>(g, st));
+      } else {
+        double* dst = bufs[i & 1];
+        g.C = dst;
+        rc = cu(gemm<double, double, double, double, double>(g, st));
+        X = dst;
+        x_bs = m * rest;
+      }
+      rest *= h->n[i];
     }
-    rest *= h->n[i];
   }
   if (bufA) cudaFreeAsync(bufA, st);
   if (bufB) cudaFreeAsync(bufB, st);
   return rc;
+}
+
+int ttice_info(ttice_t h, int* d, int64_t* dims, int* device) {
+  if (!h) return TTICE_EINVAL;
+  if (d) *d = h->d;
+  if (dims)
+    for (int i = 0; i < h->d; ++i) dims[i] = h->n[i];
+  if (device) *device = h->device;
+  return TTICE_OK;
 }
 
 int ttice_get_core(ttice_t h, int i, double* host, int64_t* rows, int64_t* cols) {
@@ -1441,6 +1460,8 @@ int64_t ttice_kernel_launches(void) { return g_kernel_launches.load(); }
 int ttice_load(ttice_t h, const int64_t* ranks, const double* const* cores, const double* last,
                int64_t n_obs) {
   if (!h || !ranks || ranks[0] != 1 || n_obs < 0 || (n_obs > 0 && !last)) return TTICE_EINVAL;
+  int64_t last_elems = 0;  // the last core at capacity width must be addressable
+  if (__builtin_mul_overflow(n_obs, h->cap[h->d], &last_elems) || last_elems > INT64_MAX / 8) return TTICE_EINVAL;
   for (int i = 1; i <= h->d; ++i) {
     if (ranks[i] < 0 || ranks[i] > h->cap[i] || ranks[i] > ranks[i - 1] * h->n[i - 1]) return TTICE_ECAPACITY;
     if (ranks[i] > 0 && !cores[i - 1]) return TTICE_EINVAL;

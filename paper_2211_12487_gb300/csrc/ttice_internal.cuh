@@ -13,6 +13,31 @@ namespace ttice {
 
 constexpr int kMaxD = 16;
 
+// Element counts of a decomposition's arrays: core i holds r_i n_{i+1} r_{i+1} elements (0-based,
+// i = 0..d-1) and the last core n_obs r_d.  Every product and the running total are checked for
+// int64 overflow, and the total must stay below INT64_MAX / 8 so that its byte count fits too.
+// Returns false on overflow or a negative size; core_elems (d entries), last_elems and total may be
+// null.
+inline bool checked_shape_elems(int d, const int64_t* dims, const int64_t* ranks, int64_t n_obs,
+                                int64_t* core_elems, int64_t* last_elems, int64_t* total) {
+  int64_t t = 0;
+  for (int i = 0; i < d; ++i) {
+    int64_t a = 0, e = 0;
+    if (dims[i] < 0 || ranks[i] < 0 || ranks[i + 1] < 0) return false;
+    if (__builtin_mul_overflow(ranks[i], dims[i], &a) || __builtin_mul_overflow(a, ranks[i + 1], &e) ||
+        __builtin_add_overflow(t, e, &t))
+      return false;
+    if (core_elems) core_elems[i] = e;
+  }
+  int64_t l = 0;
+  if (n_obs < 0 || __builtin_mul_overflow(n_obs, ranks[d], &l) || __builtin_add_overflow(t, l, &t))
+    return false;
+  if (t > INT64_MAX / 8) return false;
+  if (last_elems) *last_elems = l;
+  if (total) *total = t;
+  return true;
+}
+
 // Count of kernel launches issued by this library (process-wide), for launch accounting.
 extern std::atomic<long long> g_kernel_launches;
 inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }

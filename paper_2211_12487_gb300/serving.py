@@ -141,9 +141,12 @@ class ServingEngine:
         with self.lock:
             if not req.arrival:
                 req.arrival = time.perf_counter()
-            if req.stream in self.failed_streams:
-                req.error, req.done = self.failed_streams[req.stream], time.perf_counter()
+            if req.stream in self.failed_streams or req.stream in self.finished_streams:
+                # a stream that could not be created, or that its client released, takes no new work
+                why = self.failed_streams.get(req.stream) or RuntimeError(f"stream {req.stream} was released")
+                req.error, req.done = why, time.perf_counter()
                 self.completed.append(req)
+                self.lock.notify_all()
                 return
             self.pending[req.stream].append(req)
             if req.stream not in self.handles and req.stream not in self.waiting_admission:
@@ -153,18 +156,32 @@ class ServingEngine:
                 self._schedule(req.stream)
 
     def release(self, name: str):
-        """The client closed stream `name`: free its cores and admit waiting streams."""
+        """The client closed stream `name`: its queued requests complete with an error, an update
+        of it that a slot is running is waited for (its handle is never freed under it), then its
+        cores are freed and waiting streams admitted.  Later submits to `name` are refused."""
         with self.lock:
+            self.finished_streams.add(name)
+            now = time.perf_counter()
+            gone = RuntimeError(f"stream {name} was released")
+            while self.pending[name]:
+                req = self.pending[name].popleft()
+                req.error, req.done = gone, now
+                self.completed.append(req)
+            with contextlib.suppress(ValueError):
+                self.waiting_admission.remove(name)
+            while name in self.busy:  # a slot holds the handle: wait for its update to end
+                self.lock.wait(timeout=0.05)
             h = self.handles.pop(name, None)
             if h is not None:
                 h.close()
                 self.mem_used -= self.mem_of.pop(name, 0)
-            self.finished_streams.add(name)
             self._try_admit()
+            self.lock.notify_all()
 
     # -------------------------------------------------------------- slots
     def _worker(self, slot: int):
-        cuda_stream = torch.cuda.Stream(device=self.device)
+        on_gpu = self.device.type == "cuda"
+        cuda_stream = torch.cuda.Stream(device=self.device) if on_gpu else None
         while True:
             name = self.ready.get()
             if name is None:
@@ -177,9 +194,12 @@ class ServingEngine:
                 req = self.pending[name].popleft()
                 h = self.handles[name]
             try:
-                with torch.cuda.device(self.device), torch.cuda.stream(cuda_stream):
-                    cuda_stream.wait_stream(torch.cuda.default_stream(self.device))
-                    req.stats = self._update(name, h, req.data, cuda_stream)
+                if on_gpu:
+                    with torch.cuda.device(self.device), torch.cuda.stream(cuda_stream):
+                        cuda_stream.wait_stream(torch.cuda.default_stream(self.device))
+                        req.stats = self._update(name, h, req.data, cuda_stream)
+                else:  # host-only engine (stand-in handles): no CUDA stream
+                    req.stats = self._update(name, h, req.data, None)
             except Exception as e:  # the error is reported with the request
                 req.error = e
             req.done = time.perf_counter()
@@ -236,7 +256,9 @@ class ServingEngine:
 
     def close(self, cancel_pending: bool = False):
         """Stop the slots.  With cancel_pending, requests not yet started are dropped (the slots
-        finish only the updates already running) instead of being run first."""
+        finish only the updates already running) instead of being run first.  A handle whose slot
+        is still inside an update when the wait for the slots ends is not freed under it (it is left
+        to the process exit)."""
         if cancel_pending:
             with self.lock:
                 for dq in self.pending.values():
@@ -245,8 +267,12 @@ class ServingEngine:
             self.ready.put(None)
         for w in self.workers:
             w.join(timeout=30)
-        for name in list(self.handles):
-            self.handles.pop(name).close()
+        with self.lock:
+            for name in list(self.handles):
+                if name in self.busy:
+                    continue
+                self.handles.pop(name).close()
+                self.mem_used -= self.mem_of.pop(name, 0)
 
     # -------------------------------------------------------------- reporting
     def latencies_ms(self):

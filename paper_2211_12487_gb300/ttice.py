@@ -82,6 +82,7 @@ def _load():
         "ttice_ranks": (c_int, [c_void_p, P(c_int64)]),
         "ttice_reconstruct": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int, c_void_p]),
         "ttice_stats": (c_int, [c_void_p, P(ttice_update_stats)]),
+        "ttice_info": (c_int, [c_void_p, P(c_int), P(c_int64), P(c_int)]),
         "ttice_get_core": (c_int, [c_void_p, c_int, c_void_p, P(c_int64), P(c_int64)]),
         "ttice_get_last_core": (c_int, [c_void_p, c_void_p, P(c_int64), P(c_int64)]),
         "ttice_load": (c_int, [c_void_p, P(c_int64), P(c_void_p), c_void_p, c_int64]),
@@ -183,9 +184,33 @@ def ttice_ranks(h: int, d: int) -> list[int]:
     return list(arr)
 
 
+def ttice_info(h: int) -> tuple[list[int], int]:
+    """(dims, device index) of handle h."""
+    d = c_int()
+    dims = (c_int64 * 16)()
+    dev = c_int()
+    _check(_lib.ttice_info(h, ctypes.byref(d), dims, ctypes.byref(dev)), "ttice_info")
+    return [int(dims[i]) for i in range(d.value)], int(dev.value)
+
+
+def _check_out(h: int, count: int, out: torch.Tensor, what: str) -> int:
+    """The output of a reconstruction must be a contiguous FP32/FP64 tensor on the handle's device
+    holding exactly count observations (the library writes count * n_1 ... n_d elements)."""
+    if not (out.is_cuda and out.is_contiguous() and out.dtype in (torch.float32, torch.float64)):
+        raise ValueError(f"{what}: out must be a contiguous float32/float64 CUDA tensor")
+    dims, dev = ttice_info(h)
+    n = 1
+    for x in dims:
+        n *= x
+    if out.numel() != int(count) * n:
+        raise ValueError(f"{what}: out holds {out.numel()} elements, {int(count)} observations need {int(count) * n}")
+    if out.device.index != dev:
+        raise ValueError(f"{what}: out is on cuda:{out.device.index}, the handle on cuda:{dev}")
+    return TTICE_F32 if out.dtype == torch.float32 else TTICE_F64
+
+
 def ttice_reconstruct(h: int, first: int, count: int, out: torch.Tensor, stream=None) -> None:
-    assert out.is_cuda and out.is_contiguous() and out.dtype in (torch.float32, torch.float64)
-    dt = TTICE_F32 if out.dtype == torch.float32 else TTICE_F64
+    dt = _check_out(h, count, out, "ttice_reconstruct")
     _check(_lib.ttice_reconstruct(h, int(first), int(count), out.data_ptr(), dt, _stream_ptr(stream)),
            "ttice_reconstruct")
 
@@ -193,8 +218,7 @@ def ttice_reconstruct(h: int, first: int, count: int, out: torch.Tensor, stream=
 def ttice_reconstruct_noalloc(h: int, first: int, count: int, out: torch.Tensor, stream=None) -> None:
     """Same result as ttice_reconstruct, computed without any device allocation (fixed library
     scratch; see include/ttice.h for the size limit and the sharing rules)."""
-    assert out.is_cuda and out.is_contiguous() and out.dtype in (torch.float32, torch.float64)
-    dt = TTICE_F32 if out.dtype == torch.float32 else TTICE_F64
+    dt = _check_out(h, count, out, "ttice_reconstruct_noalloc")
     _check(_lib.ttice_reconstruct_noalloc(h, int(first), int(count), out.data_ptr(), dt,
                                           _stream_ptr(stream)), "ttice_reconstruct_noalloc")
 

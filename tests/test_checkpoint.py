@@ -161,3 +161,20 @@ def test_header_claiming_more_than_the_file_holds(tmp_path):
     with pytest.raises(T.TTICEError) as ei:
         T.ttice_checkpoint_read_header(str(path))
     assert ei.value.code == T.TTICE_EINVAL
+
+
+def test_header_whose_sizes_wrap_around(tmp_path):
+    """A crafted header whose array sizes overflow 64 bits: d = 2, dims [2^62, 1], ranks
+    [1, 2^62, 2^62].  Each core then has 2^124 elements, 2^127 bytes, and the two sum to 0 mod
+    2^128, so a length check in wrapping arithmetic would accept a file that holds only a header
+    and a checksum.  The reader must reject it (checked products) with TTICE_EINVAL."""
+    d = 2
+    body = b"TTICECK1" + struct.pack("<ii", 1, d) + struct.pack("<qq", 1 << 62, 1) + struct.pack("<d", 0.1)
+    body += struct.pack("<iii", 1, 1, 0) + struct.pack("<d", 1.0) + struct.pack("<ii", 0, 0)
+    body += struct.pack("<qqq", 1, 1 << 62, 1 << 62) + struct.pack("<q", 0)
+    body += struct.pack("<Q", _fnv1a(body))
+    path = tmp_path / "w.ttck"
+    path.write_bytes(body)
+    with pytest.raises(T.TTICEError) as ei:
+        T.ttice_checkpoint_read_header(str(path))
+    assert ei.value.code == T.TTICE_EINVAL

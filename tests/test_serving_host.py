@@ -139,3 +139,61 @@ def test_injected_allocation_failure_hook():
         assert "cudaErrorMemoryAllocation" not in str(ei.value)
     finally:
         T.ttice_test_fail_alloc(0)
+
+
+class SlowHandle:
+    """An update that runs until the test lets it finish; records whether it ever saw its handle
+    closed under it."""
+
+    def __init__(self):
+        import threading
+
+        self.started = threading.Event()
+        self.go = threading.Event()
+        self.closed = False
+        self.closed_during_update = False
+        self.updates = 0
+
+    def update(self, Y, stream=None):
+        self.started.set()
+        self.go.wait(10)
+        self.closed_during_update |= self.closed
+        self.updates += 1
+        return "stats"
+
+    def device_bytes(self):
+        return 1000
+
+    def close(self):
+        self.closed = True
+
+
+def test_release_waits_for_the_update_in_flight():
+    import threading
+    import time
+
+    spec = S.StreamSpec("s", (4, 4), 0.1, 1)
+    eng = S.ServingEngine([spec], slots=1, mem_budget=1 << 40, device="cpu")
+    h = SlowHandle()
+    eng.handles["s"] = h
+    eng.mem_of["s"] = h.device_bytes()
+    eng.mem_used = h.device_bytes()
+    eng.submit(S.Request("s", None))
+    eng.submit(S.Request("s", None))  # queued behind the first
+    assert h.started.wait(5)
+    t = threading.Thread(target=eng.release, args=("s",))
+    t.start()
+    time.sleep(0.2)
+    assert t.is_alive() and not h.closed  # release waits while a slot runs the stream's update
+    h.go.set()
+    t.join(5)
+    assert not t.is_alive()
+    assert h.closed and not h.closed_during_update and h.updates == 1
+    assert eng.mem_used == 0 and "s" not in eng.handles
+    done = sorted(eng.completed, key=lambda r: r.error is not None)
+    assert len(done) == 2 and done[0].error is None and "released" in str(done[1].error)
+    # the queued request was completed, so drain returns; a later submit to the name is refused
+    assert eng.drain(timeout=2)
+    eng.submit(S.Request("s", None))
+    assert "released" in str(eng.completed[-1].error)
+    eng.close()

@@ -89,18 +89,23 @@ def cp_cosine(t0: int, count: int, *, dims=(16, 16, 16, 16), rank: int = 6, freq
 def blob_video(t0: int, count: int, *, height: int = 480, width: int = 640, channels: int = 3,
                n_blobs: int = 12, sigma=(8.0, 40.0), speed: float = 2.0, noise_std: float = 0.01,
                scene_len: int = 0, view=(20, 24, 20, 32, 3), seed: int = 1001,
-               dtype=torch.float32, device="cpu"):
+               dtype=torch.float32, device="cpu", compute_dtype=torch.float64):
     """Frames t0 .. t0+count-1 of moving Gaussian blobs, returned with shape (count, *view).
 
     Each blob has sigma ~ U[sigma], per-channel amplitude ~ U(0,1), a start position uniform in the
     frame and a velocity ~ U(-speed, speed) px/frame per axis; positions reflect at the borders.
     With ``scene_len > 0`` every ``scene_len`` frames start a new scene with freshly drawn blobs.
     The frame is H x W x C in C order, then viewed as ``view`` (same memory order).
+    ``compute_dtype`` is the arithmetic of the frame synthesis (blob parameters are always drawn in
+    float64): float64 by default; float32 gives the same stream to ~1e-7 relative at a fraction of
+    the cost on GPUs with slow FP64 (large frames for benchmarks, never for oracle comparisons,
+    which copy one generated tensor to both sides anyway).
     """
     assert math.prod(view) == height * width * channels
-    out = torch.empty((count, height, width, channels), dtype=torch.float64, device=device)
-    yy = torch.arange(height, dtype=torch.float64, device=device)
-    xx = torch.arange(width, dtype=torch.float64, device=device)
+    cdt = compute_dtype
+    out = torch.empty((count, height, width, channels), dtype=cdt, device=device)
+    yy = torch.arange(height, dtype=cdt, device=device)
+    xx = torch.arange(width, dtype=cdt, device=device)
 
     def reflect(p, size):
         q = torch.remainder(p, 2.0 * size)
@@ -122,7 +127,8 @@ def blob_video(t0: int, count: int, *, height: int = 480, width: int = 640, chan
         local = torch.arange(t, stop, dtype=torch.float64, device=device) - (scene * scene_len if scene_len > 0 else 0)
         py = reflect(py0[None, :] + vy[None, :] * local[:, None], height)  # (k, nb)
         px = reflect(px0[None, :] + vx[None, :] * local[:, None], width)
-        inv = 1.0 / (2.0 * sig * sig)
+        inv = (1.0 / (2.0 * sig * sig)).to(cdt)
+        py, px, amp = py.to(cdt), px.to(cdt), amp.to(cdt)
         gy = torch.exp(-((yy[None, None, :] - py[:, :, None]) ** 2) * inv[None, :, None])  # (k, nb, H)
         gx = torch.exp(-((xx[None, None, :] - px[:, :, None]) ** 2) * inv[None, :, None])  # (k, nb, W)
         # frame[h, w, c] = sum_b amp[b, c] gy[b, h] gx[b, w]
