@@ -315,3 +315,42 @@ def test_video_c1_prefix_fp32(T):
     stats = []
     run_pair(T, Y, 8, 0.1, precision="fp32", tol=1e-4, stats_out=stats)
     assert sum(x[0] for x in stats) >= 1, stats
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32", 1e-6)])
+def test_skip_mean_golden_gpu(T, precision, tol):
+    """The hand-derived increment on which the paper's mean-error skip and the exact batch error
+    disagree (Sec. 4.3): same decision, ranks, cores and last core as derived by hand."""
+    g_ = json.load(open(os.path.join(GOLDEN, "skip_mean_example.json")))
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    for mode, key in (("mean", "expect_mean"), ("exact", "expect_exact")):
+        e = g_[key]
+        g = T.TTICE(g_["dims"], g_["eps"], skip_mode=mode, precision=precision, input_dtype=dt, max_batch=4)
+        g.update(torch.tensor(g_["increment_1"], dtype=dt).cuda())
+        st = g.update(torch.tensor(g_["increment_2"], dtype=dt).cuda())
+        assert bool(st.skipped) == e["skipped"]
+        assert st.rel_err_before == pytest.approx(e["rel_err_before"], rel=max(tol, 1e-12))
+        assert g.ranks() == e["ranks"]
+        np.testing.assert_allclose(g.core(1), np.array(e["U1"]), atol=tol)
+        np.testing.assert_allclose(g.last_core().T, np.array(e["last_core"]), atol=tol * 10)
+        g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32", 1e-6)])
+def test_occupancy_golden_gpu(T, precision, tol):
+    """The hand-derived increment on which occupancy tau = 0.8 keeps a core at occupancy 0.8 and
+    tau = 1 expands it (Eq. 16), with the core element count of Eq. 22."""
+    g_ = json.load(open(os.path.join(GOLDEN, "occupancy_example.json")))
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    for tau, key in ((0.8, "expect_tau_0.8"), (1.0, "expect_tau_1")):
+        e = g_[key]
+        g = T.TTICE(g_["dims"], g_["eps"], tau=tau, precision=precision, input_dtype=dt, max_batch=2)
+        g.update(torch.tensor(g_["increment_1"], dtype=dt).cuda())
+        st = g.update(torch.tensor(g_["increment_2"], dtype=dt).cuda())
+        assert st.eps_core == pytest.approx(g_["eps_core"], rel=max(tol, 1e-12))
+        assert g.ranks() == e["ranks"]
+        np.testing.assert_allclose(g.core(1), np.array(e["U1"], dtype=float), atol=tol)
+        np.testing.assert_allclose(g.core(2), np.array(e["U2"], dtype=float), atol=tol)
+        np.testing.assert_allclose(g.last_core().T, np.array(e["last_core"]), atol=tol * 10)
+        assert st.core_elems == e["core_elements"]
+        g.close()

@@ -315,3 +315,48 @@ def test_planted_mistakes_are_caught(cls):
     except (AssertionError, FloatingPointError, ValueError, np.linalg.LinAlgError):
         caught += 1
     assert caught >= 1
+
+
+# ---------------------------------------------------------------- heuristics with known outcomes
+def test_skip_mean_golden():
+    """The paper's mean-error skip surrogate against the exact batch error (Eq. 20) on a hand-derived
+    increment where they disagree."""
+    g = _load("skip_mean_example.json")
+    # the fixture separates the surrogates: only the mean of the per-observation errors is <= eps,
+    # so an oracle that took the median or the maximum would not skip
+    Y2 = np.array(g["increment_2"])
+    rel = np.linalg.norm(Y2[:, 1:], axis=1) / np.linalg.norm(Y2, axis=1)
+    assert np.mean(rel) <= g["eps"] < min(np.median(rel), np.max(rel))
+    for mode, key in ((O.SKIP_MEAN, "expect_mean"), (O.SKIP_EXACT, "expect_exact")):
+        e = g[key]
+        o = O.TTICEOracle(g["dims"], g["eps"], skip_mode=mode)
+        o.update(np.array(g["increment_1"]))
+        st = o.update(np.array(g["increment_2"]))
+        assert st.skipped == e["skipped"]
+        assert st.rel_err_before == pytest.approx(e["rel_err_before"], rel=1e-14)
+        assert st.ranks == e["ranks"]
+        np.testing.assert_allclose(o.U[0], np.array(e["U1"]), atol=1e-15)
+        np.testing.assert_allclose(o.last_core(), np.array(e["last_core"]), atol=1e-14)
+        if not e["skipped"]:
+            assert st.selected == e["selected"]
+            assert st.eps_upd == pytest.approx(e["eps_upd"], rel=1e-14)
+            assert st.eps_core == pytest.approx(e["eps_core"], rel=1e-14)
+
+
+@pytest.mark.parametrize("tau,key", [(0.8, "expect_tau_0.8"), (1.0, "expect_tau_1")])
+def test_occupancy_golden(tau, key):
+    """Occupancy tau = 0.8 keeps a core at occupancy 0.8 whose residual exceeds its share; tau = 1
+    expands it (Eq. 16).  Also pins the core element count and the compression ratio (Eq. 22)."""
+    g = _load("occupancy_example.json")
+    e = g[key]
+    o = O.TTICEOracle(g["dims"], g["eps"], tau=tau)
+    o.update(np.array(g["increment_1"], dtype=float))
+    st = o.update(np.array(g["increment_2"], dtype=float))
+    assert not st.skipped and st.n_selected == 1
+    assert st.eps_core == pytest.approx(g["eps_core"], rel=1e-14)
+    assert st.ranks == e["ranks"]
+    np.testing.assert_allclose(o.U[0], np.array(e["U1"], dtype=float), atol=1e-15)
+    np.testing.assert_allclose(o.U[1], np.array(e["U2"], dtype=float), atol=1e-15)
+    np.testing.assert_allclose(o.last_core(), np.array(e["last_core"]), atol=1e-14)
+    assert o.core_elements() == e["core_elements"]
+    assert o.compression_ratio() == pytest.approx(e["compression_ratio"], rel=1e-15)
