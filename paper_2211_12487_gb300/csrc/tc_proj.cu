@@ -1,0 +1,488 @@
+// Projection of a batch onto a core on the tensor cores: W(z) = U^T X(z) for every observation z of
+// a stage of the chain (Eq. 6 for stage 1, Eq. 12 for the later stages), with the per-observation
+// norms of the input and of the projection, whose difference is the stage's squared residual
+// ||X(z) - U W(z)||^2 = ||X(z)||^2 - ||W(z)||^2 for an orthonormal U (Pythagoras).
+//
+// Shapes.  X(z) is m x L, row-major (the stage-i unfolding, L columns per observation, observation-
+// major); U is m x r, column-major; W(z) is r x L, row-major.  One work item is a tile of 128
+// consecutive columns of one observation (the MMA's M, one tensor-memory lane per column) against
+// one N tile of NT output rows (MMA N, at most 256); K = m runs in chunks of 32 rows (one 128-byte
+// swizzle row of TF32).
+//
+// Arithmetic.  Each operand is split into a TF32 head and an FP32 tail (x_hi = tf32(x), x_lo =
+// x - x_hi, exact), and each K step issues A_hi B_hi + A_lo B_hi + A_hi B_lo (the dropped tail
+// product is ~2^-22 relative) into an FP32 accumulator in tensor memory: W to FP32 accuracy.  The
+// head/tail pair of U is kept in global memory next to the core (ttice_s::Uh, Ul) and copied
+// straight into the 128-byte-swizzled K-major B operand by TMA; X is staged raw by TMA and split by
+// converter warps, which write the K-major A operand.
+//
+// Roles (10 warps, one persistent CTA per SM):
+//   warps 0-3  converters: thread = tile column; split 32 values per chunk into the A operand and
+//              sum x^2 of the column;
+//   warps 4-7  epilogue: thread = tensor-memory lane = tile column; read the accumulator in 16-column
+//              pieces, store W, sum w^2;
+//   warp 8     one lane issues the TMA copies (X chunk, U head and tail chunk);
+//   warp 9     allocates tensor memory; one lane issues the MMAs, committing each chunk to the
+//              barriers that free its A and B slots, and each item to the accumulator barrier (two
+//              accumulators, so the MMAs of item k+1 overlap the epilogue of item k).
+// Every wait is bounded in time (the limit is a launch argument); on expiry the waiting thread
+// raises a CTA-wide abort flag, every role leaves its loop, the MMA lane waits for the MMAs it
+// issued and the producer for its copies in flight, tensor memory is freed and `status` records the
+// failure.
+#include <algorithm>
+#include <mutex>
+
+#include "tc_common.cuh"
+#include "ttice_internal.cuh"
+
+namespace ttice {
+namespace {
+
+using namespace tc;
+
+constexpr int kTile = 128;   // columns per item (MMA M)
+constexpr int kChunk = 32;   // K rows per staged chunk
+constexpr int kConvWarps = 4, kEpiWarps = 4;
+constexpr int kProducerWarp = kConvWarps + kEpiWarps, kMmaWarp = kProducerWarp + 1;
+constexpr int kThreads = (kMmaWarp + 1) * 32;
+constexpr uint32_t kRawBytes = kChunk * kTile * 4;  // 16 KB
+constexpr uint32_t kABytes = kTile * kChunk * 4;    // 16 KB per half (head or tail)
+
+// ring depths per N tile (dynamic shared memory stays within 227 KB)
+template <int NT>
+struct Cfg;
+template <>
+struct Cfg<64> { static constexpr int raw = 4, a = 2, b = 3; };
+template <>
+struct Cfg<128> { static constexpr int raw = 3, a = 2, b = 2; };
+template <>
+struct Cfg<256> { static constexpr int raw = 2, a = 2, b = 2; };
+
+template <int NT>
+constexpr size_t smem_bytes() {
+  return (size_t)Cfg<NT>::raw * kRawBytes + 2 * (size_t)Cfg<NT>::a * kABytes + 2 * (size_t)Cfg<NT>::b * NT * 128 +
+         1024;
+}
+
+struct ProjArgs {
+  int64_t L, m;
+  int r, b, nj, tpo, nch;
+  float* W;
+  double* part_x;  // [b * tpo * 4]   per item of N tile 0: sum x^2 of each converter warp's columns
+  double* part_w;  // [b * tpo * nj * 4]   per item: sum w^2 of each epilogue warp's columns
+  int* status;
+  unsigned long long wait_ns;
+  long long drop_chunk;  // test hook: CTA 0 issues no copy for its chunk of this index (-1: none)
+};
+
+template <int NT>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_proj_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap uhmap,
+                   const __grid_constant__ CUtensorMap ulmap, const ProjArgs a) {
+  constexpr int RAW = Cfg<NT>::raw, AST = Cfg<NT>::a, BST = Cfg<NT>::b;
+  constexpr uint32_t kBBytes = NT * 128;  // one half of a B chunk: NT rows of 128 bytes
+  constexpr uint32_t kTmemCols = 2 * NT;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* raw = base;
+  unsigned char* a_hi = raw + RAW * kRawBytes;
+  unsigned char* a_lo = a_hi + AST * kABytes;
+  unsigned char* b_hi = a_lo + AST * kABytes;
+  unsigned char* b_lo = b_hi + BST * kBBytes;
+
+  __shared__ __align__(8) uint64_t raw_full[RAW], raw_empty[RAW];
+  __shared__ __align__(8) uint64_t a_full[AST], a_empty[AST];
+  __shared__ __align__(8) uint64_t b_full[BST], b_empty[BST];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < RAW; ++s) {
+      mbar_init(&raw_full[s], 1);
+      mbar_init(&raw_empty[s], kConvWarps);
+    }
+    for (int s = 0; s < AST; ++s) {
+      mbar_init(&a_full[s], kConvWarps);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < BST; ++s) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], kEpiWarps);
+    }
+    mbar_init(&mma_done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    fence_before();
+  }
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int64_t nitems = (int64_t)a.b * a.tpo * a.nj;
+  const unsigned long long lim = a.wait_ns;
+
+  if (wid == kProducerWarp) {
+    if (lane == 0) {
+      int64_t g = 0;
+      bool ok = true;
+      for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
+        const int j = (int)(q % a.nj);
+        const int t = (int)((q / a.nj) % a.tpo);
+        const int z = (int)(q / ((int64_t)a.nj * a.tpo));
+        for (int c = 0; c < a.nch; ++c, ++g) {
+          const int s = (int)(g % RAW), sb = (int)(g % BST);
+          if (g >= RAW && !wait_bounded(&raw_empty[s], (uint32_t)(((g / RAW) - 1) & 1), &abort_flag, lim)) {
+            ok = false;
+            break;
+          }
+          if (!(blockIdx.x == 0 && g == a.drop_chunk)) {
+            mbar_expect_tx(&raw_full[s], kRawBytes);
+            tma_load_3d(smem_u32(raw + (size_t)s * kRawBytes), &xmap, t * kTile, c * kChunk, z, &raw_full[s]);
+          }
+          if (g >= BST && !wait_bounded(&b_empty[sb], (uint32_t)(((g / BST) - 1) & 1), &abort_flag, lim)) {
+            ok = false;
+            ++g;
+            break;
+          }
+          mbar_expect_tx(&b_full[sb], 2 * kBBytes);
+          tma_load_2d(smem_u32(b_hi + (size_t)sb * kBBytes), &uhmap, c * kChunk, j * NT, &b_full[sb]);
+          tma_load_2d(smem_u32(b_lo + (size_t)sb * kBBytes), &ulmap, c * kChunk, j * NT, &b_full[sb]);
+        }
+      }
+      // copies of the last ring slots may still be in flight (on an abort): wait for them
+      for (int64_t k = g > RAW ? g - RAW : 0; k < g; ++k)
+        wait_drain(&raw_full[k % RAW], (uint32_t)((k / RAW) & 1), lim);
+      for (int64_t k = g > BST ? g - BST : 0; k < g; ++k)
+        wait_drain(&b_full[k % BST], (uint32_t)((k / BST) & 1), lim);
+    }
+  } else if (wid == kMmaWarp) {
+    if (lane == 0) {
+      int64_t g = 0;
+      int it = 0;
+      bool ok = true;
+      for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x, ++it) {
+        const int j = (int)(q % a.nj);
+        const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);  // MMA N of this item
+        const uint32_t idesc = tf32_idesc(kTile, nN);
+        const int acc = it & 1;
+        if (it >= 2 && !wait_bounded(&acc_empty[acc], (uint32_t)(((it >> 1) - 1) & 1), &abort_flag, lim)) break;
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * NT);
+        for (int c = 0; c < a.nch; ++c, ++g) {
+          const int qa = (int)(g % AST), sb = (int)(g % BST);
+          if (!wait_bounded(&a_full[qa], (uint32_t)((g / AST) & 1), &abort_flag, lim) ||
+              !wait_bounded(&b_full[sb], (uint32_t)((g / BST) & 1), &abort_flag, lim)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t ah = smem_u32(a_hi + (size_t)qa * kABytes), al = smem_u32(a_lo + (size_t)qa * kABytes);
+          const uint32_t bh = smem_u32(b_hi + (size_t)sb * kBBytes), bl = smem_u32(b_lo + (size_t)sb * kBBytes);
+          const int64_t rows = a.m - (int64_t)c * kChunk;
+          const int nk = rows >= kChunk ? kChunk / 8 : (int)((rows + 7) / 8);
+#pragma unroll
+          for (int kk = 0; kk < kChunk / 8; ++kk) {
+            if (kk >= nk) break;
+            const uint32_t ko = (uint32_t)kk * 32;  // 8 TF32 values of K
+            mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (c | kk) != 0);
+            mma_tf32(d, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, 1);
+            mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
+          }
+          mma_commit(&a_empty[qa]);  // these slots are free once the MMAs above have read them
+          mma_commit(&b_empty[sb]);
+        }
+        if (ok) mma_commit(&acc_full[acc]);
+      }
+      // every MMA issued has completed before tensor memory is released
+      mma_commit(&mma_done);
+      wait_drain(&mma_done, 0, lim);
+    }
+  } else if (wid < kConvWarps) {
+    // converters: thread tid owns column tid of the item's tile
+    int64_t g = 0;
+    for (int64_t q = blockIdx.x; q < nitems; q += gridDim.x) {
+      const int j = (int)(q % a.nj);
+      const int t = (int)((q / a.nj) % a.tpo);
+      const int z = (int)(q / ((int64_t)a.nj * a.tpo));
+      float x2 = 0.0f;
+      bool ok = true;
+      for (int c = 0; c < a.nch; ++c, ++g) {
+        const int s = (int)(g % RAW), qa = (int)(g % AST);
+        bool got = wait_bounded(&raw_full[s], (uint32_t)((g / RAW) & 1), &abort_flag, lim);
+        if (got && g >= AST) got = wait_bounded(&a_empty[qa], (uint32_t)(((g / AST) - 1) & 1), &abort_flag, lim);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        const float* rw = reinterpret_cast<const float*>(raw + (size_t)s * kRawBytes);
+        unsigned char* ah = a_hi + (size_t)qa * kABytes + (size_t)tid * 128;
+        unsigned char* al = a_lo + (size_t)qa * kABytes + (size_t)tid * 128;
+        const int64_t rows = a.m - (int64_t)c * kChunk;
+        const int kv = rows >= kChunk ? kChunk : (int)rows;  // rows of K in this chunk
+        const int units = 2 * ((kv + 7) / 8);                // 16-byte units the MMAs read
+#pragma unroll
+        for (int u = 0; u < kChunk / 4; ++u) {
+          if (u < units) {
+            float4 hi, lo;
+            float* ph = &hi.x;
+            float* pl = &lo.x;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int kk = 4 * u + e;
+              const float y = kk < kv ? rw[kk * kTile + tid] : 0.0f;
+              x2 = fmaf(y, y, x2);
+              ph[e] = tf32_hi(y);
+              pl[e] = y - ph[e];
+            }
+            const int off = (u ^ (tid & 7)) << 4;
+            *reinterpret_cast<float4*>(ah + off) = hi;
+            *reinterpret_cast<float4*>(al + off) = lo;
+          }
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&a_full[qa]);
+          mbar_arrive(&raw_empty[s]);
+        }
+      }
+      if (!ok) break;
+      if (a.part_x && j == 0) {
+        double s = (double)x2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) a.part_x[((int64_t)z * a.tpo + t) * kConvWarps + wid] = s;
+      }
+    }
+  } else if (wid < kProducerWarp) {
+    // epilogue: thread = tensor-memory lane = tile column
+    const int ew = wid - kConvWarps;
+    int it = 0;
+    for (int64_t q = blockIdx.x; q < nitems; q += gridDim.x, ++it) {
+      const int j = (int)(q % a.nj);
+      const int t = (int)((q / a.nj) % a.tpo);
+      const int z = (int)(q / ((int64_t)a.nj * a.tpo));
+      const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);
+      const int acc = it & 1;
+      if (!__all_sync(0xffffffffu, wait_bounded(&acc_full[acc], (uint32_t)((it >> 1) & 1), &abort_flag, lim)))
+        break;
+      fence_after();
+      const int64_t l = (int64_t)t * kTile + ew * 32 + lane;
+      const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(acc * NT);
+      float* Wz = a.W + (int64_t)z * a.r * a.L + l;
+      float w2 = 0.0f;
+      for (int p = 0; p < nN / 16; ++p) {
+        float v[16];
+        tmem_ld16(taddr + (uint32_t)(16 * p), v);
+        tmem_wait_ld();
+        const int a0 = j * NT + 16 * p;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          if (a0 + e < a.r) {
+            w2 = fmaf(v[e], v[e], w2);
+            if (l < a.L) Wz[(int64_t)(a0 + e) * a.L] = v[e];
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+      if (a.part_w) {
+        double s = (double)w2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) a.part_w[(((int64_t)z * a.tpo + t) * a.nj + j) * kEpiWarps + ew] = s;
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (wid == kMmaWarp) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+  if (tid == 0 && abort_flag) atomicOr(a.status, 1);
+}
+
+// Per observation: ||X(z)||^2 and ||X(z)||^2 - ||W(z)||^2 (clamped to [0, ||X(z)||^2]: the difference
+// of the two FP32-accurate sums can round below zero when U spans the observation), summed in a
+// fixed order.
+__global__ void tc_proj_reduce_kernel(const double* part_x, const double* part_w, int tpo, int nj,
+                                      double* x2_out, double* rho2_out) {
+  const int z = blockIdx.x;
+  double sx = 0.0, sw = 0.0;
+  for (int64_t i = threadIdx.x; i < (int64_t)tpo * kConvWarps; i += blockDim.x)
+    sx += part_x[(int64_t)z * tpo * kConvWarps + i];
+  for (int64_t i = threadIdx.x; i < (int64_t)tpo * nj * kEpiWarps; i += blockDim.x)
+    sw += part_w[(int64_t)z * tpo * nj * kEpiWarps + i];
+  __shared__ double ax[256], aw[256];
+  ax[threadIdx.x] = sx;
+  aw[threadIdx.x] = sw;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      ax[threadIdx.x] += ax[threadIdx.x + o];
+      aw[threadIdx.x] += aw[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (x2_out) x2_out[z] = ax[0];
+    if (rho2_out) rho2_out[z] = fmin(fmax(ax[0] - aw[0], 0.0), ax[0]);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+int pick_nt(int r) {
+  if (r <= 64) return 64;
+  if (r <= 128) return 128;
+  return 256;
+}
+
+std::atomic<unsigned long long> g_wait_ns{2000000000ull};
+std::atomic<long long> g_drop_chunk{-1};
+
+template <int NT>
+cudaError_t run(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
+                int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part, int* status,
+                cudaStream_t st) {
+  auto enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap xmap, uhmap, ulmap;
+  {
+    const cuuint64_t gdim[3] = {(cuuint64_t)L, (cuuint64_t)m, (cuuint64_t)b};
+    const cuuint64_t gstride[2] = {(cuuint64_t)L * 4, (cuuint64_t)(m * L * 4)};
+    const cuuint32_t box[3] = {(cuuint32_t)kTile, (cuuint32_t)kChunk, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), gdim, gstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const cuuint64_t gdim[2] = {(cuuint64_t)ldhl, (cuuint64_t)hlcols};
+    const cuuint64_t gstride[1] = {(cuuint64_t)ldhl * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)NT};
+    const cuuint32_t es[2] = {1, 1};
+    if (enc(&uhmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Uh), gdim, gstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&ulmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Ul), gdim, gstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  static std::once_flag once;
+  static cudaError_t setup_err = cudaSuccess;
+  static int sms = 148;
+  std::call_once(once, [] {
+    setup_err = cudaFuncSetAttribute(tc_proj_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_bytes<NT>());
+    int dev = 0;
+    if (setup_err == cudaSuccess) setup_err = cudaGetDevice(&dev);
+    if (setup_err == cudaSuccess) setup_err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  TT_CUDA(setup_err);
+  ProjArgs a;
+  a.L = L;
+  a.m = m;
+  a.r = r;
+  a.b = b;
+  a.nj = (r + NT - 1) / NT;
+  a.tpo = (int)((L + kTile - 1) / kTile);
+  a.nch = (int)((m + kChunk - 1) / kChunk);
+  a.W = W;
+  const bool norms = x2 != nullptr || rho2 != nullptr;
+  a.part_x = norms ? part : nullptr;
+  a.part_w = norms ? part + (int64_t)b * a.tpo * kConvWarps : nullptr;
+  a.status = status;
+  a.wait_ns = g_wait_ns.load();
+  a.drop_chunk = g_drop_chunk.exchange(-1);
+  const int64_t nitems = (int64_t)b * a.tpo * a.nj;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(sms, nitems));
+  note_launch();
+  tc_proj_kernel<NT><<<(unsigned)grid, kThreads, smem_bytes<NT>(), st>>>(xmap, uhmap, ulmap, a);
+  TT_CUDA(cudaGetLastError());
+  if (norms) {
+    note_launch();
+    tc_proj_reduce_kernel<<<b, 256, 0, st>>>(a.part_x, a.part_w, a.tpo, a.nj, x2, rho2);
+    TT_CUDA(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+bool tc_proj_supported(const void* X, int64_t L, int64_t m, int r, int64_t ldhl) {
+  return encode_fn() != nullptr && (reinterpret_cast<uintptr_t>(X) % 16) == 0 && (L % 4) == 0 && L >= 32 &&
+         L < (1LL << 31) && m >= 1 && m < (1LL << 31) && r >= 1 && (ldhl % 32) == 0;
+}
+
+int64_t tc_proj_part_elems(int b, int64_t L, int64_t r) {
+  const int64_t tpo = (L + kTile - 1) / kTile;
+  const int64_t nj = (r + 63) / 64;  // the most N tiles any tile width gives
+  return (int64_t)b * tpo * (kConvWarps + nj * kEpiWarps);
+}
+
+cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
+                           int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
+                           int* status, cudaStream_t st) {
+  switch (pick_nt(r)) {
+    case 64: return run<64>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
+    case 128: return run<128>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
+    default: return run<256>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
+  }
+}
+
+void tc_set_wait_ns(unsigned long long ns) { g_wait_ns.store(ns ? ns : 2000000000ull); }
+void tc_drop_next_copy(long long chunk) { g_drop_chunk.store(chunk); }
+
+// Head / tail split of FP32 core columns [c0, c1) (all ld_in rows) into the TF32 pair the tensor
+// cores read (ld_out rows each; rows beyond ld_in are left as they are).
+__global__ void split_tf32_kernel(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,
+                                  int64_t ld_out) {
+  for (int64_t c = c0 + blockIdx.y; c < c1; c += gridDim.y)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ld_in; i += (int64_t)gridDim.x * blockDim.x) {
+      const float x = in[c * ld_in + i];
+      const float h = tf32_hi(x);
+      hi[c * ld_out + i] = h;
+      lo[c * ld_out + i] = x - h;
+    }
+}
+
+cudaError_t launch_split_tf32(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,
+                              int64_t ld_out, cudaStream_t st) {
+  if (c1 <= c0 || ld_in <= 0) return cudaSuccess;
+  const int64_t bx = std::min<int64_t>((ld_in + 255) / 256, 64);
+  const int64_t by = std::min<int64_t>(c1 - c0, 1024);
+  note_launch();
+  split_tf32_kernel<<<dim3((unsigned)bx, (unsigned)by), 256, 0, st>>>(in, ld_in, c0, c1, hi, lo, ld_out);
+  return cudaGetLastError();
+}
+
+}  // namespace ttice

@@ -42,6 +42,13 @@ struct ttice_s {
   int64_t r[kMaxD + 1] = {};    // ranks r_0..r_d (host mirror), r[0] = 1
   double* U[kMaxD] = {};
   float* Uf[kMaxD] = {};
+  // TF32 head / tail split of Uf for the tensor-core projections (mixed path): column-major, leading
+  // dimension ldhl[i] (ldu rounded up to 32), hlcols[i] columns (cap rounded up to 256), zero beyond
+  // the core; kept equal to split(Uf) column by column wherever Uf changes
+  float* Uh[kMaxD] = {};
+  float* Ul[kMaxD] = {};
+  int64_t ldhl[kMaxD] = {};
+  int64_t hlcols[kMaxD] = {};
   double* last = nullptr;
   int64_t last_cap = 0;  // observations
   int64_t n_obs = 0;
@@ -248,6 +255,7 @@ int dalloc_bytes(void** p, int64_t bytes) {
 void free_all(ttice_s* h) {
   for (int i = 0; i < kMaxD; ++i) {
     cudaFree(h->U[i]); cudaFree(h->Uf[i]); cudaFree(h->stage[i]); cudaFree(h->dstage[i]);
+    cudaFree(h->Uh[i]); cudaFree(h->Ul[i]);
   }
   void* ptrs[] = {h->G32, h->KQ, h->kstart, h->KV, h->res,
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
@@ -301,6 +309,18 @@ int sumsq(const T* X, int b, int64_t n, double* out, cudaStream_t st) {
   return cu(launch_sum_squares<T>(X, b, n, out, st));
 }
 
+// Stage i of the mixed path on the tensor cores: FP32 stage input X (the increment for i = 0, a stage
+// buffer otherwise) in a layout the projection kernel takes.
+bool tc_stage(const ttice_s* h, int i, const void* X) {
+  return h->Uh[i] != nullptr && h->r[i + 1] > 0 &&
+         tc_proj_supported(X, h->L[i], h->r[i] * h->n[i], (int)h->r[i + 1], h->ldhl[i]);
+}
+int tc_project(ttice_s* h, int i, const void* X, int b, void* W, double* x2, double* rho2, cudaStream_t st) {
+  return cu(launch_tc_proj(static_cast<const float*>(X), b, h->L[i], h->r[i] * h->n[i], (int)h->r[i + 1], h->Uh[i],
+                           h->Ul[i], h->ldhl[i], h->hlcols[i], static_cast<float*>(W), x2, rho2, h->part, h->ibuf + 5,
+                           st));
+}
+
 // ---------------------------------------------------------------- chain projection
 // Project b observations of X0 (stage-0 layout) through U_1..U_d into `bufs`; with `errors`,
 // rho2[i b + z] = ||R_i(z)||^2 for every stage i (their sum over i is ||y_z - ~y_z||^2, the orthogonal
@@ -312,10 +332,13 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
   const WT* Xw = first > 0 ? static_cast<const WT*>(bufs[first - 1]) : nullptr;
   const double sw = sizeof(WT), sy = sizeof(TY);
   // stage 1 of the mixed path on the tensor cores (FP32 increment and cores)
-  const bool tc_k1 = sizeof(TY) == 4 && sizeof(WT) == 4 && first == 0 && h->r[1] > 0 &&
+  // stage 1 of the mixed path on the tensor cores (FP32 increment and cores): the projection kernel,
+  // else the first-pass kernel limited to n_1 <= 128, r_1 <= 64
+  const bool tc0 = sizeof(TY) == 4 && sizeof(WT) == 4 && first == 0 && tc_stage(h, 0, X0);
+  const bool tc_k1 = !tc0 && sizeof(TY) == 4 && sizeof(WT) == 4 && first == 0 && h->r[1] > 0 &&
                      k1_tc_supported(X0, h->L[0], (int)h->n[0], (int)h->r[1]);
   const bool fused_k1 =
-      errors && h->r[1] > 0 && (tc_k1 || k1_supported<TY, WT>((int)h->n[0], (int)h->r[1]));
+      errors && h->r[1] > 0 && (tc0 || tc_k1 || k1_supported<TY, WT>((int)h->n[0], (int)h->r[1]));
   if (errors) {
     TT_CU(cudaMemsetAsync(h->rho2, 0, (size_t)h->d * b * sizeof(double), st));
     TT_CU(cudaMemsetAsync(h->y2, 0, b * sizeof(double), st));
@@ -361,7 +384,9 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
     }
     const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
                                      : reinterpret_cast<const WT*>(h->Uf[i]);
-    if (i == 0 && tc_k1) {
+    if (i == 0 && tc0) {
+      TT_TRY(tc_project(h, 0, X0, b, W, errors ? h->y2 : nullptr, errors ? h->rho2 : nullptr, st));
+    } else if (i == 0 && tc_k1) {
       TT_CU(launch_k1_tc(reinterpret_cast<const float*>(X0), b, L, (int)m, (int)rn,
                          reinterpret_cast<const float*>(Ui), h->ldu[i], reinterpret_cast<float*>(W),
                          errors ? h->y2 : nullptr, errors ? h->rho2 : nullptr, h->part, h->ibuf + 5, st));
@@ -382,6 +407,9 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
     } else if (i == 0) {
       TT_TRY(proj<WT, TY, WT>(Ui, h->ldu[i], X0, m, L, rn, b, W, st));
       if (errors) TT_TRY((resid<WT, WT, TY, WT>(Ui, h->ldu[i], W, X0, m, L, rn, b, nullptr, h->rho2, st)));
+    } else if (sizeof(WT) == 4 && tc_stage(h, i, Xw)) {
+      // Pythagorean residual per observation: ||X_i||^2 - ||U_i^T X_i||^2
+      TT_TRY(tc_project(h, i, Xw, b, W, nullptr, errors ? h->rho2 + (int64_t)i * b : nullptr, st));
     } else {
       TT_TRY(proj<WT, WT, WT>(Ui, h->ldu[i], Xw, m, L, rn, b, W, st));
       if (errors)
@@ -796,6 +824,8 @@ int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t s
   TT_CU(launch_canonical_sign(h->Vn, m, k, m, st));
   TT_CU(launch_copy_cols(h->Vn, m, m, k, U + r * ld, ld, h->Uf[core] ? h->Uf[core] + r * ld : nullptr,
                          st));
+  if (h->Uh[core])
+    TT_CU(launch_split_tf32(h->Uf[core], ld, r, r + k, h->Uh[core], h->Ul[core], h->ldhl[core], st));
   return TTICE_OK;
 }
 
@@ -845,6 +875,11 @@ void rollback(ttice_s* h, const int64_t* r_old, cudaStream_t st) {
       const size_t bytes = (size_t)(h->r[i + 1] - r_old[i + 1]) * ld;
       cudaMemsetAsync(h->U[i] + r_old[i + 1] * ld, 0, bytes * sizeof(double), st);
       if (h->Uf[i]) cudaMemsetAsync(h->Uf[i] + r_old[i + 1] * ld, 0, bytes * sizeof(float), st);
+      if (h->Uh[i]) {
+        const size_t hb = (size_t)(h->r[i + 1] - r_old[i + 1]) * h->ldhl[i] * sizeof(float);
+        cudaMemsetAsync(h->Uh[i] + r_old[i + 1] * h->ldhl[i], 0, hb, st);
+        cudaMemsetAsync(h->Ul[i] + r_old[i + 1] * h->ldhl[i], 0, hb, st);
+      }
     }
   }
   for (int i = 0; i <= h->d; ++i) h->r[i] = r_old[i];
@@ -1000,7 +1035,10 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
           ph_begin(h, PH_DPROJ, st, nsel * (sx * m * L + sizeof(WT) * (double)rn * L),
                    2.0 * nsel * (double)m * L * rn);
         }
-        if (i == 0 && sizeof(TY) == 4 && sizeof(WT) == 4 && k1_tc_supported(D0i, L, (int)m, (int)rn))
+        const void* Din = i == 0 ? static_cast<const void*>(D0i) : static_cast<const void*>(Xi);
+        if (sizeof(WT) == 4 && (i > 0 || sizeof(TY) == 4) && tc_stage(h, i, Din))
+          rc = tc_project(h, i, Din, nsel, Wn, nullptr, nullptr, st);
+        else if (i == 0 && sizeof(TY) == 4 && sizeof(WT) == 4 && k1_tc_supported(D0i, L, (int)m, (int)rn))
           rc = cu(launch_k1_tc(reinterpret_cast<const float*>(D0i), nsel, L, (int)m, (int)rn,
                                reinterpret_cast<const float*>(Ui), h->ldu[i], reinterpret_cast<float*>(Wn),
                                nullptr, nullptr, nullptr, h->ibuf + 5, st));
@@ -1138,6 +1176,12 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
     h->max_m = std::max(h->max_m, h->ldu[i]);
     rc = dalloc<double>(&h->U[i], h->ldu[i] * h->cap[i + 1]);
     if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->Uf[i], h->ldu[i] * h->cap[i + 1]);
+    if (h->wt_bytes == 4) {
+      h->ldhl[i] = (h->ldu[i] + 31) / 32 * 32;
+      h->hlcols[i] = (h->cap[i + 1] + 255) / 256 * 256;
+      if (rc == TTICE_OK) rc = dalloc<float>(&h->Uh[i], h->ldhl[i] * h->hlcols[i]);
+      if (rc == TTICE_OK) rc = dalloc<float>(&h->Ul[i], h->ldhl[i] * h->hlcols[i]);
+    }
     const int64_t st_elems = B * h->cap[i + 1] * h->L[i];
     if (rc == TTICE_OK) rc = dalloc_bytes(&h->stage[i], st_elems * h->wt_bytes);
     if (rc == TTICE_OK) rc = dalloc_bytes(&h->dstage[i], st_elems * h->wt_bytes);
@@ -1179,9 +1223,11 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
   int64_t maxcap = 1;
   for (int i = 1; i <= d; ++i) maxcap = std::max(maxcap, h->cap[i]);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->P, maxcap * kRR);
-  if (rc == TTICE_OK)
-    rc = dalloc<double>(&h->part, std::max<int64_t>(2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)),
-                                                    k1_tc_part_elems((int)B, h->L[0])));
+  int64_t part_elems = std::max<int64_t>(2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)),
+                                         k1_tc_part_elems((int)B, h->L[0]));
+  if (h->wt_bytes == 4)
+    for (int i = 0; i < d; ++i) part_elems = std::max(part_elems, tc_proj_part_elems((int)B, h->L[i], h->cap[i + 1]));
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->part, part_elems);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rho2, (int64_t)h->d * B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rn2, B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->y2, B);
@@ -1276,6 +1322,9 @@ int ttice_reserve_rank(ttice_t h, int k, int64_t cap) {
     if (rc == TTICE_OK && h->Uf[i])
       rc = cu(cudaMemcpy2DAsync(g->Uf[i], g->ldu[i] * sizeof(float), h->Uf[i], h->ldu[i] * sizeof(float),
                                 rows * sizeof(float), cols, cudaMemcpyDeviceToDevice, fs));
+    for (int hl = 0; hl < 2 && rc == TTICE_OK && h->Uh[i]; ++hl)
+      rc = cu(cudaMemcpy2DAsync(hl ? g->Ul[i] : g->Uh[i], g->ldhl[i] * sizeof(float), hl ? h->Ul[i] : h->Uh[i],
+                                h->ldhl[i] * sizeof(float), rows * sizeof(float), cols, cudaMemcpyDeviceToDevice, fs));
   }
   const int64_t rd = h->r[h->d];
   if (rc == TTICE_OK && h->n_obs > 0 && rd > 0)
@@ -1476,6 +1525,10 @@ int ttice_load(ttice_t h, const int64_t* ranks, const double* const* cores, cons
     if (h->Uf[i]) {
       std::vector<float> f(colmajor.begin(), colmajor.end());
       TT_CU(cudaMemcpy(h->Uf[i], f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (h->Uh[i]) {
+      TT_CU(launch_split_tf32(h->Uf[i], ld, 0, h->cap[i + 1], h->Uh[i], h->Ul[i], h->ldhl[i], nullptr));
+      TT_CU(cudaStreamSynchronize(nullptr));
     }
   }
   const int64_t capd = h->cap[h->d];

@@ -145,6 +145,26 @@ int64_t k1_tc_part_elems(int b, int64_t L);
 cudaError_t launch_k1_tc(const float* Y, int b, int64_t L, int n1, int r, const float* U, int64_t ldu,
                          float* W, double* y2, double* rho2, double* part, int* status, cudaStream_t st);
 
+// Projection of a batch onto a core on the tensor cores (tc_proj.cu): W(z) = U^T X(z) for b
+// observations, X(z) m x L row-major FP32 (16-byte aligned, L % 4 == 0, L >= 32), U given as its
+// TF32 head/tail pair Uh, Ul (column-major, ld ldhl % 32 == 0, hlcols columns allocated, zero beyond
+// the core), W(z) r x L row-major.  With x2 and/or rho2 (device, b doubles each): x2[z] = ||X(z)||^2,
+// rho2[z] = ||X(z)||^2 - ||W(z)||^2 (clamped to [0, x2]).  part: tc_proj_part_elems(b, L, r) doubles.
+// status becomes nonzero if a wait of the kernel expired.
+bool tc_proj_supported(const void* X, int64_t L, int64_t m, int r, int64_t ldhl);
+int64_t tc_proj_part_elems(int b, int64_t L, int64_t r);
+cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
+                           int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
+                           int* status, cudaStream_t st);
+// TF32 head/tail split of FP32 columns [c0, c1) (ld_in rows) into hi, lo (ld_out).
+cudaError_t launch_split_tf32(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,
+                              int64_t ld_out, cudaStream_t st);
+// Bounded-wait limit of the tensor-core kernels (0 restores the default of 2 s), and a test hook:
+// the next tc_proj launch issues no copy for chunk `chunk` of its first CTA, so that the consumers'
+// bounded wait runs out.
+void tc_set_wait_ns(unsigned long long ns);
+void tc_drop_next_copy(long long chunk);
+
 // Misc kernels.
 cudaError_t launch_fill(double* p, int64_t n, double v, cudaStream_t st);
 template <typename TI, typename TO>

@@ -354,3 +354,36 @@ def test_occupancy_golden_gpu(T, precision, tol):
         np.testing.assert_allclose(g.last_core().T, np.array(e["last_core"]), atol=tol * 10)
         assert st.core_elems == e["core_elements"]
         g.close()
+
+
+@pytest.mark.parametrize("ranks", [[1, 37, 300, 90, 8], [1, 3, 17, 64, 5]])
+def test_projection_kernel_shapes(T, ranks):
+    """The tensor-core projection of the mixed path (W = U^T X per stage, residual norms by
+    Pythagoras) against the oracle's sequential projection (Algorithm 2 'project', Eq. 12) and its
+    direct per-observation errors (Eq. 17), on cores loaded into the handle: ragged K chunks (m not a
+    multiple of 32), ragged column tiles (L not a multiple of 128), several N tiles (r_2 = 300 > 256,
+    the last one partial), r not a multiple of 16, and a batch of 3."""
+    dims = (40, 20, 36, 8)
+    rng = np.random.default_rng(5)
+    cores = []
+    for i, n in enumerate(dims):
+        q, _ = np.linalg.qr(rng.normal(size=(ranks[i] * n, ranks[i + 1])))
+        cores.append(q)
+    o = O.TTICEOracle(dims, 0.1)
+    o.ranks = list(ranks[:len(dims) + 1])
+    o.U = [c.copy() for c in cores]
+    # data: half inside the span of the cores (small residuals), half generic
+    C = rng.normal(size=(3, ranks[len(dims)]))
+    Y = o.expand(C) + 0.05 * rng.normal(size=(3,) + dims)
+    last = np.zeros((1, ranks[len(dims)]))
+    c_o, rho2, y2 = o.errors(Y)
+    for precision, tol_c, tol_e in (("fp64", 1e-12, 1e-10), ("fp32", 2e-6, 2e-5)):
+        g = T.TTICE(dims, 0.1, precision=precision, input_dtype=torch.float32, max_batch=4, max_rank=512)
+        g.load(ranks[:len(dims) + 1], cores, last)
+        Yd = torch.tensor(Y, dtype=torch.float32).cuda()
+        coeffs, rel = g.project(Yd)
+        Y32 = Yd.double().cpu().numpy()
+        c32, rho32, y32 = o.errors(Y32)
+        assert _relmax(coeffs.cpu().numpy(), c32) < tol_c, (precision, _relmax(coeffs.cpu().numpy(), c32))
+        np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho32 / y32), rtol=tol_e)
+        g.close()
