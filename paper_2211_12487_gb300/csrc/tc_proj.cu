@@ -6,12 +6,16 @@
 // Shapes.  X(z) is m x L, row-major (the stage-i unfolding, L columns per observation, observation-
 // major); U is m x r, column-major; W(z) is r x L, row-major.  One work item is a tile of 128
 // consecutive columns of one observation (the MMA's M, one tensor-memory lane per column) against
-// one N tile of NT output rows (MMA N, at most 256); K = m runs in chunks of 32 rows (one 128-byte
+// one N tile of NT output rows (MMA N, 64 or 128); K = m runs in chunks of 32 rows (one 128-byte
 // swizzle row of TF32).
 //
 // Arithmetic.  Each operand is split into a TF32 head and an FP32 tail (x_hi = tf32(x), x_lo =
 // x - x_hi, exact), and each K step issues A_hi B_hi + A_lo B_hi + A_hi B_lo (the dropped tail
-// product is ~2^-22 relative) into an FP32 accumulator in tensor memory: W to FP32 accuracy.  The
+// product is ~2^-22 relative) into an FP32 accumulator in tensor memory.  The accumulator adds K
+// in segments of kSeg chunks (256 values of K): each segment starts a fresh accumulator, and the
+// epilogue adds the segments into W with FP32 round-to-nearest.  (Accumulating thousands of
+// K steps in one tensor-memory accumulator measurably biases W, ~1e-5 relative at K = 4096, against
+// ~1e-6 for 256-long segments.)  W is then at FP32 accuracy.  The
 // head/tail pair of U is kept in global memory next to the core (ttice_s::Uh, Ul) and copied
 // straight into the 128-byte-swizzled K-major B operand by TMA; X is staged raw by TMA and split by
 // converter warps, which write the K-major A operand.
@@ -19,12 +23,12 @@
 // Roles (10 warps, one persistent CTA per SM):
 //   warps 0-3  converters: thread = tile column; split 32 values per chunk into the A operand and
 //              sum x^2 of the column;
-//   warps 4-7  epilogue: thread = tensor-memory lane = tile column; read the accumulator in 16-column
-//              pieces, store W, sum w^2;
+//   warps 4-7  epilogue: thread = tensor-memory lane = tile column; add each segment's accumulator
+//              (16-column pieces) into W, and after the last one sum w^2;
 //   warp 8     one lane issues the TMA copies (X chunk, U head and tail chunk);
 //   warp 9     allocates tensor memory; one lane issues the MMAs, committing each chunk to the
-//              barriers that free its A and B slots, and each item to the accumulator barrier (two
-//              accumulators, so the MMAs of item k+1 overlap the epilogue of item k).
+//              barriers that free its A and B slots, and each segment to its accumulator's barrier
+//              (two accumulators, so the MMAs of one segment overlap the epilogue of the previous).
 // Every wait is bounded in time (the limit is a launch argument); on expiry the waiting thread
 // raises a CTA-wide abort flag, every role leaves its loop, the MMA lane waits for the MMAs it
 // issued and the producer for its copies in flight, tensor memory is freed and `status` records the
@@ -47,6 +51,7 @@ constexpr int kProducerWarp = kConvWarps + kEpiWarps, kMmaWarp = kProducerWarp +
 constexpr int kThreads = (kMmaWarp + 1) * 32;
 constexpr uint32_t kRawBytes = kChunk * kTile * 4;  // 16 KB
 constexpr uint32_t kABytes = kTile * kChunk * 4;    // 16 KB per half (head or tail)
+constexpr int kSeg = 8;      // chunks accumulated in tensor memory before the epilogue takes them
 
 // ring depths per N tile (dynamic shared memory stays within 227 KB)
 template <int NT>
@@ -54,9 +59,7 @@ struct Cfg;
 template <>
 struct Cfg<64> { static constexpr int raw = 4, a = 2, b = 3; };
 template <>
-struct Cfg<128> { static constexpr int raw = 3, a = 2, b = 2; };
-template <>
-struct Cfg<256> { static constexpr int raw = 2, a = 2, b = 2; };
+struct Cfg<128> { static constexpr int raw = 3, a = 2, b = 3; };
 
 template <int NT>
 constexpr size_t smem_bytes() {
@@ -94,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t raw_full[RAW], raw_empty[RAW];
   __shared__ __align__(8) uint64_t a_full[AST], a_empty[AST];
   __shared__ __align__(8) uint64_t b_full[BST], b_empty[BST];
-  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
+  __shared__ __align__(8) uint64_t seg_full[2], seg_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -113,8 +116,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&b_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], kEpiWarps);
+      mbar_init(&seg_full[s], 1);
+      mbar_init(&seg_empty[s], kEpiWarps);
     }
     mbar_init(&mma_done, 1);
     abort_flag = 0;
@@ -169,18 +172,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (wid == kMmaWarp) {
     if (lane == 0) {
-      int64_t g = 0;
-      int it = 0;
+      int64_t g = 0, sg = 0;  // chunks and segments issued
       bool ok = true;
-      for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x, ++it) {
+      for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
         const int j = (int)(q % a.nj);
         const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);  // MMA N of this item
         const uint32_t idesc = tf32_idesc(kTile, nN);
-        const int acc = it & 1;
-        if (it >= 2 && !wait_bounded(&acc_empty[acc], (uint32_t)(((it >> 1) - 1) & 1), &abort_flag, lim)) break;
-        fence_after();
-        const uint32_t d = tmem + (uint32_t)(acc * NT);
+        uint32_t d = 0;
         for (int c = 0; c < a.nch; ++c, ++g) {
+          const int cs = c % kSeg;  // chunk within its segment
+          if (cs == 0) {
+            const int p = (int)(sg & 1);
+            if (sg >= 2 && !wait_bounded(&seg_empty[p], (uint32_t)(((sg >> 1) - 1) & 1), &abort_flag, lim)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            d = tmem + (uint32_t)(p * NT);
+          }
           const int qa = (int)(g % AST), sb = (int)(g % BST);
           if (!wait_bounded(&a_full[qa], (uint32_t)((g / AST) & 1), &abort_flag, lim) ||
               !wait_bounded(&b_full[sb], (uint32_t)((g / BST) & 1), &abort_flag, lim)) {
@@ -196,14 +205,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kk = 0; kk < kChunk / 8; ++kk) {
             if (kk >= nk) break;
             const uint32_t ko = (uint32_t)kk * 32;  // 8 TF32 values of K
-            mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (c | kk) != 0);
+            mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
             mma_tf32(d, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, 1);
             mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
           }
           mma_commit(&a_empty[qa]);  // these slots are free once the MMAs above have read them
           mma_commit(&b_empty[sb]);
+          if (cs == kSeg - 1 || c == a.nch - 1) {
+            mma_commit(&seg_full[sg & 1]);  // the segment's accumulator is complete
+            ++sg;
+          }
         }
-        if (ok) mma_commit(&acc_full[acc]);
       }
       // every MMA issued has completed before tensor memory is released
       mma_commit(&mma_done);
@@ -267,38 +279,50 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (wid < kProducerWarp) {
-    // epilogue: thread = tensor-memory lane = tile column
+    // epilogue: thread = tensor-memory lane = tile column.  Each segment's accumulator is added into
+    // this column's outputs in W (the first segment stores, later ones load, add and store: the
+    // tile stays in L2 and every value is touched by this thread only); the last one also sums w^2.
     const int ew = wid - kConvWarps;
-    int it = 0;
-    for (int64_t q = blockIdx.x; q < nitems; q += gridDim.x, ++it) {
+    const int nseg = (a.nch + kSeg - 1) / kSeg;
+    int64_t sg = 0;
+    bool ok = true;
+    for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
       const int j = (int)(q % a.nj);
       const int t = (int)((q / a.nj) % a.tpo);
       const int z = (int)(q / ((int64_t)a.nj * a.tpo));
       const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);
-      const int acc = it & 1;
-      if (!__all_sync(0xffffffffu, wait_bounded(&acc_full[acc], (uint32_t)((it >> 1) & 1), &abort_flag, lim)))
-        break;
-      fence_after();
       const int64_t l = (int64_t)t * kTile + ew * 32 + lane;
-      const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(acc * NT);
       float* Wz = a.W + (int64_t)z * a.r * a.L + l;
       float w2 = 0.0f;
-      for (int p = 0; p < nN / 16; ++p) {
-        float v[16];
-        tmem_ld16(taddr + (uint32_t)(16 * p), v);
-        tmem_wait_ld();
-        const int a0 = j * NT + 16 * p;
+      for (int s = 0; s < nseg; ++s, ++sg) {
+        const int p = (int)(sg & 1);
+        if (!__all_sync(0xffffffffu, wait_bounded(&seg_full[p], (uint32_t)((sg >> 1) & 1), &abort_flag, lim))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(p * NT);
+        const bool last = s == nseg - 1;
+        for (int pc = 0; pc < nN / 16; ++pc) {
+          float v[16];
+          tmem_ld16(taddr + (uint32_t)(16 * pc), v);
+          tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          if (a0 + e < a.r) {
-            w2 = fmaf(v[e], v[e], w2);
-            if (l < a.L) Wz[(int64_t)(a0 + e) * a.L] = v[e];
+          for (int e = 0; e < 16; ++e) {
+            const int ai = j * NT + pc * 16 + e;
+            if (ai < a.r && l < a.L) {
+              float* w = Wz + (int64_t)ai * a.L;
+              const float x = s == 0 ? v[e] : *w + v[e];
+              *w = x;
+              if (last) w2 = fmaf(x, x, w2);
+            }
           }
         }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&seg_empty[p]);
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+      if (!ok) break;
       if (a.part_w) {
         double s = (double)w2;
 #pragma unroll
@@ -358,11 +382,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-int pick_nt(int r) {
-  if (r <= 64) return 64;
-  if (r <= 128) return 128;
-  return 256;
-}
+int pick_nt(int r) { return r <= 64 ? 64 : 128; }
 
 std::atomic<unsigned long long> g_wait_ns{2000000000ull};
 std::atomic<long long> g_drop_chunk{-1};
@@ -452,11 +472,8 @@ int64_t tc_proj_part_elems(int b, int64_t L, int64_t r) {
 cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
                            int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
                            int* status, cudaStream_t st) {
-  switch (pick_nt(r)) {
-    case 64: return run<64>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
-    case 128: return run<128>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
-    default: return run<256>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
-  }
+  if (pick_nt(r) == 64) return run<64>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
+  return run<128>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
 }
 
 void tc_set_wait_ns(unsigned long long ns) { g_wait_ns.store(ns ? ns : 2000000000ull); }

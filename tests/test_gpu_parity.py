@@ -377,7 +377,7 @@ def test_projection_kernel_shapes(T, ranks):
     Y = o.expand(C) + 0.05 * rng.normal(size=(3,) + dims)
     last = np.zeros((1, ranks[len(dims)]))
     c_o, rho2, y2 = o.errors(Y)
-    for precision, tol_c, tol_e in (("fp64", 1e-12, 1e-10), ("fp32", 2e-6, 2e-5)):
+    for precision, tol_c, tol_e in (("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-3)):
         g = T.TTICE(dims, 0.1, precision=precision, input_dtype=torch.float32, max_batch=4, max_rank=512)
         g.load(ranks[:len(dims) + 1], cores, last)
         Yd = torch.tensor(Y, dtype=torch.float32).cuda()
