@@ -1,14 +1,21 @@
 #!/usr/bin/env python
 """TT-ICE* increment-update throughput on one GB300 (and N independent replicas under torchrun).
 
-Workload (the video-shaped stream): frames of 480x640x3 moving Gaussian blobs (12 blobs, sigma
-8-40 px, per-channel amplitude U(0,1), linear trajectories reflected at the borders, N(0, 0.01^2)
-pixel noise) viewed as the 5-way tensor 20x24x20x32x3, FP32 input, eps = 0.1, increments of 8
-frames.  A step is one TT-ICE* update of one increment through the whole path (first pass with
-per-observation errors, skip test, subselection, per-core residual / Gram / truncated eigen-solve /
-CGS2 / append / padding, final projection and last-core append).  The stream is consumed in order:
-W warm-up increments, then K timed increments, each a fresh 29.5 MB slice of a pre-generated stream
-of (W + K) x 29.5 MB, so no timed step reads input that an earlier step left in L2.
+Headline workload (the large video stream): frames of 1080x1920x3 moving Gaussian blobs (40 blobs,
+sigma 8-40 px, per-channel amplitude U(0,1), linear trajectories reflected at the borders, a new
+scene every 500 frames, N(0, 0.01^2) pixel noise) viewed as the 5-way tensor 27x40x48x40x3, FP32
+input, eps = 0.05, increments of 32 frames (796 MB each).  A step is one TT-ICE* update of one
+increment through the whole path (first pass with per-observation errors, skip test, subselection,
+per-core residual / Gram / truncated eigen-solve / CGS2 / append / padding, final projection and
+last-core append).  The stream is consumed in order: W warm-up increments, then K timed increments,
+each a fresh slice of a stream pre-generated in device memory (inputs larger than L2).
+
+Side legs, reported in the same line: the end-to-end rate from pinned host memory (`e2e`), the
+128^3 x 4 simulation-shaped stream at eps 0.05 and 0.01 timed in its skip regime (`flow`), the
+480x640x3 video stream with the plain FP64 GPU path beside the mixed one (`video_480p`), projection
+of unseen frames (`project`), the paper's heuristics against the exact defaults (`paper_variants`),
+the many-stream serving loop (`serving`), and the FP64 CPU oracle on a bounded sample
+(`cpu_baseline`).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
 """
@@ -27,35 +34,63 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DIMS = (20, 24, 20, 32, 3)
-EPS = 0.1
-WORKLOAD = "video 480x640x3 as 20x24x20x32x3, fp32 input, eps=0.1, 12 blobs, noise 0.01"
+DIMS = (27, 40, 48, 40, 3)
+EPS = 0.05
+BATCH = 32
+WORKLOAD = ("video 1080x1920x3 as 27x40x48x40x3, fp32 input, eps=0.05, 40 blobs (sigma 8-40 px), "
+            "noise 0.01, new scene every 500 frames, increments of 32 frames")
 METRIC = "increment elements/s"
+V480 = (20, 24, 20, 32, 3)
+
+# Unit each phase of an update runs on, for the roofline of the dominant phase: the algorithmic
+# flops of a phase are held against the peak of that unit, its algorithmic bytes against HBM.
+PHASE_UNIT = {"k1_stage1": "tf32", "chain": "tf32", "final": "tf32", "d_project": "tf32",
+              "residual": "fp32", "gram": "fp32", "eig": "fp32", "orth_append": "fp64"}
 
 
-# DRAM bytes (read + write) of one first-pass launch (k1_tc_kernel, 8 frames of this workload) from
-# the ncu capture summarised in profiles/, valid for the kernel source with this SHA-1; reported as
-# the roofline's `traffic` only while that source file is unchanged.
-K1_TRAFFIC = {"file": "k1_tc.cu", "sha1": "c62fd6edf3548fdc8d64535d88aa5b0758e9e67e", "bytes": 29539840 + 91904}
+def frames_1080(t0: int, n: int, seed: int = 1004, device="cuda"):
+    import torch
+
+    from tt_streams import blob_video
+
+    return blob_video(t0, n, height=1080, width=1920, n_blobs=40, view=DIMS, scene_len=500, noise_std=0.01,
+                      seed=seed, device=device, compute_dtype=torch.float32 if device != "cpu" else torch.float64)
 
 
-def _k1_traffic():
-    import hashlib
-
-    try:
-        with open(os.path.join(ROOT, "paper_2211_12487_gb300", "csrc", K1_TRAFFIC["file"]), "rb") as f:
-            h = hashlib.sha1(f.read()).hexdigest()
-    except OSError:
-        return None
-    return K1_TRAFFIC["bytes"] if K1_TRAFFIC["sha1"] == h else None
-
-
-def _peaks():
+def _peaks_file():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"])}, "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def measure_matmul_peaks():
+    """Dense matmul throughput of the GPU's FP64, FP32 and TF32 units (cuBLAS through torch, square
+    operands, a few repetitions after warm-up): the compute peaks the rooflines of the FP64 and
+    FP32 SIMT phases and of the TF32 tensor-core phases are held against."""
+    import torch
+
+    out = {}
+    for name, dt, tf32, n, reps in (("fp64", torch.float64, False, 4096, 3), ("fp32", torch.float32, False, 8192, 4),
+                                    ("tf32", torch.float32, True, 8192, 10)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dt)
+        b = torch.randn(n, n, device="cuda", dtype=dt)
+        a @ b
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_tflops"] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    torch.cuda.empty_cache()
+    return out
 
 
 class ClockSampler:
@@ -106,7 +141,7 @@ class ClockSampler:
 def replica_seed(rank: int) -> int:
     """Seed of the stream replica `rank` runs (independent streams: weak scaling, no collective on
     the data path)."""
-    return 1001 + 7919 * rank
+    return 1004 + 7919 * rank
 
 
 def max_over_ranks(x: float, ws: int, device) -> float:
@@ -132,38 +167,309 @@ def _dist():
     return ws, rank, local
 
 
-def oracle_elements_per_s(budget_s: float, batch: int):
-    """The FP64 CPU oracle on the leading increments of the same stream (bounded sample)."""
+def percentile(vals, q):
+    v = sorted(vals)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))] if v else None
+
+
+# ---------------------------------------------------------------- handles and streams
+def headline_handle(T, precision: str, n_inc: int):
+    """A handle for the 1080p stream with rank capacities for n_inc increments of 32 frames: the
+    stream's pixel noise is ~9% of its energy against the 5% target, so TT-ICE keeps most of it and
+    core 3 gains ~3300 directions per increment up to r_2 n_3 (<= 51840), core 4 ~90 per increment.
+    Capacities are raised before the stream starts, so no timed step pays for a growth."""
     import torch
 
-    from oracle.ttice_oracle import TTICEOracle
+    h = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=BATCH, max_rank=1024,
+                obs_reserve=BATCH * n_inc)
+    h.reserve_rank(2, 1080)
+    h.reserve_rank(3, min(51840, 4096 * math.ceil(n_inc * 3840 / 4096)))
+    h.reserve_rank(4, 256 * math.ceil(max(1024, 100 * n_inc) / 256))
+    return h
+
+
+def update_growing(T, h, Y, stream=None):
+    """ttice_update; an update that needs a rank above its capacity grows it (doubling) and is
+    repeated (a failed update leaves the decomposition as it was).  Returns (stats, growths)."""
+    grows = 0
+    while True:
+        try:
+            return h.update(Y, stream=stream), grows
+        except T.TTICEError as e:
+            if e.code != T.TTICE_ECAPACITY:
+                raise
+            k, need = h.capacity_miss()
+            if k == 0:
+                raise
+            h.reserve_rank(k, max(need, 2 * h.capacities()[k]))
+            grows += 1
+
+
+def phase_roofline(prof, name, peaks, peak_kind, live):
+    """Roofline of one phase over the timed updates: its algorithmic bytes against HBM and its
+    algorithmic flops against the peak of the unit it runs on; the bound is whichever gives the
+    longer lower bound on its time."""
+    ph = prof[name]
+    if not ph["count"] or ph["ms"] <= 0:
+        return None
+    t = ph["ms"] / 1e3
+    unit = PHASE_UNIT[name]
+    p_flops = live[unit + "_tflops"] * 1e12
+    p_bytes = peaks["hbm_gbs"] * 1e9
+    if ph["bytes"] / p_bytes >= ph["flops"] / p_flops:
+        ach = ph["bytes"] / t / 1e9
+        return {"bound": "hbm", "phase": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                "bytes_per_launch": ph["bytes"] / ph["count"], "avg_launch_ms": ph["ms"] / ph["count"]}
+    ach = ph["flops"] / t / 1e12
+    return {"bound": "tensor" if unit == "tf32" else "alu", "phase": name, "unit_kind": unit, "achieved": ach,
+            "peak": live[unit + "_tflops"], "unit": "TFLOP/s", "frac": ach / live[unit + "_tflops"],
+            "peak_kind": "measured live (cuBLAS " + unit + " matmul)",
+            "flops_per_launch": ph["flops"] / ph["count"], "avg_launch_ms": ph["ms"] / ph["count"]}
+
+
+def run_headline(T, args, dev, seed, precision):
+    """W warm-up and K timed updates of the 1080p stream from device-resident input."""
+    import torch
+
+    b, W, K = BATCH, args.warmup, args.steps
+    Y = torch.empty(((W + K) * b,) + DIMS, dtype=torch.float32, device=dev)
+    for k in range(0, (W + K) * b, b):
+        Y[k:k + b] = frames_1080(k, b, seed=seed)
+    torch.cuda.synchronize()
+    h = headline_handle(T, precision, W + K)
+    grows = 0
+    for k in range(W):
+        _, g = update_growing(T, h, Y[k * b:(k + 1) * b])
+        grows += g
+    h.profile(True)
+    st = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    l0 = T.ttice_kernel_launches()
+    torch.cuda.synchronize()
+    evs[0].record(st)
+    steps = []
+    for k in range(K):
+        i = W + k
+        s, g = update_growing(T, h, Y[i * b:(i + 1) * b])
+        grows += g
+        evs[k + 1].record(st)
+        steps.append({"skipped": int(s.skipped), "n_selected": s.n_selected, "ranks": list(s.ranks[:len(DIMS) + 2]),
+                      "new_dirs": list(s.new_dirs[:len(DIMS)]), "krylov": s.krylov_solves,
+                      "krylov_fallbacks": s.krylov_fallbacks, "rel_err_before": s.rel_err_before})
+    torch.cuda.synchronize()
+    launches = T.ttice_kernel_launches() - l0
+    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
+    total = evs[0].elapsed_time(evs[-1])
+    prof = h.profile_read()
+    out = {"total_ms": total, "lat": lat, "steps": steps, "prof": prof, "launches": launches, "grows": grows,
+           "core_elems": int(h.stats().core_elems), "n_obs": int(h.stats().n_obs),
+           "device_gb": h.device_bytes() / 1e9}
+    h.close()
+    del Y
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_e2e(T, args, dev, seed, precision):
+    """The same stream through the public API from pinned host memory: each step copies its increment
+    host -> device, updates, and reads its rows of the last core back, all inside the timed region."""
+    import torch
+
+    b, W, K = BATCH, args.warmup, args.steps
+    Yh = torch.empty(((W + K) * b,) + DIMS, dtype=torch.float32).pin_memory()
+    for k in range(0, (W + K) * b, b):
+        Yh[k:k + b] = frames_1080(k, b, seed=seed).cpu()
+    h = headline_handle(T, precision, W + K)
+    buf = torch.empty((b,) + DIMS, dtype=torch.float32, device=dev)
+    for k in range(W):
+        buf.copy_(Yh[k * b:(k + 1) * b], non_blocking=True)
+        update_growing(T, h, buf)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for k in range(K):
+        i = W + k
+        buf.copy_(Yh[i * b:(i + 1) * b], non_blocking=True)
+        update_growing(T, h, buf)
+        rows = h.last_core()[-b:]  # the step's result: its coefficient rows of the last core
+        d2h += rows.nbytes
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h.close()
+    torch.cuda.empty_cache()
+    return dt, b * math.prod(DIMS) * 4, int(d2h / K)
+
+
+def run_flow(T, eps: float, warmup: int, steps: int, b: int = 16, seed: int = 1002):
+    """The simulation-shaped stream (128^3 grid x 4 fields, 64 Fourier modes per field, |k|^(-5/3)
+    amplitudes, advected at (0.3, 0.1, 0.2) cells/snapshot), FP32, batches of b: `warmup` increments
+    generated on the fly (the stream reaches its skip regime after ~80), then `steps` timed ones from
+    a pre-generated device buffer.  Skip-path steps (one read of the 537 MB batch and the chain of
+    projections) are reported apart from updating ones, each against the roofline of its
+    algorithmic bytes (HBM) and flops (TF32 tensor peak)."""
+    import torch
+
+    from tt_streams import fourier_flow
+
+    dims = (128, 128, 128, 4)
+    h = T.TTICE(dims, eps, precision="fp32", input_dtype=torch.float32, max_batch=b, max_rank=1024)
+    t0 = time.perf_counter()
+    for k in range(warmup):
+        update_growing(T, h, fourier_flow(k * b, b, seed=seed, device="cuda"))
+    warm_s = time.perf_counter() - t0
+    Y = torch.empty((steps * b,) + dims, dtype=torch.float32, device="cuda")
+    for k in range(steps):
+        Y[k * b:(k + 1) * b] = fourier_flow((warmup + k) * b, b, seed=seed, device="cuda")
+    h.profile(True)
+    st = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(st)
+    flags = []
+    for k in range(steps):
+        s, _ = update_growing(T, h, Y[k * b:(k + 1) * b])
+        flags.append(bool(s.skipped))
+        evs[k + 1].record(st)
+    torch.cuda.synchronize()
+    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    total = evs[0].elapsed_time(evs[-1])
+    ranks = h.ranks()
+    prof = h.profile_read()
+    h.close()
+    del Y
+    torch.cuda.empty_cache()
+    n_el = b * math.prod(dims)
+    skip = [x for x, f in zip(lat, flags) if f]
+    upd = [x for x, f in zip(lat, flags) if not f]
+    # algorithmic amounts of a skip step: the first pass and the chain (Sec. 8(d) with u = 0)
+    k1, ch = prof["k1_stage1"], prof["chain"]
+    cnt = max(k1["count"], 1)
+    skip_bytes = (k1["bytes"] + ch["bytes"]) / cnt
+    skip_flops = (k1["flops"] + ch["flops"]) / cnt
+    out = {"workload": f"flow 128^3 x 4 (4-way 128x128x128x4), fp32 input, eps={eps}, 64 modes/field, batches of {b}",
+           "warmup_increments": warmup, "warmup_s": warm_s, "steps": steps, "value": steps * n_el / (total / 1e3),
+           "unit": "elements/s", "ms_per_step": total / steps,
+           "latency_ms": {"p50": statistics.median(lat), "p99": percentile(lat, 0.99)},
+           "skipped": len(skip), "final_ranks": ranks,
+           "skip_path_ms": {"p50": statistics.median(skip), "min": min(skip)} if skip else None,
+           "update_path_ms": {"p50": statistics.median(upd), "max": max(upd)} if upd else None,
+           "skip_step_bytes": skip_bytes, "skip_step_flops": skip_flops, "prof": prof}
+    return out
+
+
+def run_video480(T, args, precision: str, steps: int, warmup: int = 5, b: int = 8, seed: int = 1001):
+    """The 480x640x3 video stream (12 blobs, eps = 0.1, increments of 8 frames), timed after warm-up."""
+    import torch
+
     from tt_streams import blob_video
 
-    o = TTICEOracle(DIMS, EPS)
-    n_el = 0
-    t_busy = 0.0
-    k = 0
-    while t_busy < budget_s and k < 64:
-        Y = blob_video(k * batch, batch).double().numpy()
-        t = time.perf_counter()
-        o.update(Y)
-        t_busy += time.perf_counter() - t
-        n_el += Y.size
-        k += 1
-    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
-    return n_el / t_busy, k, t_busy, int(threads)
+    n = warmup + steps
+    Y = torch.empty((n * b,) + V480, dtype=torch.float32, device="cuda")
+    for k in range(0, n * b, 64):
+        c = min(64, n * b - k)
+        Y[k:k + c] = blob_video(k, c, seed=seed, device="cuda")
+    h = T.TTICE(V480, 0.1, precision=precision, input_dtype=torch.float32, max_batch=b, max_rank=512)
+    for k in range(warmup):
+        update_growing(T, h, Y[k * b:(k + 1) * b])
+    h.profile(True)
+    st = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(st)
+    for k in range(steps):
+        i = warmup + k
+        update_growing(T, h, Y[i * b:(i + 1) * b])
+        evs[k + 1].record(st)
+    torch.cuda.synchronize()
+    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    total = evs[0].elapsed_time(evs[-1])
+    rk = h.ranks()
+    built = {"ranks": rk[:len(V480) + 1], "cores": [h.core(i) for i in range(1, len(V480) + 1)],
+             "last": h.last_core()}
+    prof = h.profile_read()
+    h.close()
+    return {"precision": precision, "steps": steps, "value": steps * b * math.prod(V480) / (total / 1e3),
+            "unit": "elements/s", "ms_per_step": total / steps,
+            "latency_ms": {"p50": statistics.median(lat), "p99": percentile(lat, 0.99)},
+            "final_ranks": rk, "prof": prof}, built, Y
+
+
+def run_project(T, built: dict, batches: int, b: int = 32, seed: int = 1001):
+    """Projection of unseen frames onto the cores the 480p stream built (Algorithm 2 'project'; the
+    relative prediction error workload of Sec. 5.1): `batches` calls of ttice_project on b frames
+    each, frames 100000 onwards of the same generator, after 3 untimed calls."""
+    import torch
+
+    from tt_streams import blob_video
+
+    N = math.prod(V480)
+    hp = T.TTICE(V480, 0.1, precision="fp32", input_dtype=torch.float32, max_batch=b)
+    hp.load(built["ranks"], built["cores"], built["last"])
+    Z = torch.empty((batches * b,) + V480, dtype=torch.float32, device="cuda")
+    for k in range(0, batches * b, 64):
+        c = min(64, batches * b - k)
+        Z[k:k + c] = blob_video(100000 + k, c, seed=seed, device="cuda")
+    rd = built["ranks"][len(V480)]
+    coeffs = torch.empty((b, max(rd, 1)), dtype=torch.float64, device="cuda")
+    rel = torch.empty((batches, b), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    for k in range(3):
+        T.ttice_project(hp.h, Z[k * b:(k + 1) * b], coeffs, rel[k], st)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(batches + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(st)
+    for k in range(batches):
+        T.ttice_project(hp.h, Z[k * b:(k + 1) * b], coeffs, rel[k], st)
+        evs[k + 1].record(st)
+    torch.cuda.synchronize()
+    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(batches)]
+    total = evs[0].elapsed_time(evs[-1])
+    hp.close()
+    r = rel.cpu()
+    return {"workload": f"ttice_project of unseen 480p frames, {b} per call, onto ranks {built['ranks']}",
+            "calls": batches, "value": batches * b * N / (total / 1e3), "unit": "elements/s",
+            "ms_per_call": total / batches, "p50_ms": statistics.median(lat),
+            "rel_err_mean": float(r.mean()), "rel_err_max": float(r.max())}
+
+
+def run_variants(T, Y, steps: int, b: int = 8):
+    """The 480p stream run twice from empty cores: with the exact defaults (skip on the batch error
+    of Eq. 20, eps_upd of Eq. 18, tau = 1) and with the paper's heuristics (skip on mean(eps_Y), eps_upd
+    of Eq. 19, occupancy tau = 0.8), reconstructing every increment: the rate at which each exceeds
+    eps, with the time and core sizes the heuristics save."""
+    import torch
+
+    out = {}
+    for name, kw in (("exact", {}), ("paper", {"skip_mode": "mean", "eps_upd": "approx", "tau": 0.8})):
+        h = T.TTICE(V480, 0.1, precision="fp32", input_dtype=torch.float32, max_batch=b, **kw)
+        errs, skipped, ms = [], 0, 0.0
+        for k in range(steps):
+            Yk = Y[k * b:(k + 1) * b]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st, _ = update_growing(T, h, Yk)
+            e1.record()
+            rec = h.reconstruct(k * b, b, dtype=torch.float64)
+            errs.append(float((Yk.double() - rec).reshape(-1).norm() / Yk.double().reshape(-1).norm()))
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            skipped += int(st.skipped)
+        viol = [e for e in errs if e > 0.1 * (1 + 1e-9)]
+        out[name] = {"increments": steps, "skipped": skipped, "update_ms_total": ms, "eps_violations": len(viol),
+                     "violation_rate": len(viol) / steps, "max_rel_err": max(errs),
+                     "final_ranks": h.ranks(), "core_elems": int(h.stats().core_elems)}
+        h.close()
+    return out
 
 
 def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots: int = 16, seed: int = 1003,
                 drain_s: float = 60.0):
-    """Continuous batching over many streams (the serving workload): stream shapes drawn from
-    {16^4 cosine stream, the 20x24x20x32x3 video view, 64^3 x 4 flow, 32^4 cosine stream}, batch
-    sizes from {1, 4, 16, 32}, eps from {0.05, 0.1, 0.3}; Poisson arrivals over all streams for
-    `seconds` at each rate in `rates` (a nominal load, then a saturating one), the streams continuing
-    from one phase to the next.  Each stream cycles through a pool of pre-generated device-resident
-    increments (at most ~192 MB per stream), so later requests of a stream are mostly represented
-    already and take the skip path.  Latency = arrival -> completion of the update.  Requests still
-    queued `drain_s` after the last arrival are dropped and counted."""
+    """Continuous batching over many streams: shapes drawn from {16^4 cosine stream, the 480p video
+    view, 64^3 x 4 flow, 32^4 cosine stream}, batch sizes from {1, 4, 16, 32}, eps from {0.05, 0.1,
+    0.3}; Poisson arrivals over all streams for `seconds` at each rate in `rates`.  Each stream cycles
+    through a pool of pre-generated device-resident increments, so later requests of a stream are
+    mostly represented already and take the skip path.  Latency = arrival -> completion."""
     import collections
     import random
 
@@ -173,8 +479,7 @@ def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots:
     from tt_streams import blob_video, cp_cosine, fourier_flow
 
     rng = random.Random(seed)
-    kinds = [("cosine16", (16, 16, 16, 16)), ("video", DIMS), ("flow64", (64, 64, 64, 4)),
-             ("cosine32", (32, 32, 32, 32))]
+    kinds = [("cosine16", (16, 16, 16, 16)), ("video", V480), ("flow64", (64, 64, 64, 4)), ("cosine32", (32, 32, 32, 32))]
     specs, pools = [], {}
     for i in range(n_streams):
         kind, dims = kinds[rng.randrange(len(kinds))]
@@ -196,7 +501,6 @@ def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots:
     eng = S.ServingEngine(specs, slots=slots)
     phases = []
     try:
-        # warm-up: one increment per stream (creates every handle, first update from empty cores)
         for sp in specs:
             eng.submit(S.Request(sp.name, pools[sp.name][0]))
         eng.drain(timeout=600)
@@ -206,8 +510,7 @@ def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots:
                 eng.completed.clear()
             t0 = time.perf_counter()
             t_next = t0
-            n_sub = 0
-            elements = 0
+            n_sub, elements = 0, 0
             while True:
                 t_next += rng.expovariate(rate)
                 if t_next - t0 > seconds:
@@ -226,7 +529,7 @@ def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots:
             wall = time.perf_counter() - t0
             with eng.lock:
                 done = list(eng.completed)
-            if not ok:  # drop what is still queued so that the next phase starts empty
+            if not ok:
                 with eng.lock:
                     for dq in eng.pending.values():
                         dq.clear()
@@ -234,188 +537,50 @@ def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots:
             lat = sorted((r.done - r.arrival) * 1e3 for r in done if r.error is None)
             skipped = sum(1 for r in done if r.stats is not None and r.stats.skipped)
             errors = collections.Counter(str(r.error)[:80] for r in done if r.error is not None)
-            phases.append({"arrival_rate_per_s": rate, "seconds": seconds, "requests": n_sub,
-                           "completed": len(lat), "errors": dict(errors), "drained": ok,
-                           "dropped": n_sub - len(done), "skipped_fraction": skipped / max(len(done), 1),
+            phases.append({"arrival_rate_per_s": rate, "seconds": seconds, "requests": n_sub, "completed": len(lat),
+                           "errors": dict(errors), "drained": ok, "skipped_fraction": skipped / max(len(done), 1),
                            "p50_ms": S.percentile(lat, 0.50), "p99_ms": S.percentile(lat, 0.99),
-                           "throughput_elements_per_s": elements / wall,
-                           "throughput_updates_per_s": len(lat) / wall})
-        return {"streams": n_streams, "slots": slots, "phases": phases,
-                "capacity_grows": eng.grow_events, "device_gb": eng.mem_used / 1e9}
+                           "throughput_elements_per_s": elements / wall, "throughput_updates_per_s": len(lat) / wall})
+        return {"streams": n_streams, "slots": slots, "phases": phases, "capacity_grows": eng.grow_events,
+                "device_gb": eng.mem_used / 1e9}
     finally:
         eng.close(cancel_pending=True)
 
 
-def run_project(built: dict, precision: str, batches: int, b: int = 32, seed: int = 1001):
-    """Projection of unseen frames onto the cores the timed stream built (Algorithm 2 'project'; the
-    relative prediction error workload of Sec. 5.1): `batches` calls of ttice_project on b frames
-    each, frames 100000 onwards of the same generator, after 3 untimed calls.  The projection reads
-    each batch once and runs the chain, so it is reported against the HBM bound (input bytes read
-    once, the bare lower bound) beside the mean per-frame relative error."""
-    import torch
+def oracle_sample(frames: int = 1, seed: int = 1004):
+    """The FP64 CPU oracle on a bounded sample of the headline workload: the stream's first increment
+    of `frames` frames, from empty cores (one frame of the 1080p stream is ~10-20 s of CPU work)."""
+    from oracle.ttice_oracle import TTICEOracle
 
-    from paper_2211_12487_gb300 import ttice as T
-    from tt_streams import blob_video
-
-    N = math.prod(DIMS)
-    hp = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=b)
-    hp.load(built["ranks"], built["cores"], built["last"])
-    Z = torch.empty((batches * b,) + DIMS, dtype=torch.float32, device="cuda")
-    for k in range(0, batches * b, 64):
-        c = min(64, batches * b - k)
-        Z[k:k + c] = blob_video(100000 + k, c, seed=seed, device="cuda")
-    rd = built["ranks"][len(DIMS)]
-    coeffs = torch.empty((b, max(rd, 1)), dtype=torch.float64, device="cuda")
-    rel = torch.empty((batches, b), dtype=torch.float64, device="cuda")
-    st = torch.cuda.current_stream()
-    for k in range(3):
-        T.ttice_project(hp.h, Z[k * b:(k + 1) * b], coeffs, rel[k], st)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(batches + 1)]
-    torch.cuda.synchronize()
-    evs[0].record(st)
-    for k in range(batches):
-        T.ttice_project(hp.h, Z[k * b:(k + 1) * b], coeffs, rel[k], st)
-        evs[k + 1].record(st)
-    torch.cuda.synchronize()
-    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(batches)]
-    total = evs[0].elapsed_time(evs[-1])
-    hp.close()
-    peaks, kind = _peaks()
-    gbs = 4.0 * b * N / (total / batches / 1e3) / 1e9
-    r = rel.cpu()
-    return {"workload": f"ttice_project of unseen frames, {b} per call, onto ranks {built['ranks']}",
-            "batch": b, "calls": batches, "value": batches * b * N / (total / 1e3), "unit": "elements/s",
-            "ms_per_call": total / batches, "p50_ms": statistics.median(lat),
-            "rel_err_mean": float(r.mean()), "rel_err_max": float(r.max()),
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": gbs / peaks["hbm_gbs"], "bytes_per_call": 4.0 * b * N,
-                         "bytes": "input batch read once (the bare lower bound)", "peak_kind": kind}}
-
-
-def run_variants(Y, b: int, precision: str, steps: int):
-    """The stream run twice from empty cores: with the exact defaults (skip on the batch error of
-    Eq. 20, eps_upd of Eq. 18, tau = 1) and with the paper's heuristics (skip on mean(eps_Y), eps_upd
-    of Eq. 19, occupancy tau = 0.8).  After every increment the batch is reconstructed and its
-    relative error compared with eps: the defaults keep it within eps (Theorem 1 with the exact
-    decisions); the heuristics may exceed it, and the rate at which they do is reported with the
-    time and the core sizes they save."""
-    import torch
-
-    from paper_2211_12487_gb300 import ttice as T
-
-    out = {}
-    for name, kw in (("exact", {}), ("paper", {"skip_mode": "mean", "eps_upd": "approx", "tau": 0.8})):
-        h = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=b, **kw)
-        errs, skipped, ms = [], 0, 0.0
-        for k in range(steps):
-            Yk = Y[k * b:(k + 1) * b]
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            st = h.update(Yk)
-            e1.record()
-            rec = h.reconstruct(k * b, b, dtype=torch.float64)
-            d = (Yk.double() - rec).reshape(-1)
-            errs.append(float(d.norm() / Yk.double().reshape(-1).norm()))
-            torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
-            skipped += int(st.skipped)
-        viol = [e for e in errs if e > EPS * (1 + 1e-9)]
-        out[name] = {"increments": steps, "skipped": skipped, "update_ms_total": ms,
-                     "eps_violations": len(viol), "violation_rate": len(viol) / steps,
-                     "max_rel_err": max(errs), "mean_rel_err": sum(errs) / steps,
-                     "final_ranks": h.ranks(), "core_elems": int(h.stats().core_elems)}
-        h.close()
-    return out
-
-
-def run_flow(steps: int, warmup: int = 40, b: int = 16, eps: float = 0.05, seed: int = 1002):
-    """The simulation-shaped stream (128^3 grid, 4 fields: 4-way 128x128x128x4, FP32, 64 Fourier modes
-    per field with |k|^(-5/3) amplitudes advected at (0.3, 0.1, 0.2) cells/snapshot), batches of b,
-    eps, timed after `warmup` increments (the early ones grow core 2 to a Gram side of 4224 and cost up
-    to a second each).  Reports throughput, latency (skip-path increments, which read the 537 MB batch
-    once and run the chain, separately from updating ones), the first pass's own roofline, and the
-    update's fraction of the HBM roofline (input bytes / step time against the measured copy
-    bandwidth)."""
-    import torch
-
-    from paper_2211_12487_gb300 import ttice as T
-    from tt_streams import fourier_flow
-
-    dims = (128, 128, 128, 4)
-    n = warmup + steps
-    Y = torch.empty((n * b,) + dims, dtype=torch.float32, device="cuda")
-    for k in range(0, n * b, b):
-        Y[k:k + b] = fourier_flow(k, b, seed=seed, device="cuda")
-    h = T.TTICE(dims, eps, precision="fp32", input_dtype=torch.float32, max_batch=b, max_rank=1024)
-    for k in range(warmup):
-        h.update(Y[k * b:(k + 1) * b])
-    h.profile(True)
-    st = torch.cuda.current_stream()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    torch.cuda.synchronize()
-    evs[0].record(st)
-    skip_flags = []
-    for k in range(steps):
-        i = warmup + k
-        s_ = h.update(Y[i * b:(i + 1) * b])
-        skip_flags.append(bool(s_.skipped))
-        evs[k + 1].record(st)
-    torch.cuda.synchronize()
-    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
-    total = evs[0].elapsed_time(evs[-1])
-    ranks = h.ranks()
-    prof = h.profile_read()
-    h.close()
-    del Y
-    torch.cuda.empty_cache()
-    peaks, kind = _peaks()
-    n_el = b * math.prod(dims)
-    gbs = 4.0 * n_el / (total / steps / 1e3) / 1e9
-    skip_lat = [x for x, f in zip(lat, skip_flags) if f]
-    upd_lat = [x for x, f in zip(lat, skip_flags) if not f]
-    k1 = prof["k1_stage1"]
-    k1_roof = None
-    if k1["count"]:
-        k1_gbs = k1["bytes"] / k1["count"] / (k1["ms"] / k1["count"] / 1e3) / 1e9
-        k1_roof = {"bound": "hbm", "kernel": "k1_stage1", "achieved": k1_gbs, "peak": peaks["hbm_gbs"],
-                   "unit": "GB/s", "frac": k1_gbs / peaks["hbm_gbs"], "peak_kind": kind,
-                   "bytes_per_launch": k1["bytes"] / k1["count"], "avg_launch_ms": k1["ms"] / k1["count"]}
-    return {"workload": "flow 128^3 x 4 (4-way 128x128x128x4), fp32 input, eps=0.05, 64 modes/field",
-            "batch": b, "steps": steps, "warmup": warmup, "value": steps * n_el / (total / 1e3),
-            "unit": "elements/s", "ms_per_step": total / steps,
-            "latency_ms": {"p50": statistics.median(lat), "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},
-            "skipped": len(skip_lat), "final_ranks": ranks,
-            "skip_path_ms": {"p50": statistics.median(skip_lat), "min": min(skip_lat)} if skip_lat else None,
-            "update_path_ms": {"p50": statistics.median(upd_lat)} if upd_lat else None,
-            "roofline_k1": k1_roof,
-            "roofline_step": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                              "frac": gbs / peaks["hbm_gbs"], "bytes_per_step": 4.0 * n_el,
-                              "bytes": "input batch read once (the bare lower bound)", "peak_kind": kind}}
+    Y = frames_1080(0, frames, seed=seed, device="cpu").double().numpy()
+    o = TTICEOracle(DIMS, EPS)
+    t = time.perf_counter()
+    o.update(Y)
+    busy = time.perf_counter() - t
+    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    return Y.size / busy, busy, int(threads)
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    budget = max(2.0, 25.0 / max(args.steps + args.warmup, 1))
-    vals = []
     for _ in range(args.warmup):
-        oracle_elements_per_s(budget / 4, args.batch)
+        oracle_sample()
+    vals = []
     t0 = time.perf_counter()
-    incs = 0
     for _ in range(args.steps):
-        v, k, busy, threads = oracle_elements_per_s(budget, args.batch)
+        v, busy, threads = oracle_sample()
         vals.append(v)
-        incs += k
     wall = time.perf_counter() - t0
     val = statistics.median(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "elements/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "batch": args.batch, "stream_prefix_increments": incs},
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": BATCH, "sample": "first increment of 1 frame, from empty cores"},
         "cpu_baseline": {"value": val, "unit": "elements/s", "cores": threads, "kind": "oracle",
-                         "sample": f"leading increments of {args.batch} frames per step, ~{budget:.0f} s of CPU work each"},
+                         "sample": "first increment of the stream, 1 frame (6.2e6 elements), from empty cores, per step"},
         "e2e": {"value": val, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -424,30 +589,19 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
-    ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--fp64-steps", type=int, default=12, help="steps of the FP64 path timed for comparison")
-    ap.add_argument("--cpu-budget", type=float, default=15.0,
-                    help="seconds of oracle work for cpu_baseline (0 leaves it out)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--flow-steps", type=int, default=16,
-                    help="timed steps of the 128^3 x 4 simulation-shaped stream reported under `flow` (0 leaves it out)")
-    ap.add_argument("--project-batches", type=int, default=16,
-                    help="timed ttice_project calls (32 unseen frames each) onto the built cores, reported "
-                         "under `project` (0 leaves it out)")
-    ap.add_argument("--variant-steps", type=int, default=44,
-                    help="increments of the stream run with the paper's heuristics (mean skip, Eq. 19, "
-                         "tau = 0.8) and with the exact defaults, reported under `paper_variants` (0 leaves it out)")
-    ap.add_argument("--flow-warmup", type=int, default=40,
-                    help="untimed increments of the flow stream before its timed ones")
-    ap.add_argument("--serving-seconds", type=float, default=2.0,
-                    help="length of the many-stream serving run reported under `serving` (0 leaves it out)")
-    ap.add_argument("--profile-window", action="store_true",
-                    help="open the CUDA profiler API (cudaProfilerStart/Stop) around the timed steps only, "
-                         "for ncu --profile-from-start off")
+    ap.add_argument("--cpu-frames", type=int, default=1, help="frames of the oracle's sample (0 leaves it out)")
+    ap.add_argument("--flow-steps", type=int, default=16, help="timed steps per flow leg (0 leaves them out)")
+    ap.add_argument("--flow-warmup", type=int, default=84, help="untimed flow increments before the timed ones")
+    ap.add_argument("--v480-steps", type=int, default=20, help="timed steps of the 480p video leg (0: out)")
+    ap.add_argument("--fp64-steps", type=int, default=8, help="timed steps of the FP64 path on the 480p leg")
+    ap.add_argument("--project-batches", type=int, default=16)
+    ap.add_argument("--variant-steps", type=int, default=24)
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -464,183 +618,114 @@ def main():
     dev = torch.device("cuda", local)
 
     from paper_2211_12487_gb300 import ttice as T
-    from tt_streams import blob_video
 
-    b = args.batch
-    n_inc = args.warmup + args.steps
-    N = math.prod(DIMS)
-    seed = replica_seed(rank)  # independent replicas per rank (weak scaling)
-    Y = torch.empty((n_inc * b,) + DIMS, dtype=torch.float32, device=dev)
-    for k in range(0, n_inc * b, 64):
-        c = min(64, n_inc * b - k)
-        Y[k:k + c] = blob_video(k, c, seed=seed, device=dev)
-    torch.cuda.synchronize()
+    seed = replica_seed(rank)
+    live = measure_matmul_peaks()
+    peaks, peak_kind = _peaks_file()
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    built = {}
-
-    def timed_run(precision: str, steps: int, profile: bool):
-        h = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=b, max_rank=512)
-        for k in range(args.warmup):
-            h.update(Y[k * b:(k + 1) * b])
-        if profile:
-            h.profile(True)
-        st = torch.cuda.current_stream()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-        l0 = T.ttice_kernel_launches()
-        barrier()
-        window = profile and args.profile_window
-        if window:
-            torch.cuda.profiler.start()
-        evs[0].record(st)
-        stats = []
-        for k in range(steps):
-            i = args.warmup + k
-            s = h.update(Y[i * b:(i + 1) * b])
-            evs[k + 1].record(st)
-            stats.append((s.skipped, s.n_selected, list(s.ranks[:len(DIMS) + 2]), s.krylov_solves,
-                          s.krylov_fallbacks, s.eig_sweep_limit))
-        barrier()
-        if window:
-            torch.cuda.profiler.stop()
-        launches = T.ttice_kernel_launches() - l0
-        lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
-        total = evs[0].elapsed_time(evs[-1])
-        prof = h.profile_read() if profile else None
-        if profile:  # the cores the stream built, for the projection leg
-            rk = h.ranks()
-            built.update(ranks=rk[:len(DIMS) + 1], cores=[h.core(i) for i in range(1, len(DIMS) + 1)],
-                         last=h.last_core())
-        h.close()
-        return total, lat, stats, prof, launches
-
+    barrier()
     with ClockSampler(local) as clk:
-        total_ms, lat, stats, prof, launches = timed_run(args.precision, args.steps, True)
-    total_ms = max_over_ranks(total_ms, ws, dev)
-    value = whole_job_rate(ws, args.steps * b * N, total_ms / 1e3)
+        hl = run_headline(T, args, dev, seed, args.precision)
+    barrier()
+    total_ms = max_over_ranks(hl["total_ms"], ws, dev)
+    N = math.prod(DIMS)
+    value = whole_job_rate(ws, args.steps * BATCH * N, total_ms / 1e3)
 
-    # FP64 path on the same stream (the plain FP64 GPU TT-ICE), shorter
-    fp64 = None
-    if args.precision != "fp64" and args.fp64_steps > 0:
-        k64 = min(args.fp64_steps, args.steps)
-        tot64, lat64, _, _, _ = timed_run("fp64", k64, False)
-        fp64 = {"value": k64 * b * N / (tot64 / 1e3), "unit": "elements/s", "steps": k64,
-                "ms_per_step": tot64 / k64, "p50_ms": statistics.median(lat64)}
-
-    # end-to-end through the public API from pinned host memory, with the result read back
     e2e = None
     if not args.no_e2e:
-        Yh = Y.cpu().pin_memory()
-        h = T.TTICE(DIMS, EPS, precision=args.precision, input_dtype=torch.float32, max_batch=b)
-        buf = torch.empty((b,) + DIMS, dtype=torch.float32, device=dev)
-        d2h = 0
-        for k in range(args.warmup):
-            buf.copy_(Yh[k * b:(k + 1) * b], non_blocking=True)
-            h.update(buf)
-        barrier()
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            i = args.warmup + k
-            buf.copy_(Yh[i * b:(i + 1) * b], non_blocking=True)
-            h.update(buf)
-            coeffs = h.last_core()[-b:]  # the step's result: its rows of the last core
-            d2h += coeffs.nbytes
-        barrier()
-        dt = time.perf_counter() - t0
-        e2e = {"value": whole_job_rate(ws, args.steps * b * N, max_over_ranks(dt, ws, dev)), "unit": "elements/s",
-               "h2d_bytes_per_step": b * N * 4, "d2h_bytes_per_step": int(d2h / args.steps)}
-        h.close()
+        dt, h2d, d2h = run_e2e(T, args, dev, seed, args.precision)
+        e2e = {"value": whole_job_rate(ws, args.steps * BATCH * N, max_over_ranks(dt, ws, dev)), "unit": "elements/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    project = None
-    if args.project_batches > 0 and rank == 0 and built:
-        try:
-            project = run_project(built, args.precision, args.project_batches, seed=seed)
-        except Exception as e:
-            project = {"error": f"{type(e).__name__}: {e}"}
-    variants = None
-    if args.variant_steps > 0 and rank == 0:
-        try:
-            variants = run_variants(Y, b, args.precision, min(args.variant_steps, n_inc))
-        except Exception as e:
-            variants = {"error": f"{type(e).__name__}: {e}"}
-
-    flow = None
-    if args.flow_steps > 0 and rank == 0:
-        try:
-            flow = run_flow(args.flow_steps, warmup=args.flow_warmup)
-        except Exception as e:
-            flow = {"error": f"{type(e).__name__}: {e}"}
-    serving = None
-    if args.serving_seconds > 0 and rank == 0:
-        try:
-            serving = run_serving(args.serving_seconds)
-        except Exception as e:  # reported in the line; the headline numbers above stand
-            serving = {"error": f"{type(e).__name__}: {e}"}
+    side = {}
+    if rank == 0:
+        for key, fn in (("flow", lambda: {f"eps_{e}": run_flow(T, e, args.flow_warmup, args.flow_steps)
+                                          for e in (0.05, 0.01)} if args.flow_steps > 0 else None),):
+            try:
+                side[key] = fn()
+            except Exception as e:
+                side[key] = {"error": f"{type(e).__name__}: {e}"}
+        if args.v480_steps > 0:
+            try:
+                mixed, built, Y480 = run_video480(T, args, "fp32", args.v480_steps)
+                fp64 = run_video480(T, args, "fp64", min(args.fp64_steps, args.v480_steps))[0] if args.fp64_steps > 0 else None
+                side["video_480p"] = {"workload": "video 480x640x3 as 20x24x20x32x3, fp32 input, eps=0.1, 12 blobs, "
+                                                  "noise 0.01, increments of 8 frames",
+                                      "mixed": {k: v for k, v in mixed.items() if k != "prof"},
+                                      "fp64_path": {k: v for k, v in fp64.items() if k != "prof"} if fp64 else None,
+                                      "roofline_k1": phase_roofline(mixed["prof"], "k1_stage1", peaks, peak_kind, live)}
+                if args.project_batches > 0:
+                    side["project"] = run_project(T, built, args.project_batches)
+                if args.variant_steps > 0:
+                    side["paper_variants"] = run_variants(T, Y480, min(args.variant_steps, Y480.shape[0] // 8))
+                del Y480
+                torch.cuda.empty_cache()
+            except Exception as e:
+                side["video_480p"] = {"error": f"{type(e).__name__}: {e}"}
+        if args.serving_seconds > 0:
+            try:
+                side["serving"] = run_serving(args.serving_seconds)
+            except Exception as e:
+                side["serving"] = {"error": f"{type(e).__name__}: {e}"}
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
 
-    peaks, peak_kind = _peaks()
-    # roofline of the dominant phase that has an algorithmic byte count
+    prof = hl["prof"]
     names = [k for k in prof if k != "updates"]
+    share = {n: round(prof[n]["ms"] / max(hl["total_ms"], 1e-9), 4) for n in names}
     dom = max(names, key=lambda n: prof[n]["ms"])
-    hbm_phases = {"k1_stage1", "chain", "final", "d_project", "residual"}
-    pick = "k1_stage1"
-    roof = None
-    ph = prof[pick]
-    if ph["count"] > 0 and ph["ms"] > 0:
-        per_launch_s = ph["ms"] / ph["count"] / 1e3
-        achieved = ph["bytes"] / ph["count"] / per_launch_s / 1e9
-        roof = {"bound": "hbm", "kernel": pick, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": _k1_traffic(),
-                "peak_kind": peak_kind, "bytes_per_launch": ph["bytes"] / ph["count"],
-                "avg_launch_ms": ph["ms"] / ph["count"]}
-    # the whole update against the same bound: algorithmic bytes of every phase per update / step time
-    step_bytes = sum(prof[n]["bytes"] for n in names) / max(prof["updates"], 1)
-    step_gbs = step_bytes / (total_ms / args.steps / 1e3) / 1e9
-    roof_step = {"bound": "hbm", "achieved": step_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "frac": step_gbs / peaks["hbm_gbs"], "bytes_per_step": step_bytes,
-                 "note": "latency-bound: the truncated eigen-solves dominate (see phase_share)"}
-    phase_share = {n: round(prof[n]["ms"] / max(total_ms, 1e-9), 4) for n in names}
+    roof = phase_roofline(prof, dom, peaks, peak_kind, live)
+    if roof is not None:
+        roof["traffic"] = None  # DRAM counters are taken from ncu captures (profiles/), not in this run
+    flow = side.get("flow")
+    if isinstance(flow, dict):
+        for key, leg in flow.items():
+            if not isinstance(leg, dict) or "prof" not in leg:
+                continue
+            p = leg.pop("prof")
+            leg["roofline_k1"] = phase_roofline(p, "k1_stage1", peaks, peak_kind, live)
+            if leg["skip_path_ms"]:
+                t = leg["skip_path_ms"]["p50"] / 1e3
+                t_roof = max(leg["skip_step_bytes"] / (peaks["hbm_gbs"] * 1e9), leg["skip_step_flops"] / (live["tf32_tflops"] * 1e12))
+                leg["roofline_skip_step"] = {"t_roof_ms": t_roof * 1e3, "t_ms": t * 1e3, "frac": t_roof / t,
+                                             "bytes": leg["skip_step_bytes"], "flops": leg["skip_step_flops"],
+                                             "rule": "max(algorithmic bytes / HBM, algorithmic flops / TF32 peak) / measured"}
     cpu = None
-    if (ws == 1 or rank == 0) and args.cpu_budget > 0:
-        v, k, busy, threads = oracle_elements_per_s(args.cpu_budget, b)
+    if args.cpu_frames > 0:
+        v, busy, threads = oracle_sample(args.cpu_frames, seed=seed)
         cpu = {"value": v, "unit": "elements/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {k} increments of {b} frames of the same stream ({busy:.1f} s CPU)"}
-    skipped = sum(1 for s in stats if s[0])
+               "sample": f"first increment of {args.cpu_frames} frame(s) of the same stream from empty cores ({busy:.1f} s CPU)"}
+    steps = hl["steps"]
     line = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch": b, "precision": args.precision,
-                   "l2": f"each step reads a fresh 29.5 MB slice of a {n_inc * b * N * 4 / 1e9:.2f} GB "
-                         "pre-generated stream (no timed step re-reads an earlier step's input)",
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": BATCH, "precision": args.precision,
+                   "l2": f"each step reads a fresh 796 MB increment of a {(args.warmup + args.steps) * BATCH * N * 4 / 1e9:.1f} GB "
+                         "pre-generated stream (inputs larger than L2)",
                    "parallelism": f"replicas{ws}"},
-        "latency_ms": {"p50": statistics.median(lat), "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
-                       "max": max(lat)},
-        "increments": {"timed": args.steps, "skipped": skipped, "final_ranks": stats[-1][2]},
-        "eigen_solves": {"krylov_certified": sum(x[3] for x in stats),
-                         "krylov_fallbacks": sum(x[4] for x in stats),
-                         "sweep_limit_hits": sum(x[5] for x in stats)},
+        "latency_ms": {"p50": statistics.median(hl["lat"]), "p99": percentile(hl["lat"], 0.99), "max": max(hl["lat"])},
+        "increments": {"timed": args.steps, "skipped": sum(s["skipped"] for s in steps),
+                       "final_ranks": steps[-1]["ranks"], "new_dirs_last": steps[-1]["new_dirs"],
+                       "core_elements": hl["core_elems"], "compression_ratio": hl["n_obs"] * N / max(hl["core_elems"], 1),
+                       "capacity_growths": hl["grows"], "device_gb": hl["device_gb"]},
         "roofline": roof,
-        "roofline_step": roof_step,
         "dominant_phase": dom,
-        "phase_share": phase_share,
-        "fp64_path": fp64,
-        "flow": flow,
-        "project": project,
-        "paper_variants": variants,
-        "serving": serving,
+        "phase_share": share,
+        "phase_roofline": {n: phase_roofline(prof, n, peaks, peak_kind, live) for n in names},
+        "peaks": {"hbm_gbs": peaks["hbm_gbs"], "bf16_tflops": peaks["bf16_tflops"], "kind": peak_kind, **live},
+        **side,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int(launches),
+        "gpu_launches": int(hl["launches"]),
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

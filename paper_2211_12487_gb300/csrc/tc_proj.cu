@@ -9,9 +9,11 @@
 // one N tile of NT output rows (MMA N, 64 or 128); K = m runs in chunks of 32 rows (one 128-byte
 // swizzle row of TF32).
 //
-// Arithmetic.  Each operand is split into a TF32 head and an FP32 tail (x_hi = tf32(x), x_lo =
-// x - x_hi, exact), and each K step issues A_hi B_hi + A_lo B_hi + A_hi B_lo (the dropped tail
-// product is ~2^-22 relative) into an FP32 accumulator in tensor memory.  The accumulator adds K
+// Arithmetic.  Each operand is split into a TF32 head and a TF32 tail (x_hi = tf32(x), x_lo =
+// tf32(x - x_hi), both rounded to nearest, so the MMA reads them exactly; x_hi + x_lo carries
+// ~2^-22 relative error), and each K step issues A_hi B_hi into a main accumulator and A_lo B_hi +
+// A_hi B_lo into a cross accumulator (the dropped tail product is ~2^-22 relative), FP32 in tensor
+// memory; the epilogue adds the two.  The accumulators add K
 // in segments of kSeg chunks (256 values of K): each segment starts a fresh accumulator, and the
 // epilogue adds the segments into W with FP32 round-to-nearest.  (Accumulating thousands of
 // K steps in one tensor-memory accumulator measurably biases W, ~1e-5 relative at K = 4096, against
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ CUtensorMap ulmap, const ProjArgs a) {
   constexpr int RAW = Cfg<NT>::raw, AST = Cfg<NT>::a, BST = Cfg<NT>::b;
   constexpr uint32_t kBBytes = NT * 128;  // one half of a B chunk: NT rows of 128 bytes
-  constexpr uint32_t kTmemCols = 2 * NT;
+  constexpr uint32_t kTmemCols = 4 * NT;  // two segment buffers, each a main and a cross accumulator
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             fence_after();
-            d = tmem + (uint32_t)(p * NT);
+            d = tmem + (uint32_t)(p * 2 * NT);
           }
           const int qa = (int)(g % AST), sb = (int)(g % BST);
           if (!wait_bounded(&a_full[qa], (uint32_t)((g / AST) & 1), &abort_flag, lim) ||
@@ -205,9 +207,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kk = 0; kk < kChunk / 8; ++kk) {
             if (kk >= nk) break;
             const uint32_t ko = (uint32_t)kk * 32;  // 8 TF32 values of K
+            // head x head into the main accumulator, the two tail products (~2^-11 of it) into the
+            // cross accumulator, so that the main one takes one add per K step
             mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
-            mma_tf32(d, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, 1);
-            mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
+            mma_tf32(d + NT, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
+            mma_tf32(d + NT, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
           }
           mma_commit(&a_empty[qa]);  // these slots are free once the MMAs above have read them
           mma_commit(&b_empty[sb]);
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const float y = kk < kv ? rw[kk * kTile + tid] : 0.0f;
               x2 = fmaf(y, y, x2);
               ph[e] = tf32_hi(y);
-              pl[e] = y - ph[e];
+              pl[e] = tf32_hi(y - ph[e]);  // the tail, itself rounded to TF32: the MMA reads it exactly
             }
             const int off = (u ^ (tid & 7)) << 4;
             *reinterpret_cast<float4*>(ah + off) = hi;
@@ -301,12 +305,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(p * NT);
+        const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(p * 2 * NT);
         const bool last = s == nseg - 1;
         for (int pc = 0; pc < nN / 16; ++pc) {
-          float v[16];
+          float v[16], vc[16];
           tmem_ld16(taddr + (uint32_t)(16 * pc), v);
+          tmem_ld16(taddr + (uint32_t)(NT + 16 * pc), vc);
           tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] += vc[e];
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int ai = j * NT + pc * 16 + e;
@@ -488,7 +495,7 @@ __global__ void split_tf32_kernel(const float* in, int64_t ld_in, int64_t c0, in
       const float x = in[c * ld_in + i];
       const float h = tf32_hi(x);
       hi[c * ld_out + i] = h;
-      lo[c * ld_out + i] = x - h;
+      lo[c * ld_out + i] = tf32_hi(x - h);
     }
 }
 
