@@ -22,15 +22,17 @@
 // straight into the 128-byte-swizzled K-major B operand by TMA; X is staged raw by TMA and split by
 // converter warps, which write the K-major A operand.
 //
-// Roles (10 warps, one persistent CTA per SM):
+// Roles (14 warps, one persistent CTA per SM):
 //   warps 0-3  converters: thread = tile column; split 32 values per chunk into the A operand and
 //              sum x^2 of the column;
-//   warps 4-7  epilogue: thread = tensor-memory lane = tile column; add each segment's accumulator
-//              (16-column pieces) into W, and after the last one sum w^2;
-//   warp 8     one lane issues the TMA copies (X chunk, U head and tail chunk);
-//   warp 9     allocates tensor memory; one lane issues the MMAs, committing each chunk to the
+//   warps 4-11 epilogue: thread = tensor-memory lane = tile column, two warps per lane quarter, each
+//              holding half of the N tile in registers: add every segment's main accumulator, then
+//              the cross accumulator, store W and sum w^2;
+//   warp 12    one lane issues the TMA copies (X chunk, U head and tail chunk);
+//   warp 13    allocates tensor memory; one lane issues the MMAs, committing each chunk to the
 //              barriers that free its A and B slots, and each segment to its accumulator's barrier
-//              (two accumulators, so the MMAs of one segment overlap the epilogue of the previous).
+//              (two main and two cross accumulators, so the MMAs of one segment overlap the
+//              epilogue of the previous one).
 // Every wait is bounded in time (the limit is a launch argument); on expiry the waiting thread
 // raises a CTA-wide abort flag, every role leaves its loop, the MMA lane waits for the MMAs it
 // issued and the producer for its copies in flight, tensor memory is freed and `status` records the
@@ -48,12 +50,12 @@ using namespace tc;
 
 constexpr int kTile = 128;   // columns per item (MMA M)
 constexpr int kChunk = 32;   // K rows per staged chunk
-constexpr int kConvWarps = 4, kEpiWarps = 4;
+constexpr int kConvWarps = 4, kEpiWarps = 8;  // epilogue: two warps per 32-lane quarter, half the N tile each
 constexpr int kProducerWarp = kConvWarps + kEpiWarps, kMmaWarp = kProducerWarp + 1;
 constexpr int kThreads = (kMmaWarp + 1) * 32;
 constexpr uint32_t kRawBytes = kChunk * kTile * 4;  // 16 KB
 constexpr uint32_t kABytes = kTile * kChunk * 4;    // 16 KB per half (head or tail)
-constexpr int kSeg = 8;      // chunks accumulated in tensor memory before the epilogue takes them
+constexpr int kSeg = 2;      // chunks in one segment of the main accumulator (64 values of K)
 
 // ring depths per N tile (dynamic shared memory stays within 227 KB)
 template <int NT>
@@ -74,7 +76,7 @@ struct ProjArgs {
   int r, b, nj, tpo, nch;
   float* W;
   double* part_x;  // [b * tpo * 4]   per item of N tile 0: sum x^2 of each converter warp's columns
-  double* part_w;  // [b * tpo * nj * 4]   per item: sum w^2 of each epilogue warp's columns
+  double* part_w;  // [b * tpo * nj * 8]   per item: sum w^2 of each epilogue warp's outputs
   int* status;
   unsigned long long wait_ns;
   long long drop_chunk;  // test hook: CTA 0 issues no copy for its chunk of this index (-1: none)
@@ -86,7 +88,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ CUtensorMap ulmap, const ProjArgs a) {
   constexpr int RAW = Cfg<NT>::raw, AST = Cfg<NT>::a, BST = Cfg<NT>::b;
   constexpr uint32_t kBBytes = NT * 128;  // one half of a B chunk: NT rows of 128 bytes
-  constexpr uint32_t kTmemCols = 4 * NT;  // two segment buffers, each a main and a cross accumulator
+  // tensor memory: main accumulator of the current / next segment at [0, 2 NT), cross accumulator of
+  // the current / next item at [2 NT, 4 NT)
+  constexpr uint32_t kTmemCols = 4 * NT;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t raw_full[RAW], raw_empty[RAW];
   __shared__ __align__(8) uint64_t a_full[AST], a_empty[AST];
   __shared__ __align__(8) uint64_t b_full[BST], b_empty[BST];
-  __shared__ __align__(8) uint64_t seg_full[2], seg_empty[2], mma_done;
+  __shared__ __align__(8) uint64_t seg_full[2], seg_empty[2], cross_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -120,6 +124,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < 2; ++s) {
       mbar_init(&seg_full[s], 1);
       mbar_init(&seg_empty[s], kEpiWarps);
+      mbar_init(&cross_empty[s], kEpiWarps);
     }
     mbar_init(&mma_done, 1);
     abort_flag = 0;
@@ -175,11 +180,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (wid == kMmaWarp) {
     if (lane == 0) {
       int64_t g = 0, sg = 0;  // chunks and segments issued
+      int it = 0;
       bool ok = true;
-      for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
+      for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x, ++it) {
         const int j = (int)(q % a.nj);
         const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);  // MMA N of this item
         const uint32_t idesc = tf32_idesc(kTile, nN);
+        if (it >= 2 && !wait_bounded(&cross_empty[it & 1], (uint32_t)(((it >> 1) - 1) & 1), &abort_flag, lim)) break;
+        const uint32_t dc = tmem + (uint32_t)((2 + (it & 1)) * NT);
         uint32_t d = 0;
         for (int c = 0; c < a.nch; ++c, ++g) {
           const int cs = c % kSeg;  // chunk within its segment
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             fence_after();
-            d = tmem + (uint32_t)(p * 2 * NT);
+            d = tmem + (uint32_t)(p * NT);
           }
           const int qa = (int)(g % AST), sb = (int)(g % BST);
           if (!wait_bounded(&a_full[qa], (uint32_t)((g / AST) & 1), &abort_flag, lim) ||
@@ -207,16 +215,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kk = 0; kk < kChunk / 8; ++kk) {
             if (kk >= nk) break;
             const uint32_t ko = (uint32_t)kk * 32;  // 8 TF32 values of K
-            // head x head into the main accumulator, the two tail products (~2^-11 of it) into the
-            // cross accumulator, so that the main one takes one add per K step
+            // head x head into the segment's main accumulator; the two tail products (~2^-11 of it)
+            // into the item's cross accumulator
             mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
-            mma_tf32(d + NT, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
-            mma_tf32(d + NT, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
+            mma_tf32(dc, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, (c | kk) != 0);
+            mma_tf32(dc, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
           }
           mma_commit(&a_empty[qa]);  // these slots are free once the MMAs above have read them
           mma_commit(&b_empty[sb]);
           if (cs == kSeg - 1 || c == a.nch - 1) {
-            mma_commit(&seg_full[sg & 1]);  // the segment's accumulator is complete
+            mma_commit(&seg_full[sg & 1]);  // the segment (and, after the last one, the cross sum) is done
             ++sg;
           }
         }
@@ -283,21 +291,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (wid < kProducerWarp) {
-    // epilogue: thread = tensor-memory lane = tile column.  Each segment's accumulator is added into
-    // this column's outputs in W (the first segment stores, later ones load, add and store: the
-    // tile stays in L2 and every value is touched by this thread only); the last one also sums w^2.
-    const int ew = wid - kConvWarps;
+    // epilogue: thread = tensor-memory lane = tile column, one half of the item's N tile per warp.
+    // The main accumulator of each segment is added into NT/2 FP32 registers (round-to-nearest),
+    // then the item's cross accumulator; the result is stored as W and its squares summed.
+    constexpr int H = NT / 2;
+    const int ew = wid - kConvWarps, qd = ew & 3, hf = ew >> 2;  // lane quarter, half of the N tile
     const int nseg = (a.nch + kSeg - 1) / kSeg;
     int64_t sg = 0;
+    int it = 0;
     bool ok = true;
-    for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
+    for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x, ++it) {
       const int j = (int)(q % a.nj);
       const int t = (int)((q / a.nj) % a.tpo);
       const int z = (int)(q / ((int64_t)a.nj * a.tpo));
       const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);
-      const int64_t l = (int64_t)t * kTile + ew * 32 + lane;
-      float* Wz = a.W + (int64_t)z * a.r * a.L + l;
-      float w2 = 0.0f;
+      const int c0 = hf * H;  // first column of this warp's half
+      float run[H];
+#pragma unroll
+      for (int e = 0; e < H; ++e) run[e] = 0.0f;
+      const uint32_t lanes = (uint32_t)(qd * 32) << 16;
       for (int s = 0; s < nseg; ++s, ++sg) {
         const int p = (int)(sg & 1);
         if (!__all_sync(0xffffffffu, wait_bounded(&seg_full[p], (uint32_t)((sg >> 1) & 1), &abort_flag, lim))) {
@@ -305,24 +317,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(p * 2 * NT);
-        const bool last = s == nseg - 1;
-        for (int pc = 0; pc < nN / 16; ++pc) {
-          float v[16], vc[16];
-          tmem_ld16(taddr + (uint32_t)(16 * pc), v);
-          tmem_ld16(taddr + (uint32_t)(NT + 16 * pc), vc);
-          tmem_wait_ld();
+        const uint32_t taddr = tmem + lanes + (uint32_t)(p * NT + c0);
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] += vc[e];
+        for (int pc = 0; pc < H / 16; ++pc) {
+          if (c0 + pc * 16 < nN) {
+            float v[16];
+            tmem_ld16(taddr + (uint32_t)(16 * pc), v);
+            tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int ai = j * NT + pc * 16 + e;
-            if (ai < a.r && l < a.L) {
-              float* w = Wz + (int64_t)ai * a.L;
-              const float x = s == 0 ? v[e] : *w + v[e];
-              *w = x;
-              if (last) w2 = fmaf(x, x, w2);
-            }
+            for (int e = 0; e < 16; ++e) run[pc * 16 + e] += v[e];
           }
         }
         fence_before();
@@ -330,6 +333,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&seg_empty[p]);
       }
       if (!ok) break;
+      {  // the item's cross sum (complete with its last segment)
+        const uint32_t taddr = tmem + lanes + (uint32_t)((2 + (it & 1)) * NT + c0);
+#pragma unroll
+        for (int pc = 0; pc < H / 16; ++pc) {
+          if (c0 + pc * 16 < nN) {
+            float v[16];
+            tmem_ld16(taddr + (uint32_t)(16 * pc), v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) run[pc * 16 + e] += v[e];
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&cross_empty[it & 1]);
+      }
+      const int64_t l = (int64_t)t * kTile + qd * 32 + lane;
+      float* Wz = a.W + (int64_t)z * a.r * a.L + l;
+      float w2 = 0.0f;
+#pragma unroll
+      for (int e = 0; e < H; ++e) {
+        const int ai = j * NT + c0 + e;
+        if (c0 + e < nN && ai < a.r) {
+          w2 = fmaf(run[e], run[e], w2);
+          if (l < a.L) Wz[(int64_t)ai * a.L] = run[e];
+        }
+      }
       if (a.part_w) {
         double s = (double)w2;
 #pragma unroll
