@@ -54,10 +54,12 @@ extern "C" {
  * norms and thresholds are FP64. */
 #define TTICE_FP64 0 /* FP64 everywhere: the plain FP64 GPU TT-ICE */
 #define TTICE_FP32 1 /* FP32 projections and residuals, Gram as FP32 products summed in FP64, FP32
-                        eigen-solve candidates + FP64 Rayleigh-Ritz.  The first pass over an FP32
-                        increment (n_1 <= 128, r_1 <= 64) runs on the tensor cores in TF32 with each
-                        operand split into a TF32 head and an FP32 tail (three products), which keeps
-                        FP32 accuracy; the other projections are FP32 SIMT. */
+                        eigen-solve candidates + FP64 Rayleigh-Ritz.  The projections of the chain
+                        (every stage whose unfolding has >= 32 columns per observation, a multiple of
+                        4) run on the tensor cores in TF32 with each operand split into a TF32 head
+                        and tail (three products, FP32 accuracy), their residual norms by Pythagoras;
+                        large re-orthogonalisations (CGS work m r k >= 4e9) run their two passes on
+                        the tensor cores the same way (orthogonality ~1e-9 instead of ~1e-15). */
 #define TTICE_TF32 2 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_BF16 3 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_SPLIT_BF16 4 /* reserved (split-BF16 projections): ttice_create returns TTICE_EINVAL */
@@ -282,6 +284,18 @@ const char* ttice_last_cuda_error(void);
  * TTICE_ENOMEM as if the device were full, and ttice_last_cuda_error names
  * cudaErrorMemoryAllocation.  n <= 0 disarms it. */
 void ttice_test_fail_alloc(int64_t n);
+
+/* Test hooks of the tensor-core kernels (host-side settings; nothing here faults a GPU):
+ *  - ttice_test_wait_limit_ns: the time limit of every bounded wait inside the tensor-core kernels
+ *    (0 restores the default of 2 s).  A wait that runs out makes the kernel leave cleanly and the
+ *    update return TTICE_ETIMEOUT with the decomposition as it was.
+ *  - ttice_test_drop_copy: the next tensor-core projection launch issues no copy for chunk `chunk`
+ *    of its first thread block, so that the consumers' bounded wait runs out (-1 disarms).
+ *  - ttice_test_tc_cgs_min: the CGS work m r k from which the mixed path runs the re-orthogonalisation
+ *    of new directions on the tensor cores (0: whenever the shapes allow; negative: the default). */
+void ttice_test_wait_limit_ns(uint64_t ns);
+void ttice_test_drop_copy(int64_t chunk);
+void ttice_test_tc_cgs_min(double flops);
 
 #ifdef __cplusplus
 }

@@ -292,6 +292,7 @@ TT_GEMM_INST(float, float, float, double, double)
 TT_GEMM_INST(float, float, float, double, float)
 TT_GEMM_INST(float, float, double, double, float)
 TT_GEMM_INST(float, double, double, double, double)
+TT_GEMM_INST(float, double, double, double, float)
 // reconstruction into FP32 outputs
 TT_GEMM_INST(double, double, double, float, double)
 

@@ -71,10 +71,20 @@ constexpr size_t smem_bytes() {
          1024;
 }
 
+// Store of the result D[n][l] (n: output row, the MMA's N; l: the item's column, the MMA's M):
+enum StoreMode {
+  kStoreF32 = 0,  // out (float) = D, with the optional norm partials
+  kSubF64 = 1,    // out (double) -= D
+  kSplitF32 = 2   // out, out2 (float) = TF32 head and tail of D (the operand form of a later product)
+};
+
 struct ProjArgs {
-  int64_t L, m;
+  int64_t L, m;    // columns per observation (MMA M extent), K
   int r, b, nj, tpo, nch;
-  float* W;
+  int mode;
+  void* out;
+  void* out2;
+  int64_t o_obs, ldn, ldl;  // element (n, l) of observation z at z * o_obs + n * ldn + l * ldl
   double* part_x;  // [b * tpo * 4]   per item of N tile 0: sum x^2 of each converter warp's columns
   double* part_w;  // [b * tpo * nj * 8]   per item: sum w^2 of each epilogue warp's outputs
   int* status;
@@ -82,10 +92,14 @@ struct ProjArgs {
   long long drop_chunk;  // test hook: CTA 0 issues no copy for its chunk of this index (-1: none)
 };
 
-template <int NT>
+// APRE: the A operand (rows = the items' columns, K contiguous) is given pre-split as TF32 head /
+// tail arrays and copied by TMA straight into the A slots (xmap / xlmap are their maps); otherwise
+// xmap describes the raw FP32 X and the converter warps build the A slots.
+template <int NT, bool APRE>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_proj_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap uhmap,
-                   const __grid_constant__ CUtensorMap ulmap, const ProjArgs a) {
+    tc_proj_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xlmap,
+                   const __grid_constant__ CUtensorMap uhmap, const __grid_constant__ CUtensorMap ulmap,
+                   const ProjArgs a) {
   constexpr int RAW = Cfg<NT>::raw, AST = Cfg<NT>::a, BST = Cfg<NT>::b;
   constexpr uint32_t kBBytes = NT * 128;  // one half of a B chunk: NT rows of 128 bytes
   // tensor memory: main accumulator of the current / next segment at [0, 2 NT), cross accumulator of
@@ -114,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&raw_empty[s], kConvWarps);
     }
     for (int s = 0; s < AST; ++s) {
-      mbar_init(&a_full[s], kConvWarps);
+      mbar_init(&a_full[s], APRE ? 1 : kConvWarps);
       mbar_init(&a_empty[s], 1);
     }
     for (int s = 0; s < BST; ++s) {
@@ -152,14 +166,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int t = (int)((q / a.nj) % a.tpo);
         const int z = (int)(q / ((int64_t)a.nj * a.tpo));
         for (int c = 0; c < a.nch; ++c, ++g) {
-          const int s = (int)(g % RAW), sb = (int)(g % BST);
-          if (g >= RAW && !wait_bounded(&raw_empty[s], (uint32_t)(((g / RAW) - 1) & 1), &abort_flag, lim)) {
-            ok = false;
-            break;
-          }
-          if (!(blockIdx.x == 0 && g == a.drop_chunk)) {
-            mbar_expect_tx(&raw_full[s], kRawBytes);
-            tma_load_3d(smem_u32(raw + (size_t)s * kRawBytes), &xmap, t * kTile, c * kChunk, z, &raw_full[s]);
+          const int s = (int)(g % RAW), sb = (int)(g % BST), qa = (int)(g % AST);
+          if constexpr (APRE) {
+            if (g >= AST && !wait_bounded(&a_empty[qa], (uint32_t)(((g / AST) - 1) & 1), &abort_flag, lim)) {
+              ok = false;
+              break;
+            }
+            if (!(blockIdx.x == 0 && g == a.drop_chunk)) {
+              mbar_expect_tx(&a_full[qa], 2 * kABytes);
+              tma_load_2d(smem_u32(a_hi + (size_t)qa * kABytes), &xmap, c * kChunk, t * kTile, &a_full[qa]);
+              tma_load_2d(smem_u32(a_lo + (size_t)qa * kABytes), &xlmap, c * kChunk, t * kTile, &a_full[qa]);
+            }
+          } else {
+            if (g >= RAW && !wait_bounded(&raw_empty[s], (uint32_t)(((g / RAW) - 1) & 1), &abort_flag, lim)) {
+              ok = false;
+              break;
+            }
+            if (!(blockIdx.x == 0 && g == a.drop_chunk)) {
+              mbar_expect_tx(&raw_full[s], kRawBytes);
+              tma_load_3d(smem_u32(raw + (size_t)s * kRawBytes), &xmap, t * kTile, c * kChunk, z, &raw_full[s]);
+            }
           }
           if (g >= BST && !wait_bounded(&b_empty[sb], (uint32_t)(((g / BST) - 1) & 1), &abort_flag, lim)) {
             ok = false;
@@ -172,8 +198,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // copies of the last ring slots may still be in flight (on an abort): wait for them
-      for (int64_t k = g > RAW ? g - RAW : 0; k < g; ++k)
-        wait_drain(&raw_full[k % RAW], (uint32_t)((k / RAW) & 1), lim);
+      if constexpr (APRE) {
+        for (int64_t k = g > AST ? g - AST : 0; k < g; ++k)
+          wait_drain(&a_full[k % AST], (uint32_t)((k / AST) & 1), lim);
+      } else {
+        for (int64_t k = g > RAW ? g - RAW : 0; k < g; ++k)
+          wait_drain(&raw_full[k % RAW], (uint32_t)((k / RAW) & 1), lim);
+      }
       for (int64_t k = g > BST ? g - BST : 0; k < g; ++k)
         wait_drain(&b_full[k % BST], (uint32_t)((k / BST) & 1), lim);
     }
@@ -234,6 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       wait_drain(&mma_done, 0, lim);
     }
   } else if (wid < kConvWarps) {
+    if constexpr (!APRE) {  // with a pre-split A operand the A slots are filled by TMA
     // converters: thread tid owns column tid of the item's tile
     int64_t g = 0;
     for (int64_t q = blockIdx.x; q < nitems; q += gridDim.x) {
@@ -289,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) a.part_x[((int64_t)z * a.tpo + t) * kConvWarps + wid] = s;
       }
+    }
     }
   } else if (wid < kProducerWarp) {
     // epilogue: thread = tensor-memory lane = tile column, one half of the item's N tile per warp.
@@ -350,14 +383,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&cross_empty[it & 1]);
       }
       const int64_t l = (int64_t)t * kTile + qd * 32 + lane;
-      float* Wz = a.W + (int64_t)z * a.r * a.L + l;
+      const int64_t base = (int64_t)z * a.o_obs + l * a.ldl;
       float w2 = 0.0f;
 #pragma unroll
       for (int e = 0; e < H; ++e) {
         const int ai = j * NT + c0 + e;
         if (c0 + e < nN && ai < a.r) {
-          w2 = fmaf(run[e], run[e], w2);
-          if (l < a.L) Wz[(int64_t)ai * a.L] = run[e];
+          const float v = run[e];
+          w2 = fmaf(v, v, w2);
+          if (l < a.L) {
+            const int64_t o = base + (int64_t)ai * a.ldn;
+            if (a.mode == kStoreF32) {
+              static_cast<float*>(a.out)[o] = v;
+            } else if (a.mode == kSubF64) {
+              static_cast<double*>(a.out)[o] -= (double)v;
+            } else {
+              const float hv = tf32_hi(v);
+              static_cast<float*>(a.out)[o] = hv;
+              static_cast<float*>(a.out2)[o] = tf32_hi(v - hv);
+            }
+          }
         }
       }
       if (a.part_w) {
@@ -424,41 +469,44 @@ int pick_nt(int r) { return r <= 64 ? 64 : 128; }
 std::atomic<unsigned long long> g_wait_ns{2000000000ull};
 std::atomic<long long> g_drop_chunk{-1};
 
-template <int NT>
-cudaError_t run(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
-                int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part, int* status,
-                cudaStream_t st) {
-  auto enc = encode_fn();
-  if (!enc) return cudaErrorNotSupported;
-  CUtensorMap xmap, uhmap, ulmap;
-  {
-    const cuuint64_t gdim[3] = {(cuuint64_t)L, (cuuint64_t)m, (cuuint64_t)b};
-    const cuuint64_t gstride[2] = {(cuuint64_t)L * 4, (cuuint64_t)(m * L * 4)};
+bool encode_2d(CUtensorMap* map, const float* p, int64_t inner, int64_t outer, int64_t ld, uint32_t box_inner,
+               uint32_t box_outer, bool sw128) {
+  const cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t es[2] = {1, 1};
+  return encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), gdim, gstride, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NT, bool APRE>
+cudaError_t run(const TcGemm& g, cudaStream_t st) {
+  if (!encode_fn()) return cudaErrorNotSupported;
+  CUtensorMap xmap, xlmap, uhmap, ulmap;
+  if constexpr (APRE) {
+    if (!encode_2d(&xmap, g.ah, g.lda, g.la_alloc, g.lda, kChunk, kTile, true) ||
+        !encode_2d(&xlmap, g.al, g.lda, g.la_alloc, g.lda, kChunk, kTile, true))
+      return cudaErrorInvalidValue;
+  } else {
+    const cuuint64_t gdim[3] = {(cuuint64_t)g.L, (cuuint64_t)g.K, (cuuint64_t)g.b};
+    const cuuint64_t gstride[2] = {(cuuint64_t)g.ldx * 4, (cuuint64_t)g.x_obs * 4};
     const cuuint32_t box[3] = {(cuuint32_t)kTile, (cuuint32_t)kChunk, 1};
     const cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), gdim, gstride, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    if (encode_fn()(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(g.x), gdim, gstride, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
+    xlmap = xmap;  // unused
   }
-  {
-    const cuuint64_t gdim[2] = {(cuuint64_t)ldhl, (cuuint64_t)hlcols};
-    const cuuint64_t gstride[1] = {(cuuint64_t)ldhl * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)NT};
-    const cuuint32_t es[2] = {1, 1};
-    if (enc(&uhmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Uh), gdim, gstride, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        enc(&ulmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Ul), gdim, gstride, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
+  if (!encode_2d(&uhmap, g.bh, g.ldb, g.nb_alloc, g.ldb, kChunk, NT, true) ||
+      !encode_2d(&ulmap, g.bl, g.ldb, g.nb_alloc, g.ldb, kChunk, NT, true))
+    return cudaErrorInvalidValue;
   static std::once_flag once;
   static cudaError_t setup_err = cudaSuccess;
   static int sms = 148;
   std::call_once(once, [] {
-    setup_err = cudaFuncSetAttribute(tc_proj_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    setup_err = cudaFuncSetAttribute(tc_proj_kernel<NT, APRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_bytes<NT>());
     int dev = 0;
     if (setup_err == cudaSuccess) setup_err = cudaGetDevice(&dev);
@@ -466,28 +514,33 @@ cudaError_t run(const float* X, int b, int64_t L, int64_t m, int r, const float*
   });
   TT_CUDA(setup_err);
   ProjArgs a;
-  a.L = L;
-  a.m = m;
-  a.r = r;
-  a.b = b;
-  a.nj = (r + NT - 1) / NT;
-  a.tpo = (int)((L + kTile - 1) / kTile);
-  a.nch = (int)((m + kChunk - 1) / kChunk);
-  a.W = W;
-  const bool norms = x2 != nullptr || rho2 != nullptr;
-  a.part_x = norms ? part : nullptr;
-  a.part_w = norms ? part + (int64_t)b * a.tpo * kConvWarps : nullptr;
-  a.status = status;
+  a.L = g.L;
+  a.m = g.K;
+  a.r = g.r;
+  a.b = APRE ? 1 : g.b;
+  a.nj = (g.r + NT - 1) / NT;
+  a.tpo = (int)((g.L + kTile - 1) / kTile);
+  a.nch = (int)((g.K + kChunk - 1) / kChunk);
+  a.mode = g.mode;
+  a.out = g.out;
+  a.out2 = g.out2;
+  a.o_obs = g.o_obs;
+  a.ldn = g.ldn;
+  a.ldl = g.ldl;
+  const bool norms = !APRE && (g.x2 != nullptr || g.rho2 != nullptr);
+  a.part_x = norms ? g.part : nullptr;
+  a.part_w = norms ? g.part + (int64_t)a.b * a.tpo * kConvWarps : nullptr;
+  a.status = g.status;
   a.wait_ns = g_wait_ns.load();
   a.drop_chunk = g_drop_chunk.exchange(-1);
-  const int64_t nitems = (int64_t)b * a.tpo * a.nj;
+  const int64_t nitems = (int64_t)a.b * a.tpo * a.nj;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(sms, nitems));
   note_launch();
-  tc_proj_kernel<NT><<<(unsigned)grid, kThreads, smem_bytes<NT>(), st>>>(xmap, uhmap, ulmap, a);
+  tc_proj_kernel<NT, APRE><<<(unsigned)grid, kThreads, smem_bytes<NT>(), st>>>(xmap, xlmap, uhmap, ulmap, a);
   TT_CUDA(cudaGetLastError());
   if (norms) {
     note_launch();
-    tc_proj_reduce_kernel<<<b, 256, 0, st>>>(a.part_x, a.part_w, a.tpo, a.nj, x2, rho2);
+    tc_proj_reduce_kernel<<<a.b, 256, 0, st>>>(a.part_x, a.part_w, a.tpo, a.nj, g.x2, g.rho2);
     TT_CUDA(cudaGetLastError());
   }
   return cudaSuccess;
@@ -506,11 +559,38 @@ int64_t tc_proj_part_elems(int b, int64_t L, int64_t r) {
   return (int64_t)b * tpo * (kConvWarps + nj * kEpiWarps);
 }
 
+cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t st) {
+  if (g.L < 1 || g.K < 1 || g.r < 1 || g.b < 1) return cudaSuccess;
+  const bool pre = g.ah != nullptr;
+  if (pick_nt(g.r) == 64) return pre ? run<64, true>(g, st) : run<64, false>(g, st);
+  return pre ? run<128, true>(g, st) : run<128, false>(g, st);
+}
+
 cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
                            int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
                            int* status, cudaStream_t st) {
-  if (pick_nt(r) == 64) return run<64>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
-  return run<128>(X, b, L, m, r, Uh, Ul, ldhl, hlcols, W, x2, rho2, part, status, st);
+  TcGemm g;
+  g.x = X;
+  g.ldx = L;
+  g.x_obs = m * L;
+  g.L = L;
+  g.b = b;
+  g.K = m;
+  g.bh = Uh;
+  g.bl = Ul;
+  g.ldb = ldhl;
+  g.nb_alloc = hlcols;
+  g.r = r;
+  g.mode = kStoreF32;
+  g.out = W;
+  g.o_obs = (int64_t)r * L;
+  g.ldn = L;
+  g.ldl = 1;
+  g.x2 = x2;
+  g.rho2 = rho2;
+  g.part = part;
+  g.status = status;
+  return launch_tc_gemm(g, st);
 }
 
 void tc_set_wait_ns(unsigned long long ns) { g_wait_ns.store(ns ? ns : 2000000000ull); }
@@ -527,6 +607,28 @@ __global__ void split_tf32_kernel(const float* in, int64_t ld_in, int64_t c0, in
       hi[c * ld_out + i] = h;
       lo[c * ld_out + i] = tf32_hi(x - h);
     }
+}
+
+__global__ void split_tf32_f64_kernel(const double* in, int64_t ld_in, int64_t rows, int64_t c0, int64_t c1,
+                                      float* hi, float* lo, int64_t ld_out) {
+  const int64_t rows32 = (rows + 31) / 32 * 32;  // the last K chunk is zero past the operand
+  for (int64_t c = c0 + blockIdx.y; c < c1; c += gridDim.y)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows32; i += (int64_t)gridDim.x * blockDim.x) {
+      const double x = i < rows ? in[c * ld_in + i] : 0.0;
+      const float h = tf32_hi((float)x);
+      hi[c * ld_out + i] = h;
+      lo[c * ld_out + i] = tf32_hi((float)(x - (double)h));
+    }
+}
+
+cudaError_t launch_split_tf32_f64(const double* in, int64_t ld_in, int64_t rows, int64_t c0, int64_t c1, float* hi,
+                                  float* lo, int64_t ld_out, cudaStream_t st) {
+  if (c1 <= c0 || rows <= 0) return cudaSuccess;
+  const int64_t bx = std::min<int64_t>((rows + 255) / 256, 64);
+  const int64_t by = std::min<int64_t>(c1 - c0, 1024);
+  note_launch();
+  split_tf32_f64_kernel<<<dim3((unsigned)bx, (unsigned)by), 256, 0, st>>>(in, ld_in, rows, c0, c1, hi, lo, ld_out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_split_tf32(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,

@@ -92,6 +92,14 @@ struct ttice_s {
   int64_t dir_s = 0;
   double* Vn2 = nullptr;
   double* P = nullptr;   // cap x kRR projections for CGS2
+  // tensor-core CGS of the mixed path: TF32 head / tail of the new directions (ldv x kRR, ldv = max_m
+  // rounded up to 32) and of their projections on the core (ldp x kRR, ldp = largest capacity
+  // rounded up to 32)
+  float* Vnh = nullptr;
+  float* Vnl = nullptr;
+  float* Ph = nullptr;
+  float* Pl = nullptr;
+  int64_t ldv = 0, ldp = 0;
   int64_t max_m = 0;
   double* rho2 = nullptr;    // squared residual per TT stage and observation (stage-major, d x b)
   double* h_rho2 = nullptr;  // pinned copy (first pass of an update)
@@ -261,7 +269,7 @@ void free_all(ttice_s* h) {
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->Ebuf, h->P, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Ph, h->Pl, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
   cudaFreeHost(h->h_rn2);
@@ -775,9 +783,45 @@ int build_dirs(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int c0, 
     g.B.p = Vdir; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
     g.C = h->Vn; g.c_rs = 1; g.c_cs = m;
     g.nbatch = nsel;
-    TT_CU((gemm<WT, double, double, double, double>(g, st)));
+    // mixed path: FP32 products of the FP32 residual (FP64 accumulation); the directions are
+    // re-orthogonalised against the core and among themselves afterwards
+    using BACC = typename std::conditional<sizeof(WT) == 8, double, float>::type;
+    TT_CU((gemm<WT, double, double, double, BACC>(g, st)));
     TT_CU(launch_scale_cols_rsqrt(h->Vn, m, k, m, h->dir_scale + c0, st));
   }
+  return TTICE_OK;
+}
+
+// Mixed path: the CGS work m r k above which its two passes run on the tensor cores (the FP64
+// products would take more than a few milliseconds at GB300's FP64 rate).
+constexpr double kTcCgsMin = 4e9;
+std::atomic<double> g_tc_cgs_min{kTcCgsMin};  // ttice_test_tc_cgs_min
+
+// One CGS pass of Vn (m x k, FP64, column-major) against U[core] on the tensor cores: P = U^T Vn
+// from the TF32 head / tail splits of Vn (from FP64) and of U (three products, FP32 accuracy, 64-long
+// K segments summed in registers), stored as the head / tail of P, then Vn -= U P with U from its
+// FP32 mirror, subtracted in FP64.  P is small (the coupling left by an explicit residual), so the
+// FP32-accurate products leave a coupling of ~2^-22 |P| after the pass; the floor is the FP32
+// rounding of the tensor-core sums, ~1e-9 of unit vectors for K in the tens of thousands.
+int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
+  const int64_t r = h->r[core + 1];
+  TT_CU(launch_split_tf32_f64(h->Vn, m, m, 0, k, h->Vnh, h->Vnl, h->ldv, st));
+  TcGemm a;  // P[a][j] = sum_i U[i][a] Vn[i][j]: A rows j (K = i), B rows a (K = i)
+  a.ah = h->Vnh; a.al = h->Vnl; a.lda = h->ldv; a.la_alloc = kRR;
+  a.L = k; a.K = m;
+  a.bh = h->Uh[core]; a.bl = h->Ul[core]; a.ldb = h->ldhl[core]; a.nb_alloc = h->hlcols[core];
+  a.r = (int)r;
+  a.mode = 2; a.out = h->Ph; a.out2 = h->Pl; a.ldn = 1; a.ldl = h->ldp;  // P^T rows j: the B operand below
+  a.status = h->ibuf + 5;
+  TT_CU(launch_tc_gemm(a, st));
+  TcGemm b;  // Vn[i][j] -= sum_a U[i][a] P[a][j]: A = U (K = a rows, i contiguous), B rows j (K = a)
+  b.x = h->Uf[core]; b.ldx = h->ldu[core]; b.x_obs = h->ldu[core] * r; b.b = 1;
+  b.L = m; b.K = r;
+  b.bh = h->Ph; b.bl = h->Pl; b.ldb = h->ldp; b.nb_alloc = kRR;
+  b.r = k;
+  b.mode = 1; b.out = h->Vn; b.ldn = m; b.ldl = 1;
+  b.status = h->ibuf + 5;
+  TT_CU(launch_tc_gemm(b, st));
   return TTICE_OK;
 }
 
@@ -787,7 +831,9 @@ int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t s
   const int64_t r = h->r[core + 1];
   double* U = h->U[core];
   const int64_t ld = h->ldu[core];
-  for (int pass = 0; pass < 2 && r > 0; ++pass) {
+  const bool tc = h->Uh[core] && r > 0 && m >= 32 && ld % 4 == 0 && (double)m * r * k >= g_tc_cgs_min.load();
+  for (int pass = 0; pass < 2 && tc; ++pass) TT_TRY(cgs_pass_tc(h, core, m, k, st));
+  for (int pass = 0; pass < 2 && r > 0 && !tc; ++pass) {
     GemmArgs a;  // P = U^T Vn  (r x k, column-major ld r)
     a.M = r; a.N = k; a.K = m; a.atomic = 1; a.allow_splitk = 1;
     a.A.p = U; a.A.rs = ld; a.A.cs = 1;
@@ -1125,6 +1171,12 @@ const char* ttice_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_er
 
 void ttice_test_fail_alloc(int64_t n) { g_fail_alloc.store(n > 0 ? n : 0); }
 
+void ttice_test_wait_limit_ns(uint64_t ns) { tc_set_wait_ns(ns); }
+
+void ttice_test_drop_copy(int64_t chunk) { tc_drop_next_copy(chunk); }
+
+void ttice_test_tc_cgs_min(double flops) { g_tc_cgs_min.store(flops < 0.0 ? kTcCgsMin : flops); }
+
 }  // extern "C"
 
 namespace {
@@ -1223,6 +1275,14 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
   int64_t maxcap = 1;
   for (int i = 1; i <= d; ++i) maxcap = std::max(maxcap, h->cap[i]);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->P, maxcap * kRR);
+  if (h->wt_bytes == 4) {
+    h->ldv = (h->max_m + 31) / 32 * 32;
+    h->ldp = (maxcap + 31) / 32 * 32;
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->Vnh, h->ldv * kRR);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->Vnl, h->ldv * kRR);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->Ph, h->ldp * kRR);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->Pl, h->ldp * kRR);
+  }
   int64_t part_elems = std::max<int64_t>(2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)),
                                          k1_tc_part_elems((int)B, h->L[0]));
   if (h->wt_bytes == 4)

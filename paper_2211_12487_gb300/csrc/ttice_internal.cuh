@@ -156,9 +156,48 @@ int64_t tc_proj_part_elems(int b, int64_t L, int64_t r);
 cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
                            int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
                            int* status, cudaStream_t st);
+// General product on the tensor cores (the same kernel): D[n][l] = sum_k B(k, n) A(k, l) for
+// n < r (N), l < L (M, per observation), k < K, each operand split into TF32 head and tail (three
+// products, FP32 accuracy; the main product summed in registers over 64-long K segments).
+//   A, one of: raw FP32 X (x != nullptr): A(k, l) of observation z = x[z x_obs + k ldx + l]
+//              (16-byte aligned; ldx, x_obs multiples of 4; b observations), split by converter warps;
+//              or pre-split (ah != nullptr): A(k, l) = ah[l lda + k] + al[l lda + k] (lda % 32 == 0,
+//              la_alloc rows allocated, zero beyond the operand; b = 1), copied by TMA.
+//   B: pre-split, B(k, n) = bh[n ldb + k] + bl[n ldb + k] (ldb % 32 == 0, nb_alloc columns allocated,
+//      zero beyond the operand), copied by TMA.
+//   Store of D[n][l] of observation z at o = z o_obs + n ldn + l ldl, by `mode`: 0 float out[o] = D
+//   (with x2 / rho2 as for launch_tc_proj), 1 double out[o] -= D, 2 float out[o], out2[o] = TF32
+//   head and tail of D.
+struct TcGemm {
+  const float* x = nullptr;
+  int64_t ldx = 0, x_obs = 0;
+  const float* ah = nullptr;
+  const float* al = nullptr;
+  int64_t lda = 0, la_alloc = 0;
+  int64_t L = 0;
+  int b = 1;
+  int64_t K = 0;
+  const float* bh = nullptr;
+  const float* bl = nullptr;
+  int64_t ldb = 0, nb_alloc = 0;
+  int r = 0;
+  int mode = 0;
+  void* out = nullptr;
+  void* out2 = nullptr;
+  int64_t o_obs = 0, ldn = 0, ldl = 1;
+  double* x2 = nullptr;
+  double* rho2 = nullptr;
+  double* part = nullptr;
+  int* status = nullptr;
+};
+cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t st);
 // TF32 head/tail split of FP32 columns [c0, c1) (ld_in rows) into hi, lo (ld_out).
 cudaError_t launch_split_tf32(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,
                               int64_t ld_out, cudaStream_t st);
+// The same from FP64 columns (rows [0, rows), zero up to the next multiple of 32): head = tf32(x),
+// tail = tf32(x - head) computed in FP64.
+cudaError_t launch_split_tf32_f64(const double* in, int64_t ld_in, int64_t rows, int64_t c0, int64_t c1, float* hi,
+                                  float* lo, int64_t ld_out, cudaStream_t st);
 // Bounded-wait limit of the tensor-core kernels (0 restores the default of 2 s), and a test hook:
 // the next tc_proj launch issues no copy for chunk `chunk` of its first CTA, so that the consumers'
 // bounded wait runs out.

@@ -106,6 +106,9 @@ def _load():
         "ttice_strerror": (ctypes.c_char_p, [c_int]),
         "ttice_last_cuda_error": (ctypes.c_char_p, []),
         "ttice_test_fail_alloc": (None, [c_int64]),
+        "ttice_test_wait_limit_ns": (None, [ctypes.c_uint64]),
+        "ttice_test_drop_copy": (None, [c_int64]),
+        "ttice_test_tc_cgs_min": (None, [c_double]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -127,6 +130,18 @@ def ttice_last_cuda_error() -> str:
 
 def ttice_test_fail_alloc(n: int) -> None:
     _lib.ttice_test_fail_alloc(int(n))
+
+
+def ttice_test_wait_limit_ns(ns: int) -> None:
+    _lib.ttice_test_wait_limit_ns(int(ns))
+
+
+def ttice_test_drop_copy(chunk: int) -> None:
+    _lib.ttice_test_drop_copy(int(chunk))
+
+
+def ttice_test_tc_cgs_min(flops: float) -> None:
+    _lib.ttice_test_tc_cgs_min(float(flops))
 
 
 def _check(code: int, what: str):
