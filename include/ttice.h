@@ -59,7 +59,8 @@ extern "C" {
                         4) run on the tensor cores in TF32 with each operand split into a TF32 head
                         and tail (three products, FP32 accuracy), their residual norms by Pythagoras;
                         large re-orthogonalisations (CGS work m r k >= 4e9) run their two passes on
-                        the tensor cores the same way (orthogonality ~1e-9 instead of ~1e-15). */
+                        the tensor cores the same way (coupling ~2^-22/sqrt(m) for columns of length
+                        m, ~1e-9 at m ~ 5e4, instead of ~1e-15). */
 #define TTICE_TF32 2 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_BF16 3 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_SPLIT_BF16 4 /* reserved (split-BF16 projections): ttice_create returns TTICE_EINVAL */
