@@ -182,9 +182,11 @@ def headline_handle(T, precision: str, n_inc: int):
 
     h = T.TTICE(DIMS, EPS, precision=precision, input_dtype=torch.float32, max_batch=BATCH, max_rank=1024,
                 obs_reserve=BATCH * n_inc)
+    # rank 4 first, while rank 3's capacity (which sizes U_4's rows) is still small: each growth
+    # holds the old and the new buffers at once
     h.reserve_rank(2, 1080)
-    h.reserve_rank(3, min(51840, 4096 * math.ceil(n_inc * 3840 / 4096)))
     h.reserve_rank(4, 256 * math.ceil(max(1024, 100 * n_inc) / 256))
+    h.reserve_rank(3, min(51840, 4096 * math.ceil(n_inc * 3840 / 4096)))
     return h
 
 
@@ -277,7 +279,7 @@ def run_e2e(T, args, dev, seed, precision):
     import torch
 
     b, W, K = BATCH, args.warmup, args.steps
-    Yh = torch.empty(((W + K) * b,) + DIMS, dtype=torch.float32).pin_memory()
+    Yh = torch.empty(((W + K) * b,) + DIMS, dtype=torch.float32, pin_memory=True)
     for k in range(0, (W + K) * b, b):
         Yh[k:k + b] = frames_1080(k, b, seed=seed).cpu()
     h = headline_handle(T, precision, W + K)
