@@ -81,12 +81,17 @@ enum StoreMode {
 struct ProjArgs {
   int64_t L, m;    // columns per observation (MMA M extent), K
   int r, b, nj, tpo, nch;
+  // narrow layout (L <= 64 dividing 128): a tile holds opt = 128 / L whole observations, lane
+  // o L + l = column l of observation t opt + o; b counts tiles then, nb the observations
+  int narrow, opt, nb;
   int mode;
   void* out;
   void* out2;
   int64_t o_obs, ldn, ldl;  // element (n, l) of observation z at z * o_obs + n * ldn + l * ldl
-  double* part_x;  // [b * tpo * 4]   per item of N tile 0: sum x^2 of each converter warp's columns
-  double* part_w;  // [b * tpo * nj * 8]   per item: sum w^2 of each epilogue warp's outputs
+  // norm partials, contiguous per observation: wide layout x [obs][tile][conv warp], w [obs][tile][N
+  // tile][epilogue warp]; narrow layout x [obs][xs], w [obs][N tile][half][xs], xs = max(1, L / 32)
+  double* part_x;
+  double* part_w;
   int* status;
   unsigned long long wait_ns;
   long long drop_chunk;  // test hook: CTA 0 issues no copy for its chunk of this index (-1: none)
@@ -184,7 +189,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!(blockIdx.x == 0 && g == a.drop_chunk)) {
               mbar_expect_tx(&raw_full[s], kRawBytes);
-              tma_load_3d(smem_u32(raw + (size_t)s * kRawBytes), &xmap, t * kTile, c * kChunk, z, &raw_full[s]);
+              if (a.narrow)
+                tma_load_3d(smem_u32(raw + (size_t)s * kRawBytes), &xmap, 0, c * kChunk, z * a.opt, &raw_full[s]);
+              else
+                tma_load_3d(smem_u32(raw + (size_t)s * kRawBytes), &xmap, t * kTile, c * kChunk, z, &raw_full[s]);
             }
           }
           if (g >= BST && !wait_bounded(&b_empty[sb], (uint32_t)(((g / BST) - 1) & 1), &abort_flag, lim)) {
@@ -283,6 +291,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         const float* rw = reinterpret_cast<const float*>(raw + (size_t)s * kRawBytes);
+        // the raw chunk: [k][128 columns] (wide) or [observation][k][L] (narrow)
+        const int rbase = a.narrow ? (tid / (int)a.L) * kChunk * (int)a.L + tid % (int)a.L : tid;
+        const int rstep = a.narrow ? (int)a.L : kTile;
         unsigned char* ah = a_hi + (size_t)qa * kABytes + (size_t)tid * 128;
         unsigned char* al = a_lo + (size_t)qa * kABytes + (size_t)tid * 128;
         const int64_t rows = a.m - (int64_t)c * kChunk;
@@ -297,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int kk = 4 * u + e;
-              const float y = kk < kv ? rw[kk * kTile + tid] : 0.0f;
+              const float y = kk < kv ? rw[rbase + kk * rstep] : 0.0f;
               x2 = fmaf(y, y, x2);
               ph[e] = tf32_hi(y);
               pl[e] = tf32_hi(y - ph[e]);  // the tail, itself rounded to TF32: the MMA reads it exactly
@@ -317,9 +328,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       if (a.part_x && j == 0) {
         double s = (double)x2;
+        if (a.narrow) {  // sum over the lanes of one observation (aligned groups of min(L, 32))
+          const int gsz = min((int)a.L, 32);
+          for (int o = 1; o < gsz; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          const int ob = tid / (int)a.L, l = tid % (int)a.L, zz = z * a.opt + ob;
+          const int xs = max(1, (int)a.L / 32);
+          if (ob < a.opt && zz < a.nb && (l & 31) == 0) a.part_x[(int64_t)zz * xs + l / 32] = s;
+        } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) a.part_x[((int64_t)z * a.tpo + t) * kConvWarps + wid] = s;
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0) a.part_x[((int64_t)z * a.tpo + t) * kConvWarps + wid] = s;
+        }
       }
     }
     }
@@ -382,8 +401,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&cross_empty[it & 1]);
       }
-      const int64_t l = (int64_t)t * kTile + qd * 32 + lane;
-      const int64_t base = (int64_t)z * a.o_obs + l * a.ldl;
+      const int cl = qd * 32 + lane;  // the tile column of this lane
+      const int ob = a.narrow ? cl / (int)a.L : 0;
+      const int64_t zl = a.narrow ? (int64_t)z * a.opt + ob : z;           // its observation
+      const int64_t l = a.narrow ? cl % (int)a.L : (int64_t)t * kTile + cl;  // its column there
+      const bool lane_ok = !a.narrow || (ob < a.opt && zl < a.nb);
+      const int64_t base = zl * a.o_obs + l * a.ldl;
       float w2 = 0.0f;
 #pragma unroll
       for (int e = 0; e < H; ++e) {
@@ -391,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (c0 + e < nN && ai < a.r) {
           const float v = run[e];
           w2 = fmaf(v, v, w2);
-          if (l < a.L) {
+          if (l < a.L && lane_ok) {
             const int64_t o = base + (int64_t)ai * a.ldn;
             if (a.mode == kStoreF32) {
               static_cast<float*>(a.out)[o] = v;
@@ -407,9 +430,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (a.part_w) {
         double s = (double)w2;
+        if (a.narrow) {
+          const int gsz = min((int)a.L, 32);
+          for (int o = 1; o < gsz; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          const int xs = max(1, (int)a.L / 32);
+          if (lane_ok && (l & 31) == 0) a.part_w[(zl * a.nj + j) * 2 * xs + (int64_t)hf * xs + l / 32] = s;
+        } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) a.part_w[(((int64_t)z * a.tpo + t) * a.nj + j) * kEpiWarps + ew] = s;
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0) a.part_w[(((int64_t)z * a.tpo + t) * a.nj + j) * kEpiWarps + ew] = s;
+        }
       }
     }
   }
@@ -425,14 +455,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Per observation: ||X(z)||^2 and ||X(z)||^2 - ||W(z)||^2 (clamped to [0, ||X(z)||^2]: the difference
 // of the two FP32-accurate sums can round below zero when U spans the observation), summed in a
 // fixed order.
-__global__ void tc_proj_reduce_kernel(const double* part_x, const double* part_w, int tpo, int nj,
+__global__ void tc_proj_reduce_kernel(const double* part_x, const double* part_w, int64_t xper, int64_t wper,
                                       double* x2_out, double* rho2_out) {
   const int z = blockIdx.x;
   double sx = 0.0, sw = 0.0;
-  for (int64_t i = threadIdx.x; i < (int64_t)tpo * kConvWarps; i += blockDim.x)
-    sx += part_x[(int64_t)z * tpo * kConvWarps + i];
-  for (int64_t i = threadIdx.x; i < (int64_t)tpo * nj * kEpiWarps; i += blockDim.x)
-    sw += part_w[(int64_t)z * tpo * nj * kEpiWarps + i];
+  for (int64_t i = threadIdx.x; i < xper; i += blockDim.x) sx += part_x[(int64_t)z * xper + i];
+  for (int64_t i = threadIdx.x; i < wper; i += blockDim.x) sw += part_w[(int64_t)z * wper + i];
   __shared__ double ax[256], aw[256];
   ax[threadIdx.x] = sx;
   aw[threadIdx.x] = sw;
@@ -469,6 +497,9 @@ int pick_nt(int r) { return r <= 64 ? 64 : 128; }
 std::atomic<unsigned long long> g_wait_ns{2000000000ull};
 std::atomic<long long> g_drop_chunk{-1};
 
+// Observations of fewer than 128 columns are packed 128 / L to a tile when L divides 128 (L >= 4).
+bool narrow_layout(const TcGemm& g) { return g.ah == nullptr && g.L <= 64 && g.L >= 4 && kTile % g.L == 0; }
+
 bool encode_2d(CUtensorMap* map, const float* p, int64_t inner, int64_t outer, int64_t ld, uint32_t box_inner,
                uint32_t box_outer, bool sw128) {
   const cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
@@ -491,7 +522,9 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   } else {
     const cuuint64_t gdim[3] = {(cuuint64_t)g.L, (cuuint64_t)g.K, (cuuint64_t)g.b};
     const cuuint64_t gstride[2] = {(cuuint64_t)g.ldx * 4, (cuuint64_t)g.x_obs * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kTile, (cuuint32_t)kChunk, 1};
+    const bool nar = narrow_layout(g);
+    const cuuint32_t box[3] = {nar ? (cuuint32_t)g.L : (cuuint32_t)kTile, (cuuint32_t)kChunk,
+                               nar ? (cuuint32_t)(kTile / g.L) : 1u};
     const cuuint32_t es[3] = {1, 1, 1};
     if (encode_fn()(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(g.x), gdim, gstride, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -517,9 +550,12 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   a.L = g.L;
   a.m = g.K;
   a.r = g.r;
-  a.b = APRE ? 1 : g.b;
+  a.narrow = !APRE && narrow_layout(g);
+  a.opt = a.narrow ? (int)(kTile / g.L) : 1;
+  a.nb = APRE ? 1 : g.b;
+  a.b = a.narrow ? (a.nb + a.opt - 1) / a.opt : a.nb;
   a.nj = (g.r + NT - 1) / NT;
-  a.tpo = (int)((g.L + kTile - 1) / kTile);
+  a.tpo = a.narrow ? 1 : (int)((g.L + kTile - 1) / kTile);
   a.nch = (int)((g.K + kChunk - 1) / kChunk);
   a.mode = g.mode;
   a.out = g.out;
@@ -529,7 +565,10 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   a.ldl = g.ldl;
   const bool norms = !APRE && (g.x2 != nullptr || g.rho2 != nullptr);
   a.part_x = norms ? g.part : nullptr;
-  a.part_w = norms ? g.part + (int64_t)a.b * a.tpo * kConvWarps : nullptr;
+  const int64_t xs = std::max<int64_t>(1, g.L / 32);
+  const int64_t xper = a.narrow ? xs : (int64_t)a.tpo * kConvWarps;
+  const int64_t wper = a.narrow ? (int64_t)a.nj * 2 * xs : (int64_t)a.tpo * a.nj * kEpiWarps;
+  a.part_w = norms ? g.part + (int64_t)a.nb * xper : nullptr;
   a.status = g.status;
   a.wait_ns = g_wait_ns.load();
   a.drop_chunk = g_drop_chunk.exchange(-1);
@@ -540,7 +579,7 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   TT_CUDA(cudaGetLastError());
   if (norms) {
     note_launch();
-    tc_proj_reduce_kernel<<<a.b, 256, 0, st>>>(a.part_x, a.part_w, a.tpo, a.nj, g.x2, g.rho2);
+    tc_proj_reduce_kernel<<<a.nb, 256, 0, st>>>(a.part_x, a.part_w, xper, wper, g.x2, g.rho2);
     TT_CUDA(cudaGetLastError());
   }
   return cudaSuccess;
@@ -549,7 +588,9 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
 }  // namespace
 
 bool tc_proj_supported(const void* X, int64_t L, int64_t m, int r, int64_t ldhl) {
-  return encode_fn() != nullptr && (reinterpret_cast<uintptr_t>(X) % 16) == 0 && (L % 4) == 0 && L >= 32 &&
+  // columns per observation: >= 32 (a tile per 128 of them) or a divisor of 128 (observations packed)
+  const bool shape_ok = L >= 32 || (L >= 4 && kTile % L == 0);
+  return encode_fn() != nullptr && (reinterpret_cast<uintptr_t>(X) % 16) == 0 && (L % 4) == 0 && shape_ok &&
          L < (1LL << 31) && m >= 1 && m < (1LL << 31) && r >= 1 && (ldhl % 32) == 0;
 }
 

@@ -436,3 +436,30 @@ def test_tensor_core_cgs_matches_oracle(T):
         run_pair(T, frames, 8, 0.1, precision="fp32", tol=1e-4, orth_tol=1e-7)
     finally:
         T.ttice_test_tc_cgs_min(-1.0)
+
+
+def test_projection_kernel_packed_observations(T):
+    """Stages with fewer than 128 columns per observation (L = 4 and 16 here, dividing 128) pack
+    128 / L observations into one tile of the tensor-core projection: 40 observations fill two
+    tiles at L = 4 (32 + 8) and three at L = 16.  Coefficients and per-observation errors against
+    the oracle's projection (Eq. 12, Eq. 17)."""
+    dims = (12, 10, 16, 4)
+    ranks = [1, 12, 70, 40, 4]
+    rng = np.random.default_rng(9)
+    cores = []
+    for i, n in enumerate(dims):
+        q, _ = np.linalg.qr(rng.normal(size=(ranks[i] * n, ranks[i + 1])))
+        cores.append(q)
+    o = O.TTICEOracle(dims, 0.1)
+    o.ranks = list(ranks)
+    o.U = [c.copy() for c in cores]
+    C = rng.normal(size=(40, ranks[-1]))
+    Y = o.expand(C) + 0.05 * rng.normal(size=(40,) + dims)
+    g = T.TTICE(dims, 0.1, precision="fp32", input_dtype=torch.float32, max_batch=40, max_rank=128)
+    g.load(ranks, cores, np.zeros((1, ranks[-1])))
+    Yd = torch.tensor(Y, dtype=torch.float32).cuda()
+    coeffs, rel = g.project(Yd)
+    c32, rho32, y32 = o.errors(Yd.double().cpu().numpy())
+    assert _relmax(coeffs.cpu().numpy(), c32) < 1e-5
+    np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho32 / y32), rtol=1e-3)
+    g.close()
