@@ -439,10 +439,10 @@ def test_tensor_core_cgs_matches_oracle(T):
 
 
 def test_projection_kernel_packed_observations(T):
-    """Stages with fewer than 128 columns per observation (L = 4 and 16 here, dividing 128) pack
-    128 / L observations into one tile of the tensor-core projection: 40 observations fill two
-    tiles at L = 4 (32 + 8) and three at L = 16.  Coefficients and per-observation errors against
-    the oracle's projection (Eq. 12, Eq. 17)."""
+    """Stages with fewer than 128 columns per observation (L = 64 and 4 here, dividing 128) pack
+    128 / L observations into one tile of the tensor-core projection: 40 observations fill 20 tiles
+    at L = 64 (two per tile, each spanning two warps) and two at L = 4 (32 + 8).  Coefficients and
+    per-observation errors against the oracle's projection (Eq. 12, Eq. 17)."""
     dims = (12, 10, 16, 4)
     ranks = [1, 12, 70, 40, 4]
     rng = np.random.default_rng(9)
