@@ -75,7 +75,9 @@ constexpr size_t smem_bytes() {
 enum StoreMode {
   kStoreF32 = 0,  // out (float) = D, with the optional norm partials
   kSubF64 = 1,    // out (double) -= D
-  kSplitF32 = 2   // out, out2 (float) = TF32 head and tail of D (the operand form of a later product)
+  kSplitF32 = 2,  // out, out2 (float) = TF32 head and tail of D (the operand form of a later product)
+  kStoreF64 = 3,  // out (double) = D
+  kResidF32 = 4   // out (float) = in - D, in (float) read at its own layout (a residual)
 };
 
 struct ProjArgs {
@@ -88,6 +90,8 @@ struct ProjArgs {
   void* out;
   void* out2;
   int64_t o_obs, ldn, ldl;  // element (n, l) of observation z at z * o_obs + n * ldn + l * ldl
+  const float* in;          // kResidF32: in[(n / in_lz) in_obs + (n % in_lz) in_ldn + l in_ldl]
+  int64_t in_lz, in_obs, in_ldn, in_ldl;
   // norm partials, contiguous per observation: wide layout x [obs][tile][conv warp], w [obs][tile][N
   // tile][epilogue warp]; narrow layout x [obs][xs], w [obs][N tile][half][xs], xs = max(1, L / 32)
   double* part_x;
@@ -420,6 +424,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               static_cast<float*>(a.out)[o] = v;
             } else if (a.mode == kSubF64) {
               static_cast<double*>(a.out)[o] -= (double)v;
+            } else if (a.mode == kStoreF64) {
+              static_cast<double*>(a.out)[o] = (double)v;
+            } else if (a.mode == kResidF32) {
+              const int64_t zi = ai / a.in_lz;
+              static_cast<float*>(a.out)[o] =
+                  a.in[zi * a.in_obs + (ai - zi * a.in_lz) * a.in_ldn + l * a.in_ldl] - v;
             } else {
               const float hv = tf32_hi(v);
               static_cast<float*>(a.out)[o] = hv;
@@ -563,6 +573,11 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   a.o_obs = g.o_obs;
   a.ldn = g.ldn;
   a.ldl = g.ldl;
+  a.in = g.in;
+  a.in_lz = g.in_lz > 0 ? g.in_lz : 1;
+  a.in_obs = g.in_obs;
+  a.in_ldn = g.in_ldn;
+  a.in_ldl = g.in_ldl;
   const bool norms = !APRE && (g.x2 != nullptr || g.rho2 != nullptr);
   a.part_x = norms ? g.part : nullptr;
   const int64_t xs = std::max<int64_t>(1, g.L / 32);
@@ -641,9 +656,10 @@ void tc_drop_next_copy(long long chunk) { g_drop_chunk.store(chunk); }
 // cores read (ld_out rows each; rows beyond ld_in are left as they are).
 __global__ void split_tf32_kernel(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,
                                   int64_t ld_out) {
+  const int64_t rows = min((ld_in + 31) / 32 * 32, ld_out);  // the last K chunk is zero past the column
   for (int64_t c = c0 + blockIdx.y; c < c1; c += gridDim.y)
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ld_in; i += (int64_t)gridDim.x * blockDim.x) {
-      const float x = in[c * ld_in + i];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+      const float x = i < ld_in ? in[c * ld_in + i] : 0.0f;
       const float h = tf32_hi(x);
       hi[c * ld_out + i] = h;
       lo[c * ld_out + i] = tf32_hi(x - h);
@@ -669,6 +685,42 @@ cudaError_t launch_split_tf32_f64(const double* in, int64_t ld_in, int64_t rows,
   const int64_t by = std::min<int64_t>(c1 - c0, 1024);
   note_launch();
   split_tf32_f64_kernel<<<dim3((unsigned)bx, (unsigned)by), 256, 0, st>>>(in, ld_in, rows, c0, c1, hi, lo, ld_out);
+  return cudaGetLastError();
+}
+
+// W (b observations of r x L, row-major, observation-major) -> its transpose split: row n = z L + l
+// of hi / lo holds W[z][0..r)[l] (ld_out >= r, zero up to the next multiple of 32).  32 x 32 tiles
+// through shared memory, so that both the reads (along l) and the writes (along r) are coalesced.
+__global__ void split_tf32_transpose_kernel(const float* W, int64_t r, int64_t L, float* hi, float* lo,
+                                            int64_t ld_out) {
+  __shared__ float tile[32][33];
+  const int64_t z = blockIdx.z;
+  const int64_t a0 = (int64_t)blockIdx.y * 32, l0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8 threads
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t a = a0 + k, l = l0 + tx;
+    tile[k][tx] = (a < r && l < L) ? W[z * r * L + a * L + l] : 0.0f;
+  }
+  __syncthreads();
+  const int64_t r32 = (r + 31) / 32 * 32;
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t l = l0 + k, a = a0 + tx;
+    if (l < L && a < r32) {
+      const float x = tile[tx][k];
+      const float h = tf32_hi(x);
+      const int64_t o = (z * L + l) * ld_out + a;
+      hi[o] = h;
+      lo[o] = tf32_hi(x - h);
+    }
+  }
+}
+
+cudaError_t launch_split_tf32_transpose(const float* W, int b, int64_t r, int64_t L, float* hi, float* lo,
+                                        int64_t ld_out, cudaStream_t st) {
+  if (b <= 0 || r <= 0 || L <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((L + 31) / 32), (unsigned)((r + 31) / 32), (unsigned)b);
+  note_launch();
+  split_tf32_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(W, r, L, hi, lo, ld_out);
   return cudaGetLastError();
 }
 

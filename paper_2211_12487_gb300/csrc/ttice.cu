@@ -97,6 +97,15 @@ struct ttice_s {
   // rounded up to 32)
   float* Vnh = nullptr;
   float* Vnl = nullptr;
+  // tensor-core residual of the mixed path: the transposed TF32 split of U_i^T D_i (rows n = z L + l,
+  // ld ldwt) and the TF32 split of the residual for its Gram; rlay = layout of the residual in Rbuf:
+  // 0 the stage layout [z][i][l], 1 R^T (row n holds the m entries of column n), 2 R row-major
+  // (row i holds the c = nsel L entries)
+  float* WTh = nullptr;
+  float* WTl = nullptr;
+  float* Rh = nullptr;
+  float* Rl = nullptr;
+  int rlay = 0;
   float* Ph = nullptr;
   float* Pl = nullptr;
   int64_t ldv = 0, ldp = 0;
@@ -269,7 +278,7 @@ void free_all(ttice_s* h) {
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Ph, h->Pl, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
   cudaFreeHost(h->h_rn2);
@@ -579,13 +588,15 @@ int measure_energies(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, in
   using VT = WT;
   const VT* V = (sizeof(WT) == 8) ? reinterpret_cast<const VT*>(h->V64) : reinterpret_cast<const VT*>(h->V32);
   using ACC = typename std::conditional<sizeof(WT) == 8, double, float>::type;
+  const int64_t c = L * nsel;
   if (left) {
     GemmArgs g;  // E = V^T R, row norms
     g.M = s; g.N = L; g.K = m;
     g.A.p = V; g.A.rs = s; g.A.cs = 1;
     g.B.p = R; g.B.rs = L; g.B.cs = 1; g.B.bs1 = m * L;
+    if (h->rlay == 2) { g.N = c; g.B.rs = c; g.B.bs1 = 0; }  // row-major R: one m x c matrix
     g.store = 0; g.norm = e; g.norm_rows = 1;
-    g.nbatch = nsel;
+    g.nbatch = h->rlay == 2 ? 1 : nsel;
     TT_CU((gemm<VT, WT, double, double, ACC>(g, st)));
   } else {
     TT_CU(cudaMemsetAsync(h->Ebuf, 0, (size_t)m * s * sizeof(double), st));
@@ -593,11 +604,44 @@ int measure_energies(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, in
     g.M = m; g.N = s; g.K = L; g.atomic = 1; g.allow_splitk = 1;
     g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
     g.B.p = V; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
+    if (h->rlay == 1) { g.K = c; g.A.rs = 1; g.A.cs = m; g.A.bs1 = 0; g.B.bs1 = 0; }  // R^T storage
     g.C = h->Ebuf; g.c_rs = 1; g.c_cs = m;
-    g.nbatch = nsel;
+    g.nbatch = h->rlay == 1 ? 1 : nsel;
     TT_CU((gemm<WT, VT, double, double, ACC>(g, st)));
     TT_CU(launch_col_norms(h->Ebuf, m, (int)s, m, e, st));
   }
+  return TTICE_OK;
+}
+
+// Mixed path: residual work m r c above which R_i = D_i - U_i W runs on the tensor cores.
+constexpr double kTcResidMin = 2e8;
+
+// R = D - U_i W for the nsel selected observations on the tensor cores (D: FP32, stage layout; W =
+// U_i^T D, FP32, stage layout): the transposed split of W is the B operand, the FP32 mirror of U_i
+// the A operand (lanes = rows of R), and the epilogue subtracts from D.  R is written as R^T (for a
+// column-side Gram, c < m) or row-major (row side), the layouts the Gram's pre-split operands need.
+bool tc_resid_ok(const ttice_s* h, int i, int64_t m, int64_t L, int nsel, int64_t ri) {
+  const int64_t c = L * nsel;
+  return h->Uh[i] != nullptr && ri > 0 && m >= 32 && m % 4 == 0 && h->ldu[i] % 4 == 0 &&
+         (m > c || c % 4 == 0) && (double)m * ri * c >= kTcResidMin;
+}
+int tc_resid(ttice_s* h, int i, const float* D, const float* W, int64_t m, int64_t L, int nsel, int64_t ri,
+             float* R, cudaStream_t st) {
+  const int64_t c = L * nsel, ldwt = (ri + 31) / 32 * 32;
+  TT_CU(launch_split_tf32_transpose(W, nsel, ri, L, h->WTh, h->WTl, ldwt, st));
+  TcGemm g;
+  g.x = h->Uf[i]; g.ldx = h->ldu[i]; g.x_obs = h->ldu[i] * ri; g.b = 1;
+  g.L = m; g.K = ri;
+  g.bh = h->WTh; g.bl = h->WTl; g.ldb = ldwt; g.nb_alloc = c;
+  g.r = (int)c;
+  g.mode = 4; g.out = R;
+  g.in = D; g.in_lz = L; g.in_obs = m * L; g.in_ldn = 1; g.in_ldl = L;
+  const bool left = m <= c;
+  if (left) { g.ldn = 1; g.ldl = c; }  // row i of R: the c columns
+  else { g.ldn = m; g.ldl = 1; }       // row n of R^T: the m entries of column n
+  g.status = h->ibuf + 5;
+  TT_CU(launch_tc_gemm(g, st));
+  h->rlay = left ? 2 : 1;
   return TTICE_OK;
 }
 
@@ -613,6 +657,20 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   if (s > kMaxEig) return TTICE_ECAPACITY;
   // Gram (FP64 accumulation)
   ph_begin(h, PH_GRAM, st, (double)sizeof(WT) * m * c + 8.0 * s * s, 2.0 * (double)s * s * (left ? c : m));
+  if (h->rlay != 0) {
+    // residual from the tensor cores (R^T or row-major R): the Gram as a product of two pre-split
+    // operands on the tensor cores, every row of the residual against every other (both triangles)
+    const int64_t kdim = h->rlay == 1 ? m : c, ld32 = (kdim + 31) / 32 * 32;
+    TT_CU(launch_split_tf32(reinterpret_cast<const float*>(R), kdim, 0, s, h->Rh, h->Rl, ld32, st));
+    TcGemm g;
+    g.ah = h->Rh; g.al = h->Rl; g.lda = ld32; g.la_alloc = s;
+    g.L = s; g.K = kdim;
+    g.bh = h->Rh; g.bl = h->Rl; g.ldb = ld32; g.nb_alloc = s;
+    g.r = (int)s;
+    g.mode = 3; g.out = h->G; g.ldn = s; g.ldl = 1;
+    g.status = h->ibuf + 5;
+    TT_CU(launch_tc_gemm(g, st));
+  } else {
   TT_CU(cudaMemsetAsync(h->G, 0, (size_t)s * s * sizeof(double), st));
   {
     GemmArgs g;
@@ -636,6 +694,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     }
     if constexpr (sizeof(WT) == 8) TT_CU((gemm<WT, WT, WT, double, double>(g, st)));
     else TT_CU((gemm<WT, WT, WT, double, float>(g, st)));  // FP32 products, FP64 accumulation
+  }
   }
   TT_CU(launch_trace(h->G, s, (int)s, h->trace, st));
   ph_end(h, st);
@@ -781,8 +840,9 @@ int build_dirs(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int c0, 
     g.M = m; g.N = k; g.K = L; g.atomic = 1; g.allow_splitk = 1;
     g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
     g.B.p = Vdir; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
+    if (h->rlay == 1) { g.K = L * nsel; g.A.rs = 1; g.A.cs = m; g.A.bs1 = 0; g.B.bs1 = 0; }  // R^T storage
     g.C = h->Vn; g.c_rs = 1; g.c_cs = m;
-    g.nbatch = nsel;
+    g.nbatch = h->rlay == 1 ? 1 : nsel;
     // mixed path: FP32 products of the FP32 residual (FP64 accumulation); the directions are
     // re-orthogonalised against the core and among themselves afterwards
     using BACC = typename std::conditional<sizeof(WT) == 8, double, float>::type;
@@ -1002,13 +1062,33 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
                    4.0 * nsel * (double)m * L * ri);
         }
         bool small = false;  // ||R_i||_F <= eps_c: the rank rule gives 0 without any eigenvalue
+        h->rlay = 0;
+        // mixed path, FP32 stage input: the residual on the tensor cores
+        const void* Din = i == 0 ? static_cast<const void*>(D0i) : static_cast<const void*>(Xi);
+        const bool tcr = sizeof(WT) == 4 && (i > 0 || sizeof(TY) == 4) && tc_resid_ok(h, i, m, L, nsel, ri);
         if (ri > 0 && pristine) {
           double t = 0.0;
           for (int z = 0; z < nsel; ++z) t += h->h_rho2[(int64_t)i * b + h->h_sel[z]];
           small = std::sqrt(t) <= dec.eps_c;
-          if (!small) {
+          if (!small && tcr) {
+            rc = tc_resid(h, i, static_cast<const float*>(Din), reinterpret_cast<const float*>(Wp), m, L, nsel, ri,
+                          reinterpret_cast<float*>(R), st);
+          } else if (!small) {
             if (i == 0) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wp, D0i, m, L, ri, nsel, R, nullptr, st);
             else rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wp, Xi, m, L, ri, nsel, R, nullptr, st);
+          }
+        } else if (ri > 0 && tcr && tc_stage(h, i, Din)) {
+          // U_i^T D_i and ||D_i||^2 - ||U_i^T D_i||^2 per observation, then the explicit residual
+          rc = tc_project(h, i, Din, nsel, Wt, nullptr, h->rn2, st);
+          if (rc == TTICE_OK)
+            rc = tc_resid(h, i, static_cast<const float*>(Din), reinterpret_cast<const float*>(Wt), m, L, nsel, ri,
+                          reinterpret_cast<float*>(R), st);
+          if (rc == TTICE_OK) rc = cu(cudaMemcpyAsync(h->h_rn2, h->rn2, nsel * sizeof(double), cudaMemcpyDeviceToHost, st));
+          if (rc == TTICE_OK) rc = sync_read(h, st);
+          if (rc == TTICE_OK) {
+            double t = 0.0;
+            for (int z = 0; z < nsel; ++z) t += h->h_rn2[z];
+            small = std::sqrt(t) <= dec.eps_c;
           }
         } else if (ri > 0) {
           rc = cu(cudaMemsetAsync(h->rn2, 0, nsel * sizeof(double), st));
@@ -1282,6 +1362,16 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Vnl, h->ldv * kRR);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Ph, h->ldp * kRR);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Pl, h->ldp * kRR);
+    int64_t wt = 0, rs = 0;
+    for (int i = 0; i < d; ++i) {
+      const int64_t c = B * h->L[i], mi = h->ldu[i];
+      wt = std::max(wt, c * ((h->cap[i + 1] + 31) / 32 * 32));
+      rs = std::max(rs, std::max(c * ((mi + 31) / 32 * 32), mi * ((c + 31) / 32 * 32)));
+    }
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->WTh, wt);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->WTl, wt);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->Rh, rs);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->Rl, rs);
   }
   int64_t part_elems = std::max<int64_t>(2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)),
                                          k1_tc_part_elems((int)B, h->L[0]));

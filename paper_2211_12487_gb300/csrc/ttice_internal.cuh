@@ -167,7 +167,8 @@ cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, c
 //      zero beyond the operand), copied by TMA.
 //   Store of D[n][l] of observation z at o = z o_obs + n ldn + l ldl, by `mode`: 0 float out[o] = D
 //   (with x2 / rho2 as for launch_tc_proj), 1 double out[o] -= D, 2 float out[o], out2[o] = TF32
-//   head and tail of D.
+//   head and tail of D, 3 double out[o] = D, 4 float out[o] = in[(n / in_lz) in_obs + (n % in_lz)
+//   in_ldn + l in_ldl] - D (a residual whose input has its own layout).
 struct TcGemm {
   const float* x = nullptr;
   int64_t ldx = 0, x_obs = 0;
@@ -185,13 +186,20 @@ struct TcGemm {
   void* out = nullptr;
   void* out2 = nullptr;
   int64_t o_obs = 0, ldn = 0, ldl = 1;
+  const float* in = nullptr;
+  int64_t in_lz = 1, in_obs = 0, in_ldn = 0, in_ldl = 0;
   double* x2 = nullptr;
   double* rho2 = nullptr;
   double* part = nullptr;
   int* status = nullptr;
 };
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t st);
-// TF32 head/tail split of FP32 columns [c0, c1) (ld_in rows) into hi, lo (ld_out).
+// Transposing split of b observations of W (r x L, row-major): row z L + l of hi / lo (ld_out >= r)
+// holds the TF32 head / tail of W[z][:][l], zero up to the next multiple of 32.
+cudaError_t launch_split_tf32_transpose(const float* W, int b, int64_t r, int64_t L, float* hi, float* lo,
+                                        int64_t ld_out, cudaStream_t st);
+// TF32 head/tail split of FP32 columns [c0, c1) (ld_in rows, zero up to the next multiple of 32
+// within ld_out) into hi, lo (ld_out).
 cudaError_t launch_split_tf32(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,
                               int64_t ld_out, cudaStream_t st);
 // The same from FP64 columns (rows [0, rows), zero up to the next multiple of 32): head = tf32(x),
