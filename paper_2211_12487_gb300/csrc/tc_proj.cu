@@ -86,6 +86,10 @@ struct ProjArgs {
   // narrow layout (L <= 64 dividing 128): a tile holds opt = 128 / L whole observations, lane
   // o L + l = column l of observation t opt + o; b counts tiles then, nb the observations
   int narrow, opt, nb;
+  // split K: item q of an nsplit-fold launch covers chunks [ks cps, min(nch, (ks + 1) cps)) of
+  // K, ks = q / (b tpo nj), and stores its partial D at out + ks ws_stride (kStoreF32 only)
+  int nsplit, cps;
+  int64_t ws_stride, px_stride;  // partial D and x^2 partials of one K split
   int mode;
   void* out;
   void* out2;
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
-  const int64_t nitems = (int64_t)a.b * a.tpo * a.nj;
+  const int64_t nitems = (int64_t)a.nsplit * a.b * a.tpo * a.nj;
   const unsigned long long lim = a.wait_ns;
 
   if (wid == kProducerWarp) {
@@ -173,8 +177,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
         const int j = (int)(q % a.nj);
         const int t = (int)((q / a.nj) % a.tpo);
-        const int z = (int)(q / ((int64_t)a.nj * a.tpo));
-        for (int c = 0; c < a.nch; ++c, ++g) {
+        const int z = (int)((q / ((int64_t)a.nj * a.tpo)) % a.b);
+        const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
+        const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
+        for (int c = c_lo; c < c_hi; ++c, ++g) {
           const int s = (int)(g % RAW), sb = (int)(g % BST), qa = (int)(g % AST);
           if constexpr (APRE) {
             if (g >= AST && !wait_bounded(&a_empty[qa], (uint32_t)(((g / AST) - 1) & 1), &abort_flag, lim)) {
@@ -227,13 +233,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x, ++it) {
         const int j = (int)(q % a.nj);
+        const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
+        const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
         const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);  // MMA N of this item
         const uint32_t idesc = tf32_idesc(kTile, nN);
         if (it >= 2 && !wait_bounded(&cross_empty[it & 1], (uint32_t)(((it >> 1) - 1) & 1), &abort_flag, lim)) break;
         const uint32_t dc = tmem + (uint32_t)((2 + (it & 1)) * NT);
         uint32_t d = 0;
-        for (int c = 0; c < a.nch; ++c, ++g) {
-          const int cs = c % kSeg;  // chunk within its segment
+        for (int c = c_lo; c < c_hi; ++c, ++g) {
+          const int cs = (c - c_lo) % kSeg;  // chunk within its segment
           if (cs == 0) {
             const int p = (int)(sg & 1);
             if (sg >= 2 && !wait_bounded(&seg_empty[p], (uint32_t)(((sg >> 1) - 1) & 1), &abort_flag, lim)) {
@@ -261,12 +269,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             // head x head into the segment's main accumulator; the two tail products (~2^-11 of it)
             // into the item's cross accumulator
             mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
-            mma_tf32(dc, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, (c | kk) != 0);
+            mma_tf32(dc, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, ((c - c_lo) | kk) != 0);
             mma_tf32(dc, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
           }
           mma_commit(&a_empty[qa]);  // these slots are free once the MMAs above have read them
           mma_commit(&b_empty[sb]);
-          if (cs == kSeg - 1 || c == a.nch - 1) {
+          if (cs == kSeg - 1 || c == c_hi - 1) {
             mma_commit(&seg_full[sg & 1]);  // the segment (and, after the last one, the cross sum) is done
             ++sg;
           }
@@ -283,10 +291,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t q = blockIdx.x; q < nitems; q += gridDim.x) {
       const int j = (int)(q % a.nj);
       const int t = (int)((q / a.nj) % a.tpo);
-      const int z = (int)(q / ((int64_t)a.nj * a.tpo));
+      const int z = (int)((q / ((int64_t)a.nj * a.tpo)) % a.b);
+      const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
+      const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
+      double* part_x = a.part_x ? a.part_x + (int64_t)ks * a.px_stride : nullptr;
       float x2 = 0.0f;
       bool ok = true;
-      for (int c = 0; c < a.nch; ++c, ++g) {
+      for (int c = c_lo; c < c_hi; ++c, ++g) {
         const int s = (int)(g % RAW), qa = (int)(g % AST);
         bool got = wait_bounded(&raw_full[s], (uint32_t)((g / RAW) & 1), &abort_flag, lim);
         if (got && g >= AST) got = wait_bounded(&a_empty[qa], (uint32_t)(((g / AST) - 1) & 1), &abort_flag, lim);
@@ -330,18 +341,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) break;
-      if (a.part_x && j == 0) {
+      if (part_x && j == 0) {
         double s = (double)x2;
         if (a.narrow) {  // sum over the lanes of one observation (aligned groups of min(L, 32))
           const int gsz = min((int)a.L, 32);
           for (int o = 1; o < gsz; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
           const int ob = tid / (int)a.L, l = tid % (int)a.L, zz = z * a.opt + ob;
           const int xs = max(1, (int)a.L / 32);
-          if (ob < a.opt && zz < a.nb && (l & 31) == 0) a.part_x[(int64_t)zz * xs + l / 32] = s;
+          if (ob < a.opt && zz < a.nb && (l & 31) == 0) part_x[(int64_t)zz * xs + l / 32] = s;
         } else {
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0) a.part_x[((int64_t)z * a.tpo + t) * kConvWarps + wid] = s;
+          if (lane == 0) part_x[((int64_t)z * a.tpo + t) * kConvWarps + wid] = s;
         }
       }
     }
@@ -352,14 +363,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     // then the item's cross accumulator; the result is stored as W and its squares summed.
     constexpr int H = NT / 2;
     const int ew = wid - kConvWarps, qd = ew & 3, hf = ew >> 2;  // lane quarter, half of the N tile
-    const int nseg = (a.nch + kSeg - 1) / kSeg;
     int64_t sg = 0;
     int it = 0;
     bool ok = true;
     for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x, ++it) {
       const int j = (int)(q % a.nj);
       const int t = (int)((q / a.nj) % a.tpo);
-      const int z = (int)(q / ((int64_t)a.nj * a.tpo));
+      const int z = (int)((q / ((int64_t)a.nj * a.tpo)) % a.b);
+      const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
+      const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
+      const int nseg = (c_hi - c_lo + kSeg - 1) / kSeg;
       const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);
       const int c0 = hf * H;  // first column of this warp's half
       float run[H];
@@ -410,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t zl = a.narrow ? (int64_t)z * a.opt + ob : z;           // its observation
       const int64_t l = a.narrow ? cl % (int)a.L : (int64_t)t * kTile + cl;  // its column there
       const bool lane_ok = !a.narrow || (ob < a.opt && zl < a.nb);
-      const int64_t base = zl * a.o_obs + l * a.ldl;
+      const int64_t base = zl * a.o_obs + l * a.ldl + ks * a.ws_stride;
       float w2 = 0.0f;
 #pragma unroll
       for (int e = 0; e < H; ++e) {
@@ -479,6 +492,39 @@ __global__ void tc_proj_reduce_kernel(const double* part_x, const double* part_w
     if ((int)threadIdx.x < o) {
       ax[threadIdx.x] += ax[threadIdx.x + o];
       aw[threadIdx.x] += aw[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (x2_out) x2_out[z] = ax[0];
+    if (rho2_out) rho2_out[z] = fmin(fmax(ax[0] - aw[0], 0.0), ax[0]);
+  }
+}
+
+// After a split-K launch: W = sum over the splits of the partial products (block of o_obs elements
+// per observation), w^2 of the sum, x^2 summed over splits and slots, rho2 = x^2 - w^2 (clamped).
+__global__ void tc_splitk_reduce_kernel(const float* ws, int nsplit, int64_t ws_stride, int64_t o_obs, float* W,
+                                        const double* part_x, int64_t px_stride, int64_t xper, double* x2_out,
+                                        double* rho2_out) {
+  const int z = blockIdx.x;
+  double w2 = 0.0, sx = 0.0;
+  for (int64_t e = threadIdx.x; e < o_obs; e += blockDim.x) {
+    float acc = 0.0f;
+    for (int k = 0; k < nsplit; ++k) acc += ws[k * ws_stride + z * o_obs + e];
+    W[z * o_obs + e] = acc;
+    w2 += (double)acc * acc;
+  }
+  if (part_x)
+    for (int64_t i = threadIdx.x; i < (int64_t)nsplit * xper; i += blockDim.x)
+      sx += part_x[(i / xper) * px_stride + z * xper + i % xper];
+  __shared__ double aw[256], ax[256];
+  aw[threadIdx.x] = w2;
+  ax[threadIdx.x] = sx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      aw[threadIdx.x] += aw[threadIdx.x + o];
+      ax[threadIdx.x] += ax[threadIdx.x + o];
     }
     __syncthreads();
   }
@@ -579,20 +625,39 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   a.in_ldn = g.in_ldn;
   a.in_ldl = g.in_ldl;
   const bool norms = !APRE && (g.x2 != nullptr || g.rho2 != nullptr);
+  // split K when the output is too small to fill the GPU (few, tall contractions): chain layout only
+  const int64_t items1 = (int64_t)a.b * a.tpo * a.nj, wsz = (int64_t)a.nb * g.r * g.L;
+  a.nsplit = 1;
+  if (!APRE && g.mode == kStoreF32 && g.ws && g.o_obs == (int64_t)g.r * g.L && g.ldn == g.L && g.ldl == 1 &&
+      items1 < sms && a.nch >= 8) {
+    int64_t ns = std::min<int64_t>((2 * sms + items1 - 1) / items1, a.nch / 4);
+    ns = std::min<int64_t>(ns, g.ws_elems / std::max<int64_t>(wsz, 1));
+    if (ns >= 2) a.nsplit = (int)ns;
+  }
+  a.cps = (a.nch + a.nsplit - 1) / a.nsplit;
+  a.nsplit = (a.nch + a.cps - 1) / a.cps;  // every split has at least one chunk
+  a.ws_stride = a.nsplit > 1 ? wsz : 0;
+  if (a.nsplit > 1) a.out = g.ws;
   a.part_x = norms ? g.part : nullptr;
   const int64_t xs = std::max<int64_t>(1, g.L / 32);
   const int64_t xper = a.narrow ? xs : (int64_t)a.tpo * kConvWarps;
   const int64_t wper = a.narrow ? (int64_t)a.nj * 2 * xs : (int64_t)a.tpo * a.nj * kEpiWarps;
-  a.part_w = norms ? g.part + (int64_t)a.nb * xper : nullptr;
+  a.px_stride = (int64_t)a.nb * xper;
+  a.part_w = norms && a.nsplit == 1 ? g.part + (int64_t)a.nsplit * a.nb * xper : nullptr;
   a.status = g.status;
   a.wait_ns = g_wait_ns.load();
   a.drop_chunk = g_drop_chunk.exchange(-1);
-  const int64_t nitems = (int64_t)a.b * a.tpo * a.nj;
+  const int64_t nitems = (int64_t)a.nsplit * items1;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(sms, nitems));
   note_launch();
   tc_proj_kernel<NT, APRE><<<(unsigned)grid, kThreads, smem_bytes<NT>(), st>>>(xmap, xlmap, uhmap, ulmap, a);
   TT_CUDA(cudaGetLastError());
-  if (norms) {
+  if (a.nsplit > 1) {
+    note_launch();
+    tc_splitk_reduce_kernel<<<a.nb, 256, 0, st>>>(g.ws, a.nsplit, wsz, (int64_t)g.r * g.L, static_cast<float*>(g.out),
+                                                 a.part_x, a.px_stride, xper, g.x2, g.rho2);
+    TT_CUDA(cudaGetLastError());
+  } else if (norms) {
     note_launch();
     tc_proj_reduce_kernel<<<a.nb, 256, 0, st>>>(a.part_x, a.part_w, xper, wper, g.x2, g.rho2);
     TT_CUDA(cudaGetLastError());
@@ -609,10 +674,11 @@ bool tc_proj_supported(const void* X, int64_t L, int64_t m, int r, int64_t ldhl)
          L < (1LL << 31) && m >= 1 && m < (1LL << 31) && r >= 1 && (ldhl % 32) == 0;
 }
 
-int64_t tc_proj_part_elems(int b, int64_t L, int64_t r) {
+int64_t tc_proj_part_elems(int b, int64_t L, int64_t r, int64_t m) {
   const int64_t tpo = (L + kTile - 1) / kTile;
   const int64_t nj = (r + 63) / 64;  // the most N tiles any tile width gives
-  return (int64_t)b * tpo * (kConvWarps + nj * kEpiWarps);
+  const int64_t nch = (m + kChunk - 1) / kChunk;  // the most K splits (x^2 partials per split)
+  return (int64_t)b * tpo * (kConvWarps + nj * kEpiWarps) + (int64_t)b * std::max<int64_t>(2, tpo * kConvWarps) * (nch / 4 + 1);
 }
 
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t st) {
@@ -624,7 +690,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t st) {
 
 cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
                            int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
-                           int* status, cudaStream_t st) {
+                           float* ws, int* status, cudaStream_t st) {
   TcGemm g;
   g.x = X;
   g.ldx = L;
@@ -646,6 +712,8 @@ cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, c
   g.rho2 = rho2;
   g.part = part;
   g.status = status;
+  g.ws = ws;
+  g.ws_elems = ws ? tc_ws_elems : 0;
   return launch_tc_gemm(g, st);
 }
 

@@ -106,6 +106,7 @@ struct ttice_s {
   float* Rh = nullptr;
   float* Rl = nullptr;
   int rlay = 0;
+  float* tcws = nullptr;  // split-K workspace of the tensor-core projections (tc_ws_elems floats)
   float* Ph = nullptr;
   float* Pl = nullptr;
   int64_t ldv = 0, ldp = 0;
@@ -278,7 +279,7 @@ void free_all(ttice_s* h) {
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->tcws, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
   cudaFreeHost(h->h_rn2);
@@ -334,8 +335,8 @@ bool tc_stage(const ttice_s* h, int i, const void* X) {
 }
 int tc_project(ttice_s* h, int i, const void* X, int b, void* W, double* x2, double* rho2, cudaStream_t st) {
   return cu(launch_tc_proj(static_cast<const float*>(X), b, h->L[i], h->r[i] * h->n[i], (int)h->r[i + 1], h->Uh[i],
-                           h->Ul[i], h->ldhl[i], h->hlcols[i], static_cast<float*>(W), x2, rho2, h->part, h->ibuf + 5,
-                           st));
+                           h->Ul[i], h->ldhl[i], h->hlcols[i], static_cast<float*>(W), x2, rho2, h->part, h->tcws,
+                           h->ibuf + 5, st));
 }
 
 // ---------------------------------------------------------------- chain projection
@@ -1372,11 +1373,13 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
     if (rc == TTICE_OK) rc = dalloc<float>(&h->WTl, wt);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Rh, rs);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Rl, rs);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->tcws, tc_ws_elems);
   }
   int64_t part_elems = std::max<int64_t>(2 * std::max<int64_t>(4 * 152 + B, B * ((h->L[0] + 255) / 256)),
                                          k1_tc_part_elems((int)B, h->L[0]));
   if (h->wt_bytes == 4)
-    for (int i = 0; i < d; ++i) part_elems = std::max(part_elems, tc_proj_part_elems((int)B, h->L[i], h->cap[i + 1]));
+    for (int i = 0; i < d; ++i)
+      part_elems = std::max(part_elems, tc_proj_part_elems((int)B, h->L[i], h->cap[i + 1], h->ldu[i]));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->part, part_elems);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rho2, (int64_t)h->d * B);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->rn2, B);

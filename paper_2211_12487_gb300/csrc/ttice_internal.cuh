@@ -149,13 +149,15 @@ cudaError_t launch_k1_tc(const float* Y, int b, int64_t L, int n1, int r, const 
 // observations, X(z) m x L row-major FP32 (16-byte aligned, L % 4 == 0, L >= 32), U given as its
 // TF32 head/tail pair Uh, Ul (column-major, ld ldhl % 32 == 0, hlcols columns allocated, zero beyond
 // the core), W(z) r x L row-major.  With x2 and/or rho2 (device, b doubles each): x2[z] = ||X(z)||^2,
-// rho2[z] = ||X(z)||^2 - ||W(z)||^2 (clamped to [0, x2]).  part: tc_proj_part_elems(b, L, r) doubles.
+// rho2[z] = ||X(z)||^2 - ||W(z)||^2 (clamped to [0, x2]).  part: tc_proj_part_elems(b, L, r, m) doubles.
+// ws: tc_ws_elems floats of workspace for splitting K (may be null).
 // status becomes nonzero if a wait of the kernel expired.
 bool tc_proj_supported(const void* X, int64_t L, int64_t m, int r, int64_t ldhl);
-int64_t tc_proj_part_elems(int b, int64_t L, int64_t r);
+int64_t tc_proj_part_elems(int b, int64_t L, int64_t r, int64_t m);
+constexpr int64_t tc_ws_elems = 16LL << 20;
 cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
                            int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
-                           int* status, cudaStream_t st);
+                           float* ws, int* status, cudaStream_t st);
 // General product on the tensor cores (the same kernel): D[n][l] = sum_k B(k, n) A(k, l) for
 // n < r (N), l < L (M, per observation), k < K, each operand split into TF32 head and tail (three
 // products, FP32 accuracy; the main product summed in registers over 64-long K segments).
@@ -192,6 +194,10 @@ struct TcGemm {
   double* rho2 = nullptr;
   double* part = nullptr;
   int* status = nullptr;
+  // optional workspace (floats) for splitting K when the output alone cannot fill the GPU (mode 0 in
+  // the chain layout o_obs = r L, ldn = L, ldl = 1): partial products, then a summing pass
+  float* ws = nullptr;
+  int64_t ws_elems = 0;
 };
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t st);
 // Transposing split of b observations of W (r x L, row-major): row z L + l of hi / lo (ld_out >= r)
