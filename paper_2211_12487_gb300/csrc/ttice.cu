@@ -106,6 +106,7 @@ struct ttice_s {
   float* Rh = nullptr;
   float* Rl = nullptr;
   int rlay = 0;
+  int64_t wt_elems = 0, rs_elems = 0;  // sizes of WTh / WTl and of Rh / Rl (floats each)
   float* tcws = nullptr;  // split-K workspace of the tensor-core projections (tc_ws_elems floats)
   float* Ph = nullptr;
   float* Pl = nullptr;
@@ -599,6 +600,20 @@ int measure_energies(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, in
     g.store = 0; g.norm = e; g.norm_rows = 1;
     g.nbatch = h->rlay == 2 ? 1 : nsel;
     TT_CU((gemm<VT, WT, double, double, ACC>(g, st)));
+  } else if (sizeof(WT) == 4 && h->rlay == 1 && h->Rh && s * ((s + 31) / 32 * 32) <= h->rs_elems) {
+    // E = R V (m x s) on the tensor cores: R^T (rows n, the m entries of column n of R) as the
+    // A operand, the split FP32 eigenvectors as the B operand; then the column norms
+    const int64_t lds = (s + 31) / 32 * 32;
+    TT_CU(launch_split_tf32(reinterpret_cast<const float*>(V), s, 0, s, h->Rh, h->Rl, lds, st));
+    TcGemm g;
+    g.x = reinterpret_cast<const float*>(R); g.ldx = m; g.x_obs = m * c; g.b = 1;
+    g.L = m; g.K = c;
+    g.bh = h->Rh; g.bl = h->Rl; g.ldb = lds; g.nb_alloc = s;
+    g.r = (int)s;
+    g.mode = 3; g.out = h->Ebuf; g.ldn = m; g.ldl = 1;
+    g.status = h->ibuf + 5;
+    TT_CU(launch_tc_gemm(g, st));
+    TT_CU(launch_col_norms(h->Ebuf, m, (int)s, m, e, st));
   } else {
     TT_CU(cudaMemsetAsync(h->Ebuf, 0, (size_t)m * s * sizeof(double), st));
     GemmArgs g;  // E = R V (m x s), column norms
@@ -835,6 +850,19 @@ int build_dirs(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int c0, 
   if (h->dir_left) {
     TT_CU(cudaMemcpy2DAsync(h->Vn, m * sizeof(double), Vdir, s * sizeof(double), m * sizeof(double),
                             k, cudaMemcpyDeviceToDevice, st));
+  } else if (sizeof(WT) == 4 && h->rlay == 1 && h->WTh && ((s + 31) / 32 * 32) * k <= h->wt_elems) {
+    // u_j = R v_j on the tensor cores: R^T as the A operand, the split eigenvectors as B
+    const int64_t lds = (s + 31) / 32 * 32, c = L * nsel;
+    TT_CU(launch_split_tf32_f64(Vdir, s, s, 0, k, h->WTh, h->WTl, lds, st));
+    TcGemm g;
+    g.x = reinterpret_cast<const float*>(R); g.ldx = m; g.x_obs = m * c; g.b = 1;
+    g.L = m; g.K = c;
+    g.bh = h->WTh; g.bl = h->WTl; g.ldb = lds; g.nb_alloc = k;
+    g.r = k;
+    g.mode = 3; g.out = h->Vn; g.ldn = m; g.ldl = 1;
+    g.status = h->ibuf + 5;
+    TT_CU(launch_tc_gemm(g, st));
+    TT_CU(launch_scale_cols_rsqrt(h->Vn, m, k, m, h->dir_scale + c0, st));
   } else {
     TT_CU(cudaMemsetAsync(h->Vn, 0, (size_t)m * k * sizeof(double), st));
     GemmArgs g;
@@ -1369,6 +1397,8 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
       wt = std::max(wt, c * ((h->cap[i + 1] + 31) / 32 * 32));
       rs = std::max(rs, std::max(c * ((mi + 31) / 32 * 32), mi * ((c + 31) / 32 * 32)));
     }
+    h->wt_elems = wt;
+    h->rs_elems = rs;
     if (rc == TTICE_OK) rc = dalloc<float>(&h->WTh, wt);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->WTl, wt);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Rh, rs);
