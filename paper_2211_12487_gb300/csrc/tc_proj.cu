@@ -13,11 +13,13 @@
 // tf32(x - x_hi), both rounded to nearest, so the MMA reads them exactly; x_hi + x_lo carries
 // ~2^-22 relative error), and each K step issues A_hi B_hi into a main accumulator and A_lo B_hi +
 // A_hi B_lo into a cross accumulator (the dropped tail product is ~2^-22 relative), FP32 in tensor
-// memory; the epilogue adds the two.  The accumulators add K
-// in segments of kSeg chunks (256 values of K): each segment starts a fresh accumulator, and the
-// epilogue adds the segments into W with FP32 round-to-nearest.  (Accumulating thousands of
-// K steps in one tensor-memory accumulator measurably biases W, ~1e-5 relative at K = 4096, against
-// ~1e-6 for 256-long segments.)  W is then at FP32 accuracy.  The
+// memory.  Every add into a tensor-memory accumulator carries a rounding biased towards zero (about
+// half an ulp, measured through the per-observation residuals), so the main accumulator adds K in
+// 32-long segments (4 adds; one segment when K <= 256) that the epilogue sums into FP32 registers
+// with round-to-nearest, from a ring of segment accumulators so that the MMAs run ahead of the
+// epilogue; the cross products, ~2^-11 of the main ones, keep one accumulator per item.  W is then
+// at FP32 accuracy up to that bias, which grows like sqrt(K / 32) ulps (~3e-6 relative at K = 2e4);
+// the Pythagorean residual ||X||^2 - ||W||^2 inherits it multiplied by ||X||^2 / ||R||^2.  The
 // head/tail pair of U is kept in global memory next to the core (ttice_s::Uh, Ul) and copied
 // straight into the 128-byte-swizzled K-major B operand by TMA; X is staged raw by TMA and split by
 // converter warps, which write the K-major A operand.
@@ -31,8 +33,7 @@
 //   warp 12    one lane issues the TMA copies (X chunk, U head and tail chunk);
 //   warp 13    allocates tensor memory; one lane issues the MMAs, committing each chunk to the
 //              barriers that free its A and B slots, and each segment to its accumulator's barrier
-//              (two main and two cross accumulators, so the MMAs of one segment overlap the
-//              epilogue of the previous one).
+//              (a ring of 6 main and 2 cross accumulators at N = 64, 3 and 1 at N = 128).
 // Every wait is bounded in time (the limit is a launch argument); on expiry the waiting thread
 // raises a CTA-wide abort flag, every role leaves its loop, the MMA lane waits for the MMAs it
 // issued and the producer for its copies in flight, tensor memory is freed and `status` records the
@@ -55,7 +56,14 @@ constexpr int kProducerWarp = kConvWarps + kEpiWarps, kMmaWarp = kProducerWarp +
 constexpr int kThreads = (kMmaWarp + 1) * 32;
 constexpr uint32_t kRawBytes = kChunk * kTile * 4;  // 16 KB
 constexpr uint32_t kABytes = kTile * kChunk * 4;    // 16 KB per half (head or tail)
-constexpr int kSeg = 1;      // chunks in one segment of the main accumulator (32 values of K)
+// ring depths of the main-accumulator segments and of the per-item cross accumulator in tensor
+// memory (SEGB + CB accumulators of NT columns <= 512)
+template <int NT>
+struct Tm;
+template <>
+struct Tm<64> { static constexpr int segb = 6, cb = 2; };
+template <>
+struct Tm<128> { static constexpr int segb = 3, cb = 1; };
 
 // ring depths per N tile (dynamic shared memory stays within 227 KB)
 template <int NT>
@@ -89,6 +97,7 @@ struct ProjArgs {
   // split K: item q of an nsplit-fold launch covers chunks [ks cps, min(nch, (ks + 1) cps)) of
   // K, ks = q / (b tpo nj), and stores its partial D at out + ks ws_stride (kStoreF32 only)
   int nsplit, cps;
+  int seglen;  // chunks per main-accumulator segment
   int64_t ws_stride, px_stride;  // partial D and x^2 partials of one K split
   int mode;
   void* out;
@@ -117,7 +126,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t kBBytes = NT * 128;  // one half of a B chunk: NT rows of 128 bytes
   // tensor memory: main accumulator of the current / next segment at [0, 2 NT), cross accumulator of
   // the current / next item at [2 NT, 4 NT)
-  constexpr uint32_t kTmemCols = 4 * NT;
+  constexpr int SEGB = Tm<NT>::segb, CB = Tm<NT>::cb;
+  constexpr uint32_t kTmemCols = 512;  // main segments at [0, SEGB NT), cross at [SEGB NT, (SEGB + CB) NT)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t raw_full[RAW], raw_empty[RAW];
   __shared__ __align__(8) uint64_t a_full[AST], a_empty[AST];
   __shared__ __align__(8) uint64_t b_full[BST], b_empty[BST];
-  __shared__ __align__(8) uint64_t seg_full[2], seg_empty[2], cross_empty[2], mma_done;
+  __shared__ __align__(8) uint64_t seg_full[Tm<NT>::segb], seg_empty[Tm<NT>::segb], cross_empty[Tm<NT>::cb], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -148,11 +158,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&b_full[s], 1);
       mbar_init(&b_empty[s], 1);
     }
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < SEGB; ++s) {
       mbar_init(&seg_full[s], 1);
       mbar_init(&seg_empty[s], kEpiWarps);
-      mbar_init(&cross_empty[s], kEpiWarps);
     }
+    for (int s = 0; s < CB; ++s) mbar_init(&cross_empty[s], kEpiWarps);
     mbar_init(&mma_done, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -237,14 +247,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
         const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);  // MMA N of this item
         const uint32_t idesc = tf32_idesc(kTile, nN);
-        if (it >= 2 && !wait_bounded(&cross_empty[it & 1], (uint32_t)(((it >> 1) - 1) & 1), &abort_flag, lim)) break;
-        const uint32_t dc = tmem + (uint32_t)((2 + (it & 1)) * NT);
+        const int cbi = it % CB;
+        if (it >= CB && !wait_bounded(&cross_empty[cbi], (uint32_t)(((it / CB) - 1) & 1), &abort_flag, lim)) break;
+        const uint32_t dc = tmem + (uint32_t)((SEGB + cbi) * NT);
         uint32_t d = 0;
         for (int c = c_lo; c < c_hi; ++c, ++g) {
-          const int cs = (c - c_lo) % kSeg;  // chunk within its segment
+          const int cs = (c - c_lo) % a.seglen;  // chunk within its segment
           if (cs == 0) {
-            const int p = (int)(sg & 1);
-            if (sg >= 2 && !wait_bounded(&seg_empty[p], (uint32_t)(((sg >> 1) - 1) & 1), &abort_flag, lim)) {
+            const int p = (int)(sg % SEGB);
+            if (sg >= SEGB && !wait_bounded(&seg_empty[p], (uint32_t)(((sg / SEGB) - 1) & 1), &abort_flag, lim)) {
               ok = false;
               break;
             }
@@ -274,8 +285,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mma_commit(&a_empty[qa]);  // these slots are free once the MMAs above have read them
           mma_commit(&b_empty[sb]);
-          if (cs == kSeg - 1 || c == c_hi - 1) {
-            mma_commit(&seg_full[sg & 1]);  // the segment (and, after the last one, the cross sum) is done
+          if (cs == a.seglen - 1 || c == c_hi - 1) {
+            mma_commit(&seg_full[sg % SEGB]);  // the segment (and, after the last one, the cross sum) is done
             ++sg;
           }
         }
@@ -372,51 +383,49 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int z = (int)((q / ((int64_t)a.nj * a.tpo)) % a.b);
       const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
       const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
-      const int nseg = (c_hi - c_lo + kSeg - 1) / kSeg;
+      const int nseg = (c_hi - c_lo + a.seglen - 1) / a.seglen;
       const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);
       const int c0 = hf * H;  // first column of this warp's half
       float run[H];
 #pragma unroll
       for (int e = 0; e < H; ++e) run[e] = 0.0f;
       const uint32_t lanes = (uint32_t)(qd * 32) << 16;
+      // add the accumulator at column offset `col` of tensor memory into run (two 16-column loads in
+      // flight per wait)
+      auto take = [&](uint32_t col) {
+        const uint32_t taddr = tmem + lanes + col + (uint32_t)c0;
+#pragma unroll
+        for (int pc = 0; pc < H / 16; pc += 2) {
+          if (c0 + pc * 16 < nN) {
+            float v[32];
+            tmem_ld16(taddr + (uint32_t)(16 * pc), v);
+            if (pc + 1 < H / 16) tmem_ld16(taddr + (uint32_t)(16 * (pc + 1)), v + 16);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+              if (pc * 16 + e < H) run[pc * 16 + e] += v[e];
+          }
+        }
+      };
       for (int s = 0; s < nseg; ++s, ++sg) {
-        const int p = (int)(sg & 1);
-        if (!__all_sync(0xffffffffu, wait_bounded(&seg_full[p], (uint32_t)((sg >> 1) & 1), &abort_flag, lim))) {
+        const int p = (int)(sg % SEGB);
+        if (!__all_sync(0xffffffffu, wait_bounded(&seg_full[p], (uint32_t)((sg / SEGB) & 1), &abort_flag, lim))) {
           ok = false;
           break;
         }
         fence_after();
-        const uint32_t taddr = tmem + lanes + (uint32_t)(p * NT + c0);
-#pragma unroll
-        for (int pc = 0; pc < H / 16; ++pc) {
-          if (c0 + pc * 16 < nN) {
-            float v[16];
-            tmem_ld16(taddr + (uint32_t)(16 * pc), v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int e = 0; e < 16; ++e) run[pc * 16 + e] += v[e];
-          }
-        }
+        take((uint32_t)(p * NT));
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&seg_empty[p]);
       }
       if (!ok) break;
       {  // the item's cross sum (complete with its last segment)
-        const uint32_t taddr = tmem + lanes + (uint32_t)((2 + (it & 1)) * NT + c0);
-#pragma unroll
-        for (int pc = 0; pc < H / 16; ++pc) {
-          if (c0 + pc * 16 < nN) {
-            float v[16];
-            tmem_ld16(taddr + (uint32_t)(16 * pc), v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int e = 0; e < 16; ++e) run[pc * 16 + e] += v[e];
-          }
-        }
+        const int cbi = it % CB;
+        take((uint32_t)((SEGB + cbi) * NT));
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&cross_empty[it & 1]);
+        if (lane == 0) mbar_arrive(&cross_empty[cbi]);
       }
       const int cl = qd * 32 + lane;  // the tile column of this lane
       const int ob = a.narrow ? cl / (int)a.L : 0;
@@ -636,6 +645,9 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   }
   a.cps = (a.nch + a.nsplit - 1) / a.nsplit;
   a.nsplit = (a.nch + a.cps - 1) / a.cps;  // every split has at least one chunk
+  // one segment for a short K range (<= 256: its rounding bias is a few ulps); 32-long segments
+  // beyond, where the bias would otherwise grow with the number of adds
+  a.seglen = a.cps <= 8 ? a.cps : 1;
   a.ws_stride = a.nsplit > 1 ? wsz : 0;
   if (a.nsplit > 1) a.out = g.ws;
   a.part_x = norms ? g.part : nullptr;
