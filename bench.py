@@ -42,10 +42,12 @@ WORKLOAD = ("video 1080x1920x3 as 27x40x48x40x3, fp32 input, eps=0.05, 40 blobs 
 METRIC = "increment elements/s"
 V480 = (20, 24, 20, 32, 3)
 
-# Unit each phase of an update runs on, for the roofline of the dominant phase: the algorithmic
-# flops of a phase are held against the peak of that unit, its algorithmic bytes against HBM.
+# Unit each phase of an update runs on (mixed path), for the roofline of a phase: its algorithmic
+# flops are held against the peak of that unit, its algorithmic bytes against HBM.  The projections,
+# residuals, Grams and the large re-orthogonalisations run on the tensor cores (TF32 head/tail
+# split); the block-Jacobi eigen-solve is FP32 SIMT (its flops: 8 s^3 per sweep).
 PHASE_UNIT = {"k1_stage1": "tf32", "chain": "tf32", "final": "tf32", "d_project": "tf32",
-              "residual": "fp32", "gram": "fp32", "eig": "fp32", "orth_append": "fp64"}
+              "residual": "tf32", "gram": "tf32", "eig": "fp32", "orth_append": "tf32"}
 
 
 def frames_1080(t0: int, n: int, seed: int = 1004, device="cuda"):

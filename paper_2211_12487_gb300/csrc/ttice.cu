@@ -780,6 +780,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     ph_end(h, st);
     TT_TRY(sync_read(h, st));
     h->stats.eig_sweeps += h->h_int[10];
+    if (h->prof_on) h->prof.flops[PH_EIG] += 8.0 * (double)s * s * s * h->h_int[10];  // A and V rotations
     if (h->h_int[11]) h->stats.eig_sweep_limit += 1;
     ph_begin(h, PH_EIG, st, 0.0, 0.0);
     // size of the Rayleigh-Ritz subspace from the FP32 spectrum (only sizes a buffer; the rank
@@ -814,7 +815,10 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   TT_TRY(sync_read(h, st));
   int rR = h->h_int[0];
   if (h->h_int[1] != 0) h->stats.eig_sweep_limit += 1;  // unconverged sweeps: energies are still measured
-  if (sizeof(WT) == 8 && s > kDirectEig) h->stats.eig_sweeps += h->h_int[3];
+  if (sizeof(WT) == 8 && s > kDirectEig) {
+    h->stats.eig_sweeps += h->h_int[3];
+    if (h->prof_on) h->prof.flops[PH_EIG] += 8.0 * (double)s * s * s * h->h_int[3];
+  }
   if (rR < 0 && rr_on_jacobi) {
     // the FP32 spectrum placed the rank more than 8 below what the FP64 Ritz values need: decide on
     // the complete FP32 eigenbasis instead, with the energies measured on R (as for a rank beyond
