@@ -405,12 +405,15 @@ __global__ void rank_rule_kernel(const double* theta, int K, int full, const dou
 }
 
 // Inverse of the upper Cholesky factor of an SPD k x k matrix (column-major, ld k), one CTA.
-__global__ void chol_inv_kernel(const double* S, int k, double* Rinv, int* status) {
+__global__ void chol_inv_kernel(const double* S, int k, const double* diag, double* Rinv, int* status) {
   extern __shared__ double sm[];
   double* R = sm;          // k x k, column-major
   double* Ri = sm + k * k; // k x k
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < k * k; e += nt) { R[e] = S[e]; Ri[e] = 0.0; }
+  for (int e = tid; e < k * k; e += nt) {
+    R[e] = (diag && e % (k + 1) == 0) ? diag[e / (k + 1)] : S[e];
+    Ri[e] = 0.0;
+  }
   __syncthreads();
   __shared__ int bad;
   if (tid == 0) bad = 0;
@@ -508,7 +511,8 @@ cudaError_t launch_rank_rule(const double* theta, int K, int full, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st) {
+cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st,
+                            const double* diag) {
   if (k <= 0) return cudaSuccess;
   if (k > 112) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)k * k * sizeof(double);
@@ -520,7 +524,7 @@ cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, c
   });
   TT_CUDA(attr_err);
   note_launch();
-  chol_inv_kernel<<<1, 256, smem, st>>>(S, k, Rinv, status);
+  chol_inv_kernel<<<1, 256, smem, st>>>(S, k, diag, Rinv, status);
   return cudaGetLastError();
 }
 

@@ -112,6 +112,18 @@ __global__ void gather_obs_kernel(const T* Y, T* out, const int* sel, int nsel, 
 }
 
 template <typename T>
+__global__ void expand_stage_kernel(const T* src, const int* sel, int64_t r0, const T* add, int64_t k, int64_t L,
+                                    T* out) {
+  const int z = blockIdx.y;
+  const int64_t no = r0 * L, nn = (r0 + k) * L;
+  const T* s = src + (int64_t)(sel ? sel[z] : z) * no;
+  const T* a = add + (int64_t)z * k * L;
+  T* d = out + (int64_t)z * nn;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = e < no ? s[e] : a[e - no];
+}
+
+template <typename T>
 __global__ void sum_squares_kernel(const T* x, int64_t N, double* out) {
   const int j = blockIdx.y;
   const T* p = x + (int64_t)j * N;
@@ -298,6 +310,21 @@ template cudaError_t launch_gather_obs<float>(const float*, float*, const int*, 
                                               cudaStream_t);
 template cudaError_t launch_gather_obs<double>(const double*, double*, const int*, int, int64_t,
                                                cudaStream_t);
+
+template <typename T>
+cudaError_t launch_expand_stage(const T* src, const int* sel, int64_t r0, const T* add, int64_t k, int64_t L,
+                                int nobs, T* out, cudaStream_t st) {
+  const int64_t nn = (r0 + k) * L;
+  if (nobs <= 0 || nn <= 0) return cudaSuccess;
+  dim3 grid(std::min<unsigned>(grid_for(nn), 1024u), (unsigned)nobs);
+  note_launch();
+  expand_stage_kernel<T><<<grid, kThreads, 0, st>>>(src, sel, r0, add, k, L, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_expand_stage<float>(const float*, const int*, int64_t, const float*, int64_t, int64_t,
+                                                int, float*, cudaStream_t);
+template cudaError_t launch_expand_stage<double>(const double*, const int*, int64_t, const double*, int64_t,
+                                                 int64_t, int, double*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_sum_squares(const T* x, int b, int64_t N, double* out, cudaStream_t st) {

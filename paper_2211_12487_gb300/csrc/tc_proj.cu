@@ -85,7 +85,8 @@ enum StoreMode {
   kSubF64 = 1,    // out (double) -= D
   kSplitF32 = 2,  // out, out2 (float) = TF32 head and tail of D (the operand form of a later product)
   kStoreF64 = 3,  // out (double) = D
-  kResidF32 = 4   // out (float) = in - D, in (float) read at its own layout (a residual)
+  kResidF32 = 4,  // out (float) = in - D, in (float) read at its own layout (a residual)
+  kAddF64 = 5     // out (double) += D atomically (K may be split: the splits add into one output)
 };
 
 struct ProjArgs {
@@ -448,6 +449,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               static_cast<double*>(a.out)[o] -= (double)v;
             } else if (a.mode == kStoreF64) {
               static_cast<double*>(a.out)[o] = (double)v;
+            } else if (a.mode == kAddF64) {
+              atomicAdd(static_cast<double*>(a.out) + o, (double)v);
             } else if (a.mode == kResidF32) {
               const int64_t zi = ai / a.in_lz;
               static_cast<float*>(a.out)[o] =
@@ -643,13 +646,18 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
     ns = std::min<int64_t>(ns, g.ws_elems / std::max<int64_t>(wsz, 1));
     if (ns >= 2) a.nsplit = (int)ns;
   }
+  if (g.mode == kAddF64 && items1 < sms && a.nch >= 8) {  // the splits add into the output directly
+    const int64_t ns = std::min<int64_t>((2 * sms + items1 - 1) / items1, a.nch / 4);
+    if (ns >= 2) a.nsplit = (int)ns;
+  }
   a.cps = (a.nch + a.nsplit - 1) / a.nsplit;
   a.nsplit = (a.nch + a.cps - 1) / a.cps;  // every split has at least one chunk
   // one segment for a short K range (<= 256: its rounding bias is a few ulps); 32-long segments
   // beyond, where the bias would otherwise grow with the number of adds
   a.seglen = a.cps <= 8 ? a.cps : 1;
-  a.ws_stride = a.nsplit > 1 ? wsz : 0;
-  if (a.nsplit > 1) a.out = g.ws;
+  const bool ws_split = a.nsplit > 1 && g.mode != kAddF64;
+  a.ws_stride = ws_split ? wsz : 0;
+  if (ws_split) a.out = g.ws;
   a.part_x = norms ? g.part : nullptr;
   const int64_t xs = std::max<int64_t>(1, g.L / 32);
   const int64_t xper = a.narrow ? xs : (int64_t)a.tpo * kConvWarps;
@@ -664,7 +672,7 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   note_launch();
   tc_proj_kernel<NT, APRE><<<(unsigned)grid, kThreads, smem_bytes<NT>(), st>>>(xmap, xlmap, uhmap, ulmap, a);
   TT_CUDA(cudaGetLastError());
-  if (a.nsplit > 1) {
+  if (ws_split) {
     note_launch();
     tc_splitk_reduce_kernel<<<a.nb, 256, 0, st>>>(g.ws, a.nsplit, wsz, (int64_t)g.r * g.L, static_cast<float*>(g.out),
                                                  a.part_x, a.px_stride, xper, g.x2, g.rho2);
@@ -747,24 +755,60 @@ __global__ void split_tf32_kernel(const float* in, int64_t ld_in, int64_t c0, in
 }
 
 __global__ void split_tf32_f64_kernel(const double* in, int64_t ld_in, int64_t rows, int64_t c0, int64_t c1,
-                                      float* hi, float* lo, int64_t ld_out) {
+                                      float* hi, float* lo, int64_t ld_out, float* f32, double* sumsq) {
+  __shared__ double red[8];
   const int64_t rows32 = (rows + 31) / 32 * 32;  // the last K chunk is zero past the operand
-  for (int64_t c = c0 + blockIdx.y; c < c1; c += gridDim.y)
+  for (int64_t c = c0 + blockIdx.y; c < c1; c += gridDim.y) {
+    double q = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows32; i += (int64_t)gridDim.x * blockDim.x) {
       const double x = i < rows ? in[c * ld_in + i] : 0.0;
       const float h = tf32_hi((float)x);
       hi[c * ld_out + i] = h;
       lo[c * ld_out + i] = tf32_hi((float)(x - (double)h));
+      if (f32) f32[c * ld_out + i] = (float)x;
+      q = fma(x, x, q);
     }
+    if (sumsq) {  // block sum, one atomic per block and column
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(sumsq + (c - c0), t);
+      }
+      __syncthreads();
+    }
+  }
 }
 
 cudaError_t launch_split_tf32_f64(const double* in, int64_t ld_in, int64_t rows, int64_t c0, int64_t c1, float* hi,
-                                  float* lo, int64_t ld_out, cudaStream_t st) {
+                                  float* lo, int64_t ld_out, cudaStream_t st, float* f32, double* sumsq) {
   if (c1 <= c0 || rows <= 0) return cudaSuccess;
   const int64_t bx = std::min<int64_t>((rows + 255) / 256, 64);
   const int64_t by = std::min<int64_t>(c1 - c0, 1024);
   note_launch();
-  split_tf32_f64_kernel<<<dim3((unsigned)bx, (unsigned)by), 256, 0, st>>>(in, ld_in, rows, c0, c1, hi, lo, ld_out);
+  split_tf32_f64_kernel<<<dim3((unsigned)bx, (unsigned)by), 256, 0, st>>>(in, ld_in, rows, c0, c1, hi, lo, ld_out,
+                                                                            f32, sumsq);
+  return cudaGetLastError();
+}
+
+// B operand of Vn (I - R^{-1}): row j, entry l = TF32 head / tail of delta_lj - Rinv[l + j k] (Rinv
+// k x k column-major); the ld x ld block is zero outside the k x k corner.
+__global__ void eye_minus_split_kernel(const double* Rinv, int k, float* hi, float* lo, int ld) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ld * ld; e += gridDim.x * blockDim.x) {
+    const int j = e / ld, l = e % ld;
+    const double f = (j < k && l < k) ? (l == j ? 1.0 : 0.0) - Rinv[l + (int64_t)j * k] : 0.0;
+    const float h = tf32_hi((float)f);
+    hi[e] = h;
+    lo[e] = tf32_hi((float)(f - (double)h));
+  }
+}
+
+cudaError_t launch_eye_minus_split(const double* Rinv, int k, float* hi, float* lo, int ld, cudaStream_t st) {
+  if (k <= 0 || k > ld) return cudaErrorInvalidValue;
+  note_launch();
+  eye_minus_split_kernel<<<(ld * ld + 255) / 256, 256, 0, st>>>(Rinv, k, hi, lo, ld);
   return cudaGetLastError();
 }
 

@@ -97,6 +97,9 @@ struct ttice_s {
   // rounded up to 32)
   float* Vnh = nullptr;
   float* Vnl = nullptr;
+  float* Fh = nullptr;  // TF32 head / tail of I - R^{-1} of a tensor-core CholQR pass (kRR x kRR)
+  float* Fl = nullptr;
+  double* dsq = nullptr;  // FP64 squared column norms of the chunk (the Gram's diagonal), kRR
   // tensor-core residual of the mixed path: the transposed TF32 split of U_i^T D_i (rows n = z L + l,
   // ld ldwt) and the TF32 split of the residual for its Gram; rlay = layout of the residual in Rbuf:
   // 0 the stage layout [z][i][l], 1 R^T (row n holds the m entries of column n), 2 R row-major
@@ -280,7 +283,7 @@ void free_all(ttice_s* h) {
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->tcws, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Fh, h->Fl, h->dsq, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->tcws, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
   cudaFreeHost(h->h_rn2);
@@ -891,22 +894,27 @@ constexpr double kTcCgsMin = 4e9;
 std::atomic<double> g_tc_cgs_min{kTcCgsMin};  // ttice_test_tc_cgs_min
 
 // One CGS pass of Vn (m x k, FP64, column-major) against U[core] on the tensor cores: P = U^T Vn
-// from the TF32 head / tail splits of Vn (from FP64) and of U (three products, FP32 accuracy, 64-long
-// K segments summed in registers), stored as the head / tail of P, then Vn -= U P with U from its
-// FP32 mirror, subtracted in FP64.  P is small (the coupling left by an explicit residual), so the
+// from the TF32 head / tail splits of Vn (from FP64) and of U (three products, FP32 accuracy, short
+// K segments summed in registers, K splits in FP64), stored as the head / tail of P, then Vn -= U P
+// with U from its FP32 mirror, subtracted in FP64.  P is small (the coupling left by an explicit residual), so the
 // FP32-accurate products leave a coupling of ~2^-22 |P| after the pass; the floor is the FP32
 // rounding of the tensor-core sums, ~1e-9 of unit vectors for K in the tens of thousands.
 int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
   const int64_t r = h->r[core + 1];
   TT_CU(launch_split_tf32_f64(h->Vn, m, m, 0, k, h->Vnh, h->Vnl, h->ldv, st));
-  TcGemm a;  // P[a][j] = sum_i U[i][a] Vn[i][j]: A rows j (K = i), B rows a (K = i)
+  // P[a][j] = sum_i U[i][a] Vn[i][j]: A rows j (K = i), B rows a (K = i); summed in FP64 as P^T (row j
+  // at h->P + j r), K split across CTAs when the output is small (few rows of U, tall columns), then
+  // split into the TF32 head / tail that the product below reads as its B operand (rows j, K = a)
+  TT_CU(cudaMemsetAsync(h->P, 0, (size_t)r * k * sizeof(double), st));
+  TcGemm a;
   a.ah = h->Vnh; a.al = h->Vnl; a.lda = h->ldv; a.la_alloc = kRR;
   a.L = k; a.K = m;
   a.bh = h->Uh[core]; a.bl = h->Ul[core]; a.ldb = h->ldhl[core]; a.nb_alloc = h->hlcols[core];
   a.r = (int)r;
-  a.mode = 2; a.out = h->Ph; a.out2 = h->Pl; a.ldn = 1; a.ldl = h->ldp;  // P^T rows j: the B operand below
+  a.mode = 5; a.out = h->P; a.ldn = 1; a.ldl = r;
   a.status = h->ibuf + 5;
   TT_CU(launch_tc_gemm(a, st));
+  TT_CU(launch_split_tf32_f64(h->P, r, r, 0, k, h->Ph, h->Pl, h->ldp, st));
   TcGemm b;  // Vn[i][j] -= sum_a U[i][a] P[a][j]: A = U (K = a rows, i contiguous), B rows j (K = a)
   b.x = h->Uf[core]; b.ldx = h->ldu[core]; b.x_obs = h->ldu[core] * r; b.b = 1;
   b.L = m; b.K = r;
@@ -915,6 +923,40 @@ int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
   b.mode = 1; b.out = h->Vn; b.ldn = m; b.ldl = 1;
   b.status = h->ibuf + 5;
   TT_CU(launch_tc_gemm(b, st));
+  return TTICE_OK;
+}
+
+// One CholQR pass of Vn (m x k, FP64) on the tensor cores: the off-diagonal of S = Vn^T Vn from the
+// TF32 head / tail of Vn (three products, FP32 segment sums, the K splits added in FP64), its
+// diagonal summed in FP64 (the tensor core's FP32 sums of positive terms carry a rounding bias of
+// ~1e-7 that would be left in the column norms), S = R^T R and R^{-1} in FP64, then Vn <- Vn R^{-1}
+// written as Vn - Vn (I - R^{-1}): the product on the tensor cores from the FP32 rounding of Vn, the
+// subtraction in FP64.  The chunk is near-orthonormal (unit-scaled directions, already orthogonal to
+// the core), so I - R^{-1} is small and the product's FP32 accuracy costs ~2^-22 of it; the floor is
+// the FP32 rounding of the off-diagonal sums, as in the tensor-core CGS.
+int cholqr_pass_tc(ttice_s* h, int64_t m, int k, cudaStream_t st) {
+  float* Vf = reinterpret_cast<float*>(h->Vn2);  // FP32 Vn at ld ldv (ldv k floats fit: m >= 32)
+  TT_CU(cudaMemsetAsync(h->dsq, 0, (size_t)k * sizeof(double), st));
+  TT_CU(launch_split_tf32_f64(h->Vn, m, m, 0, k, h->Vnh, h->Vnl, h->ldv, st, Vf, h->dsq));
+  TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)k * k * sizeof(double), st));
+  TcGemm g;  // S[a][j] = sum_i Vn[i][a] Vn[i][j]: A and B both the split of Vn (K = i)
+  g.ah = h->Vnh; g.al = h->Vnl; g.lda = h->ldv; g.la_alloc = kRR;
+  g.L = k; g.K = m;
+  g.bh = h->Vnh; g.bl = h->Vnl; g.ldb = h->ldv; g.nb_alloc = kRR;
+  g.r = k;
+  g.mode = 5; g.out = h->Ssm; g.ldn = k; g.ldl = 1;
+  g.status = h->ibuf + 5;
+  TT_CU(launch_tc_gemm(g, st));
+  TT_CU(launch_chol_inv(h->Ssm, k, h->Rinv, h->ibuf + 2, st, h->dsq));
+  TT_CU(launch_eye_minus_split(h->Rinv, k, h->Fh, h->Fl, kRR, st));
+  TcGemm q;  // Vn[i][j] -= sum_l Vn[i][l] F[l][j]: A = FP32 Vn (i contiguous, K = l), B rows j (K = l)
+  q.x = Vf; q.ldx = h->ldv; q.x_obs = h->ldv * k; q.b = 1;
+  q.L = m; q.K = k;
+  q.bh = h->Fh; q.bl = h->Fl; q.ldb = kRR; q.nb_alloc = kRR;
+  q.r = k;
+  q.mode = 1; q.out = h->Vn; q.ldn = m; q.ldl = 1;
+  q.status = h->ibuf + 5;
+  TT_CU(launch_tc_gemm(q, st));
   return TTICE_OK;
 }
 
@@ -943,7 +985,8 @@ int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t s
     b.C = h->Vn; b.c_rs = 1; b.c_cs = m;
     TT_CU((gemm<double, double, double, double, double>(b, st)));
   }
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < 2 && tc; ++pass) TT_TRY(cholqr_pass_tc(h, m, k, st));
+  for (int pass = 0; pass < 2 && !tc; ++pass) {
     TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)k * k * sizeof(double), st));
     GemmArgs g;  // S = Vn^T Vn
     g.M = k; g.N = k; g.K = m; g.atomic = 1; g.allow_splitk = 1;
@@ -1025,6 +1068,21 @@ void rollback(ttice_s* h, const int64_t* r_old, cudaStream_t st) {
   cudaStreamSynchronize(st);
 }
 
+// Rows [r0, r0 + k) of the stage output U_i^T X for nobs observations of the stage input X (the
+// columns core i appended), into out (nobs x k x L_i).
+template <typename WT, typename TY>
+int new_rows(ttice_s* h, int i, const void* X, int nobs, int64_t r0, int k, WT* out, cudaStream_t st) {
+  const int64_t m = h->r[i] * h->n[i], L = h->L[i];
+  if (sizeof(WT) == 4 && h->Uh[i] && (i > 0 || sizeof(TY) == 4) && tc_proj_supported(X, L, m, k, h->ldhl[i]))
+    return cu(launch_tc_proj(static_cast<const float*>(X), nobs, L, m, k, h->Uh[i] + r0 * h->ldhl[i],
+                             h->Ul[i] + r0 * h->ldhl[i], h->ldhl[i], h->hlcols[i] - r0, reinterpret_cast<float*>(out),
+                             nullptr, nullptr, h->part, h->tcws, h->ibuf + 5, st));
+  const WT* Ui = ((sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i]) : reinterpret_cast<const WT*>(h->Uf[i])) +
+                 r0 * h->ldu[i];
+  if (i == 0) return proj<WT, TY, WT>(Ui, h->ldu[i], static_cast<const TY*>(X), m, L, k, nobs, out, st);
+  return proj<WT, WT, WT>(Ui, h->ldu[i], static_cast<const WT*>(X), m, L, k, nobs, out, st);
+}
+
 template <typename WT, typename TY>
 int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
   nvtx_close(h);
@@ -1070,9 +1128,10 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
       const int64_t m = h->r[i] * h->n[i], L = h->L[i];
       const int64_t ri = h->r[i + 1];
       int grew = 0;
-      // pristine: the first pass's projections U_i^T D_i of the selected observations
+      // U_i^T D_i of the selected observations is the first pass's, also after earlier cores grew:
+      // D_i then gained the rows of the new rank indices, where U_i is zero (padded)
       const WT* Wp = nullptr;
-      if (pristine && ri > 0 && m > 0) {
+      if (ri > 0 && m > 0) {
         if (nsel == b) {
           Wp = static_cast<const WT*>(S1[i]);
         } else {
@@ -1110,27 +1169,17 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
             if (i == 0) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wp, D0i, m, L, ri, nsel, R, nullptr, st);
             else rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wp, Xi, m, L, ri, nsel, R, nullptr, st);
           }
-        } else if (ri > 0 && tcr && tc_stage(h, i, Din)) {
-          // U_i^T D_i and ||D_i||^2 - ||U_i^T D_i||^2 per observation, then the explicit residual
-          rc = tc_project(h, i, Din, nsel, Wt, nullptr, h->rn2, st);
-          if (rc == TTICE_OK)
-            rc = tc_resid(h, i, static_cast<const float*>(Din), reinterpret_cast<const float*>(Wt), m, L, nsel, ri,
-                          reinterpret_cast<float*>(R), st);
-          if (rc == TTICE_OK) rc = cu(cudaMemcpyAsync(h->h_rn2, h->rn2, nsel * sizeof(double), cudaMemcpyDeviceToHost, st));
-          if (rc == TTICE_OK) rc = sync_read(h, st);
-          if (rc == TTICE_OK) {
-            double t = 0.0;
-            for (int z = 0; z < nsel; ++z) t += h->h_rn2[z];
-            small = std::sqrt(t) <= dec.eps_c;
-          }
         } else if (ri > 0) {
+          // an earlier core grew: the residual D_i - U_i Wp now also holds D_i's new rows, and its
+          // norm is summed from the explicit residual
           rc = cu(cudaMemsetAsync(h->rn2, 0, nsel * sizeof(double), st));
-          if (rc == TTICE_OK && i == 0) {
-            rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0i, m, L, ri, nsel, Wt, st);
-            if (rc == TTICE_OK) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wt, D0i, m, L, ri, nsel, R, h->rn2, st);
+          if (rc == TTICE_OK && tcr) {
+            rc = tc_resid(h, i, static_cast<const float*>(Din), reinterpret_cast<const float*>(Wp), m, L, nsel, ri,
+                          reinterpret_cast<float*>(R), st);
+            if (rc == TTICE_OK) rc = sumsq<WT>(R, 1, m * L * nsel, h->rn2, st);
           } else if (rc == TTICE_OK) {
-            rc = proj<WT, WT, WT>(Ui, h->ldu[i], Xi, m, L, ri, nsel, Wt, st);
-            if (rc == TTICE_OK) rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wt, Xi, m, L, ri, nsel, R, h->rn2, st);
+            if (i == 0) rc = resid<WT, WT, TY, WT>(Ui, h->ldu[i], Wp, D0i, m, L, ri, nsel, R, h->rn2, st);
+            else rc = resid<WT, WT, WT, WT>(Ui, h->ldu[i], Wp, Xi, m, L, ri, nsel, R, h->rn2, st);
           }
           if (rc == TTICE_OK) rc = cu(cudaMemcpyAsync(h->h_rn2, h->rn2, nsel * sizeof(double),
                                                       cudaMemcpyDeviceToHost, st));
@@ -1177,40 +1226,31 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
       }
       h->stats.new_dirs[i] = grew;
       if (grew > 0 && first_grown == h->d) first_grown = i;
-      // D_{i+1} = reshape(U_i^T D_i) with the updated core
-      if (i + 1 < h->d) {
-        const int64_t rn = h->r[i + 1];
-        if (m == 0 || rn == 0) break;  // nothing flows to the next cores
-        if (pristine && grew == 0) {
-          X = Wp;  // U_i is unchanged: the first pass's stage output
-          continue;
-        }
-        pristine = false;
-        const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
-                                         : reinterpret_cast<const WT*>(h->Uf[i]);
-        WT* Wn = static_cast<WT*>(h->dstage[i]);
-        {
-          const double sx = (i == 0) ? sizeof(TY) : sizeof(WT);
-          ph_begin(h, PH_DPROJ, st, nsel * (sx * m * L + sizeof(WT) * (double)rn * L),
-                   2.0 * nsel * (double)m * L * rn);
-        }
-        const void* Din = i == 0 ? static_cast<const void*>(D0i) : static_cast<const void*>(Xi);
-        if (sizeof(WT) == 4 && (i > 0 || sizeof(TY) == 4) && tc_stage(h, i, Din))
-          rc = tc_project(h, i, Din, nsel, Wn, nullptr, nullptr, st);
-        else if (i == 0 && sizeof(TY) == 4 && sizeof(WT) == 4 && k1_tc_supported(D0i, L, (int)m, (int)rn))
-          rc = cu(launch_k1_tc(reinterpret_cast<const float*>(D0i), nsel, L, (int)m, (int)rn,
-                               reinterpret_cast<const float*>(Ui), h->ldu[i], reinterpret_cast<float*>(Wn),
-                               nullptr, nullptr, nullptr, h->ibuf + 5, st));
-        else if (i == 0 && sizeof(TY) == 4 && k1_tma_supported(D0i, L, (int)m, (int)rn))
-          rc = cu(launch_k1_tma<WT>(reinterpret_cast<const float*>(D0i), nsel, L, (int)m, (int)rn, Ui,
-                                    h->ldu[i], Wn, nullptr, nullptr, nullptr, h->ibuf + 5, st));
-        else if (i == 0) rc = proj<WT, TY, WT>(Ui, h->ldu[i], D0i, m, L, rn, nsel, Wn, st);
-        else rc = proj<WT, WT, WT>(Ui, h->ldu[i], Xi, m, L, rn, nsel, Wn, st);
-        ph_end(h, st);
-        X = Wn;
-      } else if (grew > 0) {
-        pristine = false;
+      if (grew > 0) pristine = false;
+      // D_{i+1} = reshape(U_i^T D_i) with the updated core: the first pass's Wp followed by the rows of
+      // the appended columns, U_i[:, ri:rn]^T D_i.  Formed also for the last TT core when every
+      // observation was selected: those are then the coefficients of the updated decomposition.
+      const int64_t rn = h->r[i + 1];
+      if (m == 0 || rn == 0) break;  // nothing flows to the next cores
+      if (grew == 0) {
+        if (i + 1 < h->d) X = Wp;  // U_i is unchanged on every row of D_i
+        continue;
       }
+      if (i + 1 == h->d && nsel < b) break;
+      {
+        const double sx = (i == 0) ? sizeof(TY) : sizeof(WT);
+        ph_begin(h, PH_DPROJ, st, nsel * (sx * m * L + sizeof(WT) * ((double)rn + grew) * L),
+                 2.0 * nsel * (double)m * L * grew);
+      }
+      WT* add = static_cast<WT*>(h->Rbuf);  // the residual is no longer needed
+      WT* Wn = static_cast<WT*>(h->dstage[i]);
+      const void* Din = i == 0 ? static_cast<const void*>(D0i) : static_cast<const void*>(Xi);
+      rc = new_rows<WT, TY>(h, i, Din, nsel, ri, grew, add, st);
+      if (rc == TTICE_OK)
+        rc = cu(launch_expand_stage<WT>(static_cast<const WT*>(S1[i]), nsel < b ? h->sel : nullptr, ri, add, grew, L,
+                                        nsel, Wn, st));
+      ph_end(h, st);
+      X = Wn;
     }
     if (rc != TTICE_OK) {
       rollback(h, r_old, st);
@@ -1218,9 +1258,26 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
       h->ev_used = 0;
       return rc;
     }
-    // project every observation onto the updated cores (Algorithm 2, last two steps); the stages
-    // before the first core that grew are the first pass's, unchanged
-    if (first_grown < h->d) TT_TRY((chain<WT, TY>(h, Y, b, S1, false, st, first_grown)));
+    // project every observation onto the updated cores (Algorithm 2, last two steps): the stage
+    // outputs of cores that did not grow are the first pass's (the rows their inputs gained meet zero
+    // rows of the core), those of cores that grew gain the rows of their new columns.  With every
+    // observation selected, these are the D projections formed above.
+    for (int i = first_grown; i < h->d; ++i) {
+      const int grew = h->stats.new_dirs[i];
+      if (grew == 0) continue;
+      const int64_t m = h->r[i] * h->n[i], L = h->L[i], r0 = h->r[i + 1] - grew;
+      if (nsel < b) {
+        ph_begin(h, PH_FINAL, st, b * (sizeof(WT) * (double)m * L + sizeof(WT) * (2.0 * r0 + grew) * L),
+                 2.0 * b * (double)m * L * grew);
+        WT* add = static_cast<WT*>(h->Rbuf);
+        const void* Xin = i == 0 ? static_cast<const void*>(Y) : S1[i - 1];
+        TT_TRY((new_rows<WT, TY>(h, i, Xin, b, r0, grew, add, st)));
+        TT_CU(launch_expand_stage<WT>(static_cast<const WT*>(S1[i]), nullptr, r0, add, grew, L, b,
+                                      static_cast<WT*>(h->dstage[i]), st));
+        ph_end(h, st);
+      }
+      std::swap(h->stage[i], h->dstage[i]);
+    }
   }
   const int rd = (int)h->r[h->d];
   TT_CU(launch_append_last_t<WT>(static_cast<const WT*>(S1[h->d - 1]), b, rd, h->last, h->n_obs,
@@ -1393,6 +1450,9 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
     h->ldp = (maxcap + 31) / 32 * 32;
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Vnh, h->ldv * kRR);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Vnl, h->ldv * kRR);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->Fh, kRR * kRR);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->Fl, kRR * kRR);
+    if (rc == TTICE_OK) rc = dalloc<double>(&h->dsq, kRR);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Ph, h->ldp * kRR);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Pl, h->ldp * kRR);
     int64_t wt = 0, rs = 0;

@@ -209,9 +209,14 @@ cudaError_t launch_split_tf32_transpose(const float* W, int b, int64_t r, int64_
 cudaError_t launch_split_tf32(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,
                               int64_t ld_out, cudaStream_t st);
 // The same from FP64 columns (rows [0, rows), zero up to the next multiple of 32): head = tf32(x),
-// tail = tf32(x - head) computed in FP64.
+// tail = tf32(x - head) computed in FP64; f32 (optional, ld_out) receives the FP32 rounding of x and
+// sumsq (optional, zeroed by the caller) gains the FP64 sum of squares of each column c at sumsq[c - c0].
 cudaError_t launch_split_tf32_f64(const double* in, int64_t ld_in, int64_t rows, int64_t c0, int64_t c1, float* hi,
-                                  float* lo, int64_t ld_out, cudaStream_t st);
+                                  float* lo, int64_t ld_out, cudaStream_t st, float* f32 = nullptr,
+                                  double* sumsq = nullptr);
+// TF32 head / tail of I - Rinv (k x k, column-major), transposed into rows of ld (the B operand of a
+// product X (I - Rinv)); zero outside the k x k corner of the ld x ld block.
+cudaError_t launch_eye_minus_split(const double* Rinv, int k, float* hi, float* lo, int ld, cudaStream_t st);
 // Bounded-wait limit of the tensor-core kernels (0 restores the default of 2 s), and a test hook:
 // the next tc_proj launch issues no copy for chunk `chunk` of its first CTA, so that the consumers'
 // bounded wait runs out.
@@ -225,6 +230,11 @@ cudaError_t launch_cast(const TI* in, TO* out, int64_t n, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gather_obs(const T* Y, T* out, const int* sel, int nsel, int64_t N,
                               cudaStream_t st);
+// Stage outputs of a core that gained k columns: out[z] (r0 + k rows of L) = src[sel[z]] (r0 rows of
+// L; sel == nullptr: src[z]) followed by add[z] (k rows of L), for z < nobs.
+template <typename T>
+cudaError_t launch_expand_stage(const T* src, const int* sel, int64_t r0, const T* add, int64_t k, int64_t L,
+                                int nobs, T* out, cudaStream_t st);
 template <typename T>
 cudaError_t launch_sum_squares(const T* x, int b, int64_t N, double* out, cudaStream_t st);
 // diag sum of an FP64 s x s matrix into *out
@@ -233,7 +243,9 @@ cudaError_t launch_trace(const double* G, int64_t ldg, int s, double* out, cudaS
 cudaError_t launch_canonical_sign(double* V, int64_t m, int k, int64_t ld, cudaStream_t st);
 // Cholesky-QR step support: given S = V^T V (k x k, FP64, ld k), overwrite Rinv (k x k, ld k) with
 // the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  status=1 if not positive definite.
-cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st);
+// diag (optional, k entries) replaces the diagonal of S.
+cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st,
+                            const double* diag = nullptr);
 // Block-Krylov basis Q (s x 8 nblk, FP32, nblk in 2..8) of the Gram G and H = Q^T G Q
 // (8 nblk x 8 nblk, FP64, ld 8 nblk) in one thread-block cluster (krylov.cu).  G32: s x s FP32
 // scratch (used when a CTA's rows of G do not fit in shared memory); *lost is set if a block lost
