@@ -58,10 +58,12 @@ extern "C" {
                         (every stage whose unfolding has >= 32 columns per observation, a multiple of
                         4) run on the tensor cores in TF32 with each operand split into a TF32 head
                         and tail (three products, FP32 accuracy), their residual norms by Pythagoras;
-                        large re-orthogonalisations (CGS work m r k >= 4e9) run their two CGS and
-                        two CholQR passes on the tensor cores the same way, the column norms in FP64
-                        (coupling ~2^-22/sqrt(m) for columns of length m, ~1e-9 at m ~ 5e4, instead
-                        of ~1e-15). */
+                        large re-orthogonalisations (CGS work m r k >= 4e9) run their two CGS passes
+                        on the tensor cores the same way, and their Cholesky-QR too once m k^2 >=
+                        5e8 (column norms in FP64).  The coupling they leave is the tensor core's
+                        FP32 summation error, ~2^-23 of the products' magnitudes per 8-term MMA:
+                        ~1e-9 for delocalised columns at m ~ 5e4, up to ~1e-7 for short or
+                        localised ones (FP64: ~1e-15). */
 #define TTICE_TF32 2 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_BF16 3 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_SPLIT_BF16 4 /* reserved (split-BF16 projections): ttice_create returns TTICE_EINVAL */
@@ -294,8 +296,8 @@ void ttice_test_fail_alloc(int64_t n);
  *  - ttice_test_drop_copy: the next tensor-core projection launch issues no copy for chunk `chunk`
  *    of its first thread block, so that the consumers' bounded wait runs out (-1 disarms).
  *  - ttice_test_tc_cgs_min: the CGS work m r k from which the mixed path runs the re-orthogonalisation
- *    of new directions (CGS2 and CholQR2) on the tensor cores (0: whenever the shapes allow; negative:
- *    the default). */
+ *    of new directions (CGS2, and CholQR2 from the smaller of this and m k^2 = 5e8) on the tensor
+ *    cores (0: whenever the shapes allow; negative: the defaults). */
 void ttice_test_wait_limit_ns(uint64_t ns);
 void ttice_test_drop_copy(int64_t chunk);
 void ttice_test_tc_cgs_min(double flops);

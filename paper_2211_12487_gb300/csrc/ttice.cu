@@ -926,6 +926,10 @@ int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
   return TTICE_OK;
 }
 
+// Mixed path: the CholQR work m k^2 from which a chunk's Cholesky-QR runs on the tensor cores (with
+// the CGS on them): its FP64 form costs 8 m k^2 flops, milliseconds at GB300's FP64 rate from here.
+constexpr double kTcCholMin = 5e8;
+
 // One CholQR pass of Vn (m x k, FP64) on the tensor cores: the off-diagonal of S = Vn^T Vn from the
 // TF32 head / tail of Vn (three products, FP32 segment sums, the K splits added in FP64), its
 // diagonal summed in FP64 (the tensor core's FP32 sums of positive terms carry a rounding bias of
@@ -985,8 +989,9 @@ int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t s
     b.C = h->Vn; b.c_rs = 1; b.c_cs = m;
     TT_CU((gemm<double, double, double, double, double>(b, st)));
   }
-  for (int pass = 0; pass < 2 && tc; ++pass) TT_TRY(cholqr_pass_tc(h, m, k, st));
-  for (int pass = 0; pass < 2 && !tc; ++pass) {
+  const bool tc_chol = tc && (double)m * k * k >= std::min(kTcCholMin, g_tc_cgs_min.load());
+  for (int pass = 0; pass < 2 && tc_chol; ++pass) TT_TRY(cholqr_pass_tc(h, m, k, st));
+  for (int pass = 0; pass < 2 && !tc_chol; ++pass) {
     TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)k * k * sizeof(double), st));
     GemmArgs g;  // S = Vn^T Vn
     g.M = k; g.N = k; g.K = m; g.atomic = 1; g.allow_splitk = 1;

@@ -426,15 +426,17 @@ def test_bounded_wait_expiry_returns_etimeout(T):
 
 
 def test_tensor_core_cgs_matches_oracle(T):
-    """The tensor-core re-orthogonalisation of new directions (forced for every append the shapes
-    allow) on the 480p video prefix: same decisions and ranks as the oracle on every increment, eps
-    met, and cores orthonormal to 1e-7.  The coupling the tensor-core passes leave is set by the
-    2^-22 precision of the head/tail operands and the FP32 sums inside the tensor core, ~2^-22/sqrt(m)
-    for columns of length m (here m is a few hundred; ~1e-9 at the m ~ 5e4 of the 1080p stream)."""
+    """The tensor-core re-orthogonalisation of new directions, CGS2 and CholQR2 (forced for every
+    append the shapes allow), on the 480p video prefix: same decisions and ranks as the oracle on
+    every increment, eps met, and cores orthonormal to 2e-7.  The column norms are FP64 sums; the
+    coupling left between columns is the tensor core's FP32 summation of products (~2^-23 of the
+    products' magnitudes per 8-term MMA), largest for short columns with a few large entries (here
+    m is a few hundred and entries reach 0.2: ~1e-7; ~1e-9 for the delocalised columns of length
+    ~5e4 of the 1080p stream)."""
     frames = blob_video(0, 16)
     try:
         T.ttice_test_tc_cgs_min(0.0)
-        run_pair(T, frames, 8, 0.1, precision="fp32", tol=1e-4, orth_tol=1e-7)
+        run_pair(T, frames, 8, 0.1, precision="fp32", tol=1e-4, orth_tol=2e-7)
     finally:
         T.ttice_test_tc_cgs_min(-1.0)
 
