@@ -590,6 +590,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(case: str, warm: int) -> None:
+    """Small, self-contained cases for ncu (each inside one cudaProfilerStart/Stop window, for
+    `ncu --profile-from-start off`); prints one line and exits.
+
+    c4_update: `warm` increments of the 1080p stream, then one steady-state update profiled (the whole
+      handle, ~180 GB at warm = 24: only one-pass metrics such as the launch list on this case).
+    flow_project: ttice_project of 16 snapshots of the 128^3 x 4 flow (537 MB) onto seeded random
+      orthonormal cores at ranks [1, 33, 1177, 431, 207], twice (a few GB on the device): the first
+      pass (tc_proj_kernel<64, 0>), stage 1 (tc_proj_kernel<128, 0>), stage 2 (K split), stage 3.
+    c4_stage2: ttice_project of 32 frames of the 1080p view onto seeded random orthonormal cores at
+      ranks [1, 27, 1005, 4096, 256, 64] (2.8 GB of cores): stage 2 is the large-K contraction of
+      the 1080p stream's core 3 (K = 48240, 120 columns per frame) at a twelfth of its rank."""
+    import numpy as np
+    import torch
+
+    from paper_2211_12487_gb300 import ttice as T
+
+    if case == "c4_update":
+        h = headline_handle(T, "fp32", warm + 1)
+        for k in range(warm):
+            update_growing(T, h, frames_1080(k * BATCH, BATCH))
+        Y = frames_1080(warm * BATCH, BATCH)
+        torch.cuda.synchronize()
+        l0 = T.ttice_kernel_launches()
+        torch.cuda.profiler.start()
+        s, _ = update_growing(T, h, Y)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"case": case, "warm": warm, "ranks": list(s.ranks[:len(DIMS) + 2]),
+                          "new_dirs": list(s.new_dirs[:len(DIMS)]), "krylov": s.krylov_solves,
+                          "krylov_fallbacks": s.krylov_fallbacks, "eig_sweeps": s.eig_sweeps,
+                          "launches": T.ttice_kernel_launches() - l0}))
+        h.close()
+        return
+    from tt_streams import fourier_flow
+
+    if case == "flow_project":
+        dims, ranks, b = (128, 128, 128, 4), [1, 33, 1177, 431, 207], 16
+        Y = fourier_flow(0, b, seed=1002, device="cuda")
+    elif case == "c4_stage2":
+        dims, ranks, b = DIMS, [1, 27, 1005, 4096, 256, 64], BATCH
+        Y = frames_1080(0, b)
+    else:
+        raise SystemExit(f"unknown profile case {case}")
+    rng = np.random.default_rng(3)
+    cores = [np.linalg.qr(rng.normal(size=(ranks[i] * n, ranks[i + 1])))[0] for i, n in enumerate(dims)]
+    h = T.TTICE(dims, 0.01, precision="fp32", input_dtype=torch.float32, max_batch=b, max_rank=max(ranks))
+    h.load(ranks, cores, np.zeros((1, ranks[-1])))
+    coeffs = torch.empty((b, ranks[-1]), dtype=torch.float64, device="cuda")
+    rel = torch.empty((b,), dtype=torch.float64, device="cuda")
+    T.ttice_project(h.h, Y, coeffs, rel)  # warm-up (module load, tensor maps)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(2):
+        T.ttice_project(h.h, Y, coeffs, rel)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"case": case, "ranks": ranks, "rel_mean": float(rel.mean()),
+                      "device_gb": h.device_bytes() / 1e9}))
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,7 +668,12 @@ def main():
     ap.add_argument("--project-batches", type=int, default=16)
     ap.add_argument("--variant-steps", type=int, default=24)
     ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--profile-case", choices=["c4_update", "flow_project", "c4_stage2"],
+                    help="run one small case for ncu instead of the benchmark")
+    ap.add_argument("--profile-warm", type=int, default=24, help="warm-up increments of the c4_update case")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case, args.profile_warm)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -720,7 +787,9 @@ def main():
         "increments": {"timed": args.steps, "skipped": sum(s["skipped"] for s in steps),
                        "final_ranks": steps[-1]["ranks"], "new_dirs_last": steps[-1]["new_dirs"],
                        "core_elements": hl["core_elems"], "compression_ratio": hl["n_obs"] * N / max(hl["core_elems"], 1),
-                       "capacity_growths": hl["grows"], "device_gb": hl["device_gb"]},
+                       "capacity_growths": hl["grows"], "device_gb": hl["device_gb"],
+                       "krylov_solves": sum(s["krylov"] for s in steps),
+                       "krylov_fallbacks": sum(s["krylov_fallbacks"] for s in steps)},
         "roofline": roof,
         "dominant_phase": dom,
         "phase_share": share,

@@ -297,7 +297,8 @@ void ttice_test_fail_alloc(int64_t n);
  *    of its first thread block, so that the consumers' bounded wait runs out (-1 disarms).
  *  - ttice_test_tc_cgs_min: the CGS work m r k from which the mixed path runs the re-orthogonalisation
  *    of new directions (CGS2, and CholQR2 from the smaller of this and m k^2 = 5e8) on the tensor
- *    cores (0: whenever the shapes allow; negative: the defaults). */
+ *    cores, and the transposed projection of stages with few columns per observation from the smaller
+ *    of this and m r b L = 2e8 (0: whenever the shapes allow; negative: the defaults). */
 void ttice_test_wait_limit_ns(uint64_t ns);
 void ttice_test_drop_copy(int64_t chunk);
 void ttice_test_tc_cgs_min(double flops);

@@ -452,7 +452,7 @@ __global__ void chol_inv_kernel(const double* S, int k, const double* diag, doub
     const int i = e % k, c = e / k;
     Rinv[e] = (i <= c) ? Ri[e] : 0.0;
   }
-  if (tid == 0 && status) *status = bad;
+  if (tid == 0 && status && bad) *status = 1;  // sticky: a caller may check several factorisations at once
 }
 
 }  // namespace

@@ -12,6 +12,7 @@ std::atomic<long long> g_kernel_launches{0};
 namespace {
 
 constexpr int kThreads = 256;
+constexpr unsigned kSignSlices = 64;  // row slices per column of the canonical-sign search
 
 inline unsigned grid_for(int64_t n, int per = kThreads) {
   int64_t g = (n + per - 1) / per;
@@ -88,6 +89,17 @@ __global__ void decision_kernel(const double* rho2s, int nst, const double* y2, 
   *dec = D;
 }
 
+// Pseudo-random start vectors in [-1, 1): splitmix64 of (seed, index).
+__global__ void fill_random_kernel(float* p, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    p[i] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+
 __global__ void fill_kernel(double* p, int64_t n, double v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -161,11 +173,14 @@ __global__ void trace_kernel(const double* G, int64_t ldg, int s, double* out) {
 }
 
 // one CTA per column: index of the largest |v| (lowest index on ties), flip the column if negative
-__global__ void canonical_sign_kernel(double* V, int64_t m, int64_t ld) {
-  double* v = V + (int64_t)blockIdx.x * ld;
+// Canonical sign, step 1: per column c and row slice blockIdx.x, the largest |V| and its lowest index
+// into part[(c nb + slice) 2 + {0, 1}].
+__global__ void sign_partial_kernel(const double* V, int64_t m, int64_t ld, double* part) {
+  const int c = blockIdx.y, nb = gridDim.x;
+  const double* v = V + (int64_t)c * ld;
   double best = -1.0;
   int64_t bi = 0;
-  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)nb * blockDim.x) {
     const double a = fabs(v[i]);
     if (a > best) { best = a; bi = i; }
   }
@@ -185,10 +200,22 @@ __global__ void canonical_sign_kernel(double* V, int64_t m, int64_t ld) {
     }
     __syncthreads();
   }
-  const bool flip = v[si[0]] < 0.0;
-  __syncthreads();
-  if (flip)
-    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) v[i] = -v[i];
+  if (threadIdx.x == 0) {
+    part[((int64_t)c * nb + blockIdx.x) * 2] = sb[0];
+    part[((int64_t)c * nb + blockIdx.x) * 2 + 1] = (double)si[0];
+  }
+}
+
+// Step 2: sign[c] = -1 if the column's largest-|.| entry (lowest index on ties) is negative, else 1.
+__global__ void sign_finish_kernel(const double* V, int64_t ld, const double* part, int nb, double* sign) {
+  const int c = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  double best = -1.0, bi = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    const double b2 = part[((int64_t)c * nb + j) * 2], i2 = part[((int64_t)c * nb + j) * 2 + 1];
+    if (b2 > best || (b2 == best && i2 < bi)) { best = b2; bi = i2; }
+  }
+  sign[c] = (best >= 0.0 && V[(int64_t)c * ld + (int64_t)bi] < 0.0) ? -1.0 : 1.0;
 }
 
 __global__ void scale_cols_rsqrt_kernel(double* V, int64_t m, int64_t ld, const double* theta) {
@@ -200,11 +227,12 @@ __global__ void scale_cols_rsqrt_kernel(double* V, int64_t m, int64_t ld, const 
 }
 
 __global__ void copy_cols_kernel(const double* in, int64_t ld_in, int64_t m, double* out,
-                                 int64_t ld_out, float* mirror) {
+                                 int64_t ld_out, float* mirror, const double* sign) {
   const int c = blockIdx.y;
+  const double sg = sign ? sign[c] : 1.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = in[c * ld_in + i];
+    const double v = sg * in[c * ld_in + i];
     out[c * ld_out + i] = v;
     if (mirror) mirror[c * ld_out + i] = (float)v;
   }
@@ -278,6 +306,13 @@ cudaError_t launch_decision(const double* rho2s, int nst, const double* y2, int 
   return cudaGetLastError();
 }
 
+cudaError_t launch_fill_random(float* p, int64_t n, uint64_t seed, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  fill_random_kernel<<<grid_for(n), kThreads, 0, st>>>(p, n, seed);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill(double* p, int64_t n, double v, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   note_launch();
@@ -343,10 +378,15 @@ cudaError_t launch_trace(const double* G, int64_t ldg, int s, double* out, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_canonical_sign(double* V, int64_t m, int k, int64_t ld, cudaStream_t st) {
+cudaError_t launch_canonical_sign(const double* V, int64_t m, int k, int64_t ld, double* part, double* sign,
+                                  cudaStream_t st) {
   if (k <= 0) return cudaSuccess;
+  const unsigned nb = std::max<unsigned>(1u, std::min<unsigned>(grid_for(m), kSignSlices));
   note_launch();
-  canonical_sign_kernel<<<k, kThreads, 0, st>>>(V, m, ld);
+  sign_partial_kernel<<<dim3(nb, (unsigned)k), kThreads, 0, st>>>(V, m, ld, part);
+  TT_CUDA(cudaGetLastError());
+  note_launch();
+  sign_finish_kernel<<<k, 32, 0, st>>>(V, ld, part, (int)nb, sign);
   return cudaGetLastError();
 }
 
@@ -360,11 +400,11 @@ cudaError_t launch_scale_cols_rsqrt(double* V, int64_t m, int k, int64_t ld, con
 }
 
 cudaError_t launch_copy_cols(const double* in, int64_t ld_in, int64_t m, int k, double* out,
-                             int64_t ld_out, float* mirror, cudaStream_t st) {
+                             int64_t ld_out, float* mirror, cudaStream_t st, const double* sign) {
   if (k <= 0 || m <= 0) return cudaSuccess;
   dim3 grid(std::min<unsigned>(grid_for(m), 64u), (unsigned)k);
   note_launch();
-  copy_cols_kernel<<<grid, kThreads, 0, st>>>(in, ld_in, m, out, ld_out, mirror);
+  copy_cols_kernel<<<grid, kThreads, 0, st>>>(in, ld_in, m, out, ld_out, mirror, sign);
   return cudaGetLastError();
 }
 

@@ -848,6 +848,52 @@ cudaError_t launch_split_tf32_transpose(const float* W, int b, int64_t r, int64_
   return cudaGetLastError();
 }
 
+// Stage outputs from the FP64 sums of a transposed projection: W[z][n][l] = P[(z L + l) k + n] for
+// n < k, l < L; w2[z] (optional) gains the squares.
+__global__ void scatter_stage_kernel(const double* P, int64_t k, int64_t L, float* W, double* w2) {
+  __shared__ double red[8];
+  const int64_t z = blockIdx.y, per = k * L;
+  double q = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = e / L, l = e - n * L;
+    const double v = P[(z * L + l) * k + n];
+    W[z * per + e] = (float)v;
+    q = fma(v, v, q);
+  }
+  if (w2) {
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      atomicAdd(w2 + z, t);
+    }
+  }
+}
+
+__global__ void pythagoras_kernel(const double* x2, const double* w2, int b, double* rho2) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < b) rho2[z] += x2[z] - w2[z];
+}
+
+cudaError_t launch_scatter_stage(const double* P, int b, int64_t k, int64_t L, float* W, double* w2,
+                                 cudaStream_t st) {
+  const int64_t per = k * L;
+  if (b <= 0 || per <= 0) return cudaSuccess;
+  const unsigned bx = (unsigned)std::min<int64_t>((per + 255) / 256, 256);
+  note_launch();
+  scatter_stage_kernel<<<dim3(bx, (unsigned)b), 256, 0, st>>>(P, k, L, W, w2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pythagoras(const double* x2, const double* w2, int b, double* rho2, cudaStream_t st) {
+  if (b <= 0) return cudaSuccess;
+  note_launch();
+  pythagoras_kernel<<<(b + 255) / 256, 256, 0, st>>>(x2, w2, b, rho2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split_tf32(const float* in, int64_t ld_in, int64_t c0, int64_t c1, float* hi, float* lo,
                               int64_t ld_out, cudaStream_t st) {
   if (c1 <= c0 || ld_in <= 0) return cudaSuccess;

@@ -78,6 +78,14 @@ struct ttice_s {
   double* Z = nullptr;   // kRR x kRR eigenvectors
   double* theta = nullptr;
   float* G32 = nullptr;   // FP32 copy of the Gram for the Krylov solver
+  // block Krylov with its basis in global memory (large Grams): basis (s x kBigK), G times it, two
+  // s x kBigP work blocks, CGS coefficients (kBigK x kBigP), and the projected matrix (kBigK^2, FP64)
+  float* BQ = nullptr;
+  float* BGQ = nullptr;
+  float* BY = nullptr;
+  float* BY2 = nullptr;
+  float* BC = nullptr;
+  double* BH = nullptr;
   float* KQ = nullptr;    // block-Krylov basis, s_max x kKry
   float* kstart = nullptr;  // start block of a restarted Krylov solve, s_max x kKryP
   double* KV = nullptr;   // s_max x kKryP (start block), also kKry x kKry eigenvectors of H
@@ -100,6 +108,8 @@ struct ttice_s {
   float* Fh = nullptr;  // TF32 head / tail of I - R^{-1} of a tensor-core CholQR pass (kRR x kRR)
   float* Fl = nullptr;
   double* dsq = nullptr;  // FP64 squared column norms of the chunk (the Gram's diagonal), kRR
+  double* sgn = nullptr;       // canonical sign of each new column (kRR)
+  double* sgn_part = nullptr;  // its per-slice partial maxima (128 kRR)
   // tensor-core residual of the mixed path: the transposed TF32 split of U_i^T D_i (rows n = z L + l,
   // ld ldwt) and the TF32 split of the residual for its Gram; rlay = layout of the residual in Rbuf:
   // 0 the stage layout [z][i][l], 1 R^T (row n holds the m entries of column n), 2 R row-major
@@ -209,6 +219,14 @@ constexpr int kKryP = 8;         // block size of the Krylov eigen-solver
 constexpr int kKryBlocks = 8;    // blocks: a basis of kKry = 64 vectors
 constexpr int kKry = kKryP * kKryBlocks;
 constexpr int kKrylovMin = 96;   // mixed path: Gram matrices above this size try the Krylov solver first
+// Mixed path, Gram sides from kBigKrylovMin: a block Krylov basis of kBigK vectors in global memory
+// (blocks of kBigP) is tried first.  Flat residual spectra (noise) have leading eigenvalues a few
+// 1e-3 apart, which a 64-vector basis cannot resolve; 96 blocks of 8 certify the leading ~30 pairs
+// of a 3840-sided Marchenko-Pastur spectrum to ~1e-14 in exact arithmetic.
+constexpr int kBigP = 8;
+constexpr int kBigBlocks = 96;
+constexpr int kBigK = kBigP * kBigBlocks;
+constexpr int kBigKrylovMin = 1024;
 constexpr int64_t kMaxGridZ = 65535;  // batch (grid z) limit of one contraction launch
 
 // The CUDA error behind the last TTICE_ECUDA returned to this thread (ttice_last_cuda_error).
@@ -279,11 +297,11 @@ void free_all(ttice_s* h) {
     cudaFree(h->U[i]); cudaFree(h->Uf[i]); cudaFree(h->stage[i]); cudaFree(h->dstage[i]);
     cudaFree(h->Uh[i]); cudaFree(h->Ul[i]);
   }
-  void* ptrs[] = {h->G32, h->KQ, h->kstart, h->KV, h->res,
+  void* ptrs[] = {h->G32, h->BQ, h->BGQ, h->BY, h->BY2, h->BC, h->BH, h->KQ, h->kstart, h->KV, h->res,
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Fh, h->Fl, h->dsq, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->tcws, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Fh, h->Fl, h->dsq, h->sgn, h->sgn_part, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->tcws, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
   cudaFreeHost(h->h_rn2);
@@ -341,6 +359,46 @@ int tc_project(ttice_s* h, int i, const void* X, int b, void* W, double* x2, dou
   return cu(launch_tc_proj(static_cast<const float*>(X), b, h->L[i], h->r[i] * h->n[i], (int)h->r[i + 1], h->Uh[i],
                            h->Ul[i], h->ldhl[i], h->hlcols[i], static_cast<float*>(W), x2, rho2, h->part, h->tcws,
                            h->ibuf + 5, st));
+}
+
+// Stages of the mixed path whose unfolding has too few or unaligned columns per observation for the
+// projection kernel's tile layouts (L_i not a multiple of 4: the 1080p view's last core has L = 3):
+// the stage input transposed and split (rows z L + l, K = its m rows), against columns [r0, r0 + k)
+// of U_i's split on the tensor cores with FP64 sums across K splits (the output, k x b L, cannot fill
+// the GPU by itself), then scattered to the stage layout [z][n][l] in FP32.  With rho2:
+// rho2[z] += ||X_z||^2 - ||W_z||^2.
+constexpr double kTcStageTMin = 2e8;  // m k b L below which the SIMT GEMM is as fast
+// Mixed path: the CGS work m r k above which its two passes run on the tensor cores (the FP64
+// products would take more than a few milliseconds at GB300's FP64 rate).
+constexpr double kTcCgsMin = 4e9;
+std::atomic<double> g_tc_cgs_min{kTcCgsMin};  // ttice_test_tc_cgs_min (0 forces the tensor-core forms)
+bool tc_stage_t_ok(const ttice_s* h, int i, int b, int64_t k) {
+  const int64_t m = h->r[i] * h->n[i], L = h->L[i], ldm = (m + 31) / 32 * 32;
+  return h->Uh[i] != nullptr && k > 0 && m >= 32 && (m + 31) / 32 <= 65535 && b * L * ldm <= h->rs_elems &&
+         b * L * k <= h->max_ms && (double)m * k * b * L >= std::min(kTcStageTMin, g_tc_cgs_min.load());
+}
+int tc_project_t(ttice_s* h, int i, const float* X, int b, int64_t r0, int k, float* W, double* rho2,
+                 cudaStream_t st) {
+  const int64_t m = h->r[i] * h->n[i], L = h->L[i], ldm = (m + 31) / 32 * 32;
+  double* P = h->Ebuf;  // b L x k
+  TT_CU(launch_split_tf32_transpose(X, b, m, L, h->Rh, h->Rl, ldm, st));
+  TT_CU(cudaMemsetAsync(P, 0, (size_t)b * L * k * sizeof(double), st));
+  TcGemm g;  // P[z L + l][n] = sum_a X[z][a][l] U[a][r0 + n]
+  g.ah = h->Rh; g.al = h->Rl; g.lda = ldm; g.la_alloc = b * L;
+  g.L = b * L; g.K = m;
+  g.bh = h->Uh[i] + r0 * h->ldhl[i]; g.bl = h->Ul[i] + r0 * h->ldhl[i]; g.ldb = h->ldhl[i];
+  g.nb_alloc = h->hlcols[i] - r0;
+  g.r = k;
+  g.mode = 5; g.out = P; g.ldn = 1; g.ldl = k;
+  g.status = h->ibuf + 5;
+  TT_CU(launch_tc_gemm(g, st));
+  if (rho2) {
+    TT_CU(cudaMemsetAsync(h->part, 0, 2 * (size_t)b * sizeof(double), st));
+    TT_TRY(sumsq<float>(X, b, m * L, h->part, st));
+  }
+  TT_CU(launch_scatter_stage(P, b, k, L, W, rho2 ? h->part + b : nullptr, st));
+  if (rho2) TT_CU(launch_pythagoras(h->part, h->part + b, b, rho2, st));
+  return TTICE_OK;
 }
 
 // ---------------------------------------------------------------- chain projection
@@ -432,6 +490,9 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
     } else if (sizeof(WT) == 4 && tc_stage(h, i, Xw)) {
       // Pythagorean residual per observation: ||X_i||^2 - ||U_i^T X_i||^2
       TT_TRY(tc_project(h, i, Xw, b, W, nullptr, errors ? h->rho2 + (int64_t)i * b : nullptr, st));
+    } else if (sizeof(WT) == 4 && tc_stage_t_ok(h, i, b, rn)) {
+      TT_TRY(tc_project_t(h, i, reinterpret_cast<const float*>(Xw), b, 0, (int)rn, reinterpret_cast<float*>(W),
+                          errors ? h->rho2 + (int64_t)i * b : nullptr, st));
     } else {
       TT_TRY(proj<WT, WT, WT>(Ui, h->ldu[i], Xw, m, L, rn, b, W, st));
       if (errors)
@@ -545,6 +606,109 @@ int krylov_candidates(ttice_s* h, int64_t s, double eps_c, int nblk, const float
   return TTICE_OK;
 }
 
+// Large Grams (s >= kBigKrylovMin, mixed path): block Krylov with the basis in global memory, FP32
+// products.  X_0 pseudo-random; X_i = G X_{i-1} projected out of the earlier blocks twice (CGS2) and
+// orthonormalised by Cholesky-QR twice; H = Q^T G Q in FP64 sums, diagonalised by FP32 Jacobi; the
+// leading Ritz vectors the rank rule needs (plus 8) become the FP64 candidates h->Q of the
+// Rayleigh-Ritz step.  *K_out = 0 when the blocks lost rank or the subspace is too small.
+int krylov_big_candidates(ttice_s* h, int64_t s, double eps_c, int* K_out, cudaStream_t st) {
+  *K_out = 0;
+  const int P = kBigP, k = kBigK;
+  float* Q = h->BQ;
+  TT_CU((launch_cast<double, float>(h->G, h->G32, s * s, st)));
+  TT_CU(cudaMemsetAsync(h->ibuf + 6, 0, sizeof(int), st));
+  TT_CU(launch_fill_random(h->BY, s * P, 0x5eedull + (uint64_t)s, st));
+  for (int i = 0; i < kBigBlocks; ++i) {
+    const int64_t q0 = (int64_t)i * P;  // columns of the basis so far
+    if (i > 0) {
+      GemmArgs y;  // Y = G X_{i-1}
+      y.M = s; y.N = P; y.K = s;
+      y.A.p = h->G32; y.A.rs = s; y.A.cs = 1;
+      y.B.p = Q + (q0 - P) * s; y.B.rs = 1; y.B.cs = s;
+      y.C = h->BY; y.c_rs = 1; y.c_cs = s;
+      TT_CU((gemm<float, float, float, float, float>(y, st)));
+      for (int pass = 0; pass < 2; ++pass) {
+        TT_CU(cudaMemsetAsync(h->BC, 0, (size_t)q0 * P * sizeof(float), st));
+        GemmArgs c;  // C = Q^T Y
+        c.M = q0; c.N = P; c.K = s; c.atomic = 1; c.allow_splitk = 1;
+        c.A.p = Q; c.A.rs = s; c.A.cs = 1;
+        c.B.p = h->BY; c.B.rs = 1; c.B.cs = s;
+        c.C = h->BC; c.c_rs = 1; c.c_cs = q0;
+        TT_CU((gemm<float, float, float, float, float>(c, st)));
+        GemmArgs u;  // Y -= Q C
+        u.M = s; u.N = P; u.K = q0;
+        u.A.p = Q; u.A.rs = 1; u.A.cs = s;
+        u.B.p = h->BC; u.B.rs = 1; u.B.cs = q0;
+        u.X.p = h->BY; u.X.rs = 1; u.X.cs = s;
+        u.alpha = -1.0; u.beta = 1.0;
+        u.C = h->BY; u.c_rs = 1; u.c_cs = s;
+        TT_CU((gemm<float, float, float, float, float>(u, st)));
+      }
+    }
+    for (int pass = 0; pass < 2; ++pass) {  // CholQR2 of the block into the basis
+      const float* src = pass == 0 ? h->BY : h->BY2;
+      float* dst = pass == 0 ? h->BY2 : Q + q0 * s;
+      TT_CU(cudaMemsetAsync(h->Ssm, 0, (size_t)P * P * sizeof(double), st));
+      GemmArgs g;  // S = Y^T Y
+      g.M = P; g.N = P; g.K = s; g.atomic = 1; g.allow_splitk = 1;
+      g.A.p = src; g.A.rs = s; g.A.cs = 1;
+      g.B.p = src; g.B.rs = 1; g.B.cs = s;
+      g.C = h->Ssm; g.c_rs = 1; g.c_cs = P;
+      TT_CU((gemm<float, float, float, double, double>(g, st)));
+      TT_CU(launch_chol_inv(h->Ssm, P, h->Rinv, h->ibuf + 6, st));
+      GemmArgs q;  // Y Rinv
+      q.M = s; q.N = P; q.K = P;
+      q.A.p = src; q.A.rs = 1; q.A.cs = s;
+      q.B.p = h->Rinv; q.B.rs = 1; q.B.cs = P;
+      q.C = dst; q.c_rs = 1; q.c_cs = s;
+      TT_CU((gemm<float, double, float, float, float>(q, st)));
+    }
+  }
+  {  // H = Q^T (G Q)
+    GemmArgs g;
+    g.M = s; g.N = k; g.K = s;
+    g.A.p = h->G32; g.A.rs = s; g.A.cs = 1;
+    g.B.p = Q; g.B.rs = 1; g.B.cs = s;
+    g.C = h->BGQ; g.c_rs = 1; g.c_cs = s;
+    TT_CU((gemm<float, float, float, float, float>(g, st)));
+    TT_CU(cudaMemsetAsync(h->BH, 0, (size_t)k * k * sizeof(double), st));
+    GemmArgs hh;
+    hh.M = k; hh.N = k; hh.K = s; hh.atomic = 1; hh.allow_splitk = 1;
+    hh.A.p = Q; hh.A.rs = s; hh.A.cs = 1;
+    hh.B.p = h->BGQ; hh.B.rs = 1; hh.B.cs = s;
+    hh.C = h->BH; hh.c_rs = 1; hh.c_cs = k;
+    TT_CU((gemm<float, float, float, double, double>(hh, st)));
+  }
+  TT_CU(block_jacobi_eig<float>(h->BH, k, k, h->w32, h->V32, h->bjw32, h->fro, h->bjflags, kMaxSweeps32, st));
+  TT_CU(cudaMemcpyAsync(h->h_w32, h->w32, k * sizeof(float), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_dbl, h->trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_int + 6, h->ibuf + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_int + 8, h->bjflags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  ph_end(h, st);
+  TT_TRY(sync_read(h, st));
+  ph_begin(h, PH_EIG, st, 0.0, 0.0);
+  if (h->prof_on) h->prof.flops[PH_EIG] += 8.0 * (double)k * k * k * h->h_int[10];
+  if (h->h_int[6]) return TTICE_OK;  // the blocks lost rank: leave it to the full solver
+  const double tr = h->h_dbl[0];
+  double acc = 0.0;
+  int r32 = -1;
+  if (std::sqrt(std::max(tr, 0.0)) <= eps_c) r32 = 0;
+  for (int j = 0; j < k && r32 < 0; ++j) {
+    acc += std::max((double)h->h_w32[j], 0.0);
+    if (std::sqrt(std::max(tr - acc, 0.0)) <= eps_c) r32 = j + 1;
+  }
+  if (r32 < 0 || r32 + 8 > kRR) return TTICE_OK;  // more than one Rayleigh-Ritz problem: full solver
+  const int K = r32 + 8;
+  GemmArgs c;  // candidates Q V[:, :K] in FP64
+  c.M = s; c.N = K; c.K = k;
+  c.A.p = Q; c.A.rs = 1; c.A.cs = s;
+  c.B.p = h->V32; c.B.rs = 1; c.B.cs = k;
+  c.C = h->Q; c.c_rs = 1; c.c_cs = s;
+  TT_CU((gemm<float, float, float, double, double>(c, st)));
+  *K_out = K;
+  return TTICE_OK;
+}
+
 // After rayleigh_ritz: accept the Krylov result iff every Ritz pair the rank rule used has a
 // residual ||G z - theta z|| <= 1e-6 theta_1, i.e. the Ritz values are converged far below the
 // truncation threshold (errors are second order in the residual).  The rule at rank rR reads
@@ -575,6 +739,32 @@ int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
   bool good = true;
   for (int j = 0; j < jm; ++j) good = good && (h->h_dbl[j] <= tol);
   *ok = good;
+  return TTICE_OK;
+}
+
+// After krylov_certify turned a Krylov result down (some Ritz pair the rule used has a residual above
+// 1e-6 theta_1, as in flat spectra whose leading eigenvalues lie 1e-3 apart): accept the rank
+// decision itself when its margin exceeds what the residuals allow.  With Ritz values theta_j and
+// residual matrix G Q - Q H of Frobenius norm rho, G - E (||E|| <= 2 rho) has Q as an invariant
+// subspace, so the leading eigenvalues of G exceed the matching Ritz values by at most 2 rho each
+// (Weyl), given that the Krylov space holds the leading eigenvectors (a random start).  The rule's
+// rank rR has Ritz tail(rR) <= eps^2, which bounds the true tail of the appended directions exactly
+// (their captured energy is the sum of their Ritz values); the true rank is rR as well when
+// tail(rR - 1) - 2 rho (rR - 1) > eps^2.  Reads the residuals krylov_certify left in h->h_dbl.
+int krylov_margin_ok(ttice_s* h, int K, double eps_c, bool* ok, cudaStream_t st) {
+  *ok = false;
+  const int rR = h->h_int[0];
+  if (rR <= 0 || rR > K) return TTICE_OK;
+  TT_CU(cudaMemcpyAsync(h->h_dbl + 130, h->theta, K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CU(cudaMemcpyAsync(h->h_dbl + 250, h->trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_TRY(sync_read(h, st));
+  double rho2 = 0.0;
+  for (int j = 0; j < K; ++j) rho2 += h->h_dbl[j] * h->h_dbl[j];
+  const double tr = h->h_dbl[250];
+  double tail = tr;  // tail(rR - 1) from the Ritz values
+  for (int j = 0; j < rR - 1; ++j) tail -= h->h_dbl[130 + j];
+  const double slack = 2.0 * std::sqrt(rho2) * (rR - 1) + 1e-12 * std::fabs(tr);
+  *ok = tail - slack > eps_c * eps_c;
   return TTICE_OK;
 }
 
@@ -686,8 +876,9 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     g.L = s; g.K = kdim;
     g.bh = h->Rh; g.bl = h->Rl; g.ldb = ld32; g.nb_alloc = s;
     g.r = (int)s;
-    g.mode = 3; g.out = h->G; g.ldn = s; g.ldl = 1;
+    g.mode = 5; g.out = h->G; g.ldn = s; g.ldl = 1;  // FP64 sums; K split when s is small and K long
     g.status = h->ibuf + 5;
+    TT_CU(cudaMemsetAsync(h->G, 0, (size_t)s * s * sizeof(double), st));
     TT_CU(launch_tc_gemm(g, st));
   } else {
   TT_CU(cudaMemsetAsync(h->G, 0, (size_t)s * s * sizeof(double), st));
@@ -741,7 +932,20 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     Vdir = h->V64; thet = h->w64; K = (int)s;
   } else {
     bool have = false, big = false;
-    if (s > kKrylovMin) {
+    const bool try_big = s >= kBigKrylovMin && h->BQ;  // a 64-vector basis cannot do better
+    if (try_big) {
+      int Kk = 0;
+      TT_TRY(krylov_big_candidates(h, s, eps_c, &Kk, st));
+      if (Kk > 0) {
+        TT_TRY(rayleigh_ritz(h, s, Kk, d_eps, max_new, st));
+        bool ok = false;
+        TT_TRY(krylov_certify(h, s, Kk, &ok, st));
+        if (!ok) TT_TRY(krylov_margin_ok(h, Kk, eps_c, &ok, st));
+        if (ok) { have = true; K = Kk; h->stats.krylov_solves += 1; }
+      }
+      if (!have) h->stats.krylov_fallbacks += 1;
+    }
+    if (!have && !try_big && s > kKrylovMin) {
       // block Krylov candidates + FP64 Rayleigh-Ritz, kept only if certified: a 32-vector basis
       // first (enough for a few new directions, and an 8x smaller Ritz problem), then 64 — restarted
       // from the first attempt's leading Ritz vectors when it got as far as Rayleigh-Ritz, and from a
@@ -888,10 +1092,6 @@ int build_dirs(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int c0, 
   return TTICE_OK;
 }
 
-// Mixed path: the CGS work m r k above which its two passes run on the tensor cores (the FP64
-// products would take more than a few milliseconds at GB300's FP64 rate).
-constexpr double kTcCgsMin = 4e9;
-std::atomic<double> g_tc_cgs_min{kTcCgsMin};  // ttice_test_tc_cgs_min
 
 // One CGS pass of Vn (m x k, FP64, column-major) against U[core] on the tensor cores: P = U^T Vn
 // from the TF32 head / tail splits of Vn (from FP64) and of U (three products, FP32 accuracy, short
@@ -1008,9 +1208,9 @@ int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t s
     TT_CU((gemm<double, double, double, double, double>(q, st)));
     std::swap(h->Vn, h->Vn2);
   }
-  TT_CU(launch_canonical_sign(h->Vn, m, k, m, st));
+  TT_CU(launch_canonical_sign(h->Vn, m, k, m, h->sgn_part, h->sgn, st));
   TT_CU(launch_copy_cols(h->Vn, m, m, k, U + r * ld, ld, h->Uf[core] ? h->Uf[core] + r * ld : nullptr,
-                         st));
+                         st, h->sgn));
   if (h->Uh[core])
     TT_CU(launch_split_tf32(h->Uf[core], ld, r, r + k, h->Uh[core], h->Ul[core], h->ldhl[core], st));
   return TTICE_OK;
@@ -1082,6 +1282,8 @@ int new_rows(ttice_s* h, int i, const void* X, int nobs, int64_t r0, int k, WT* 
     return cu(launch_tc_proj(static_cast<const float*>(X), nobs, L, m, k, h->Uh[i] + r0 * h->ldhl[i],
                              h->Ul[i] + r0 * h->ldhl[i], h->ldhl[i], h->hlcols[i] - r0, reinterpret_cast<float*>(out),
                              nullptr, nullptr, h->part, h->tcws, h->ibuf + 5, st));
+  if (sizeof(WT) == 4 && i > 0 && tc_stage_t_ok(h, i, nobs, k))
+    return tc_project_t(h, i, static_cast<const float*>(X), nobs, r0, k, reinterpret_cast<float*>(out), nullptr, st);
   const WT* Ui = ((sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i]) : reinterpret_cast<const WT*>(h->Uf[i])) +
                  r0 * h->ldu[i];
   if (i == 0) return proj<WT, TY, WT>(Ui, h->ldu[i], static_cast<const TY*>(X), m, L, k, nobs, out, st);
@@ -1432,6 +1634,14 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
   if (rc == TTICE_OK) rc = dalloc<double>(&h->fro, 3);  // ||A||^2, off-norm^2 now and one sweep back
   if (rc == TTICE_OK) rc = dalloc<int>(&h->bjflags, 8);
   if (rc == TTICE_OK && h->wt_bytes == 4) rc = dalloc<float>(&h->G32, s * s);
+  if (h->wt_bytes == 4 && s >= kBigKrylovMin) {
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->BQ, s * kBigK);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->BGQ, s * kBigK);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->BY, s * kBigP);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->BY2, s * kBigP);
+    if (rc == TTICE_OK) rc = dalloc<float>(&h->BC, (int64_t)kBigK * kBigP);
+    if (rc == TTICE_OK) rc = dalloc<double>(&h->BH, (int64_t)kBigK * kBigK);
+  }
   if (rc == TTICE_OK) rc = dalloc<float>(&h->KQ, s * kKry);
   if (rc == TTICE_OK) rc = dalloc<float>(&h->kstart, s * kKryP);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->KV, std::max<int64_t>(s * kKryP, kKry * kKry));
@@ -1447,6 +1657,8 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Ebuf, std::max<int64_t>(h->max_ms, 1));
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Vn, h->max_m * kRR);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->Vn2, h->max_m * kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->sgn, kRR);
+  if (rc == TTICE_OK) rc = dalloc<double>(&h->sgn_part, 128 * kRR);
   int64_t maxcap = 1;
   for (int i = 1; i <= d; ++i) maxcap = std::max(maxcap, h->cap[i]);
   if (rc == TTICE_OK) rc = dalloc<double>(&h->P, maxcap * kRR);

@@ -214,6 +214,12 @@ cudaError_t launch_split_tf32(const float* in, int64_t ld_in, int64_t c0, int64_
 cudaError_t launch_split_tf32_f64(const double* in, int64_t ld_in, int64_t rows, int64_t c0, int64_t c1, float* hi,
                                   float* lo, int64_t ld_out, cudaStream_t st, float* f32 = nullptr,
                                   double* sumsq = nullptr);
+// W[z][n][l] = P[(z L + l) k + n] (FP64 -> FP32) for b observations, n < k, l < L; w2[z] (optional,
+// zeroed by the caller) gains the sum of squares of observation z.
+cudaError_t launch_scatter_stage(const double* P, int b, int64_t k, int64_t L, float* W, double* w2,
+                                 cudaStream_t st);
+// rho2[z] += x2[z] - w2[z], z < b
+cudaError_t launch_pythagoras(const double* x2, const double* w2, int b, double* rho2, cudaStream_t st);
 // TF32 head / tail of I - Rinv (k x k, column-major), transposed into rows of ld (the B operand of a
 // product X (I - Rinv)); zero outside the k x k corner of the ld x ld block.
 cudaError_t launch_eye_minus_split(const double* Rinv, int k, float* hi, float* lo, int ld, cudaStream_t st);
@@ -225,6 +231,8 @@ void tc_drop_next_copy(long long chunk);
 
 // Misc kernels.
 cudaError_t launch_fill(double* p, int64_t n, double v, cudaStream_t st);
+// n pseudo-random values in [-1, 1) (splitmix64 of seed + index)
+cudaError_t launch_fill_random(float* p, int64_t n, uint64_t seed, cudaStream_t st);
 template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* in, TO* out, int64_t n, cudaStream_t st);
 template <typename T>
@@ -239,10 +247,13 @@ template <typename T>
 cudaError_t launch_sum_squares(const T* x, int b, int64_t N, double* out, cudaStream_t st);
 // diag sum of an FP64 s x s matrix into *out
 cudaError_t launch_trace(const double* G, int64_t ldg, int s, double* out, cudaStream_t st);
-// columns of V (m x k, ld m): flip each so that its largest-|.| entry (lowest index on ties) is > 0
-cudaError_t launch_canonical_sign(double* V, int64_t m, int k, int64_t ld, cudaStream_t st);
+// canonical sign of the k columns of V (m x k, ld): sign[c] = -1 if the column's largest-|.| entry
+// (lowest index on ties) is negative, else 1.  part: scratch of 128 k doubles.
+cudaError_t launch_canonical_sign(const double* V, int64_t m, int k, int64_t ld, double* part, double* sign,
+                                  cudaStream_t st);
 // Cholesky-QR step support: given S = V^T V (k x k, FP64, ld k), overwrite Rinv (k x k, ld k) with
-// the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  status=1 if not positive definite.
+// the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  *status is set to 1 if S is not
+// positive definite (left as it is otherwise).
 // diag (optional, k entries) replaces the diagonal of S.
 cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st,
                             const double* diag = nullptr);
@@ -256,9 +267,10 @@ cudaError_t launch_krylov(const double* G, float* G32, int64_t s, int nblk, floa
 // scale column j of V (m x k, ld) by 1/sqrt(theta[j])
 cudaError_t launch_scale_cols_rsqrt(double* V, int64_t m, int k, int64_t ld, const double* theta,
                                     cudaStream_t st);
-// copy an m x k column-major block (ld_in) into U columns [c0, c0+k) (ld_out), with FP32 mirror
+// copy an m x k column-major block (ld_in) into U columns [c0, c0+k) (ld_out), with FP32 mirror,
+// column c multiplied by sign[c] (optional)
 cudaError_t launch_copy_cols(const double* in, int64_t ld_in, int64_t m, int k, double* out,
-                             int64_t ld_out, float* mirror, cudaStream_t st);
+                             int64_t ld_out, float* mirror, cudaStream_t st, const double* sign = nullptr);
 // append b coefficient vectors (b x r, row-major) to the last core rows [n0, n0+b) (ld cap)
 cudaError_t launch_append_last(const double* coef, int b, int r, double* last, int64_t n0,
                                int64_t ld, cudaStream_t st);

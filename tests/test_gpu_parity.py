@@ -390,6 +390,75 @@ def test_projection_kernel_shapes(T, ranks):
         g.close()
 
 
+def test_large_gram_block_krylov(T):
+    """Gram sides of 1024 (core 2 of a 16 x 80 x 64 stream, batches of 16) take the block Krylov
+    solver with its 768-vector basis in global memory: on a random TT stream (ranks 16, 40, 48)
+    with 1e-3 noise, same ranks and decisions as the oracle on every increment, eps met, and the
+    Krylov result certified (no fall-back to the full Jacobi solver)."""
+    from tt_streams import random_tt
+
+    Y = random_tt(0, 32, dims=(16, 80, 64), ranks=(1, 16, 40, 48, 1), length=64)
+    g = torch.Generator().manual_seed(3)
+    Y = (Y + 1e-3 * Y.std() * torch.randn(Y.shape, generator=g, dtype=Y.dtype)).float()
+    stats = []
+    run_pair(T, Y, 16, 0.1, precision="fp32", tol=1e-4, stats_out=stats)
+    assert sum(x[0] for x in stats) >= 1 and sum(x[1] for x in stats) == 0, stats
+
+
+def test_transposed_stage_projection_and_growth(T):
+    """Stages with 3 columns per observation (not a multiple of 4: no tile layout of the projection
+    kernel takes them) run as a transposed tensor-core projection with FP64 sums across K splits.
+    On seeded orthonormal cores loaded into the handle and the oracle (ranks [1,8,160,400,600,60];
+    stage 3 has m = 16000, L = 3, r = 600): coefficients and per-observation errors equal to the
+    oracle's (Eq. 12, Eq. 17) at FP32 accuracy.  Then one update (tensor-core forms forced) of data
+    with four rank-one tensors outside the cores' span: the inner cores gain columns, and the new
+    rows of the L = 3 and L = 1 stages are projected from an offset into the core (Algorithm 2, last
+    steps).  Same ranks as the oracle, the batch's reconstruction within FP32-level error of the
+    oracle's and within eps."""
+    dims = (8, 20, 20, 40, 3)
+    ranks = [1, 8, 160, 400, 600, 60]
+    rng = np.random.default_rng(17)
+    cores = [np.linalg.qr(rng.normal(size=(ranks[i] * n, ranks[i + 1])))[0] for i, n in enumerate(dims)]
+    o = O.TTICEOracle(dims, 0.1)
+    o.ranks = list(ranks)
+    o.U = [c.copy() for c in cores]
+    o.last = [np.zeros(ranks[-1])]  # the handle is loaded with one (zero) observation
+    b = 8
+    Y = o.expand(rng.normal(size=(b, ranks[-1]))) + 0.005 * rng.normal(size=(b,) + dims)
+    Y32 = torch.tensor(Y, dtype=torch.float32)
+    g = T.TTICE(dims, 0.1, precision="fp32", input_dtype=torch.float32, max_batch=b, max_rank=1024)
+    g.load(ranks, cores, np.zeros((1, ranks[-1])))
+    coeffs, rel = g.project(Y32.cuda())
+    c_o, rho2, y2 = o.errors(Y32.double().numpy())
+    assert _relmax(coeffs.cpu().numpy(), c_o) < 1e-5, _relmax(coeffs.cpu().numpy(), c_o)
+    np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho2 / y2), rtol=2e-3)
+
+    def rank_one():
+        v = [rng.normal(size=n) for n in dims]
+        t = v[0] / np.linalg.norm(v[0])
+        for x in v[1:]:
+            t = np.multiply.outer(t, x / np.linalg.norm(x))
+        return t
+
+    P = np.stack([rank_one() for _ in range(4)])
+    Z = o.expand(rng.normal(size=(b, ranks[-1]))) + np.einsum("zp,p...->z...", 3.0 * rng.normal(size=(b, 4)), P)
+    Z32 = torch.tensor(Z, dtype=torch.float32)
+    try:
+        T.ttice_test_tc_cgs_min(0.0)
+        st = g.update(Z32.cuda())
+    finally:
+        T.ttice_test_tc_cgs_min(-1.0)
+    so = o.update(Z32.double().numpy())
+    assert list(st.ranks[:len(dims) + 1]) == so.ranks[:len(dims) + 1]
+    assert st.new_dirs[3] > 0 and st.new_dirs[4] > 0
+    rec = g.reconstruct(1, b).cpu().numpy()
+    ref = o.reconstruct(1, b)
+    assert _relmax(rec, ref) < 1e-4, _relmax(rec, ref)
+    err = math.sqrt(((Z - rec) ** 2).sum() / (Z ** 2).sum())
+    assert err <= 0.1 * (1 + 1e-6), err
+    g.close()
+
+
 def test_bounded_wait_expiry_returns_etimeout(T):
     """A wait inside the tensor-core projection that runs out (a copy the producer was told not to
     issue, with a 20 ms wait limit) ends the kernel cleanly: ttice_update returns TTICE_ETIMEOUT, the
@@ -426,9 +495,11 @@ def test_bounded_wait_expiry_returns_etimeout(T):
 
 
 def test_tensor_core_cgs_matches_oracle(T):
-    """The tensor-core re-orthogonalisation of new directions, CGS2 and CholQR2 (forced for every
-    append the shapes allow), on the 480p video prefix: same decisions and ranks as the oracle on
-    every increment, eps met, and cores orthonormal to 2e-7.  The column norms are FP64 sums; the
+    """The tensor-core re-orthogonalisation of new directions, CGS2 and CholQR2, and the transposed
+    projection of the narrow stages (all forced wherever the shapes allow), on the 480p video
+    prefix: same decisions and ranks as the oracle on every increment, eps met, batch errors within
+    2e-4 relative (the forced narrow stages' residual norms by Pythagoras carry FP32 rounding
+    amplified by ||x||^2 / ||R||^2), and cores orthonormal to 2e-7.  The column norms are FP64 sums; the
     coupling left between columns is the tensor core's FP32 summation of products (~2^-23 of the
     products' magnitudes per 8-term MMA), largest for short columns with a few large entries (here
     m is a few hundred and entries reach 0.2: ~1e-7; ~1e-9 for the delocalised columns of length
@@ -436,7 +507,7 @@ def test_tensor_core_cgs_matches_oracle(T):
     frames = blob_video(0, 16)
     try:
         T.ttice_test_tc_cgs_min(0.0)
-        run_pair(T, frames, 8, 0.1, precision="fp32", tol=1e-4, orth_tol=2e-7)
+        run_pair(T, frames, 8, 0.1, precision="fp32", tol=2e-4, orth_tol=2e-7)
     finally:
         T.ttice_test_tc_cgs_min(-1.0)
 
