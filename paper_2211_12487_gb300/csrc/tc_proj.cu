@@ -111,6 +111,7 @@ struct ProjArgs {
   double* part_x;
   double* part_w;
   int* status;
+  const int* run_if;  // the kernel returns at once unless *run_if != 0 (nullptr: always runs)
   unsigned long long wait_ns;
   long long drop_chunk;  // test hook: CTA 0 issues no copy for its chunk of this index (-1: none)
 };
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_proj_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xlmap,
                    const __grid_constant__ CUtensorMap uhmap, const __grid_constant__ CUtensorMap ulmap,
                    const ProjArgs a) {
+  if (a.run_if && *a.run_if == 0) return;  // every thread reads the same flag before any barrier
   constexpr int RAW = Cfg<NT>::raw, AST = Cfg<NT>::a, BST = Cfg<NT>::b;
   constexpr uint32_t kBBytes = NT * 128;  // one half of a B chunk: NT rows of 128 bytes
   // tensor memory: main accumulator of the current / next segment at [0, 2 NT), cross accumulator of
@@ -665,6 +667,8 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   a.px_stride = (int64_t)a.nb * xper;
   a.part_w = norms && a.nsplit == 1 ? g.part + (int64_t)a.nsplit * a.nb * xper : nullptr;
   a.status = g.status;
+  if (g.run_if && (ws_split || norms)) return cudaErrorInvalidValue;  // no follow-up pass checks the flag
+  a.run_if = g.run_if;
   a.wait_ns = g_wait_ns.load();
   a.drop_chunk = g_drop_chunk.exchange(-1);
   const int64_t nitems = (int64_t)a.nsplit * items1;
@@ -875,6 +879,29 @@ __global__ void scatter_stage_kernel(const double* P, int64_t k, int64_t L, floa
 __global__ void pythagoras_kernel(const double* x2, const double* w2, int b, double* rho2) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z < b) rho2[z] += x2[z] - w2[z];
+}
+
+__global__ void cols_above_kernel(const double* P, int64_t r, int64_t ld, double thr2, int* flag) {
+  __shared__ double red[8];
+  const double* p = P + (int64_t)blockIdx.x * ld;
+  double q = 0.0;
+  for (int64_t a = threadIdx.x; a < r; a += blockDim.x) q = fma(p[a], p[a], q);
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    if (!(t <= thr2)) atomicExch(flag, 1);  // also raised by NaN
+  }
+}
+
+cudaError_t launch_cols_above(const double* P, int64_t r, int k, int64_t ld, double thr, int* flag,
+                              cudaStream_t st) {
+  if (k <= 0 || r <= 0) return cudaSuccess;
+  note_launch();
+  cols_above_kernel<<<k, 256, 0, st>>>(P, r, ld, thr * thr, flag);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_stage(const double* P, int b, int64_t k, int64_t L, float* W, double* w2,

@@ -745,9 +745,10 @@ int krylov_certify(ttice_s* h, int64_t s, int K, bool* ok, cudaStream_t st) {
 // After krylov_certify turned a Krylov result down (some Ritz pair the rule used has a residual above
 // 1e-6 theta_1, as in flat spectra whose leading eigenvalues lie 1e-3 apart): accept the rank
 // decision itself when its margin exceeds what the residuals allow.  With Ritz values theta_j and
-// residual matrix G Q - Q H of Frobenius norm rho, G - E (||E|| <= 2 rho) has Q as an invariant
-// subspace, so the leading eigenvalues of G exceed the matching Ritz values by at most 2 rho each
-// (Weyl), given that the Krylov space holds the leading eigenvectors (a random start).  The rule's
+// Ritz vectors Z (the rule's leading rR) and residual matrix G Z - Z Theta of Frobenius norm rho,
+// G - E (||E|| <= 2 rho) has span(Z) as an invariant subspace, so the leading eigenvalues of G
+// exceed the matching Ritz values by at most 2 rho each (Weyl), given that the Krylov space holds the
+// leading eigenvectors (a random start).  The rule's
 // rank rR has Ritz tail(rR) <= eps^2, which bounds the true tail of the appended directions exactly
 // (their captured energy is the sum of their Ritz values); the true rank is rR as well when
 // tail(rR - 1) - 2 rho (rR - 1) > eps^2.  Reads the residuals krylov_certify left in h->h_dbl.
@@ -759,7 +760,7 @@ int krylov_margin_ok(ttice_s* h, int K, double eps_c, bool* ok, cudaStream_t st)
   TT_CU(cudaMemcpyAsync(h->h_dbl + 250, h->trace, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_TRY(sync_read(h, st));
   double rho2 = 0.0;
-  for (int j = 0; j < K; ++j) rho2 += h->h_dbl[j] * h->h_dbl[j];
+  for (int j = 0; j < rR; ++j) rho2 += h->h_dbl[j] * h->h_dbl[j];
   const double tr = h->h_dbl[250];
   double tail = tr;  // tail(rR - 1) from the Ritz values
   for (int j = 0; j < rR - 1; ++j) tail -= h->h_dbl[130 + j];
@@ -1099,7 +1100,7 @@ int build_dirs(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int c0, 
 // with U from its FP32 mirror, subtracted in FP64.  P is small (the coupling left by an explicit residual), so the
 // FP32-accurate products leave a coupling of ~2^-22 |P| after the pass; the floor is the FP32
 // rounding of the tensor-core sums, ~1e-9 of unit vectors for K in the tens of thousands.
-int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
+int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st, const int* run_if = nullptr) {
   const int64_t r = h->r[core + 1];
   TT_CU(launch_split_tf32_f64(h->Vn, m, m, 0, k, h->Vnh, h->Vnl, h->ldv, st));
   // P[a][j] = sum_i U[i][a] Vn[i][j]: A rows j (K = i), B rows a (K = i); summed in FP64 as P^T (row j
@@ -1113,6 +1114,7 @@ int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
   a.r = (int)r;
   a.mode = 5; a.out = h->P; a.ldn = 1; a.ldl = r;
   a.status = h->ibuf + 5;
+  a.run_if = run_if;
   TT_CU(launch_tc_gemm(a, st));
   TT_CU(launch_split_tf32_f64(h->P, r, r, 0, k, h->Ph, h->Pl, h->ldp, st));
   TcGemm b;  // Vn[i][j] -= sum_a U[i][a] P[a][j]: A = U (K = a rows, i contiguous), B rows j (K = a)
@@ -1122,9 +1124,15 @@ int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
   b.r = k;
   b.mode = 1; b.out = h->Vn; b.ldn = m; b.ldl = 1;
   b.status = h->ibuf + 5;
+  b.run_if = run_if;
   TT_CU(launch_tc_gemm(b, st));
   return TTICE_OK;
 }
+
+// Coupling |U^T v| above which the tensor-core CGS runs its second pass.  One pass leaves ~2^-22 of
+// the coupling it removes plus the floor of the FP32 sums; directions built from an explicit
+// residual start near 1e-6, so the second pass only matters for inputs far from orthogonal.
+constexpr double kCgsRepeat = 1.0 / 1024;
 
 // Mixed path: the CholQR work m k^2 from which a chunk's Cholesky-QR runs on the tensor cores (with
 // the CGS on them): its FP64 form costs 8 m k^2 flops, milliseconds at GB300's FP64 rate from here.
@@ -1165,13 +1173,19 @@ int cholqr_pass_tc(ttice_s* h, int64_t m, int k, cudaStream_t st) {
 }
 
 // CGS2 of the new directions Vn (m x k) against U[core] (m x r), CholQR2 among themselves,
-// canonical sign, and append as columns r..r+k-1 of U[core] (Eq. 10).
+// canonical sign, and append as columns r..r+k-1 of U[core] (Eq. 10).  On the tensor cores the
+// second CGS pass runs only when the first met a coupling above kCgsRepeat (a device flag).
 int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
   const int64_t r = h->r[core + 1];
   double* U = h->U[core];
   const int64_t ld = h->ldu[core];
   const bool tc = h->Uh[core] && r > 0 && m >= 32 && ld % 4 == 0 && (double)m * r * k >= g_tc_cgs_min.load();
-  for (int pass = 0; pass < 2 && tc; ++pass) TT_TRY(cgs_pass_tc(h, core, m, k, st));
+  if (tc) {
+    TT_TRY(cgs_pass_tc(h, core, m, k, st));
+    TT_CU(cudaMemsetAsync(h->ibuf + 7, 0, sizeof(int), st));
+    TT_CU(launch_cols_above(h->P, r, k, r, kCgsRepeat, h->ibuf + 7, st));
+    TT_TRY(cgs_pass_tc(h, core, m, k, st, h->ibuf + 7));  // runs only if the flag was raised
+  }
   for (int pass = 0; pass < 2 && r > 0 && !tc; ++pass) {
     GemmArgs a;  // P = U^T Vn  (r x k, column-major ld r)
     a.M = r; a.N = k; a.K = m; a.atomic = 1; a.allow_splitk = 1;
@@ -1354,7 +1368,6 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
         WT* R = static_cast<WT*>(h->Rbuf);
         const WT* Ui = (sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i])
                                          : reinterpret_cast<const WT*>(h->Uf[i]);
-        WT* Wt = static_cast<WT*>(h->dstage[i]);
         {
           const double sx = (i == 0) ? sizeof(TY) : sizeof(WT), sw = sizeof(WT);
           ph_begin(h, PH_RESID, st, nsel * (sx * m * L + sw * m * L + 2.0 * sw * ri * L),

@@ -198,8 +198,15 @@ struct TcGemm {
   // the chain layout o_obs = r L, ldn = L, ldl = 1): partial products, then a summing pass
   float* ws = nullptr;
   int64_t ws_elems = 0;
+  // optional device flag: the product runs only if *run_if != 0 (decided by earlier kernels on the
+  // stream, so the host need not synchronise)
+  const int* run_if = nullptr;
 };
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t st);
+// flag = 1 if some column j < k of P (FP64, column j at P + j ld, r entries) has norm > thr (flag is
+// only ever raised: the caller zeroes it)
+cudaError_t launch_cols_above(const double* P, int64_t r, int k, int64_t ld, double thr, int* flag,
+                              cudaStream_t st);
 // Transposing split of b observations of W (r x L, row-major): row z L + l of hi / lo (ld_out >= r)
 // holds the TF32 head / tail of W[z][:][l], zero up to the next multiple of 32.
 cudaError_t launch_split_tf32_transpose(const float* W, int b, int64_t r, int64_t L, float* hi, float* lo,
