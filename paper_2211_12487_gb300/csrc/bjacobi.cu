@@ -1,4 +1,5 @@
-// Multi-CTA block Jacobi eigen-solver for the residual Gram matrices of Eq. 9 (s up to 1024).
+// Multi-CTA block Jacobi eigen-solver for the residual Gram matrices of Eq. 9 (s up to 4608; blocks
+// of BS = 32 in FP32, 16 in FP64).
 //
 // Two-sided cyclic block Jacobi (Golub & Van Loan, Sec. 8.5, block variant): the matrix is split
 // into nb blocks of BS rows/columns; the block pairs (I, J) of one round come from the round-robin
@@ -28,7 +29,7 @@ namespace {
 
 template <typename T> struct BJ;
 template <> struct BJ<float> {
-  static constexpr int BS = 16;
+  static constexpr int BS = 32;  // 64 x 64 sub-problems: half the rounds per sweep of BS = 16
   static __device__ float eps() { return FLT_EPSILON; }
 };
 template <> struct BJ<double> {
@@ -71,8 +72,8 @@ __global__ void bj_init(const double* G, int64_t ldg, int s, int sp, T* A, T* V,
 template <typename T>
 __global__ void __launch_bounds__(32 * BJ<T>::BS) bj_solve(const T* A, int sp, int nb, int round,
                                                            T* Qb, const double* fro, int* flags) {
-  constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
-  static_assert(N2 == 32, "one lane per row/column element");
+  constexpr int BS = BJ<T>::BS, N2 = 2 * BS, EL = N2 / 32;  // elements of a row / column per lane
+  static_assert(N2 % 32 == 0, "whole warps per row / column");
   if (flags[1]) return;
   __shared__ T S[N2][N2 + 1];
   __shared__ T Q[N2][N2 + 1];
@@ -110,18 +111,26 @@ __global__ void __launch_bounds__(32 * BJ<T>::BS) bj_solve(const T* A, int sp, i
     c = __shfl_sync(0xffffffffu, c, 0);
     sn = __shfl_sync(0xffffffffu, sn, 0);
     if (sn != T(0)) {  // rows p, q of S
-      const T xp = S[p][lane], xq = S[q][lane];
-      S[p][lane] = c * xp - sn * xq;
-      S[q][lane] = sn * xp + c * xq;
+#pragma unroll
+      for (int h = 0; h < EL; ++h) {
+        const int x = lane + 32 * h;
+        const T xp = S[p][x], xq = S[q][x];
+        S[p][x] = c * xp - sn * xq;
+        S[q][x] = sn * xp + c * xq;
+      }
     }
     __syncthreads();
     if (sn != T(0)) {  // columns p, q of S and of Q
-      const T xp = S[lane][p], xq = S[lane][q];
-      S[lane][p] = c * xp - sn * xq;
-      S[lane][q] = sn * xp + c * xq;
-      const T vp = Q[lane][p], vq = Q[lane][q];
-      Q[lane][p] = c * vp - sn * vq;
-      Q[lane][q] = sn * vp + c * vq;
+#pragma unroll
+      for (int h = 0; h < EL; ++h) {
+        const int x = lane + 32 * h;
+        const T xp = S[x][p], xq = S[x][q];
+        S[x][p] = c * xp - sn * xq;
+        S[x][q] = sn * xp + c * xq;
+        const T vp = Q[x][p], vq = Q[x][q];
+        Q[x][p] = c * vp - sn * vq;
+        Q[x][q] = sn * vp + c * vq;
+      }
     }
     __syncthreads();
   }
@@ -140,9 +149,13 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
                                                       const T* Qb, const int* flags) {
   constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
   if (flags[1]) return;
-  __shared__ T Qa[N2][N2 + 1];
-  __shared__ T Qc[N2][N2 + 1];
-  __shared__ T X[kTile][N2 + 1];  // A block (N2 x N2), then the product; or a V tile (kTile x N2)
+  // dynamic shared memory (over 48 KB for FP32 at BS = 32): Qa, Qc (N2 x N2) and X, the A block
+  // (N2 x N2) then its product, or a V tile (kTile x N2); rows padded to N2 + 1
+  extern __shared__ __align__(16) unsigned char bj_smem[];
+  using Row = T[N2 + 1];
+  Row* Qa = reinterpret_cast<Row*>(bj_smem);
+  Row* Qc = Qa + N2;
+  Row* X = Qc + N2;
   const int npairs = nb / 2;
   const int tid = threadIdx.x;
   const int64_t nA = (int64_t)npairs * npairs;
@@ -304,6 +317,13 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
   }
   const int tiles = (sp + kTile - 1) / kTile;
   const int64_t upd_ctas = (int64_t)npairs * npairs + (int64_t)npairs * tiles;
+  const size_t upd_smem = (size_t)(2 * N2 + (N2 > kTile ? N2 : kTile)) * (N2 + 1) * sizeof(T);
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(bj_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem);
+  });
+  TT_CUDA(attr_err);
   // Two sweeps of rounds (the buffer parity repeats after two, since a sweep has nb - 1 rounds, an
   // odd count) are captured once into a CUDA graph per (buffers, size) and replayed until the sweep
   // cap; every kernel returns at once after the solve has ended.  Capture goes to a private stream
@@ -315,7 +335,7 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
         T* Ain = cur ? A1 : A0;
         T* Aout = cur ? A0 : A1;
         bj_solve<T><<<npairs, 32 * BS, 0, cs>>>(Ain, sp, nb, round, Qb, fro, flags);
-        bj_update<T><<<(unsigned)upd_ctas, kThreads, 0, cs>>>(Ain, Aout, V, sp, nb, round, Qb, flags);
+        bj_update<T><<<(unsigned)upd_ctas, kThreads, upd_smem, cs>>>(Ain, Aout, V, sp, nb, round, Qb, flags);
         cur ^= 1;
       }
       const int64_t n = (int64_t)sp * sp;

@@ -116,6 +116,17 @@ struct ProjArgs {
   long long drop_chunk;  // test hook: CTA 0 issues no copy for its chunk of this index (-1: none)
 };
 
+// Item q -> (observation z, column tile t, N tile j, K split ks), observations fastest: the CTAs
+// running at one time share a few N tiles of B across all observations, so each B tile streams
+// from HBM about once and its other readers hit L2 (with N tiles fastest, every observation would
+// re-read all of B: 32x the core's bytes on the 1080p stream's third core).
+__device__ __forceinline__ void decode_item(int64_t q, const ProjArgs& a, int* z, int* t, int* j, int* ks) {
+  *z = (int)(q % a.b);
+  *j = (int)((q / a.b) % a.nj);
+  *t = (int)((q / ((int64_t)a.b * a.nj)) % a.tpo);
+  *ks = (int)(q / ((int64_t)a.b * a.nj * a.tpo));
+}
+
 // APRE: the A operand (rows = the items' columns, K contiguous) is given pre-split as TF32 head /
 // tail arrays and copied by TMA straight into the A slots (xmap / xlmap are their maps); otherwise
 // xmap describes the raw FP32 X and the converter warps build the A slots.
@@ -188,10 +199,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t g = 0;
       bool ok = true;
       for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
-        const int j = (int)(q % a.nj);
-        const int t = (int)((q / a.nj) % a.tpo);
-        const int z = (int)((q / ((int64_t)a.nj * a.tpo)) % a.b);
-        const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
+        int z, t, j, ks;
+        decode_item(q, a, &z, &t, &j, &ks);
         const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
         for (int c = c_lo; c < c_hi; ++c, ++g) {
           const int s = (int)(g % RAW), sb = (int)(g % BST), qa = (int)(g % AST);
@@ -245,8 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0;
       bool ok = true;
       for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x, ++it) {
-        const int j = (int)(q % a.nj);
-        const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
+        int z, t, j, ks;
+        decode_item(q, a, &z, &t, &j, &ks);
         const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
         const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);  // MMA N of this item
         const uint32_t idesc = tf32_idesc(kTile, nN);
@@ -303,10 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // converters: thread tid owns column tid of the item's tile
     int64_t g = 0;
     for (int64_t q = blockIdx.x; q < nitems; q += gridDim.x) {
-      const int j = (int)(q % a.nj);
-      const int t = (int)((q / a.nj) % a.tpo);
-      const int z = (int)((q / ((int64_t)a.nj * a.tpo)) % a.b);
-      const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
+      int z, t, j, ks;
+      decode_item(q, a, &z, &t, &j, &ks);
       const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
       double* part_x = a.part_x ? a.part_x + (int64_t)ks * a.px_stride : nullptr;
       float x2 = 0.0f;
@@ -381,10 +388,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     int it = 0;
     bool ok = true;
     for (int64_t q = blockIdx.x; q < nitems && ok; q += gridDim.x, ++it) {
-      const int j = (int)(q % a.nj);
-      const int t = (int)((q / a.nj) % a.tpo);
-      const int z = (int)((q / ((int64_t)a.nj * a.tpo)) % a.b);
-      const int ks = (int)(q / ((int64_t)a.nj * a.tpo * a.b));
+      int z, t, j, ks;
+      decode_item(q, a, &z, &t, &j, &ks);
       const int c_lo = ks * a.cps, c_hi = min(a.nch, c_lo + a.cps);
       const int nseg = (c_hi - c_lo + a.seglen - 1) / a.seglen;
       const int nN = min(NT, (a.r - j * NT + 15) / 16 * 16);

@@ -40,6 +40,7 @@ struct ttice_s {
   int64_t cap[kMaxD + 1] = {};  // rank capacities, cap[0] = 1
   int64_t ldu[kMaxD] = {};      // rows of the U[i] allocation = cap[i] * n[i]
   int64_t r[kMaxD + 1] = {};    // ranks r_0..r_d (host mirror), r[0] = 1
+  int last_new[kMaxD] = {};      // directions each core gained in its last truncation (sizes solver choice)
   double* U[kMaxD] = {};
   float* Uf[kMaxD] = {};
   // TF32 head / tail split of Uf for the tensor-core projections (mixed path): column-major, leading
@@ -933,7 +934,9 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
     Vdir = h->V64; thet = h->w64; K = (int)s;
   } else {
     bool have = false, big = false;
-    const bool try_big = s >= kBigKrylovMin && h->BQ;  // a 64-vector basis cannot do better
+    // a 64-vector basis cannot do better; a core that last gained more directions than one Rayleigh-
+    // Ritz problem holds most likely needs the full solver again (the basis would be built in vain)
+    const bool try_big = s >= kBigKrylovMin && h->BQ && h->last_new[core] <= kRR - 8;
     if (try_big) {
       int Kk = 0;
       TT_TRY(krylov_big_candidates(h, s, eps_c, &Kk, st));
@@ -1044,6 +1047,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
   }
   if (rR < 0) return TTICE_ECAPACITY;  // no subspace holds the tolerance (not reached in practice)
   *rR_out = rR;
+  h->last_new[core] = rR;
   if (rR == 0) return TTICE_OK;
   h->dir_src = Vdir;
   h->dir_scale = thet;
