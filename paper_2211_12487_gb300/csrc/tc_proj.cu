@@ -99,6 +99,7 @@ struct ProjArgs {
   // K, ks = q / (b tpo nj), and stores its partial D at out + ks ws_stride (kStoreF32 only)
   int nsplit, cps;
   int seglen;  // chunks per main-accumulator segment
+  int tfast;   // item order: column tiles fastest (else observations, then N tiles)
   int64_t ws_stride, px_stride;  // partial D and x^2 partials of one K split
   int mode;
   void* out;
@@ -120,10 +121,18 @@ struct ProjArgs {
 // running at one time share a few N tiles of B across all observations, so each B tile streams
 // from HBM about once and its other readers hit L2 (with N tiles fastest, every observation would
 // re-read all of B: 32x the core's bytes on the 1080p stream's third core).
+// With a pre-split A operand (one observation, several A tiles), A tiles go fastest instead: the
+// running CTAs then share each B tile across all A tiles.
 __device__ __forceinline__ void decode_item(int64_t q, const ProjArgs& a, int* z, int* t, int* j, int* ks) {
-  *z = (int)(q % a.b);
-  *j = (int)((q / a.b) % a.nj);
-  *t = (int)((q / ((int64_t)a.b * a.nj)) % a.tpo);
+  if (a.tfast) {
+    *t = (int)(q % a.tpo);
+    *z = (int)((q / a.tpo) % a.b);
+    *j = (int)((q / ((int64_t)a.tpo * a.b)) % a.nj);
+  } else {
+    *z = (int)(q % a.b);
+    *j = (int)((q / a.b) % a.nj);
+    *t = (int)((q / ((int64_t)a.b * a.nj)) % a.tpo);
+  }
   *ks = (int)(q / ((int64_t)a.b * a.nj * a.tpo));
 }
 
@@ -631,6 +640,7 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   a.b = a.narrow ? (a.nb + a.opt - 1) / a.opt : a.nb;
   a.nj = (g.r + NT - 1) / NT;
   a.tpo = a.narrow ? 1 : (int)((g.L + kTile - 1) / kTile);
+  a.tfast = APRE ? 1 : 0;
   a.nch = (int)((g.K + kChunk - 1) / kChunk);
   a.mode = g.mode;
   a.out = g.out;

@@ -106,6 +106,16 @@ struct ttice_s {
   // rounded up to 32)
   float* Vnh = nullptr;
   float* Vnl = nullptr;
+  // mixed path: a block of up to kb[i] new directions of core i re-orthogonalised against the core's
+  // earlier columns at once (VB, m x kb FP64, its TF32 head / tail at ld ldv) with its projections
+  // (PB, FP64, and their split at ld ldp); kb[i] = 0 where the block would not fit kVBudget
+  double* VB = nullptr;
+  float* VBh = nullptr;
+  float* VBl = nullptr;
+  double* PB = nullptr;
+  float* PBh = nullptr;
+  float* PBl = nullptr;
+  int kb[kMaxD] = {};
   float* Fh = nullptr;  // TF32 head / tail of I - R^{-1} of a tensor-core CholQR pass (kRR x kRR)
   float* Fl = nullptr;
   double* dsq = nullptr;  // FP64 squared column norms of the chunk (the Gram's diagonal), kRR
@@ -228,6 +238,11 @@ constexpr int kBigP = 8;
 constexpr int kBigBlocks = 96;
 constexpr int kBigK = kBigP * kBigBlocks;
 constexpr int kBigKrylovMin = 1024;
+// Mixed path: new directions of a core are re-orthogonalised against its earlier columns in blocks
+// of up to kBlockDirs (one pass over the core per block instead of per 96-column chunk), where the
+// block's m x kb FP64 array stays within kVBudget doubles.
+constexpr int64_t kBlockDirs = 768;
+constexpr int64_t kVBudget = int64_t(64) << 20;
 constexpr int64_t kMaxGridZ = 65535;  // batch (grid z) limit of one contraction launch
 
 // The CUDA error behind the last TTICE_ECUDA returned to this thread (ttice_last_cuda_error).
@@ -302,7 +317,7 @@ void free_all(ttice_s* h) {
                   h->bjw64, h->bjw32, h->fro, h->bjflags,
                   h->last, h->dgather, h->Rbuf, h->G, h->w32, h->V32, h->w64, h->V64,
                   h->work64, h->Q, h->Q2, h->GQ, h->Ssm, h->Rinv, h->H, h->Z, h->theta, h->Vn,
-                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Fh, h->Fl, h->dsq, h->sgn, h->sgn_part, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->tcws, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
+                  h->Vn2, h->Ebuf, h->P, h->Vnh, h->Vnl, h->Fh, h->Fl, h->VB, h->VBh, h->VBl, h->PB, h->PBh, h->PBl, h->dsq, h->sgn, h->sgn_part, h->Ph, h->Pl, h->WTh, h->WTl, h->Rh, h->Rl, h->tcws, h->part, h->rho2, h->y2, h->rn2, h->trace, h->dec, h->sel, h->ibuf};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(h->h_dec); cudaFreeHost(h->h_sel); cudaFreeHost(h->h_int); cudaFreeHost(h->h_w32); cudaFreeHost(h->h_dbl);
   cudaFreeHost(h->h_rn2);
@@ -949,7 +964,7 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
       }
       if (!have) h->stats.krylov_fallbacks += 1;
     }
-    if (!have && !try_big && s > kKrylovMin) {
+    if (!have && !try_big && s > kKrylovMin && !(s >= kBigKrylovMin && h->last_new[core] > kRR - 8)) {
       // block Krylov candidates + FP64 Rayleigh-Ritz, kept only if certified: a 32-vector basis
       // first (enough for a few new directions, and an 8x smaller Ritz problem), then 64 — restarted
       // from the first attempt's leading Ritz vectors when it got as far as Rayleigh-Ritz, and from a
@@ -1060,11 +1075,12 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
 // eigenvectors themselves for a row-side Gram, u_j = R v_j / sqrt(theta_j) for a column-side one.
 template <typename WT>
 int build_dirs(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int c0, int k,
-               cudaStream_t st) {
+               cudaStream_t st, double* dst = nullptr) {
+  double* Vn = dst ? dst : h->Vn;  // m x k, ld m
   const int64_t s = h->dir_s;
   const double* Vdir = h->dir_src + (int64_t)c0 * s;
   if (h->dir_left) {
-    TT_CU(cudaMemcpy2DAsync(h->Vn, m * sizeof(double), Vdir, s * sizeof(double), m * sizeof(double),
+    TT_CU(cudaMemcpy2DAsync(Vn, m * sizeof(double), Vdir, s * sizeof(double), m * sizeof(double),
                             k, cudaMemcpyDeviceToDevice, st));
   } else if (sizeof(WT) == 4 && h->rlay == 1 && h->WTh && ((s + 31) / 32 * 32) * k <= h->wt_elems) {
     // u_j = R v_j on the tensor cores: R^T as the A operand, the split eigenvectors as B
@@ -1075,58 +1091,76 @@ int build_dirs(ttice_s* h, const WT* R, int64_t m, int64_t L, int nsel, int c0, 
     g.L = m; g.K = c;
     g.bh = h->WTh; g.bl = h->WTl; g.ldb = lds; g.nb_alloc = k;
     g.r = k;
-    g.mode = 3; g.out = h->Vn; g.ldn = m; g.ldl = 1;
+    g.mode = 3; g.out = Vn; g.ldn = m; g.ldl = 1;
     g.status = h->ibuf + 5;
     TT_CU(launch_tc_gemm(g, st));
-    TT_CU(launch_scale_cols_rsqrt(h->Vn, m, k, m, h->dir_scale + c0, st));
+    TT_CU(launch_scale_cols_rsqrt(Vn, m, k, m, h->dir_scale + c0, st));
   } else {
-    TT_CU(cudaMemsetAsync(h->Vn, 0, (size_t)m * k * sizeof(double), st));
+    TT_CU(cudaMemsetAsync(Vn, 0, (size_t)m * k * sizeof(double), st));
     GemmArgs g;
     g.M = m; g.N = k; g.K = L; g.atomic = 1; g.allow_splitk = 1;
     g.A.p = R; g.A.rs = L; g.A.cs = 1; g.A.bs1 = m * L;
     g.B.p = Vdir; g.B.rs = 1; g.B.cs = s; g.B.bs1 = L;
     if (h->rlay == 1) { g.K = L * nsel; g.A.rs = 1; g.A.cs = m; g.A.bs1 = 0; g.B.bs1 = 0; }  // R^T storage
-    g.C = h->Vn; g.c_rs = 1; g.c_cs = m;
+    g.C = Vn; g.c_rs = 1; g.c_cs = m;
     g.nbatch = h->rlay == 1 ? 1 : nsel;
     // mixed path: FP32 products of the FP32 residual (FP64 accumulation); the directions are
     // re-orthogonalised against the core and among themselves afterwards
     using BACC = typename std::conditional<sizeof(WT) == 8, double, float>::type;
     TT_CU((gemm<WT, double, double, double, BACC>(g, st)));
-    TT_CU(launch_scale_cols_rsqrt(h->Vn, m, k, m, h->dir_scale + c0, st));
+    TT_CU(launch_scale_cols_rsqrt(Vn, m, k, m, h->dir_scale + c0, st));
   }
   return TTICE_OK;
 }
 
 
-// One CGS pass of Vn (m x k, FP64, column-major) against U[core] on the tensor cores: P = U^T Vn
-// from the TF32 head / tail splits of Vn (from FP64) and of U (three products, FP32 accuracy, short
-// K segments summed in registers, K splits in FP64), stored as the head / tail of P, then Vn -= U P
-// with U from its FP32 mirror, subtracted in FP64.  P is small (the coupling left by an explicit residual), so the
-// FP32-accurate products leave a coupling of ~2^-22 |P| after the pass; the floor is the FP32
-// rounding of the tensor-core sums, ~1e-9 of unit vectors for K in the tens of thousands.
-int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st, const int* run_if = nullptr) {
-  const int64_t r = h->r[core + 1];
-  TT_CU(launch_split_tf32_f64(h->Vn, m, m, 0, k, h->Vnh, h->Vnl, h->ldv, st));
-  // P[a][j] = sum_i U[i][a] Vn[i][j]: A rows j (K = i), B rows a (K = i); summed in FP64 as P^T (row j
-  // at h->P + j r), K split across CTAs when the output is small (few rows of U, tall columns), then
-  // split into the TF32 head / tail that the product below reads as its B operand (rows j, K = a)
-  TT_CU(cudaMemsetAsync(h->P, 0, (size_t)r * k * sizeof(double), st));
+// Operands of a tensor-core CGS pass: the directions V (FP64, m x k, ld m) with their TF32 head /
+// tail (ld ldv, valloc columns allocated) and the projections P (FP64, ncols x k) with theirs (ld
+// ldp, palloc columns).
+struct CgsWs {
+  double* V;
+  float* Vh;
+  float* Vl;
+  int64_t ldv, valloc;
+  double* P;
+  float* Ph;
+  float* Pl;
+  int64_t ldp, palloc;
+};
+CgsWs chunk_ws(ttice_s* h) { return {h->Vn, h->Vnh, h->Vnl, h->ldv, kRR, h->P, h->Ph, h->Pl, h->ldp, kRR}; }
+
+// One CGS pass of V (m x k, FP64, column-major) against columns [c0, c0 + ncols) of U[core] on the
+// tensor cores: P = U^T V from the TF32 head / tail splits of V (from FP64) and of U (three products,
+// FP32 accuracy, short K segments summed in registers, K splits in FP64), stored as the head / tail
+// of P, then V -= U P with U from its FP32 mirror, subtracted in FP64.  P is small (the coupling left
+// by an explicit residual), so the FP32-accurate products leave a coupling of ~2^-22 |P| after the
+// pass; the floor is the FP32 rounding of the tensor-core sums, ~1e-9 of unit vectors for K in the
+// tens of thousands.
+int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, int64_t c0, int64_t ncols, const CgsWs& w, cudaStream_t st,
+                const int* run_if = nullptr) {
+  const int64_t r = ncols;
+  TT_CU(launch_split_tf32_f64(w.V, m, m, 0, k, w.Vh, w.Vl, w.ldv, st));
+  // P[a][j] = sum_i U[i][c0 + a] V[i][j]: A rows j (K = i), B rows a (K = i); summed in FP64 as P^T
+  // (row j at P + j r), K split across CTAs when the output is small (few rows of U, tall columns),
+  // then split into the TF32 head / tail that the product below reads as its B operand (rows j, K = a)
+  TT_CU(cudaMemsetAsync(w.P, 0, (size_t)r * k * sizeof(double), st));
   TcGemm a;
-  a.ah = h->Vnh; a.al = h->Vnl; a.lda = h->ldv; a.la_alloc = kRR;
+  a.ah = w.Vh; a.al = w.Vl; a.lda = w.ldv; a.la_alloc = w.valloc;
   a.L = k; a.K = m;
-  a.bh = h->Uh[core]; a.bl = h->Ul[core]; a.ldb = h->ldhl[core]; a.nb_alloc = h->hlcols[core];
+  a.bh = h->Uh[core] + c0 * h->ldhl[core]; a.bl = h->Ul[core] + c0 * h->ldhl[core]; a.ldb = h->ldhl[core];
+  a.nb_alloc = h->hlcols[core] - c0;
   a.r = (int)r;
-  a.mode = 5; a.out = h->P; a.ldn = 1; a.ldl = r;
+  a.mode = 5; a.out = w.P; a.ldn = 1; a.ldl = r;
   a.status = h->ibuf + 5;
   a.run_if = run_if;
   TT_CU(launch_tc_gemm(a, st));
-  TT_CU(launch_split_tf32_f64(h->P, r, r, 0, k, h->Ph, h->Pl, h->ldp, st));
-  TcGemm b;  // Vn[i][j] -= sum_a U[i][a] P[a][j]: A = U (K = a rows, i contiguous), B rows j (K = a)
-  b.x = h->Uf[core]; b.ldx = h->ldu[core]; b.x_obs = h->ldu[core] * r; b.b = 1;
+  TT_CU(launch_split_tf32_f64(w.P, r, r, 0, k, w.Ph, w.Pl, w.ldp, st));
+  TcGemm b;  // V[i][j] -= sum_a U[i][c0 + a] P[a][j]: A = U (K = a rows, i contiguous), B rows j (K = a)
+  b.x = h->Uf[core] + c0 * h->ldu[core]; b.ldx = h->ldu[core]; b.x_obs = h->ldu[core] * r; b.b = 1;
   b.L = m; b.K = r;
-  b.bh = h->Ph; b.bl = h->Pl; b.ldb = h->ldp; b.nb_alloc = kRR;
+  b.bh = w.Ph; b.bl = w.Pl; b.ldb = w.ldp; b.nb_alloc = w.palloc;
   b.r = k;
-  b.mode = 1; b.out = h->Vn; b.ldn = m; b.ldl = 1;
+  b.mode = 1; b.out = w.V; b.ldn = m; b.ldl = 1;
   b.status = h->ibuf + 5;
   b.run_if = run_if;
   TT_CU(launch_tc_gemm(b, st));
@@ -1138,9 +1172,19 @@ int cgs_pass_tc(ttice_s* h, int core, int64_t m, int k, cudaStream_t st, const i
 // residual start near 1e-6, so the second pass only matters for inputs far from orthogonal.
 constexpr double kCgsRepeat = 1.0 / 1024;
 
+// Tensor-core CGS of w.V against columns [c0, c0 + ncols) of U[core]: one pass, and a second one only
+// where the first met a coupling above kCgsRepeat (decided on the device).
+int cgs_tc(ttice_s* h, int core, int64_t m, int k, int64_t c0, int64_t ncols, const CgsWs& w, cudaStream_t st) {
+  if (ncols <= 0) return TTICE_OK;
+  TT_TRY(cgs_pass_tc(h, core, m, k, c0, ncols, w, st));
+  TT_CU(cudaMemsetAsync(h->ibuf + 7, 0, sizeof(int), st));
+  TT_CU(launch_cols_above(w.P, ncols, k, ncols, kCgsRepeat, h->ibuf + 7, st));
+  return cgs_pass_tc(h, core, m, k, c0, ncols, w, st, h->ibuf + 7);  // runs only if the flag was raised
+}
+
 // Mixed path: the CholQR work m k^2 from which a chunk's Cholesky-QR runs on the tensor cores (with
 // the CGS on them): its FP64 form costs 8 m k^2 flops, milliseconds at GB300's FP64 rate from here.
-constexpr double kTcCholMin = 5e8;
+constexpr double kTcCholMin = 1e8;
 
 // One CholQR pass of Vn (m x k, FP64) on the tensor cores: the off-diagonal of S = Vn^T Vn from the
 // TF32 head / tail of Vn (three products, FP32 segment sums, the K splits added in FP64), its
@@ -1179,17 +1223,16 @@ int cholqr_pass_tc(ttice_s* h, int64_t m, int k, cudaStream_t st) {
 // CGS2 of the new directions Vn (m x k) against U[core] (m x r), CholQR2 among themselves,
 // canonical sign, and append as columns r..r+k-1 of U[core] (Eq. 10).  On the tensor cores the
 // second CGS pass runs only when the first met a coupling above kCgsRepeat (a device flag).
-int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t st) {
+// cgs_from > 0 (with `blocked`, tensor-core path only): the chunk was already re-orthogonalised
+// against columns [0, cgs_from) together with the rest of its block, and only [cgs_from, r) remain.
+int orthonormalize_append(ttice_s* h, int core, int64_t m, int k, cudaStream_t st, int64_t cgs_from = 0,
+                          bool blocked = false) {
   const int64_t r = h->r[core + 1];
   double* U = h->U[core];
   const int64_t ld = h->ldu[core];
-  const bool tc = h->Uh[core] && r > 0 && m >= 32 && ld % 4 == 0 && (double)m * r * k >= g_tc_cgs_min.load();
-  if (tc) {
-    TT_TRY(cgs_pass_tc(h, core, m, k, st));
-    TT_CU(cudaMemsetAsync(h->ibuf + 7, 0, sizeof(int), st));
-    TT_CU(launch_cols_above(h->P, r, k, r, kCgsRepeat, h->ibuf + 7, st));
-    TT_TRY(cgs_pass_tc(h, core, m, k, st, h->ibuf + 7));  // runs only if the flag was raised
-  }
+  const bool tc = blocked || (h->Uh[core] && r > 0 && m >= 32 && ld % 4 == 0 &&
+                              (double)m * r * k >= g_tc_cgs_min.load());
+  if (tc) TT_TRY(cgs_tc(h, core, m, k, cgs_from, r - cgs_from, chunk_ws(h), st));
   for (int pass = 0; pass < 2 && r > 0 && !tc; ++pass) {
     GemmArgs a;  // P = U^T Vn  (r x k, column-major ld r)
     a.M = r; a.N = k; a.K = m; a.atomic = 1; a.allow_splitk = 1;
@@ -1433,16 +1476,40 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
             break;
           }
           // append in chunks of at most kRR directions; each chunk is re-orthogonalised against the
-          // core including the chunks already appended (block CGS2)
-          for (int c0 = 0; c0 < rR && rc == TTICE_OK; c0 += kRR) {
-            const int kc = std::min(kRR, rR - c0);
-            const int64_t rcur = h->r[i + 1];
-            ph_begin(h, PH_ORTH, st, 8.0 * m * (2.0 * rcur + 3.0 * kc),
-                     8.0 * m * rcur * kc + 8.0 * m * (double)kc * kc);
-            rc = build_dirs<WT>(h, R, m, L, nsel, c0, kc, st);
-            if (rc == TTICE_OK) rc = orthonormalize_append(h, i, m, kc, st);
-            ph_end(h, st);
-            if (rc == TTICE_OK) h->r[i + 1] = rcur + kc;
+          // core including the chunks already appended (block CGS2).  Mixed path, many directions
+          // and a large core: blocks of up to kb[i] directions are first re-orthogonalised against
+          // the core's earlier columns together (one pass over the core per block), then each chunk
+          // only against the chunks of its block already appended.
+          const bool blocked = sizeof(WT) == 4 && h->kb[i] > 0 && rR > kRR && h->Uh[i] && m >= 32 &&
+                               h->ldu[i] % 4 == 0 && (double)m * ri * rR >= g_tc_cgs_min.load();
+          const int kblk = blocked ? h->kb[i] : rR;
+          for (int b0 = 0; b0 < rR && rc == TTICE_OK; b0 += kblk) {
+            const int kbb = std::min(kblk, rR - b0);
+            const int64_t r_blk = h->r[i + 1];  // columns before this block
+            if (blocked) {
+              const int64_t ldvb = (h->ldu[i] + 31) / 32 * 32, ldpb = (h->cap[i + 1] + 31) / 32 * 32;
+              const CgsWs w{h->VB, h->VBh, h->VBl, ldvb, h->kb[i], h->PB, h->PBh, h->PBl, ldpb, h->kb[i]};
+              ph_begin(h, PH_ORTH, st, 8.0 * m * (2.0 * r_blk + 2.0 * kbb), 12.0 * m * r_blk * kbb);
+              rc = build_dirs<WT>(h, R, m, L, nsel, b0, kbb, st, h->VB);
+              if (rc == TTICE_OK) rc = cgs_tc(h, i, m, kbb, 0, r_blk, w, st);
+              ph_end(h, st);
+            }
+            for (int c0 = 0; c0 < kbb && rc == TTICE_OK; c0 += kRR) {
+              const int kc = std::min(kRR, kbb - c0);
+              const int64_t rcur = h->r[i + 1];
+              ph_begin(h, PH_ORTH, st, 8.0 * m * (2.0 * rcur + 3.0 * kc),
+                       8.0 * m * rcur * kc + 8.0 * m * (double)kc * kc);
+              if (blocked) {
+                rc = cu(cudaMemcpyAsync(h->Vn, h->VB + (int64_t)c0 * m, (size_t)m * kc * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+                if (rc == TTICE_OK) rc = orthonormalize_append(h, i, m, kc, st, r_blk, true);
+              } else {
+                rc = build_dirs<WT>(h, R, m, L, nsel, b0 + c0, kc, st);
+                if (rc == TTICE_OK) rc = orthonormalize_append(h, i, m, kc, st);
+              }
+              ph_end(h, st);
+              if (rc == TTICE_OK) h->r[i + 1] = rcur + kc;
+            }
           }
           if (rc != TTICE_OK) break;
           grew = rR;
@@ -1689,6 +1756,24 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
     if (rc == TTICE_OK) rc = dalloc<double>(&h->dsq, kRR);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Ph, h->ldp * kRR);
     if (rc == TTICE_OK) rc = dalloc<float>(&h->Pl, h->ldp * kRR);
+    int64_t vb = 0, pb = 0, vbs = 0, pbs = 0;
+    for (int i = 0; i < d; ++i) {
+      const int64_t k = std::min<int64_t>(kBlockDirs, kVBudget / std::max<int64_t>(h->ldu[i], 1) / 32 * 32);
+      h->kb[i] = k >= 2 * kRR && h->cap[i + 1] > kRR ? (int)k : 0;
+      if (!h->kb[i]) continue;
+      vb = std::max(vb, h->ldu[i] * h->kb[i]);
+      pb = std::max(pb, h->cap[i + 1] * h->kb[i]);
+      vbs = std::max(vbs, (h->ldu[i] + 31) / 32 * 32 * h->kb[i]);     // split of V at ld rounded to 32
+      pbs = std::max(pbs, (h->cap[i + 1] + 31) / 32 * 32 * h->kb[i]);  // split of P likewise
+    }
+    if (vb > 0) {
+      if (rc == TTICE_OK) rc = dalloc<double>(&h->VB, vb);
+      if (rc == TTICE_OK) rc = dalloc<float>(&h->VBh, vbs);
+      if (rc == TTICE_OK) rc = dalloc<float>(&h->VBl, vbs);
+      if (rc == TTICE_OK) rc = dalloc<double>(&h->PB, pb);
+      if (rc == TTICE_OK) rc = dalloc<float>(&h->PBh, pbs);
+      if (rc == TTICE_OK) rc = dalloc<float>(&h->PBl, pbs);
+    }
     int64_t wt = 0, rs = 0;
     for (int i = 0; i < d; ++i) {
       const int64_t c = B * h->L[i], mi = h->ldu[i];
@@ -1819,6 +1904,7 @@ int ttice_reserve_rank(ttice_t h, int k, int64_t cap) {
     return rc;
   }
   for (int i = 0; i <= h->d; ++i) g->r[i] = h->r[i];
+  for (int i = 0; i < h->d; ++i) g->last_new[i] = h->last_new[i];
   g->n_obs = h->n_obs;
   g->stats = h->stats;
   g->prof_on = h->prof_on;

@@ -390,6 +390,25 @@ def test_projection_kernel_shapes(T, ranks):
         g.close()
 
 
+def test_blocked_reorthogonalisation(T):
+    """Increments that add more directions to a core than one chunk holds (~240 per increment to the
+    third core of a 8 x 16 x 16 x 16 Gaussian-noise stream at eps = 0.3) take the blocked
+    tensor-core re-orthogonalisation (forced here for every shape): the block against the core's
+    earlier columns in one pass, then each 96-column chunk against the chunks of its block already
+    appended.  Same ranks and decisions as the oracle on every increment, eps met, reconstructions and
+    interface projectors within FP32-level error, cores orthonormal to 2e-7."""
+    g = torch.Generator().manual_seed(11)
+    Y = torch.randn((48, 8, 16, 16, 16), generator=g, dtype=torch.float32)
+    stats = []
+    try:
+        T.ttice_test_tc_cgs_min(0.0)
+        run_pair(T, Y, 16, 0.3, precision="fp32", tol=1e-4, orth_tol=2e-7, stats_out=stats,
+                 gpu_kw={"max_rank": 1024})
+    finally:
+        T.ttice_test_tc_cgs_min(-1.0)
+    assert all(x[2][2] > 96 for x in stats[1:]), stats
+
+
 def test_large_gram_block_krylov(T):
     """Gram sides of 1024 (core 2 of a 16 x 80 x 64 stream, batches of 16) take the block Krylov
     solver with its 768-vector basis in global memory: on a random TT stream (ranks 16, 40, 48)
