@@ -601,7 +601,9 @@ def profile_case(case: str, warm: int) -> None:
       pass (tc_proj_kernel<64, 0>), stage 1 (tc_proj_kernel<128, 0>), stage 2 (K split), stage 3.
     c4_stage2: ttice_project of 32 frames of the 1080p view onto seeded random orthonormal cores at
       ranks [1, 27, 1005, 4096, 256, 64] (2.8 GB of cores): stage 2 is the large-K contraction of
-      the 1080p stream's core 3 (K = 48240, 120 columns per frame) at a twelfth of its rank."""
+      the 1080p stream's core 3 (K = 48240, 120 columns per frame) at a twelfth of its rank.
+    noise_update: the first update of a 32^4 stream of N(0, 1) noise, 32 tensors, eps = 0.3 (a
+      1024-sided Gram with a flat spectrum: the full block-Jacobi eigen-solve), profiled alone."""
     import numpy as np
     import torch
 
@@ -626,6 +628,21 @@ def profile_case(case: str, warm: int) -> None:
         return
     from tt_streams import fourier_flow
 
+    if case == "noise_update":
+        g = torch.Generator(device="cuda").manual_seed(5)
+        Y = torch.randn((32, 32, 32, 32, 32), generator=g, device="cuda", dtype=torch.float32)
+        h = T.TTICE((32, 32, 32, 32), 0.3, precision="fp32", input_dtype=torch.float32, max_batch=32,
+                    max_rank=1024)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        s = h.update(Y)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"case": case, "ranks": list(s.ranks[:6]), "krylov": s.krylov_solves,
+                          "krylov_fallbacks": s.krylov_fallbacks, "eig_sweeps": s.eig_sweeps,
+                          "device_gb": h.device_bytes() / 1e9}))
+        h.close()
+        return
     if case == "flow_project":
         dims, ranks, b = (128, 128, 128, 4), [1, 33, 1177, 431, 207], 16
         Y = fourier_flow(0, b, seed=1002, device="cuda")
@@ -668,7 +685,7 @@ def main():
     ap.add_argument("--project-batches", type=int, default=16)
     ap.add_argument("--variant-steps", type=int, default=24)
     ap.add_argument("--serving-seconds", type=float, default=2.0)
-    ap.add_argument("--profile-case", choices=["c4_update", "flow_project", "c4_stage2"],
+    ap.add_argument("--profile-case", choices=["c4_update", "flow_project", "c4_stage2", "noise_update"],
                     help="run one small case for ncu instead of the benchmark")
     ap.add_argument("--profile-warm", type=int, default=24, help="warm-up increments of the c4_update case")
     args = ap.parse_args()
