@@ -144,20 +144,23 @@ __global__ void __launch_bounds__(32 * BJ<T>::BS) bj_solve(const T* A, int sp, i
 //   V[:, P_a] <- V[:, P_a] Q_a                  (in place: the column sets are disjoint).
 // CTAs [0, npairs^2) take the A blocks (those below the diagonal exit; each block above it also
 // writes its mirror, so A stays exactly symmetric); the CTAs after them take 64-row tiles of V.
+// The products are register-tiled: the 256 threads form a 16 x 16 grid and each computes an R x R
+// (A block, R = 2BS / 16) or 4 x R (V tile) piece of the result from rows of the shared-memory
+// operands, so that a shared-memory load feeds R fused multiply-adds instead of one.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* V, int sp, int nb, int round,
                                                       const T* Qb, const int* flags) {
-  constexpr int BS = BJ<T>::BS, N2 = 2 * BS;
+  constexpr int BS = BJ<T>::BS, N2 = 2 * BS, R = N2 / 16, RV = kTile / 16, LD = N2 + 4;
+  constexpr int LDX = (N2 > kTile ? N2 : kTile) + 4;  // X holds N2 x N2 (A block) or N2 x kTile (V)
+  static_assert(N2 % 16 == 0 && kThreads == 256, "16 x 16 thread grid");
   if (flags[1]) return;
-  // dynamic shared memory (over 48 KB for FP32 at BS = 32): Qa, Qc (N2 x N2) and X, the A block
-  // (N2 x N2) then its product, or a V tile (kTile x N2); rows padded to N2 + 1
+  // dynamic shared memory: Qa, Qc (N2 rows of LD) and X (N2 rows of LDX)
   extern __shared__ __align__(16) unsigned char bj_smem[];
-  using Row = T[N2 + 1];
-  Row* Qa = reinterpret_cast<Row*>(bj_smem);
-  Row* Qc = Qa + N2;
-  Row* X = Qc + N2;
+  T* Qa = reinterpret_cast<T*>(bj_smem);
+  T* Qc = Qa + N2 * LD;
+  T* X = Qc + N2 * LD;
   const int npairs = nb / 2;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t nA = (int64_t)npairs * npairs;
   if ((int64_t)blockIdx.x < nA) {
     const int a = (int)(blockIdx.x / npairs), b = (int)(blockIdx.x % npairs);
@@ -171,40 +174,64 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
     const T* Qb_g = Qb + (int64_t)b * N2 * N2;
     for (int e = tid; e < N2 * N2; e += kThreads) {
       const int r = e / N2, c = e % N2;
-      Qa[r][c] = Qa_g[e];
-      Qc[r][c] = Qb_g[e];
-      X[r][c] = Ain[(int64_t)ga(r) * sp + gb(c)];
+      Qa[r * LD + c] = Qa_g[e];
+      Qc[r * LD + c] = Qb_g[e];
+      X[r * LDX + c] = Ain[(int64_t)ga(r) * sp + gb(c)];
     }
     __syncthreads();
-    // M = Qa^T X  (4 outputs per thread), then O = M Qb
-    T m[N2 * N2 / kThreads];
+    // M = Qa^T X: M[r][c] = sum_k Qa[k][r] X[k][c], rows r = R ty + i, columns c = R tx + j
+    T m[R][R];
 #pragma unroll
-    for (int q = 0; q < N2 * N2 / kThreads; ++q) {
-      const int e = tid + q * kThreads, r = e / N2, c = e % N2;
-      T v = T(0);
-#pragma unroll 8
-      for (int k = 0; k < N2; ++k) v = fma(Qa[k][r], X[k][c], v);
-      m[q] = v;
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) m[i][j] = T(0);
+#pragma unroll 4
+    for (int k = 0; k < N2; ++k) {
+      T av[R], bv[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) av[i] = Qa[k * LD + R * ty + i];
+#pragma unroll
+      for (int j = 0; j < R; ++j) bv[j] = X[k * LDX + R * tx + j];
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) m[i][j] = fma(av[i], bv[j], m[i][j]);
     }
     __syncthreads();
+    // M transposed into X: X[c][r] = M[r][c], so that the second product reads rows again
 #pragma unroll
-    for (int q = 0; q < N2 * N2 / kThreads; ++q) {
-      const int e = tid + q * kThreads;
-      X[e / N2][e % N2] = m[q];
-    }
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) X[(R * tx + j) * LDX + R * ty + i] = m[i][j];
     __syncthreads();
+    // O = M Qc: O[r][c] = sum_k M[r][k] Qc[k][c] = sum_k X[k][r] Qc[k][c]
 #pragma unroll
-    for (int q = 0; q < N2 * N2 / kThreads; ++q) {
-      const int e = tid + q * kThreads, r = e / N2, c = e % N2;
-      T v = T(0);
-#pragma unroll 8
-      for (int k = 0; k < N2; ++k) v = fma(X[r][k], Qc[k][c], v);
-      Aout[(int64_t)ga(r) * sp + gb(c)] = v;
-      if (a != b) Aout[(int64_t)gb(c) * sp + ga(r)] = v;
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) m[i][j] = T(0);
+#pragma unroll 4
+    for (int k = 0; k < N2; ++k) {
+      T av[R], bv[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) av[i] = X[k * LDX + R * ty + i];
+#pragma unroll
+      for (int j = 0; j < R; ++j) bv[j] = Qc[k * LD + R * tx + j];
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) m[i][j] = fma(av[i], bv[j], m[i][j]);
     }
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int r = R * ty + i, c = R * tx + j;
+        Aout[(int64_t)ga(r) * sp + gb(c)] = m[i][j];
+        if (a != b) Aout[(int64_t)gb(c) * sp + ga(r)] = m[i][j];
+      }
     return;
   }
-  // V tile: rows [r0, r0 + kTile) of the columns P_a
+  // V tile: rows [r0, r0 + kTile) of the columns P_a; X[c][i] = V[r0 + i][P_a(c)] (V column-major)
   const int64_t vt = blockIdx.x - nA;
   const int tiles = (sp + kTile - 1) / kTile;
   const int a = (int)(vt / tiles), r0 = (int)(vt % tiles) * kTile;
@@ -212,19 +239,36 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
   circle_pair(nb, round, a, &ai, &aj);
   auto ga = [&](int t) { return t < BS ? ai * BS + t : aj * BS + (t - BS); };
   const T* Qa_g = Qb + (int64_t)a * N2 * N2;
-  for (int e = tid; e < N2 * N2; e += kThreads) Qa[e / N2][e % N2] = Qa_g[e];
+  for (int e = tid; e < N2 * N2; e += kThreads) Qa[(e / N2) * LD + e % N2] = Qa_g[e];
   for (int e = tid; e < N2 * kTile; e += kThreads) {
     const int c = e / kTile, i = e % kTile;
-    X[i][c] = (r0 + i < sp) ? V[(int64_t)ga(c) * sp + r0 + i] : T(0);
+    X[c * LDX + i] = (r0 + i < sp) ? V[(int64_t)ga(c) * sp + r0 + i] : T(0);
   }
   __syncthreads();
-  for (int e = tid; e < N2 * kTile; e += kThreads) {
-    const int c = e / kTile, i = e % kTile;
+  // Vnew[i][c] = sum_k X[k][i] Qa[k][c]: rows i = RV ty + u, columns c = R tx + j
+  T v[RV][R];
+#pragma unroll
+  for (int u = 0; u < RV; ++u)
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[u][j] = T(0);
+#pragma unroll 4
+  for (int k = 0; k < N2; ++k) {
+    T av[RV], bv[R];
+#pragma unroll
+    for (int u = 0; u < RV; ++u) av[u] = X[k * LDX + RV * ty + u];
+#pragma unroll
+    for (int j = 0; j < R; ++j) bv[j] = Qa[k * LD + R * tx + j];
+#pragma unroll
+    for (int u = 0; u < RV; ++u)
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[u][j] = fma(av[u], bv[j], v[u][j]);
+  }
+#pragma unroll
+  for (int u = 0; u < RV; ++u) {
+    const int i = RV * ty + u;
     if (r0 + i >= sp) continue;
-    T v = T(0);
-#pragma unroll 8
-    for (int k = 0; k < N2; ++k) v = fma(X[i][k], Qa[k][c], v);
-    V[(int64_t)ga(c) * sp + r0 + i] = v;
+#pragma unroll
+    for (int j = 0; j < R; ++j) V[(int64_t)ga(R * tx + j) * sp + r0 + i] = v[u][j];
   }
 }
 
@@ -317,7 +361,7 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
   }
   const int tiles = (sp + kTile - 1) / kTile;
   const int64_t upd_ctas = (int64_t)npairs * npairs + (int64_t)npairs * tiles;
-  const size_t upd_smem = (size_t)(2 * N2 + (N2 > kTile ? N2 : kTile)) * (N2 + 1) * sizeof(T);
+  const size_t upd_smem = ((size_t)2 * N2 * (N2 + 4) + (size_t)N2 * ((N2 > kTile ? N2 : kTile) + 4)) * sizeof(T);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
