@@ -405,7 +405,9 @@ __global__ void rank_rule_kernel(const double* theta, int K, int full, const dou
 }
 
 // Inverse of the upper Cholesky factor of an SPD k x k matrix (column-major, ld k), one CTA.
-__global__ void chol_inv_kernel(const double* S, int k, const double* diag, double* Rinv, int* status) {
+__global__ void chol_inv_kernel(const double* S, int k, const double* diag, double* Rinv, int* status,
+                                const int* run_if) {
+  if (run_if && *run_if == 0) return;
   extern __shared__ double sm[];
   double* R = sm;          // k x k, column-major
   double* Ri = sm + k * k; // k x k
@@ -512,7 +514,7 @@ cudaError_t launch_rank_rule(const double* theta, int K, int full, const double*
 }
 
 cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st,
-                            const double* diag) {
+                            const double* diag, const int* run_if) {
   if (k <= 0) return cudaSuccess;
   if (k > 112) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)k * k * sizeof(double);
@@ -524,7 +526,7 @@ cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, c
   });
   TT_CUDA(attr_err);
   note_launch();
-  chol_inv_kernel<<<1, 256, smem, st>>>(S, k, diag, Rinv, status);
+  chol_inv_kernel<<<1, 256, smem, st>>>(S, k, diag, Rinv, status, run_if);
   return cudaGetLastError();
 }
 

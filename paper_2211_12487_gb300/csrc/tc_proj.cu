@@ -814,7 +814,8 @@ cudaError_t launch_split_tf32_f64(const double* in, int64_t ld_in, int64_t rows,
 
 // B operand of Vn (I - R^{-1}): row j, entry l = TF32 head / tail of delta_lj - Rinv[l + j k] (Rinv
 // k x k column-major); the ld x ld block is zero outside the k x k corner.
-__global__ void eye_minus_split_kernel(const double* Rinv, int k, float* hi, float* lo, int ld) {
+__global__ void eye_minus_split_kernel(const double* Rinv, int k, float* hi, float* lo, int ld, const int* run_if) {
+  if (run_if && *run_if == 0) return;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ld * ld; e += gridDim.x * blockDim.x) {
     const int j = e / ld, l = e % ld;
     const double f = (j < k && l < k) ? (l == j ? 1.0 : 0.0) - Rinv[l + (int64_t)j * k] : 0.0;
@@ -824,10 +825,76 @@ __global__ void eye_minus_split_kernel(const double* Rinv, int k, float* hi, flo
   }
 }
 
-cudaError_t launch_eye_minus_split(const double* Rinv, int k, float* hi, float* lo, int ld, cudaStream_t st) {
+cudaError_t launch_eye_minus_split(const double* Rinv, int k, float* hi, float* lo, int ld, cudaStream_t st,
+                                   const int* run_if) {
   if (k <= 0 || k > ld) return cudaErrorInvalidValue;
   note_launch();
-  eye_minus_split_kernel<<<(ld * ld + 255) / 256, 256, 0, st>>>(Rinv, k, hi, lo, ld);
+  eye_minus_split_kernel<<<(ld * ld + 255) / 256, 256, 0, st>>>(Rinv, k, hi, lo, ld, run_if);
+  return cudaGetLastError();
+}
+
+constexpr int kLowdinThreads = 1024;
+constexpr int kLowdinMax = 112;  // largest k (two k x k FP32 matrices in shared memory)
+
+__global__ void __launch_bounds__(kLowdinThreads)
+    lowdin_split_kernel(const double* S, int k, const double* diag, float* hi, float* lo, int ld, int* fallback) {
+  extern __shared__ float lw[];
+  float* E = lw;           // E[l][j], l-major rows of k
+  float* E2 = lw + k * k;  // E^2
+  __shared__ double red[kLowdinThreads / 32];
+  __shared__ int small;
+  const int tid = threadIdx.x, kk = k * k;
+  double q = 0.0;
+  for (int e = tid; e < kk; e += kLowdinThreads) {
+    const int l = e / k, j = e % k;
+    const double v = (l == j) ? (diag ? diag[j] : S[(int64_t)j * k + j]) - 1.0 : S[(int64_t)j * k + l];
+    E[e] = (float)v;
+    q = fma(v, v, q);
+  }
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if ((tid & 31) == 0) red[tid >> 5] = q;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kLowdinThreads / 32; ++w) t += red[w];
+    small = t <= 1e-8;  // ||E||_F <= 1e-4 (NaN fails too)
+    if (!small) *fallback = 1;
+  }
+  __syncthreads();
+  if (!small) return;
+  for (int e = tid; e < kk; e += kLowdinThreads) {  // E^2
+    const int l = e / k, j = e % k;
+    float v = 0.0f;
+    for (int m = 0; m < k; ++m) v = fmaf(E[l * k + m], E[m * k + j], v);
+    E2[e] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < ld * ld; e += kLowdinThreads) {  // F = E/2 - 3 E^2/8 + 5 E^3/16, row j of B
+    const int j = e / ld, l = e % ld;
+    float f = 0.0f;
+    if (j < k && l < k) {
+      float e3 = 0.0f;
+      for (int m = 0; m < k; ++m) e3 = fmaf(E2[l * k + m], E[m * k + j], e3);
+      f = 0.5f * E[l * k + j] - 0.375f * E2[l * k + j] + 0.3125f * e3;
+    }
+    const float h = tf32_hi(f);
+    hi[e] = h;
+    lo[e] = tf32_hi(f - h);
+  }
+}
+
+cudaError_t launch_lowdin_split(const double* S, int k, const double* diag, float* hi, float* lo, int ld,
+                                int* fallback, cudaStream_t st) {
+  if (k <= 0 || k > ld || k > kLowdinMax) return cudaErrorInvalidValue;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(lowdin_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(2 * kLowdinMax * kLowdinMax * sizeof(float)));
+  });
+  TT_CUDA(attr_err);
+  note_launch();
+  lowdin_split_kernel<<<1, kLowdinThreads, 2 * (size_t)k * k * sizeof(float), st>>>(S, k, diag, hi, lo, ld, fallback);
   return cudaGetLastError();
 }
 

@@ -1192,11 +1192,12 @@ constexpr double kTcCholMin = 1e8;
 // One CholQR pass of Vn (m x k, FP64) on the tensor cores: the off-diagonal of S = Vn^T Vn from the
 // TF32 head / tail of Vn (three products, FP32 segment sums, the K splits added in FP64), its
 // diagonal summed in FP64 (the tensor core's FP32 sums of positive terms carry a rounding bias of
-// ~1e-7 that would be left in the column norms), S = R^T R and R^{-1} in FP64, then Vn <- Vn R^{-1}
-// written as Vn - Vn (I - R^{-1}): the product on the tensor cores from the FP32 rounding of Vn, the
-// subtraction in FP64.  The chunk is near-orthonormal (unit-scaled directions, already orthogonal to
-// the core), so I - R^{-1} is small and the product's FP32 accuracy costs ~2^-22 of it; the floor is
-// the FP32 rounding of the off-diagonal sums, as in the tensor-core CGS.
+// ~1e-7 that would be left in the column norms), then Vn <- Vn T written as Vn - Vn (I - T): the
+// product on the tensor cores from the FP32 rounding of Vn, the subtraction in FP64.  T = S^{-1/2}
+// (the symmetric orthonormalisation, from a series in E = S - I) when ||E||_F <= 1e-4, as it is for
+// unit-scaled directions already orthogonal to the core; otherwise T = R^{-1} with S = R^T R in FP64
+// (the Cholesky-QR step).  I - T is small, so the product's FP32 accuracy costs ~2^-22 of it; the
+// floor is the FP32 rounding of the off-diagonal sums, as in the tensor-core CGS.
 int cholqr_pass_tc(ttice_s* h, int64_t m, int k, cudaStream_t st) {
   float* Vf = reinterpret_cast<float*>(h->Vn2);  // FP32 Vn at ld ldv (ldv k floats fit: m >= 32)
   TT_CU(cudaMemsetAsync(h->dsq, 0, (size_t)k * sizeof(double), st));
@@ -1210,8 +1211,12 @@ int cholqr_pass_tc(ttice_s* h, int64_t m, int k, cudaStream_t st) {
   g.mode = 5; g.out = h->Ssm; g.ldn = k; g.ldl = 1;
   g.status = h->ibuf + 5;
   TT_CU(launch_tc_gemm(g, st));
-  TT_CU(launch_chol_inv(h->Ssm, k, h->Rinv, h->ibuf + 2, st, h->dsq));
-  TT_CU(launch_eye_minus_split(h->Rinv, k, h->Fh, h->Fl, kRR, st));
+  // near-orthonormal chunk (the usual case): the symmetric orthonormalisation from a short series in
+  // E = S - I, with no FP64 factorisation; otherwise (flag raised on the device) Cholesky in FP64
+  TT_CU(cudaMemsetAsync(h->ibuf + 8, 0, sizeof(int), st));
+  TT_CU(launch_lowdin_split(h->Ssm, k, h->dsq, h->Fh, h->Fl, kRR, h->ibuf + 8, st));
+  TT_CU(launch_chol_inv(h->Ssm, k, h->Rinv, h->ibuf + 2, st, h->dsq, h->ibuf + 8));
+  TT_CU(launch_eye_minus_split(h->Rinv, k, h->Fh, h->Fl, kRR, st, h->ibuf + 8));
   TcGemm q;  // Vn[i][j] -= sum_l Vn[i][l] F[l][j]: A = FP32 Vn (i contiguous, K = l), B rows j (K = l)
   q.x = Vf; q.ldx = h->ldv; q.x_obs = h->ldv * k; q.b = 1;
   q.L = m; q.K = k;

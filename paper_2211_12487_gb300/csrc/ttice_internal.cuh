@@ -229,7 +229,14 @@ cudaError_t launch_scatter_stage(const double* P, int b, int64_t k, int64_t L, f
 cudaError_t launch_pythagoras(const double* x2, const double* w2, int b, double* rho2, cudaStream_t st);
 // TF32 head / tail of I - Rinv (k x k, column-major), transposed into rows of ld (the B operand of a
 // product X (I - Rinv)); zero outside the k x k corner of the ld x ld block.
-cudaError_t launch_eye_minus_split(const double* Rinv, int k, float* hi, float* lo, int ld, cudaStream_t st);
+cudaError_t launch_eye_minus_split(const double* Rinv, int k, float* hi, float* lo, int ld, cudaStream_t st,
+                                   const int* run_if = nullptr);
+// Near-orthonormal columns (S = V^T V = I + E, ||E||_F <= 1e-4): the same operand for the symmetric
+// orthonormalisation V S^{-1/2} = V - V F, F = I - S^{-1/2} = E/2 - 3 E^2/8 + 5 E^3/16 (the next
+// term, 35 E^4/128, is below 3e-17), formed in FP32 from E (FP64 S - I, diagonal from diag) in one
+// CTA.  Otherwise *fallback is set to 1 and the operand is left alone (for the Cholesky route).
+cudaError_t launch_lowdin_split(const double* S, int k, const double* diag, float* hi, float* lo, int ld,
+                                int* fallback, cudaStream_t st);
 // Bounded-wait limit of the tensor-core kernels (0 restores the default of 2 s), and a test hook:
 // the next tc_proj launch issues no copy for chunk `chunk` of its first CTA, so that the consumers'
 // bounded wait runs out.
@@ -261,9 +268,10 @@ cudaError_t launch_canonical_sign(const double* V, int64_t m, int k, int64_t ld,
 // Cholesky-QR step support: given S = V^T V (k x k, FP64, ld k), overwrite Rinv (k x k, ld k) with
 // the inverse of the upper Cholesky factor (S = R^T R).  One CTA.  *status is set to 1 if S is not
 // positive definite (left as it is otherwise).
-// diag (optional, k entries) replaces the diagonal of S.
+// diag (optional, k entries) replaces the diagonal of S; run_if (optional device flag): the kernel
+// does nothing unless *run_if != 0.
 cudaError_t launch_chol_inv(const double* S, int k, double* Rinv, int* status, cudaStream_t st,
-                            const double* diag = nullptr);
+                            const double* diag = nullptr, const int* run_if = nullptr);
 // Block-Krylov basis Q (s x 8 nblk, FP32, nblk in 2..8) of the Gram G and H = Q^T G Q
 // (8 nblk x 8 nblk, FP64, ld 8 nblk) in one thread-block cluster (krylov.cu).  G32: s x s FP32
 // scratch (used when a CTA's rows of G do not fit in shared memory); *lost is set if a block lost
