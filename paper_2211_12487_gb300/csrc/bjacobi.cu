@@ -21,6 +21,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "ttice_internal.cuh"
 
@@ -152,6 +153,9 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
                                                       const T* Qb, const int* flags) {
   constexpr int BS = BJ<T>::BS, N2 = 2 * BS, R = N2 / 16, RV = kTile / 16, LD = N2 + 4;
   constexpr int LDX = (N2 > kTile ? N2 : kTile) + 4;  // X holds N2 x N2 (A block) or N2 x kTile (V)
+  constexpr int VEC = 16 / (int)sizeof(T);
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  static_assert(BS % VEC == 0 && LD % VEC == 0 && LDX % VEC == 0, "16-byte aligned rows");
   static_assert(N2 % 16 == 0 && kThreads == 256, "16 x 16 thread grid");
   if (flags[1]) return;
   // dynamic shared memory: Qa, Qc (N2 rows of LD) and X (N2 rows of LDX)
@@ -172,11 +176,14 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
     auto gb = [&](int t) { return t < BS ? bi * BS + t : bj * BS + (t - BS); };
     const T* Qa_g = Qb + (int64_t)a * N2 * N2;
     const T* Qb_g = Qb + (int64_t)b * N2 * N2;
-    for (int e = tid; e < N2 * N2; e += kThreads) {
-      const int r = e / N2, c = e % N2;
-      Qa[r * LD + c] = Qa_g[e];
-      Qc[r * LD + c] = Qb_g[e];
-      X[r * LDX + c] = Ain[(int64_t)ga(r) * sp + gb(c)];
+    // 16-byte loads and stores (VEC elements), several in flight per thread: the loads come from L2
+    // and would otherwise be exposed one by one
+#pragma unroll 4
+    for (int e = tid * VEC; e < N2 * N2; e += kThreads * VEC) {
+      const int r = e / N2, c = e % N2;  // c is a multiple of VEC: within one half of the pair
+      *reinterpret_cast<Vec*>(Qa + r * LD + c) = *reinterpret_cast<const Vec*>(Qa_g + e);
+      *reinterpret_cast<Vec*>(Qc + r * LD + c) = *reinterpret_cast<const Vec*>(Qb_g + e);
+      *reinterpret_cast<Vec*>(X + r * LDX + c) = *reinterpret_cast<const Vec*>(Ain + (int64_t)ga(r) * sp + gb(c));
     }
     __syncthreads();
     // M = Qa^T X: M[r][c] = sum_k Qa[k][r] X[k][c], rows r = R ty + i, columns c = R tx + j
@@ -239,10 +246,16 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
   circle_pair(nb, round, a, &ai, &aj);
   auto ga = [&](int t) { return t < BS ? ai * BS + t : aj * BS + (t - BS); };
   const T* Qa_g = Qb + (int64_t)a * N2 * N2;
-  for (int e = tid; e < N2 * N2; e += kThreads) Qa[(e / N2) * LD + e % N2] = Qa_g[e];
-  for (int e = tid; e < N2 * kTile; e += kThreads) {
-    const int c = e / kTile, i = e % kTile;
-    X[c * LDX + i] = (r0 + i < sp) ? V[(int64_t)ga(c) * sp + r0 + i] : T(0);
+#pragma unroll 4
+  for (int e = tid * VEC; e < N2 * N2; e += kThreads * VEC)
+    *reinterpret_cast<Vec*>(Qa + (e / N2) * LD + e % N2) = *reinterpret_cast<const Vec*>(Qa_g + e);
+#pragma unroll 4
+  for (int e = tid * VEC; e < N2 * kTile; e += kThreads * VEC) {
+    const int c = e / kTile, i = e % kTile;  // sp is a multiple of 32: a vector is all in or all out
+    Vec v;
+    if (r0 + i < sp) v = *reinterpret_cast<const Vec*>(V + (int64_t)ga(c) * sp + r0 + i);
+    else v = Vec{};
+    *reinterpret_cast<Vec*>(X + c * LDX + i) = v;
   }
   __syncthreads();
   // Vnew[i][c] = sum_k X[k][i] Qa[k][c]: rows i = RV ty + u, columns c = R tx + j
