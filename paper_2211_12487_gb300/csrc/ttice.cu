@@ -463,7 +463,9 @@ int chain(ttice_s* h, const TY* X0, int b, void** bufs, bool errors, cudaStream_
       for (int j = 1; j < h->d; ++j) {
         const double mj = (double)h->r[j] * h->n[j];
         by += sw * b * (mj * h->L[j] + (double)h->r[j + 1] * h->L[j]);
-        fl += (double)b * h->L[j] * (4.0 * mj * h->r[j + 1] + 2.0 * mj);
+        // the projection, and on the FP64 path the back-projection of the direct residual too (the
+        // mixed path takes the residual norm by Pythagoras)
+        fl += (double)b * h->L[j] * ((sizeof(WT) == 4 ? 2.0 : 4.0) * mj * h->r[j + 1] + 2.0 * mj);
       }
       ph_begin(h, PH_CHAIN, st, by, fl);
     }
@@ -1426,7 +1428,7 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
         {
           const double sx = (i == 0) ? sizeof(TY) : sizeof(WT), sw = sizeof(WT);
           ph_begin(h, PH_RESID, st, nsel * (sx * m * L + sw * m * L + 2.0 * sw * ri * L),
-                   4.0 * nsel * (double)m * L * ri);
+                   2.0 * nsel * (double)m * L * ri);  // R = D - U W, with W the first pass's
         }
         bool small = false;  // ||R_i||_F <= eps_c: the rank rule gives 0 without any eigenvalue
         h->rlay = 0;
