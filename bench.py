@@ -467,7 +467,7 @@ def run_variants(T, Y, steps: int, b: int = 8):
     return out
 
 
-def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0), slots: int = 16, seed: int = 1003,
+def run_serving(seconds: float, n_streams: int = 64, rates=(50.0, 400.0, 2000.0), slots: int = 16, seed: int = 1003,
                 drain_s: float = 60.0):
     """Continuous batching over many streams: shapes drawn from {16^4 cosine stream, the 480p video
     view, 64^3 x 4 flow, 32^4 cosine stream}, batch sizes from {1, 4, 16, 32}, eps from {0.05, 0.1,

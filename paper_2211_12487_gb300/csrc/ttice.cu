@@ -221,6 +221,7 @@ void ph_collect(ttice_s* h) {
 }
 
 constexpr int kRR = 96;         // largest Rayleigh-Ritz subspace
+constexpr int kRRFast = 90;     // largest whose FP64 Jacobi runs in one CTA's shared memory
 constexpr int kDirectEig = 32;  // Gram matrices up to this size are diagonalised in FP64 directly
 constexpr int kDirectEig32 = 96;  // mixed path: FP32 Jacobi in one CTA up to this size
 constexpr int kMaxEig = 4608;  // largest Gram side (128^3 x 4 flow: 33 x 128 = 4224)
@@ -1023,10 +1024,11 @@ int truncated_dirs(ttice_s* h, int core, const WT* R, int64_t m, int64_t L, int 
       if (std::sqrt(tail) <= eps_c) r32 = j; else break;
     }
     K = std::min<int>((int)s, std::min(r32 + 8, kRR));
-    if (r32 + 8 > kRR) {
-      // more directions than one Rayleigh-Ritz problem holds: use the whole FP32 eigenbasis, promoted
-      // to FP64, with the energy of R along each vector measured on R itself (complete basis, so the
-      // truncation tail is a direct sum, as on the FP64 path)
+    if (r32 + 8 > kRRFast) {
+      // more directions than a fast Rayleigh-Ritz problem holds (above 90 its FP64 Jacobi leaves
+      // shared memory and takes ~8 ms): use the whole FP32 eigenbasis, promoted to FP64, with the
+      // energy of R along each vector measured on R itself (complete basis, so the truncation tail is
+      // a direct sum, as on the FP64 path)
       TT_CU(launch_to_f64<float>(h->V32, s * s, h->V64, st));
       TT_CU(launch_to_f64<float>(h->w32, s, h->w64, st));
       TT_TRY((measure_energies<WT>(h, R, m, L, nsel, s, left, st)));
