@@ -58,25 +58,36 @@ constexpr uint32_t kRawBytes = kChunk * kTile * 4;  // 16 KB
 constexpr uint32_t kABytes = kTile * kChunk * 4;    // 16 KB per half (head or tail)
 // ring depths of the main-accumulator segments and of the per-item cross accumulator in tensor
 // memory (SEGB + CB accumulators of NT columns <= 512)
-template <int NT>
+// With the converters (raw A), the A operand lives in tensor memory: its a stages of 64 columns
+// (head at +0, tail at +32, one K value per column) follow the accumulators.
+template <int NT, bool APRE>
 struct Tm;
 template <>
-struct Tm<64> { static constexpr int segb = 6, cb = 2; };
+struct Tm<64, true> { static constexpr int segb = 6, cb = 2; };
 template <>
-struct Tm<128> { static constexpr int segb = 3, cb = 1; };
+struct Tm<128, true> { static constexpr int segb = 3, cb = 1; };
+template <>
+struct Tm<64, false> { static constexpr int segb = 4, cb = 2; };
+template <>
+struct Tm<128, false> { static constexpr int segb = 2, cb = 1; };
 
-// ring depths per N tile (dynamic shared memory stays within 227 KB)
-template <int NT>
+// ring depths per N tile (dynamic shared memory stays within 227 KB): raw X chunks, A stages (in
+// shared memory with a pre-split A, in tensor memory otherwise), B chunks
+template <int NT, bool APRE>
 struct Cfg;
 template <>
-struct Cfg<64> { static constexpr int raw = 4, a = 2, b = 3; };
+struct Cfg<64, true> { static constexpr int raw = 1, a = 4, b = 6; };
 template <>
-struct Cfg<128> { static constexpr int raw = 3, a = 2, b = 3; };
+struct Cfg<128, true> { static constexpr int raw = 1, a = 3, b = 4; };
+template <>
+struct Cfg<64, false> { static constexpr int raw = 6, a = 2, b = 8; };
+template <>
+struct Cfg<128, false> { static constexpr int raw = 4, a = 2, b = 5; };
 
-template <int NT>
+template <int NT, bool APRE>
 constexpr size_t smem_bytes() {
-  return (size_t)Cfg<NT>::raw * kRawBytes + 2 * (size_t)Cfg<NT>::a * kABytes + 2 * (size_t)Cfg<NT>::b * NT * 128 +
-         1024;
+  return (APRE ? 0 : (size_t)Cfg<NT, APRE>::raw * kRawBytes) +
+         (APRE ? 2 * (size_t)Cfg<NT, APRE>::a * kABytes : 0) + 2 * (size_t)Cfg<NT, APRE>::b * NT * 128 + 1024;
 }
 
 // Store of the result D[n][l] (n: output row, the MMA's N; l: the item's column, the MMA's M):
@@ -145,25 +156,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ CUtensorMap uhmap, const __grid_constant__ CUtensorMap ulmap,
                    const ProjArgs a) {
   if (a.run_if && *a.run_if == 0) return;  // every thread reads the same flag before any barrier
-  constexpr int RAW = Cfg<NT>::raw, AST = Cfg<NT>::a, BST = Cfg<NT>::b;
+  constexpr int RAW = Cfg<NT, APRE>::raw, AST = Cfg<NT, APRE>::a, BST = Cfg<NT, APRE>::b;
   constexpr uint32_t kBBytes = NT * 128;  // one half of a B chunk: NT rows of 128 bytes
-  // tensor memory: main accumulator of the current / next segment at [0, 2 NT), cross accumulator of
-  // the current / next item at [2 NT, 4 NT)
-  constexpr int SEGB = Tm<NT>::segb, CB = Tm<NT>::cb;
-  constexpr uint32_t kTmemCols = 512;  // main segments at [0, SEGB NT), cross at [SEGB NT, (SEGB + CB) NT)
+  // tensor memory: main-accumulator segments at [0, SEGB NT), cross accumulators at
+  // [SEGB NT, (SEGB + CB) NT), and (raw A) the A stages after them, 64 columns each
+  constexpr int SEGB = Tm<NT, APRE>::segb, CB = Tm<NT, APRE>::cb;
+  constexpr uint32_t kTmemCols = 512;
+  constexpr uint32_t kACol = (uint32_t)((SEGB + CB) * NT);
+  static_assert(APRE || kACol + 64 * AST <= kTmemCols, "tensor memory holds accumulators and A stages");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* raw = base;
-  unsigned char* a_hi = raw + RAW * kRawBytes;
-  unsigned char* a_lo = a_hi + AST * kABytes;
-  unsigned char* b_hi = a_lo + AST * kABytes;
+  unsigned char* raw = base;  // raw X chunks (raw A only)
+  unsigned char* a_hi = raw + (APRE ? 0 : RAW * kRawBytes);  // A stages (pre-split A only)
+  unsigned char* a_lo = a_hi + (APRE ? AST * kABytes : 0);
+  unsigned char* b_hi = a_lo + (APRE ? AST * kABytes : 0);
   unsigned char* b_lo = b_hi + BST * kBBytes;
 
   __shared__ __align__(8) uint64_t raw_full[RAW], raw_empty[RAW];
   __shared__ __align__(8) uint64_t a_full[AST], a_empty[AST];
   __shared__ __align__(8) uint64_t b_full[BST], b_empty[BST];
-  __shared__ __align__(8) uint64_t seg_full[Tm<NT>::segb], seg_empty[Tm<NT>::segb], cross_empty[Tm<NT>::cb], mma_done;
+  __shared__ __align__(8) uint64_t seg_full[SEGB], seg_empty[SEGB], cross_empty[CB], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -290,19 +303,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           fence_after();
-          const uint32_t ah = smem_u32(a_hi + (size_t)qa * kABytes), al = smem_u32(a_lo + (size_t)qa * kABytes);
           const uint32_t bh = smem_u32(b_hi + (size_t)sb * kBBytes), bl = smem_u32(b_lo + (size_t)sb * kBBytes);
           const int64_t rows = a.m - (int64_t)c * kChunk;
           const int nk = rows >= kChunk ? kChunk / 8 : (int)((rows + 7) / 8);
+          if constexpr (APRE) {
+            const uint32_t ah = smem_u32(a_hi + (size_t)qa * kABytes), al = smem_u32(a_lo + (size_t)qa * kABytes);
 #pragma unroll
-          for (int kk = 0; kk < kChunk / 8; ++kk) {
-            if (kk >= nk) break;
-            const uint32_t ko = (uint32_t)kk * 32;  // 8 TF32 values of K
-            // head x head into the segment's main accumulator; the two tail products (~2^-11 of it)
-            // into the item's cross accumulator
-            mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
-            mma_tf32(dc, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, ((c - c_lo) | kk) != 0);
-            mma_tf32(dc, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
+            for (int kk = 0; kk < kChunk / 8; ++kk) {
+              if (kk >= nk) break;
+              const uint32_t ko = (uint32_t)kk * 32;  // 8 TF32 values of K
+              // head x head into the segment's main accumulator; the two tail products (~2^-11 of it)
+              // into the item's cross accumulator
+              mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
+              mma_tf32(dc, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, ((c - c_lo) | kk) != 0);
+              mma_tf32(dc, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
+            }
+          } else {
+            const uint32_t at = tmem + kACol + 64u * (uint32_t)qa;  // head; tail 32 columns on
+#pragma unroll
+            for (int kk = 0; kk < kChunk / 8; ++kk) {
+              if (kk >= nk) break;
+              const uint32_t ko = (uint32_t)kk * 32;
+              mma_tf32_ta(d, at + 8u * kk, kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
+              mma_tf32_ta(dc, at + 32u + 8u * kk, kmajor_sw128_desc(bh + ko), idesc, ((c - c_lo) | kk) != 0);
+              mma_tf32_ta(dc, at + 8u * kk, kmajor_sw128_desc(bl + ko), idesc, 1);
+            }
           }
           mma_commit(&a_empty[qa]);  // these slots are free once the MMAs above have read them
           mma_commit(&b_empty[sb]);
@@ -339,31 +364,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         // the raw chunk: [k][128 columns] (wide) or [observation][k][L] (narrow)
         const int rbase = a.narrow ? (tid / (int)a.L) * kChunk * (int)a.L + tid % (int)a.L : tid;
         const int rstep = a.narrow ? (int)a.L : kTile;
-        unsigned char* ah = a_hi + (size_t)qa * kABytes + (size_t)tid * 128;
-        unsigned char* al = a_lo + (size_t)qa * kABytes + (size_t)tid * 128;
         const int64_t rows = a.m - (int64_t)c * kChunk;
         const int kv = rows >= kChunk ? kChunk : (int)rows;  // rows of K in this chunk
-        const int units = 2 * ((kv + 7) / 8);                // 16-byte units the MMAs read
+        // this thread's row of A (tensor-memory lane tid): 32 K values, head and tail (the tail itself
+        // rounded to TF32: the MMA reads it exactly), zero past the chunk's rows
+        uint32_t hv[kChunk], lv[kChunk];
 #pragma unroll
-        for (int u = 0; u < kChunk / 4; ++u) {
-          if (u < units) {
-            float4 hi, lo;
-            float* ph = &hi.x;
-            float* pl = &lo.x;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int kk = 4 * u + e;
-              const float y = kk < kv ? rw[rbase + kk * rstep] : 0.0f;
-              x2 = fmaf(y, y, x2);
-              ph[e] = tf32_hi(y);
-              pl[e] = tf32_hi(y - ph[e]);  // the tail, itself rounded to TF32: the MMA reads it exactly
-            }
-            const int off = (u ^ (tid & 7)) << 4;
-            *reinterpret_cast<float4*>(ah + off) = hi;
-            *reinterpret_cast<float4*>(al + off) = lo;
-          }
+        for (int kk = 0; kk < kChunk; ++kk) {
+          const float y = kk < kv ? rw[rbase + kk * rstep] : 0.0f;
+          x2 = fmaf(y, y, x2);
+          const float hy = tf32_hi(y);
+          hv[kk] = __float_as_uint(hy);
+          lv[kk] = __float_as_uint(tf32_hi(y - hy));
         }
-        fence_async_smem();
+        const uint32_t at = tmem + ((uint32_t)(wid * 32) << 16) + kACol + 64u * (uint32_t)qa;
+        tmem_st32(at, hv);
+        tmem_st32(at + 32u, lv);
+        tmem_wait_st();
+        fence_before();
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&a_full[qa]);
@@ -624,7 +642,7 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   static int sms = 148;
   std::call_once(once, [] {
     setup_err = cudaFuncSetAttribute(tc_proj_kernel<NT, APRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_bytes<NT>());
+                                     (int)smem_bytes<NT, APRE>());
     int dev = 0;
     if (setup_err == cudaSuccess) setup_err = cudaGetDevice(&dev);
     if (setup_err == cudaSuccess) setup_err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -689,7 +707,7 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   const int64_t nitems = (int64_t)a.nsplit * items1;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(sms, nitems));
   note_launch();
-  tc_proj_kernel<NT, APRE><<<(unsigned)grid, kThreads, smem_bytes<NT>(), st>>>(xmap, xlmap, uhmap, ulmap, a);
+  tc_proj_kernel<NT, APRE><<<(unsigned)grid, kThreads, smem_bytes<NT, APRE>(), st>>>(xmap, xlmap, uhmap, ulmap, a);
   TT_CUDA(cudaGetLastError());
   if (ws_split) {
     note_launch();
