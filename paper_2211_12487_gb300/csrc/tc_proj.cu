@@ -687,9 +687,10 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   }
   a.cps = (a.nch + a.nsplit - 1) / a.nsplit;
   a.nsplit = (a.nch + a.cps - 1) / a.cps;  // every split has at least one chunk
-  // one segment for a short K range (<= 256: its rounding bias is a few ulps); 32-long segments
-  // beyond, where the bias would otherwise grow with the number of adds
-  a.seglen = a.cps <= 8 ? a.cps : 1;
+  // one segment for a short K range (<= 256: its rounding bias is a few ulps); beyond, 32-long
+  // segments where residual norms are taken by Pythagoras (which amplifies the bias by
+  // ||x||^2 / ||R||^2), 64-long ones elsewhere (half the promotions, ~1.4e-7 relative bias)
+  a.seglen = a.cps <= 8 ? a.cps : (norms ? 1 : 2);
   const bool ws_split = a.nsplit > 1 && g.mode != kAddF64;
   a.ws_stride = ws_split ? wsz : 0;
   if (ws_split) a.out = g.ws;
