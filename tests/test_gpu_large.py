@@ -1,5 +1,5 @@
 """The large workloads on the FP32 path: the 1080x1920x3 video (27x40x48x40x3, batches of 32,
-eps = 0.05, scene cut) and the 128^3 x 4 Fourier flow (batches of 16, eps = 0.05).
+eps = 0.05, scene cut) and the 128^3 x 4 Fourier flow (batches of 16, eps = 0.05 and 0.01).
 
 The oracle cannot run these sizes in a test's time, so the checks are the paper's guarantees on the
 GPU result itself: every increment is represented within eps (Theorem 1 / Corollary 1, measured
@@ -66,11 +66,14 @@ def test_large_video_27x40x48x40x3(T):
     assert ranks[1] >= 1
 
 
-def test_flow_128cubed_x4(T):
+@pytest.mark.parametrize("eps", [0.05, 0.01])
+def test_flow_128cubed_x4(T, eps):
+    """The simulation-shaped stream at both of its workload's tolerances (eps = 0.01 keeps more
+    modes: larger ranks and Gram sides on the inner cores)."""
     dims = (128, 128, 128, 4)
 
     def frames(t0, n):
         return fourier_flow(t0, n, device="cuda")
 
-    ranks = _run(T, frames, dims, 16, 0.05, 2, max_rank=1024)
+    ranks = _run(T, frames, dims, 16, eps, 2, max_rank=2048)
     assert ranks[1] <= 33  # cos/sin of at most 17 distinct |k_1| values per mode-1 fibre
