@@ -3,19 +3,24 @@
 //
 // Two-sided cyclic block Jacobi (Golub & Van Loan, Sec. 8.5, block variant): the matrix is split
 // into nb blocks of BS rows/columns; the block pairs (I, J) of one round come from the round-robin
-// ordering on block indices, so the nb/2 pairs of a round are disjoint.  One round is two kernels:
-//   solve:  one CTA per pair loads the 2BS x 2BS submatrix A[I u J, I u J] into shared memory and
-//           applies one cyclic sweep of scalar Jacobi rotations to it, accumulating the orthogonal
-//           Q (2BS x 2BS) of the sweep;
-//   update: A_out[P_a, P_b] = Q_a^T A_in[P_a, P_b] Q_b for every pair of index sets (one 2BS x 2BS
-//           block per CTA; A is double-buffered, so rows and columns are combined in one pass), and
-//           V[:, P_a] <- V[:, P_a] Q_a in 64-row tiles.
-// A sweep is nb-1 rounds; a flag raised by any significant rotation keeps the next sweep alive, and
-// a sweep that leaves the off-diagonal norm at the working precision's rounding level without
-// halving it ends the solve too (rotations of rounding noise would otherwise run to the sweep cap);
-// every kernel returns at once after the solve has ended, so a fixed launch sequence costs almost
-// nothing once converged.  Two sweeps of launches are captured once into a CUDA graph and replayed.  Padding to nb*BS adds zero rows/columns, which no rotation touches (their
-// off-diagonal entries are exactly zero), so the first s coordinates carry the eigenpairs.
+// ordering on block indices, so the nb/2 pairs of a round are disjoint.  One round is three kernels:
+//   solve:    one CTA per pair loads the 2BS x 2BS submatrix A[I u J, I u J] into shared memory and
+//             applies one cyclic sweep of scalar Jacobi rotations to it, accumulating the orthogonal
+//             Q (2BS x 2BS) of the sweep;
+//   update A: A_out[P_a, P_b] = Q_a^T A_in[P_a, P_b] Q_b for every pair of index sets (one 2BS x 2BS
+//             block per CTA; A is double-buffered, so rows and columns are combined in one pass);
+//   update V: V[:, P_a] <- V[:, P_a] Q_a in 64-row tiles.
+// The next round's solve needs only A, so the V update of a round runs on a second branch of the
+// graph, beside the next round's solve and A update (the Q factors alternate between two buffers,
+// and a solve waits for the V update that read its buffer two rounds before).
+// A sweep is nb-1 rounds; a flag raised by any significant rotation keeps the next sweep alive.  A
+// sweep that leaves the off-diagonal norm at the rounding level of the working precision ends the
+// solve (below sqrt(s) eps_T ||A||_F, the level of the FP rounding of A itself; or below 64 times
+// that without halving it, when the rotations are turning rounding noise); every kernel returns at
+// once after the solve has ended, so a fixed launch sequence costs almost nothing once converged.
+// Two sweeps of launches are captured once into a CUDA graph and replayed.  Padding to nb*BS adds
+// zero rows/columns, which no rotation touches (their off-diagonal entries are exactly zero), so
+// the first s coordinates carry the eigenpairs.
 #include <algorithm>
 #include <cfloat>
 #include <map>
@@ -143,14 +148,14 @@ __global__ void __launch_bounds__(32 * BJ<T>::BS) bj_solve(const T* A, int sp, i
 // One round's update of A and V with the pairs' orthogonal factors Q (2BS x 2BS each):
 //   A_out[P_a, P_b] = Q_a^T A_in[P_a, P_b] Q_b  for every pair of index sets P_a = I_a u J_a, and
 //   V[:, P_a] <- V[:, P_a] Q_a                  (in place: the column sets are disjoint).
-// CTAs [0, npairs^2) take the A blocks (those below the diagonal exit; each block above it also
-// writes its mirror, so A stays exactly symmetric); the CTAs after them take 64-row tiles of V.
+// part 0: one CTA per A block on or above the diagonal (each block above it also writes its mirror,
+// so A stays exactly symmetric); part 1: one CTA per 64-row tile of V and pair.
 // The products are register-tiled: the 256 threads form a 16 x 16 grid and each computes an R x R
 // (A block, R = 2BS / 16) or 4 x R (V tile) piece of the result from rows of the shared-memory
 // operands, so that a shared-memory load feeds R fused multiply-adds instead of one.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* V, int sp, int nb, int round,
-                                                      const T* Qb, const int* flags) {
+                                                      const T* Qb, const int* flags, int part) {
   constexpr int BS = BJ<T>::BS, N2 = 2 * BS, R = N2 / 16, RV = kTile / 16, LD = N2 + 4;
   constexpr int LDX = (N2 > kTile ? N2 : kTile) + 4;  // X holds N2 x N2 (A block) or N2 x kTile (V)
   constexpr int VEC = 16 / (int)sizeof(T);
@@ -163,12 +168,14 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
   T* Qa = reinterpret_cast<T*>(bj_smem);
   T* Qc = Qa + N2 * LD;
   T* X = Qc + N2 * LD;
-  const int npairs = nb / 2;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t nA = (int64_t)npairs * npairs;
-  if ((int64_t)blockIdx.x < nA) {
-    const int a = (int)(blockIdx.x / npairs), b = (int)(blockIdx.x % npairs);
-    if (a > b) return;
+  if (part == 0) {
+    // block index -> (a, b), a <= b, column by column of the upper triangle: b (b + 1) / 2 + a
+    const int64_t q = blockIdx.x;
+    int b = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    while ((int64_t)b * (b + 1) / 2 > q) --b;
+    while ((int64_t)(b + 1) * (b + 2) / 2 <= q) ++b;
+    const int a = (int)(q - (int64_t)b * (b + 1) / 2);
     int ai, aj, bi, bj;
     circle_pair(nb, round, a, &ai, &aj);
     circle_pair(nb, round, b, &bi, &bj);
@@ -239,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
     return;
   }
   // V tile: rows [r0, r0 + kTile) of the columns P_a; X[c][i] = V[r0 + i][P_a(c)] (V column-major)
-  const int64_t vt = blockIdx.x - nA;
+  const int64_t vt = blockIdx.x;
   const int tiles = (sp + kTile - 1) / kTile;
   const int a = (int)(vt / tiles), r0 = (int)(vt % tiles) * kTile;
   int ai, aj;
@@ -300,16 +307,20 @@ __global__ void bj_offnorm(const T* A, int sp, double* off, const int* flags) {
 }
 
 // End of a sweep.  norms: [0] ||A||_F^2, [1] off-diagonal^2 after this sweep (reset here), [2] after
-// the previous sweep.  The solve has converged when a sweep rotated nothing, or when the
-// off-diagonal norm is at the rounding level of T (below 64 sqrt(s) eps_T ||A||_F) and the sweep
-// did not halve it: the rotations left are rotating rounding noise (the rule of jacobi_kernel).
+// the previous sweep.  The solve has converged when a sweep rotated nothing; when the off-diagonal
+// norm is below sqrt(s) eps_T ||A||_F, the size of the rounding of A's own entries in T (what is
+// left is not resolved by the working precision: another sweep would only turn it); or when it is
+// below 64 times that and the sweep did not halve it (rotations of rounding noise, the rule of
+// jacobi_kernel).
 // `cur` is the buffer (0 or 1) that holds A after this sweep; it is recorded in flags[4] when the
 // solve ends here, since the launches after that return at once and swap nothing.
 template <typename T>
 __global__ void bj_sweep_end(int* flags, int max_sweeps, double* norms, int s, int cur) {
   if (flags[1]) return;
-  const double gate = 64.0 * sqrt((double)s) * (double)BJ<T>::eps() * sqrt(norms[0]);
-  const bool stalled = flags[2] >= 1 && norms[1] > 0.25 * norms[2] && norms[1] <= gate * gate;
+  const double floor2 = (double)s * (double)BJ<T>::eps() * (double)BJ<T>::eps() * norms[0];
+  const double gate = 64.0 * sqrt(floor2);
+  const bool stalled = (flags[2] >= 1 && norms[1] > 0.25 * norms[2] && norms[1] <= gate * gate) ||
+                       norms[1] <= floor2;
   flags[2] += 1;
   flags[4] = cur;
   if (flags[0] == 0 || stalled) flags[1] = 1;
@@ -347,7 +358,7 @@ int64_t block_jacobi_work(int s) {
   int nb = (s + BS - 1) / BS;
   nb += nb & 1;
   const int64_t sp = (int64_t)nb * BS;
-  return 3 * sp * sp + (int64_t)(nb / 2) * N2 * N2 + 16;
+  return 3 * sp * sp + 2 * (int64_t)(nb / 2) * N2 * N2 + 16;  // A twice, V, Q of two rounds
 }
 
 template <typename T>
@@ -362,8 +373,8 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
   T* A0 = work;                       // A, double-buffered: each round reads one, writes the other
   T* A1 = work + (int64_t)sp * sp;
   T* V = A1 + (int64_t)sp * sp;
-  T* Qb = V + (int64_t)sp * sp;
   const int npairs = nb / 2;
+  T* Qbuf[2] = {V + (int64_t)sp * sp, V + (int64_t)sp * sp + (int64_t)npairs * N2 * N2};
   TT_CUDA(cudaMemsetAsync(fro, 0, 3 * sizeof(double), st));
   TT_CUDA(cudaMemsetAsync(flags, 0, 5 * sizeof(int), st));
   {
@@ -373,7 +384,7 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
     bj_init<T><<<grid, kThreads, 0, st>>>(G, ldg, s, sp, A0, V, fro, flags);
   }
   const int tiles = (sp + kTile - 1) / kTile;
-  const int64_t upd_ctas = (int64_t)npairs * npairs + (int64_t)npairs * tiles;
+  const int64_t a_ctas = (int64_t)npairs * (npairs + 1) / 2, v_ctas = (int64_t)npairs * tiles;
   const size_t upd_smem = ((size_t)2 * N2 * (N2 + 4) + (size_t)N2 * ((N2 > kTile ? N2 : kTile) + 4)) * sizeof(T);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -381,25 +392,36 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
     attr_err = cudaFuncSetAttribute(bj_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem);
   });
   TT_CUDA(attr_err);
-  // Two sweeps of rounds (the buffer parity repeats after two, since a sweep has nb - 1 rounds, an
+  // Two sweeps of rounds (the buffer parities repeat after two, since a sweep has nb - 1 rounds, an
   // odd count) are captured once into a CUDA graph per (buffers, size) and replayed until the sweep
-  // cap; every kernel returns at once after the solve has ended.  Capture goes to a private stream
-  // of the calling thread: nothing runs there, the graph is launched on st.
-  auto enqueue_two_sweeps = [&](cudaStream_t cs) {
-    int cur = 0;
+  // cap; every kernel returns at once after the solve has ended.  Capture goes to private streams
+  // of the calling thread (the main branch cs, the V branch cv): nothing runs there, the graph is
+  // launched on st.  Edges: solve(g) -> V update(g) -> V update(g + 1) on cv; V update(g) ->
+  // solve(g + 2), which overwrites its Q buffer; the last V update of a sweep -> the sweep's end
+  // test, which may end the solve (a V update still to start would then skip its rotations).
+  auto enqueue_two_sweeps = [&](cudaStream_t cs, cudaStream_t cv, cudaEvent_t ev_q, cudaEvent_t* ev_v) -> cudaError_t {
+    int cur = 0, g = 0;
     for (int sweep = 0; sweep < 2; ++sweep) {
-      for (int round = 0; round < nb - 1; ++round) {
+      for (int round = 0; round < nb - 1; ++round, ++g) {
         T* Ain = cur ? A1 : A0;
         T* Aout = cur ? A0 : A1;
+        T* Qb = Qbuf[g & 1];
+        if (g >= 2) TT_CUDA(cudaStreamWaitEvent(cs, ev_v[g & 1], 0));
         bj_solve<T><<<npairs, 32 * BS, 0, cs>>>(Ain, sp, nb, round, Qb, fro, flags);
-        bj_update<T><<<(unsigned)upd_ctas, kThreads, upd_smem, cs>>>(Ain, Aout, V, sp, nb, round, Qb, flags);
+        TT_CUDA(cudaEventRecord(ev_q, cs));
+        bj_update<T><<<(unsigned)a_ctas, kThreads, upd_smem, cs>>>(Ain, Aout, V, sp, nb, round, Qb, flags, 0);
+        TT_CUDA(cudaStreamWaitEvent(cv, ev_q, 0));
+        bj_update<T><<<(unsigned)v_ctas, kThreads, upd_smem, cv>>>(Ain, Aout, V, sp, nb, round, Qb, flags, 1);
+        TT_CUDA(cudaEventRecord(ev_v[g & 1], cv));
         cur ^= 1;
       }
       const int64_t n = (int64_t)sp * sp;
       const int grid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 2);
       bj_offnorm<T><<<grid, kThreads, 0, cs>>>(cur ? A1 : A0, sp, fro + 1, flags);
+      TT_CUDA(cudaStreamWaitEvent(cs, ev_v[(g - 1) & 1], 0));
       bj_sweep_end<T><<<1, 1, 0, cs>>>(flags, max_sweeps, fro, s, cur);
     }
+    return cudaGetLastError();
   };
   using Key = std::tuple<const void*, const void*, const void*, int, int>;
   static std::mutex mu;
@@ -412,12 +434,21 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
     if (it != cache.end()) exec = it->second;
   }
   if (!exec) {
-    thread_local cudaStream_t cs = nullptr;
+    thread_local cudaStream_t cs = nullptr, cv = nullptr;
+    thread_local cudaEvent_t ev_q = nullptr, ev_v[2] = {nullptr, nullptr};
     if (!cs) TT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    if (!cv) TT_CUDA(cudaStreamCreateWithFlags(&cv, cudaStreamNonBlocking));
+    if (!ev_q) TT_CUDA(cudaEventCreateWithFlags(&ev_q, cudaEventDisableTiming));
+    for (cudaEvent_t& e : ev_v)
+      if (!e) TT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     TT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    enqueue_two_sweeps(cs);
+    const cudaError_t ee = enqueue_two_sweeps(cs, cv, ev_q, ev_v);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return ee;
+    }
     if (ce != cudaSuccess) return ce;
     const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -429,7 +460,7 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
     }
     cache[key] = exec;
   }
-  const int per_graph = 2 * (2 * (nb - 1) + 2);  // kernels in one replay
+  const int per_graph = 2 * (3 * (nb - 1) + 2);  // kernels in one replay
   for (int g = 0; g < (max_sweeps + 1) / 2; ++g) {
     for (int k = 0; k < per_graph; ++k) note_launch();
     TT_CUDA(cudaGraphLaunch(exec, st));
