@@ -233,7 +233,10 @@ def phase_roofline(prof, name, peaks, peak_kind, live):
 
 
 def run_headline(T, args, dev, seed, precision):
-    """W warm-up and K timed updates of the 1080p stream from device-resident input."""
+    """W warm-up and K timed updates of the 1080p stream from device-resident input; afterwards the
+    relative error of the last timed increment, measured in FP64 from its reconstruction (Theorem 2:
+    later updates would leave it as it was right after its own).  One increment only: the FP64
+    reconstruction of 32 frames through the grown cores takes ~15 s."""
     import torch
 
     b, W, K = BATCH, args.warmup, args.steps
@@ -242,37 +245,58 @@ def run_headline(T, args, dev, seed, precision):
         Y[k:k + b] = frames_1080(k, b, seed=seed)
     torch.cuda.synchronize()
     h = headline_handle(T, precision, W + K)
-    grows = 0
-    for k in range(W):
-        _, g = update_growing(T, h, Y[k * b:(k + 1) * b])
-        grows += g
-    h.profile(True)
-    st = torch.cuda.current_stream()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
-    l0 = T.ttice_kernel_launches()
-    torch.cuda.synchronize()
-    evs[0].record(st)
-    steps = []
-    for k in range(K):
-        i = W + k
-        s, g = update_growing(T, h, Y[i * b:(i + 1) * b])
-        grows += g
-        evs[k + 1].record(st)
-        steps.append({"skipped": int(s.skipped), "n_selected": s.n_selected, "ranks": list(s.ranks[:len(DIMS) + 2]),
-                      "new_dirs": list(s.new_dirs[:len(DIMS)]), "krylov": s.krylov_solves,
-                      "krylov_fallbacks": s.krylov_fallbacks, "rel_err_before": s.rel_err_before})
-    torch.cuda.synchronize()
-    launches = T.ttice_kernel_launches() - l0
-    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
-    total = evs[0].elapsed_time(evs[-1])
-    prof = h.profile_read()
-    out = {"total_ms": total, "lat": lat, "steps": steps, "prof": prof, "launches": launches, "grows": grows,
-           "core_elems": int(h.stats().core_elems), "n_obs": int(h.stats().n_obs),
-           "device_gb": h.device_bytes() / 1e9}
-    h.close()
-    del Y
-    torch.cuda.empty_cache()
-    return out
+    try:
+        grows = 0
+        for k in range(W):
+            _, g = update_growing(T, h, Y[k * b:(k + 1) * b])
+            grows += g
+        h.profile(True)
+        st = torch.cuda.current_stream()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        l0 = T.ttice_kernel_launches()
+        torch.cuda.synchronize()
+        evs[0].record(st)
+        steps = []
+        for k in range(K):
+            i = W + k
+            s, g = update_growing(T, h, Y[i * b:(i + 1) * b])
+            grows += g
+            evs[k + 1].record(st)
+            steps.append({"skipped": int(s.skipped), "n_selected": s.n_selected, "ranks": list(s.ranks[:len(DIMS) + 2]),
+                          "new_dirs": list(s.new_dirs[:len(DIMS)]), "krylov": s.krylov_solves,
+                          "krylov_fallbacks": s.krylov_fallbacks, "rel_err_before": s.rel_err_before})
+        torch.cuda.synchronize()
+        launches = T.ttice_kernel_launches() - l0
+        lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
+        total = evs[0].elapsed_time(evs[-1])
+        prof = h.profile_read()
+        errs = []
+        for i in (W + K - 1,):
+            Yi = Y[i * b:(i + 1) * b].double()
+            rec = h.reconstruct(i * b, b)
+            errs.append(math.sqrt(float(((Yi - rec) ** 2).sum()) / float((Yi ** 2).sum())))
+            del Yi, rec
+        out = {"total_ms": total, "lat": lat, "steps": steps, "prof": prof, "launches": launches, "grows": grows,
+               "core_elems": int(h.stats().core_elems), "n_obs": int(h.stats().n_obs),
+               "device_gb": h.device_bytes() / 1e9, "errs": errs}
+        return out
+    finally:  # also when an update fails (e.g. a capacity growth out of memory)
+        h.close()
+        del Y
+        torch.cuda.empty_cache()
+
+
+def sweep_row(hl, K: int) -> dict:
+    """One precision's row of the 1080p precision sweep."""
+    N = math.prod(DIMS)
+    steps = hl["steps"]
+    return {"value": K * BATCH * N / (hl["total_ms"] / 1e3), "unit": "elements/s", "ms_per_step": hl["total_ms"] / K,
+            "latency_ms": {"p50": statistics.median(hl["lat"]), "p99": percentile(hl["lat"], 0.99)},
+            "final_ranks": steps[-1]["ranks"], "core_elements": hl["core_elems"],
+            "compression_ratio": hl["n_obs"] * N / max(hl["core_elems"], 1),
+            "skipped": sum(s["skipped"] for s in steps),
+            "eps_check": {"eps": EPS, "rel_err_last": hl["errs"][-1], "over_eps": hl["errs"][-1] > EPS * (1 + 1e-9),
+                          "measured": "FP64, from the last timed increment's reconstruction"}}
 
 
 def run_e2e(T, args, dev, seed, precision):
@@ -590,7 +614,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(case: str, warm: int) -> None:
+def profile_case(case: str, warm: int, precision: str = "fp32") -> None:
     """Small, self-contained cases for ncu (each inside one cudaProfilerStart/Stop window, for
     `ncu --profile-from-start off`); prints one line and exits.
 
@@ -653,18 +677,23 @@ def profile_case(case: str, warm: int) -> None:
         raise SystemExit(f"unknown profile case {case}")
     rng = np.random.default_rng(3)
     cores = [np.linalg.qr(rng.normal(size=(ranks[i] * n, ranks[i + 1])))[0] for i, n in enumerate(dims)]
-    h = T.TTICE(dims, 0.01, precision="fp32", input_dtype=torch.float32, max_batch=b, max_rank=max(ranks))
+    eps = 0.1 if precision == "tf32" else 0.01
+    h = T.TTICE(dims, eps, precision=precision, input_dtype=torch.float32, max_batch=b, max_rank=max(ranks))
     h.load(ranks, cores, np.zeros((1, ranks[-1])))
     coeffs = torch.empty((b, ranks[-1]), dtype=torch.float64, device="cuda")
     rel = torch.empty((b,), dtype=torch.float64, device="cuda")
     T.ttice_project(h.h, Y, coeffs, rel)  # warm-up (module load, tensor maps)
     torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.profiler.start()
-    for _ in range(2):
+    ev[0].record()
+    for k in range(2):
         T.ttice_project(h.h, Y, coeffs, rel)
+        ev[k + 1].record()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    print(json.dumps({"case": case, "ranks": ranks, "rel_mean": float(rel.mean()),
+    print(json.dumps({"case": case, "precision": precision, "ranks": ranks, "rel_mean": float(rel.mean()),
+                      "ms_per_call": [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])],
                       "device_gb": h.device_bytes() / 1e9}))
     h.close()
 
@@ -675,7 +704,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=1, help="frames of the oracle's sample (0 leaves it out)")
     ap.add_argument("--flow-steps", type=int, default=16, help="timed steps per flow leg (0 leaves them out)")
@@ -685,12 +714,14 @@ def main():
     ap.add_argument("--project-batches", type=int, default=16)
     ap.add_argument("--variant-steps", type=int, default=24)
     ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="leave out the other precision of the 1080p stream (same warm-up and timed steps)")
     ap.add_argument("--profile-case", choices=["c4_update", "flow_project", "c4_stage2", "noise_update"],
                     help="run one small case for ncu instead of the benchmark")
     ap.add_argument("--profile-warm", type=int, default=24, help="warm-up increments of the c4_update case")
     args = ap.parse_args()
     if args.profile_case:
-        return profile_case(args.profile_case, args.profile_warm)
+        return profile_case(args.profile_case, args.profile_warm, args.precision)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -731,6 +762,19 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     side = {}
+    if rank == 0 and not args.no_sweep:
+        try:
+            rows = {args.precision: sweep_row(hl, args.steps)}
+            for p in ("tf32", "fp32"):
+                if p not in rows:
+                    rows[p] = sweep_row(run_headline(T, args, dev, seed, p), args.steps)
+            side["precision_sweep"] = {
+                "workload": WORKLOAD, "rows": rows,
+                "fp64": "not run at this size: the FP64 GPU path takes ~36x the mixed path's time per update "
+                        "(measured on the 480p stream, video_480p.fp64_path)",
+                "not_built": "bf16 and split-bf16 (TTICE_BF16, TTICE_SPLIT_BF16 are rejected by ttice_create)"}
+        except Exception as e:
+            side["precision_sweep"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         for key, fn in (("flow", lambda: {f"eps_{e}": run_flow(T, e, args.flow_warmup, args.flow_steps)
                                           for e in (0.05, 0.01)} if args.flow_steps > 0 else None),):
@@ -795,7 +839,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch": BATCH, "precision": args.precision,
                    "l2": f"each step reads a fresh 796 MB increment of a {(args.warmup + args.steps) * BATCH * N * 4 / 1e9:.1f} GB "
                          "pre-generated stream (inputs larger than L2)",
@@ -806,7 +850,9 @@ def main():
                        "core_elements": hl["core_elems"], "compression_ratio": hl["n_obs"] * N / max(hl["core_elems"], 1),
                        "capacity_growths": hl["grows"], "device_gb": hl["device_gb"],
                        "krylov_solves": sum(s["krylov"] for s in steps),
-                       "krylov_fallbacks": sum(s["krylov_fallbacks"] for s in steps)},
+                       "krylov_fallbacks": sum(s["krylov_fallbacks"] for s in steps),
+                       "eps_check": {"eps": EPS, "rel_err_last": hl["errs"][-1],
+                                     "over_eps": hl["errs"][-1] > EPS * (1 + 1e-9)}},
         "roofline": roof,
         "dominant_phase": dom,
         "phase_share": share,

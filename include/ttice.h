@@ -64,7 +64,20 @@ extern "C" {
                         FP32 summation error, ~2^-23 of the products' magnitudes per 8-term MMA:
                         ~1e-9 for delocalised columns at m ~ 5e4, up to ~1e-7 for short or
                         localised ones (FP64: ~1e-15). */
-#define TTICE_TF32 2 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
+#define TTICE_TF32 2 /* as TTICE_FP32, but the projections of the large stages of the chain (Eq. 6,
+                        Eq. 12: r_{i-1} n_i >= 256 rows and >= 65536 entries per observation) and
+                        their new rows take one TF32 product (heads only, FP32 accumulation) instead
+                        of three; small stages, the first pass's kernel for n_1 <= 128, the
+                        residuals of updated cores, the Grams, the re-orthogonalisation and the
+                        eigen-solve keep the TTICE_FP32 arithmetic.  Error budget: 1/16 of each
+                        increment's eps^2 ||Y||^2 is reserved for the TF32 rounding (2^-11 relative
+                        per operand): every decision of Algorithm 2 (skip test, subselection,
+                        eps_upd, per-core thresholds) runs at eps sqrt(15/16), so the reported
+                        errors and the coefficients may be off by that share before Theorem 1's
+                        bound eps ||Y|| is at risk.  The share holds where the rounding averages
+                        out (measured: 5.5e-5 ||y||^2 per observation on a 480p video stream) but not
+                        on every input (6.6e-4 ||y||^2 on a 64^3 x 4 flow stream with localised core
+                        columns: within the share from eps = 0.1); TTICE_FP32 has no such limit. */
 #define TTICE_BF16 3 /* reserved (tensor-core projections): ttice_create returns TTICE_EINVAL */
 #define TTICE_SPLIT_BF16 4 /* reserved (split-BF16 projections): ttice_create returns TTICE_EINVAL */
 

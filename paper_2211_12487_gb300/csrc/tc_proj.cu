@@ -19,7 +19,10 @@
 // with round-to-nearest, from a ring of segment accumulators so that the MMAs run ahead of the
 // epilogue; the cross products, ~2^-11 of the main ones, keep one accumulator per item.  W is then
 // at FP32 accuracy up to that bias, which grows like sqrt(K / 32) ulps (~3e-6 relative at K = 2e4);
-// the Pythagorean residual ||X||^2 - ||W||^2 inherits it multiplied by ||X||^2 / ||R||^2.  The
+// the Pythagorean residual ||X||^2 - ||W||^2 inherits it multiplied by ||X||^2 / ||R||^2.  With
+// nprod = 1 (the TF32 mode of the path) only A_hi B_hi is taken: no tail operands are copied or
+// written and the cross accumulator stays unused, so W carries the TF32 rounding of both operands
+// (2^-11 relative each, unbiased).  The
 // head/tail pair of U is kept in global memory next to the core (ttice_s::Uh, Ul) and copied
 // straight into the 128-byte-swizzled K-major B operand by TMA; X is staged raw by TMA and split by
 // converter warps, which write the K-major A operand.
@@ -113,6 +116,7 @@ struct ProjArgs {
   int tfast;   // item order: column tiles fastest (else observations, then N tiles)
   int64_t ws_stride, px_stride;  // partial D and x^2 partials of one K split
   int mode;
+  int nprod;  // 3: head x head + the two tail products; 1: head x head only
   void* out;
   void* out2;
   int64_t o_obs, ldn, ldl;  // element (n, l) of observation z at z * o_obs + n * ldn + l * ldl
@@ -232,9 +236,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             if (!(blockIdx.x == 0 && g == a.drop_chunk)) {
-              mbar_expect_tx(&a_full[qa], 2 * kABytes);
+              mbar_expect_tx(&a_full[qa], (a.nprod == 3 ? 2 : 1) * kABytes);
               tma_load_2d(smem_u32(a_hi + (size_t)qa * kABytes), &xmap, c * kChunk, t * kTile, &a_full[qa]);
-              tma_load_2d(smem_u32(a_lo + (size_t)qa * kABytes), &xlmap, c * kChunk, t * kTile, &a_full[qa]);
+              if (a.nprod == 3)
+                tma_load_2d(smem_u32(a_lo + (size_t)qa * kABytes), &xlmap, c * kChunk, t * kTile, &a_full[qa]);
             }
           } else {
             if (g >= RAW && !wait_bounded(&raw_empty[s], (uint32_t)(((g / RAW) - 1) & 1), &abort_flag, lim)) {
@@ -254,9 +259,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             ++g;
             break;
           }
-          mbar_expect_tx(&b_full[sb], 2 * kBBytes);
+          mbar_expect_tx(&b_full[sb], (a.nprod == 3 ? 2 : 1) * kBBytes);
           tma_load_2d(smem_u32(b_hi + (size_t)sb * kBBytes), &uhmap, c * kChunk, j * NT, &b_full[sb]);
-          tma_load_2d(smem_u32(b_lo + (size_t)sb * kBBytes), &ulmap, c * kChunk, j * NT, &b_full[sb]);
+          if (a.nprod == 3)
+            tma_load_2d(smem_u32(b_lo + (size_t)sb * kBBytes), &ulmap, c * kChunk, j * NT, &b_full[sb]);
         }
       }
       // copies of the last ring slots may still be in flight (on an abort): wait for them
@@ -315,8 +321,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               // head x head into the segment's main accumulator; the two tail products (~2^-11 of it)
               // into the item's cross accumulator
               mma_tf32(d, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
-              mma_tf32(dc, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, ((c - c_lo) | kk) != 0);
-              mma_tf32(dc, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
+              if (a.nprod == 3) {
+                mma_tf32(dc, kmajor_sw128_desc(al + ko), kmajor_sw128_desc(bh + ko), idesc, ((c - c_lo) | kk) != 0);
+                mma_tf32(dc, kmajor_sw128_desc(ah + ko), kmajor_sw128_desc(bl + ko), idesc, 1);
+              }
             }
           } else {
             const uint32_t at = tmem + kACol + 64u * (uint32_t)qa;  // head; tail 32 columns on
@@ -325,8 +333,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (kk >= nk) break;
               const uint32_t ko = (uint32_t)kk * 32;
               mma_tf32_ta(d, at + 8u * kk, kmajor_sw128_desc(bh + ko), idesc, (cs | kk) != 0);
-              mma_tf32_ta(dc, at + 32u + 8u * kk, kmajor_sw128_desc(bh + ko), idesc, ((c - c_lo) | kk) != 0);
-              mma_tf32_ta(dc, at + 8u * kk, kmajor_sw128_desc(bl + ko), idesc, 1);
+              if (a.nprod == 3) {
+                mma_tf32_ta(dc, at + 32u + 8u * kk, kmajor_sw128_desc(bh + ko), idesc, ((c - c_lo) | kk) != 0);
+                mma_tf32_ta(dc, at + 8u * kk, kmajor_sw128_desc(bl + ko), idesc, 1);
+              }
             }
           }
           mma_commit(&a_empty[qa]);  // these slots are free once the MMAs above have read them
@@ -379,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const uint32_t at = tmem + ((uint32_t)(wid * 32) << 16) + kACol + 64u * (uint32_t)qa;
         tmem_st32(at, hv);
-        tmem_st32(at + 32u, lv);
+        if (a.nprod == 3) tmem_st32(at + 32u, lv);
         tmem_wait_st();
         fence_before();
         __syncwarp();
@@ -455,9 +465,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&seg_empty[p]);
       }
       if (!ok) break;
-      {  // the item's cross sum (complete with its last segment)
+      {  // the item's cross sum (complete with its last segment; unused with one product)
         const int cbi = it % CB;
-        take((uint32_t)((SEGB + cbi) * NT));
+        if (a.nprod == 3) take((uint32_t)((SEGB + cbi) * NT));
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&cross_empty[cbi]);
@@ -661,6 +671,7 @@ cudaError_t run(const TcGemm& g, cudaStream_t st) {
   a.tfast = APRE ? 1 : 0;
   a.nch = (int)((g.K + kChunk - 1) / kChunk);
   a.mode = g.mode;
+  a.nprod = g.nprod == 1 ? 1 : 3;
   a.out = g.out;
   a.out2 = g.out2;
   a.o_obs = g.o_obs;
@@ -748,7 +759,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t st) {
 
 cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
                            int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
-                           float* ws, int* status, cudaStream_t st) {
+                           float* ws, int* status, cudaStream_t st, int nprod) {
   TcGemm g;
   g.x = X;
   g.ldx = L;
@@ -772,6 +783,7 @@ cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, c
   g.status = status;
   g.ws = ws;
   g.ws_elems = ws ? tc_ws_elems : 0;
+  g.nprod = nprod;
   return launch_tc_gemm(g, st);
 }
 

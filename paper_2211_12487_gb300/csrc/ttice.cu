@@ -28,6 +28,27 @@
 
 using namespace ttice;
 
+// TTICE_TF32: the share of each increment's squared error bound (eps^2 ||Y||^2) reserved for the
+// error of its one-product TF32 projections.  Every decision of Algorithm 2 (skip, subselection,
+// eps_upd, the per-core thresholds) runs at eps sqrt(1 - kTf32Share), so the projections may move
+// the squared errors they report, and the reconstruction through the coefficients they produce,
+// by kTf32Share eps^2 ||Y||^2 before the bound eps ||Y|| of Theorem 1 can be exceeded.
+// What the TF32 rounding (2^-11 relative per operand, unbiased) does to a Pythagorean residual
+// ||x||^2 - ||U~^T x~||^2: the rounded core U~ is orthonormal only to ~2^-11 / sqrt(3 m) per column
+// (m = r_{i-1} n_i rows), which moves ||w||^2 by about twice that times the energy along the column;
+// and the rounded input x~ moves it by ~2^-11 ||x||^2 / sqrt(the entries holding its energy).  Both
+// average out only on large stages, so a stage takes one product only from kTf32MinRows rows and
+// kTf32MinEntries entries per observation (about 3e-5 ||y||^2 per stage there); the small stages,
+// the first pass's kernel, the residuals of the updated cores, the Grams, the re-orthogonalisation
+// and the eigen-solve keep the split products.  The rule does not bound the effect for every input:
+// columns of a core concentrated on few rows (2^-11 per column however large m is) or stage inputs
+// whose energy sits in few entries keep it near 2^-11.  Measured with the rule in FP64 (numpy,
+// TF32 operands rounded to nearest): up to 5.5e-5 ||y||^2 per observation on the 480p video stream
+// (0.5% of eps^2 at eps = 0.1), up to 6.6e-4 ||y||^2 on the 64^3 x 4 flow stream (26% of eps^2 at
+// eps = 0.05, 6.6% at eps = 0.1), where the cores' columns are localised.
+constexpr double kTf32Share = 1.0 / 16.0;
+constexpr int64_t kTf32MinRows = 256, kTf32MinEntries = 65536;
+
 struct ttice_s {
   int d = 0;
   int device = 0;  // CUDA device the handle's buffers live on (current at creation)
@@ -54,6 +75,12 @@ struct ttice_s {
   int64_t last_cap = 0;  // observations
   int64_t n_obs = 0;
   int wt_bytes = 8;  // working type of stage buffers: 8 (FP64 path) or 4
+  // tensor-core products of the large stage projections and new rows: 3 (split operands, FP32
+  // accuracy) or 1 (TTICE_TF32: one TF32 product)
+  int nprod = 3;
+  // tolerance of the decisions (skip test, subselection, eps_upd, per-core thresholds): eps, or in
+  // the TF32 mode eps sqrt(1 - kTf32Share), the rest of eps^2 left to the projection error
+  double eps_dec = 0.0;
   // workspace
   void* stage[kMaxD] = {};
   void* dstage[kMaxD] = {};
@@ -372,10 +399,16 @@ bool tc_stage(const ttice_s* h, int i, const void* X) {
   return h->Uh[i] != nullptr && h->r[i + 1] > 0 &&
          tc_proj_supported(X, h->L[i], h->r[i] * h->n[i], (int)h->r[i + 1], h->ldhl[i]);
 }
+// Products of stage i's projection on the tensor cores: one in the TF32 mode on a large stage, else
+// the three of the split operands.
+int stage_nprod(const ttice_s* h, int i) {
+  const int64_t m = h->r[i] * h->n[i];
+  return (h->nprod == 1 && m >= kTf32MinRows && m * h->L[i] >= kTf32MinEntries) ? 1 : 3;
+}
 int tc_project(ttice_s* h, int i, const void* X, int b, void* W, double* x2, double* rho2, cudaStream_t st) {
   return cu(launch_tc_proj(static_cast<const float*>(X), b, h->L[i], h->r[i] * h->n[i], (int)h->r[i + 1], h->Uh[i],
                            h->Ul[i], h->ldhl[i], h->hlcols[i], static_cast<float*>(W), x2, rho2, h->part, h->tcws,
-                           h->ibuf + 5, st));
+                           h->ibuf + 5, st, stage_nprod(h, i)));
 }
 
 // Stages of the mixed path whose unfolding has too few or unaligned columns per observation for the
@@ -408,6 +441,7 @@ int tc_project_t(ttice_s* h, int i, const float* X, int b, int64_t r0, int k, fl
   g.r = k;
   g.mode = 5; g.out = P; g.ldn = 1; g.ldl = k;
   g.status = h->ibuf + 5;
+  g.nprod = stage_nprod(h, i);
   TT_CU(launch_tc_gemm(g, st));
   if (rho2) {
     TT_CU(cudaMemsetAsync(h->part, 0, 2 * (size_t)b * sizeof(double), st));
@@ -1354,7 +1388,7 @@ int new_rows(ttice_s* h, int i, const void* X, int nobs, int64_t r0, int k, WT* 
   if (sizeof(WT) == 4 && h->Uh[i] && (i > 0 || sizeof(TY) == 4) && tc_proj_supported(X, L, m, k, h->ldhl[i]))
     return cu(launch_tc_proj(static_cast<const float*>(X), nobs, L, m, k, h->Uh[i] + r0 * h->ldhl[i],
                              h->Ul[i] + r0 * h->ldhl[i], h->ldhl[i], h->hlcols[i] - r0, reinterpret_cast<float*>(out),
-                             nullptr, nullptr, h->part, h->tcws, h->ibuf + 5, st));
+                             nullptr, nullptr, h->part, h->tcws, h->ibuf + 5, st, stage_nprod(h, i)));
   if (sizeof(WT) == 4 && i > 0 && tc_stage_t_ok(h, i, nobs, k))
     return tc_project_t(h, i, static_cast<const float*>(X), nobs, r0, k, reinterpret_cast<float*>(out), nullptr, st);
   const WT* Ui = ((sizeof(WT) == 8) ? reinterpret_cast<const WT*>(h->U[i]) : reinterpret_cast<const WT*>(h->Uf[i])) +
@@ -1371,7 +1405,7 @@ int update_impl(ttice_s* h, const TY* Y, int b, cudaStream_t st) {
   TT_TRY(grow_last(h, h->n_obs + b));
   void** S1 = h->stage;
   TT_TRY((chain<WT, TY>(h, Y, b, S1, true, st)));
-  TT_CU(launch_decision(h->rho2, h->d, h->y2, b, h->eps, h->d, h->h.skip_mode, h->h.subselect,
+  TT_CU(launch_decision(h->rho2, h->d, h->y2, b, h->eps_dec, h->d, h->h.skip_mode, h->h.subselect,
                         h->h.eps_upd_mode, h->dec, h->sel, st));
   TT_CU(cudaMemcpyAsync(h->h_dec, h->dec, sizeof(Decision), cudaMemcpyDeviceToHost, st));
   TT_CU(cudaMemcpyAsync(h->h_sel, h->sel, b * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1666,11 +1700,16 @@ int create_handle(const int64_t* dims, int d, double eps, const ttice_heuristics
   ttice_default_capacity(&h->capc);
   if (hp) h->h = *hp;
   if (cp) h->capc = *cp;
-  if (h->h.precision != TTICE_FP64 && h->h.precision != TTICE_FP32) { delete h; return TTICE_EINVAL; }
+  if (h->h.precision != TTICE_FP64 && h->h.precision != TTICE_FP32 && h->h.precision != TTICE_TF32) {
+    delete h;
+    return TTICE_EINVAL;
+  }
   if (h->h.input_dtype != TTICE_F32 && h->h.input_dtype != TTICE_F64) { delete h; return TTICE_EINVAL; }
   if (h->capc.max_batch < 1 || h->capc.max_rank < 1) { delete h; return TTICE_EINVAL; }
   h->d = d;
   h->eps = eps;
+  h->nprod = h->h.precision == TTICE_TF32 ? 1 : 3;
+  h->eps_dec = h->h.precision == TTICE_TF32 ? eps * std::sqrt(1.0 - kTf32Share) : eps;
   h->N = 1;
   // the current device (without one, the first allocation below fails and reports why)
   if (!g_dry_run && cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); h->device = 0; }

@@ -157,10 +157,11 @@ int64_t tc_proj_part_elems(int b, int64_t L, int64_t r, int64_t m);
 constexpr int64_t tc_ws_elems = 16LL << 20;
 cudaError_t launch_tc_proj(const float* X, int b, int64_t L, int64_t m, int r, const float* Uh, const float* Ul,
                            int64_t ldhl, int64_t hlcols, float* W, double* x2, double* rho2, double* part,
-                           float* ws, int* status, cudaStream_t st);
+                           float* ws, int* status, cudaStream_t st, int nprod = 3);
 // General product on the tensor cores (the same kernel): D[n][l] = sum_k B(k, n) A(k, l) for
 // n < r (N), l < L (M, per observation), k < K, each operand split into TF32 head and tail (three
-// products, FP32 accuracy; the main product summed in registers over 64-long K segments).
+// products, FP32 accuracy; the main product summed in registers over 64-long K segments), or with
+// nprod = 1 the heads alone (one TF32 product, FP32 accumulation).
 //   A, one of: raw FP32 X (x != nullptr): A(k, l) of observation z = x[z x_obs + k ldx + l]
 //              (16-byte aligned; ldx, x_obs multiples of 4; b observations), split by converter warps;
 //              or pre-split (ah != nullptr): A(k, l) = ah[l lda + k] + al[l lda + k] (lda % 32 == 0,
@@ -185,6 +186,7 @@ struct TcGemm {
   int64_t ldb = 0, nb_alloc = 0;
   int r = 0;
   int mode = 0;
+  int nprod = 3;  // 3: split operands (FP32 accuracy); 1: one TF32 product
   void* out = nullptr;
   void* out2 = nullptr;
   int64_t o_obs = 0, ldn = 0, ldl = 1;

@@ -47,14 +47,17 @@ def _interface_projectors(cores, max_rows=2048):
 
 
 def run_pair(T, frames, batch, eps, *, precision="fp64", tol=1e-10, check_eps=True,
-             oracle_kw=None, gpu_kw=None, stats_out=None, orth_tol=1e-12):
+             oracle_kw=None, gpu_kw=None, stats_out=None, orth_tol=1e-12, oracle_eps=None, err2_tol=None):
     """Stream `frames` through the GPU and the oracle; compare after every increment.  With
-    `stats_out` (a list), the GPU's per-update statistics are appended to it."""
+    `stats_out` (a list), the GPU's per-update statistics are appended to it.  `oracle_eps`: the
+    oracle's tolerance when the GPU mode decides at another one than its eps (the errors are still
+    checked against eps); `err2_tol`: absolute bound on the difference of the squared batch errors
+    before each update (instead of `tol` relative to the error)."""
     dims = frames.shape[1:]
     in_dtype = frames.dtype
     g = T.TTICE(dims, eps, precision=precision, input_dtype=in_dtype, max_batch=batch,
                 **(gpu_kw or {}))
-    o = O.TTICEOracle(dims, eps, **(oracle_kw or {}))
+    o = O.TTICEOracle(dims, eps if oracle_eps is None else oracle_eps, **(oracle_kw or {}))
     dev = frames.to("cuda")
     for k in range(0, frames.shape[0], batch):
         Yk = frames[k:k + batch]
@@ -65,7 +68,10 @@ def run_pair(T, frames, batch, eps, *, precision="fp64", tol=1e-10, check_eps=Tr
         assert list(st.ranks[:len(dims) + 1]) == so.ranks[:len(dims) + 1], (k, list(st.ranks[:len(dims) + 2]), so.ranks)
         assert bool(st.skipped) == so.skipped, k
         assert st.n_selected == so.n_selected, k
-        assert st.rel_err_before == pytest.approx(so.rel_err_before, rel=max(tol, 1e-9), abs=1e-12)
+        if err2_tol is None:
+            assert st.rel_err_before == pytest.approx(so.rel_err_before, rel=max(tol, 1e-9), abs=1e-12)
+        else:
+            assert abs(st.rel_err_before ** 2 - so.rel_err_before ** 2) <= err2_tol, (k, st.rel_err_before, so.rel_err_before)
         if check_eps:
             rec = g.reconstruct(k, Yk.shape[0]).cpu().numpy()
             Y64 = Yk.double().numpy()
@@ -388,6 +394,59 @@ def test_projection_kernel_shapes(T, ranks):
         assert _relmax(coeffs.cpu().numpy(), c32) < tol_c, (precision, _relmax(coeffs.cpu().numpy(), c32))
         np.testing.assert_allclose(rel.cpu().numpy(), np.sqrt(rho32 / y32), rtol=tol_e)
         g.close()
+
+
+# decision tolerance of the TF32 mode: eps sqrt(1 - 1/16), the rest of eps^2 left to its projections
+TF32_SHARE = 1.0 / 16.0
+
+
+def test_tf32_mode_projection_budget(T):
+    """TTICE_TF32 (one TF32 product per stage projection) against the oracle's FP64 projection of the
+    same FP32 data onto the same cores (Eq. 12 per stage, Eq. 17 per observation): per observation,
+    the error of its squared residual plus the squared error of its coefficients stays within the
+    mode's budget, 1/16 of eps^2 ||y||^2; and the mode is visibly less accurate than the split
+    products of TTICE_FP32, so the one-product path is the one that ran (stages 1 and 2 here: 740 x
+    288 and 10800 x 8 per observation).  Shapes as in test_projection_kernel_shapes (ragged K chunks
+    and column tiles, several N tiles)."""
+    dims, ranks, eps = (40, 20, 36, 8), [1, 37, 300, 90, 8], 0.1
+    rng = np.random.default_rng(6)
+    cores = [np.linalg.qr(rng.normal(size=(ranks[i] * n, ranks[i + 1])))[0] for i, n in enumerate(dims)]
+    o = O.TTICEOracle(dims, eps)
+    o.ranks = list(ranks)
+    o.U = [c.copy() for c in cores]
+    C = rng.normal(size=(4, ranks[-1]))
+    Y = o.expand(C) + 0.05 * rng.normal(size=(4,) + dims)
+    Yd = torch.tensor(Y, dtype=torch.float32).cuda()
+    c32, rho32, y32 = o.errors(Yd.double().cpu().numpy())
+    err = {}
+    for precision in ("fp32", "tf32"):
+        g = T.TTICE(dims, eps, precision=precision, input_dtype=torch.float32, max_batch=4, max_rank=512)
+        g.load(ranks, cores, np.zeros((1, ranks[-1])))
+        coeffs, rel = g.project(Yd)
+        coeffs, rel = coeffs.cpu().numpy(), rel.cpu().numpy()
+        drho = np.abs(rel ** 2 * y32 - rho32)
+        dc2 = ((coeffs - c32) ** 2).sum(axis=1)
+        assert np.all(drho + dc2 <= TF32_SHARE * eps ** 2 * y32), (precision, drho / y32, dc2 / y32)
+        err[precision] = _relmax(coeffs, c32)
+        g.close()
+    assert err["tf32"] > 10 * err["fp32"], err
+
+
+@pytest.mark.parametrize("stream", ["small", "c1_prefix"])
+def test_tf32_mode_stream(T, stream):
+    """TTICE_TF32 through whole updates: decisions and ranks equal to the oracle's at the mode's
+    decision tolerance eps sqrt(15/16), squared batch errors before each update within the mode's
+    share of eps^2, eps itself met on every increment (measured in FP64 from the reconstruction),
+    cores orthonormal, reconstructions within the TF32 rounding of the oracle's.  On the 480x640
+    frames (20x24x20x32x3) the second stage (r_1 24 rows x 1920 columns per frame) takes one product;
+    the small stream's stages are all below the size rule (the decision tolerance alone differs)."""
+    if stream == "small":
+        Y, b = blob_video(0, 24, height=48, width=64, n_blobs=5, sigma=(3, 10), view=(6, 8, 8, 8, 3), seed=7), 4
+    else:
+        Y, b = blob_video(0, 24), 8
+    eps = 0.1
+    run_pair(T, Y, b, eps, precision="tf32", tol=2e-3, oracle_eps=eps * math.sqrt(1.0 - TF32_SHARE),
+             err2_tol=TF32_SHARE * eps ** 2)
 
 
 def test_blocked_reorthogonalisation(T):
