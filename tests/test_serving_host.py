@@ -118,6 +118,14 @@ def test_projected_bytes_from_the_creation_code():
     h = T.ttice_default_heuristics()
     h.precision = T.TTICE_FP32
     assert T.ttice_projected_bytes(dims, h, c32) != b32  # FP32 mirrors and FP32 stage buffers
+    f32 = T.ttice_projected_bytes(dims, h, c32)
+    h.precision = T.TTICE_TF32  # the same buffers: it differs in the products taken and the decisions
+    assert T.ttice_projected_bytes(dims, h, c32) == f32
+    for unbuilt in (T.TTICE_BF16, T.TTICE_SPLIT_BF16):
+        h.precision = unbuilt
+        with pytest.raises(T.TTICEError) as ei:
+            T.ttice_projected_bytes(dims, h, c32)
+        assert ei.value.code == T.TTICE_EINVAL
     with pytest.raises(T.TTICEError):
         T.ttice_projected_bytes((4, 0, 3))
 
