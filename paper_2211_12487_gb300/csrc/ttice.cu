@@ -38,7 +38,8 @@ using namespace ttice;
 // (m = r_{i-1} n_i rows), which moves ||w||^2 by about twice that times the energy along the column;
 // and the rounded input x~ moves it by ~2^-11 ||x||^2 / sqrt(the entries holding its energy).  Both
 // average out only on large stages, so a stage takes one product only from kTf32MinRows rows and
-// kTf32MinEntries entries per observation (about 3e-5 ||y||^2 per stage there); the small stages,
+// kTf32MinEntries entries per observation (a few 1e-5 ||y||^2 per stage where the core's columns
+// and the input's energy are spread); the small stages,
 // the first pass's kernel, the residuals of the updated cores, the Grams, the re-orthogonalisation
 // and the eigen-solve keep the split products.  The rule does not bound the effect for every input:
 // columns of a core concentrated on few rows (2^-11 per column however large m is) or stage inputs
