@@ -235,14 +235,31 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
 #pragma unroll
         for (int j = 0; j < R; ++j) m[i][j] = fma(av[i], bv[j], m[i][j]);
     }
+    // O through shared memory (X, row-major), so that the stores to A are whole 16-byte vectors of
+    // consecutive columns (stored straight from the registers, a warp's store would touch 16-32
+    // rows at once)
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int r = R * ty + i, c = R * tx + j;
-        Aout[(int64_t)ga(r) * sp + gb(c)] = m[i][j];
-        if (a != b) Aout[(int64_t)gb(c) * sp + ga(r)] = m[i][j];
+      for (int j = 0; j < R; ++j) X[(R * ty + i) * LDX + R * tx + j] = m[i][j];
+    __syncthreads();
+#pragma unroll 4
+    for (int e = tid * VEC; e < N2 * N2; e += kThreads * VEC) {  // A_out[P_a(r)][P_b(c .. c + VEC)]
+      const int r = e / N2, c = e % N2;  // c is a multiple of VEC: within one half of the pair
+      *reinterpret_cast<Vec*>(Aout + (int64_t)ga(r) * sp + gb(c)) = *reinterpret_cast<const Vec*>(X + r * LDX + c);
+    }
+    if (a != b) {
+#pragma unroll 4
+      for (int e = tid * VEC; e < N2 * N2; e += kThreads * VEC) {  // the mirror: A_out[P_b(c)][P_a(r ..)]
+        const int c = e / N2, r = e % N2;
+        Vec w;
+        T* wq = reinterpret_cast<T*>(&w);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) wq[q] = X[(r + q) * LDX + c];
+        *reinterpret_cast<Vec*>(Aout + (int64_t)gb(c) * sp + ga(r)) = w;
       }
+    }
     return;
   }
   // V tile: rows [r0, r0 + kTile) of the columns P_a; X[c][i] = V[r0 + i][P_a(c)] (V column-major)
@@ -283,12 +300,17 @@ __global__ void __launch_bounds__(kThreads) bj_update(const T* Ain, T* Aout, T* 
 #pragma unroll
       for (int j = 0; j < R; ++j) v[u][j] = fma(av[u], bv[j], v[u][j]);
   }
+  // the tile back through shared memory (X, the input's layout) as whole 16-byte vectors of rows
+  __syncthreads();
 #pragma unroll
-  for (int u = 0; u < RV; ++u) {
-    const int i = RV * ty + u;
-    if (r0 + i >= sp) continue;
+  for (int u = 0; u < RV; ++u)
 #pragma unroll
-    for (int j = 0; j < R; ++j) V[(int64_t)ga(R * tx + j) * sp + r0 + i] = v[u][j];
+    for (int j = 0; j < R; ++j) X[(R * tx + j) * LDX + RV * ty + u] = v[u][j];
+  __syncthreads();
+#pragma unroll 4
+  for (int e = tid * VEC; e < N2 * kTile; e += kThreads * VEC) {
+    const int c = e / kTile, i = e % kTile;  // sp is a multiple of 32: a vector is all in or all out
+    if (r0 + i < sp) *reinterpret_cast<Vec*>(V + (int64_t)ga(c) * sp + r0 + i) = *reinterpret_cast<const Vec*>(X + c * LDX + i);
   }
 }
 
@@ -331,23 +353,33 @@ __global__ void bj_sweep_end(int* flags, int max_sweeps, double* norms, int s, i
 }
 
 // eigenvalues = diag(A)[0..s), sorted descending (ties by index); eigenvectors follow.  A is the
-// buffer flags[4] names.
+// buffer flags[4] names.  One CTA per eigenpair i (kFinishThreads threads): its rank among the
+// diagonal entries, counted by the whole CTA, then its vector copied with consecutive threads on
+// consecutive entries.
+constexpr int kFinishThreads = 128;
 template <typename T>
-__global__ void bj_finish(const T* A0, const T* A1, const T* V, int sp, int s, T* w, T* Vout,
-                          const int* flags) {
+__global__ void __launch_bounds__(kFinishThreads) bj_finish(const T* A0, const T* A1, const T* V, int sp, int s,
+                                                            T* w, T* Vout, const int* flags) {
   const T* A = flags[4] ? A1 : A0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
-    const T di = A[(int64_t)i * sp + i];
-    int rank = 0;
-    for (int j = 0; j < s; ++j) {
-      const T dj = A[(int64_t)j * sp + j];
-      rank += (dj > di) || (dj == di && j < i);
-    }
-    w[rank] = di;
-    const T* src = V + (int64_t)i * sp;
-    T* dst = Vout + (int64_t)rank * s;
-    for (int r = 0; r < s; ++r) dst[r] = src[r];
+  const int i = blockIdx.x;
+  const T di = A[(int64_t)i * sp + i];
+  int cnt = 0;
+  for (int j = threadIdx.x; j < s; j += kFinishThreads) {
+    const T dj = A[(int64_t)j * sp + j];
+    cnt += (dj > di) || (dj == di && j < i);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  __shared__ int part[kFinishThreads / 32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  int rank = 0;
+#pragma unroll
+  for (int k = 0; k < kFinishThreads / 32; ++k) rank += part[k];
+  if (threadIdx.x == 0) w[rank] = di;
+  const T* src = V + (int64_t)i * sp;
+  T* dst = Vout + (int64_t)rank * s;
+  for (int r = threadIdx.x; r < s; r += kFinishThreads) dst[r] = src[r];
 }
 
 }  // namespace
@@ -466,7 +498,7 @@ cudaError_t block_jacobi_eig(const double* G, int64_t ldg, int s, T* w, T* Vout,
     TT_CUDA(cudaGraphLaunch(exec, st));
   }
   note_launch();
-  bj_finish<T><<<(s + 127) / 128, 128, 0, st>>>(A0, A1, V, sp, s, w, Vout, flags);
+  bj_finish<T><<<s, kFinishThreads, 0, st>>>(A0, A1, V, sp, s, w, Vout, flags);
   (void)N2;
   return cudaGetLastError();
 }
